@@ -1,0 +1,193 @@
+/*
+ * anova_gb300.h -- C ABI of the GB300 (sm_103a) ANOVA-Gaussian fast summation
+ * and kernel ridge regression library (libanova_gb300.so).
+ *
+ * Method: Nestler, Stoll, Wagner, "Learning in High-Dimensional Feature Spaces
+ * Using ANOVA-Based Fast Matrix-Vector Multiplication", arXiv 2111.10140.
+ *
+ *   K alpha = sum_l eta_l K_l alpha,  (K_l)_{ij} = exp(-||x_i^{W_l} - x_j^{W_l}||^2 / ell^2)
+ *     (Sec. 3, Eq. extended_Gaussian_ANOVA_kernel; Sec. 5 weights eta_l)
+ *   K_l alpha ~= Phi D Phi^* alpha  (Sec. 4.3), computed per window by the NFFT
+ *     fast summation of Sec. 4.2, Eq. (fastsum): Kaiser-Bessel spreading onto a
+ *     sigma*n oversampled grid (adjoint NFFT, Eq. adjnfft), FFT, multiplication
+ *     by the Fourier coefficients of the periodised kernel, inverse FFT, and
+ *     gathering (NFFT, Eq. nfft).
+ *   (K + lambda I) alpha = y solved by conjugate gradients (Sec. 2).
+ *   s(z) = sum_j alpha_j kappa(z, x_j) at test points (Sec. 4.2 Eq. kernelsum,
+ *     Sec. 4.3 "Phi_z D Phi^* alpha").
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" must be CUDA device (or managed) memory on the
+ *     current device; "host" pointers are ordinary host memory.  The caller
+ *     owns every buffer it passes; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; entry points that must return a host
+ *     value (plan creation, CG iteration counts) synchronise that stream.
+ *   - Errors are returned as anova_status; no exception crosses the ABI.
+ *     anova_last_error() returns a thread-local detail string for the last
+ *     failure on the calling thread.
+ *   - Arrays of points are row-major: point i, feature f at [i*ld + f].
+ *   - Multiple right-hand sides are column-major: column r at [r*ld + i].
+ */
+#ifndef ANOVA_GB300_H
+#define ANOVA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct anova_plan anova_plan;   /* opaque; owned by the library */
+
+typedef enum {
+    ANOVA_OK = 0,
+    ANOVA_EINVAL = 1,    /* bad argument (sizes, windows, ell, n, m, lambda ...) */
+    ANOVA_ENOMEM = 2,    /* device allocation failed */
+    ANOVA_ECUDA = 3,     /* a CUDA call failed; see anova_last_error() */
+    ANOVA_ENOCONV = 4,   /* CG reached maxit; outputs hold the last iterate */
+    ANOVA_ERANGE = 5,    /* input outside the supported range */
+    ANOVA_ETIMEOUT = 6   /* a bounded device-side wait expired */
+} anova_status;
+
+/* precision bitmask for anova_fastsum_plan: which operators the plan holds */
+#define ANOVA_FP64  1    /* FP64 spread / FFT / gather */
+#define ANOVA_FP32  2    /* FP32 spread / FFT / gather */
+#define ANOVA_MIXED 3    /* both: FP32 bulk work with FP64 refinement in CG */
+
+/*
+ * anova_fastsum_plan -- build the fast-summation plan for the node set X
+ * (Sec. 4.2 scaling of the nodes into the torus, Sec. 4.2 Fourier coefficients
+ * of the periodised kernel, Sec. 5 windows and weights).
+ *
+ *   points   device, N x d FP64, row-major with leading dimension ld >= d.
+ *   windows  host, P x 3 int32, 0-based feature indices, unused slots -1;
+ *            each window holds 1 to 3 distinct features (Sec. 3 Eq. index_window).
+ *            Windows may overlap.
+ *   weights  host, P FP64 kernel weights eta_l; NULL means eta_l = 1/P (Sec. 5).
+ *   ell      Gaussian width in the units of `points`, kernel exp(-r^2/ell^2).
+ *   n        host, P int32 bandwidths (even, >= 4); NULL means 32 for every window.
+ *   m        Kaiser-Bessel cutoff (1..12); 2m+2 <= sigma*n is required.
+ *   sigma    oversampling factor; sigma*n must be an even integer (2 is usual).
+ *   eps_B    regularisation width of the periodised kernel, 0 < eps_B < 1/2
+ *            (nodes are scaled into the ball of radius 1/4 - eps_B/2).
+ *   p        smoothness of the transition polynomial (degree 2p-1), 1..16.
+ *   precision  ANOVA_FP64, ANOVA_FP32 or ANOVA_MIXED.
+ *   out      host, receives the plan.
+ *
+ * The plan copies what it needs (the window coordinates), so `points` may be
+ * freed after return.  It synchronises `stream`.  Errors: EINVAL for invalid
+ * arguments, ENOMEM, ECUDA.
+ */
+anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int64_t ld,
+                                const int32_t* windows, int32_t P, const double* weights,
+                                double ell, const int32_t* n, int32_t m, double sigma,
+                                double eps_B, int32_t p, int32_t precision,
+                                void* stream, anova_plan** out);
+
+/*
+ * anova_matvec -- out = K alpha with the fast operator (Sec. 4.3, K alpha ~=
+ * sum_l eta_l Phi_l D_l Phi_l^* alpha).
+ *
+ *   dtype  ANOVA_FP64 (alpha, out are double*) or ANOVA_FP32 (float*); the
+ *          plan must hold that precision.
+ *   alpha  device, nrhs columns of N entries, column r at alpha + r*ld.
+ *   out    device, same layout; overwritten.  Must not alias alpha.
+ *   nrhs   >= 1; ld >= N.
+ * Asynchronous on `stream`.  Errors: EINVAL.
+ */
+anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, void* out,
+                          int32_t nrhs, int64_t ld, void* stream);
+
+/*
+ * krr_cg_solve -- solve (K + lambda I) alpha = y by conjugate gradients
+ * (Sec. 2; Hestenes-Stiefel, alpha_0 = 0), stopping when the recursive residual
+ * satisfies ||r||_2 <= tol ||y||_2 or after maxit iterations.
+ *
+ *   y, alpha  device FP64, nrhs columns with leading dimension ld >= N.
+ *   iters     host, nrhs int32 (may be NULL): iterations used per column.
+ *   relres    host, nrhs FP64 (may be NULL): true relative residual
+ *             ||y - (K + lambda I) alpha|| / ||y|| recomputed at the end with
+ *             the FP64 operator when the plan holds it, else the FP32 one.
+ * Plans with ANOVA_FP64 run CG with the FP64 operator; ANOVA_FP32 with the
+ * FP32 operator (FP64 vectors and scalars); ANOVA_MIXED runs FP32 inner CG
+ * inside FP64 iterative refinement until the FP64 residual meets tol.
+ * Synchronises `stream`.  Errors: EINVAL (lambda <= 0, tol <= 0 ...),
+ * ENOCONV (maxit reached; alpha and relres hold the last iterate).
+ */
+anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, double* alpha,
+                          int32_t nrhs, int64_t ld, double tol, int32_t maxit,
+                          int32_t* iters, double* relres, void* stream);
+
+/*
+ * krr_predict -- out_i = sum_l eta_l sum_j alpha_j kappa_l(z_i, x_j) at M test
+ * points (Sec. 4.3 "s ~= Phi_z D Phi^* alpha").
+ *
+ *   alpha  device FP64, N coefficients.
+ *   Z      device FP64, M x d row-major, leading dimension ldz >= d.
+ *   out    device FP64, M entries.
+ * Uses the plan's highest precision (FP64 when held).  When a test point maps
+ * outside the plan's ball the library builds a temporary frame over X and Z
+ * together (the kernel is shift- and scale-invariant in user units), so the
+ * call still returns ANOVA_OK.  Synchronises `stream`.
+ */
+anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
+                         int64_t ldz, double* out, void* stream);
+
+/* Free every device buffer of the plan.  NULL is ignored. */
+void anova_plan_destroy(anova_plan* plan);
+
+/* Static description of a status code. */
+const char* anova_status_string(anova_status status);
+
+/* Thread-local detail of the last error on the calling thread ("" if none). */
+const char* anova_last_error(void);
+
+/* ----------------------------------------------------------------------------
+ * Introspection used by tests and benchmarks.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * anova_plan_window -- frame and grid of window l (Sec. 4.2 scaled nodes):
+ * torus coordinate = scale * (x - centre).  centre (host, 3 doubles, unused
+ * entries 0), scale, ell_l = scale * ell, dims (1..3), n, nos = sigma*n.
+ */
+anova_status anova_plan_window(const anova_plan* plan, int32_t l, double* centre, double* scale,
+                               double* ell_l, int32_t* dims, int32_t* n, int32_t* nos);
+
+/*
+ * anova_debug_spread -- spreading step alone for window l (the window step of
+ * the adjoint NFFT, Eq. adjnfft): grid (device, nos^dims entries of dtype,
+ * centred index u + nos/2 per axis, last axis fastest) receives
+ *   g_u = sum_j alpha_j prod_t psi(nos x_{j,t} - u_t),
+ * where psi is the Kaiser-Bessel window normalised to psi(0) = 1, i.e. the
+ * window phi(t) = sinh(b sqrt(m^2-t^2)) / (pi sqrt(m^2-t^2)) divided by phi(0).
+ */
+anova_status anova_debug_spread(anova_plan* plan, int32_t l, int32_t dtype, const void* alpha,
+                                void* grid, void* stream);
+
+/*
+ * anova_debug_diag -- copy window l's FP64 multiplier D_k (host, n^dims
+ * doubles, centred index) = b_k / prod_t psihat(k_t)^2 with the normalised
+ * window (Sec. 4.3 D = diag(c_k) with the window deconvolution folded in).
+ */
+anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host);
+
+/*
+ * Stage timing.  When enabled, the library records CUDA events on the launch
+ * stream around each stage of the fast summation; anova_stage_times returns
+ * the accumulated milliseconds and kernel launch counts per stage since the
+ * last call (which resets them):
+ *   0 grid clearing and spreading, 1 forward FFT, multiply by D, inverse FFT,
+ *   2 gathering, 3 window sum and CG vector kernels.
+ * `ms` and `launches` are host arrays of `cap` entries; returns the number of
+ * stages written.  Reading synchronises the recorded events.
+ */
+anova_status anova_set_profiling(anova_plan* plan, int32_t enable);
+int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANOVA_GB300_H */

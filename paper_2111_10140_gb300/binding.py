@@ -1,0 +1,219 @@
+"""ctypes binding of libanova_gb300.so (argument marshalling only).
+
+Every function mirrors the C entry point of the same name declared in
+``include/anova_gb300.h``; tensors are passed as raw device pointers together
+with torch's current CUDA stream.  There is no fallback: if the library has not
+been built (``__graft_entry__.build()``) or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANGE, ETIMEOUT = range(7)
+FP64, FP32, MIXED = 1, 2, 3
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_pi32 = ctypes.POINTER(ctypes.c_int32)
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_pf64 = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "anova_fastsum_plan": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64,
+                                  _f64, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "anova_matvec": (_i32, [_vp, _i32, _vp, _vp, _i32, _i64, _vp]),
+    "krr_cg_solve": (_i32, [_vp, _f64, _vp, _vp, _i32, _i64, _f64, _i32, _pi32, _pf64, _vp]),
+    "krr_predict": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
+    "anova_plan_destroy": (None, [_vp]),
+    "anova_status_string": (ctypes.c_char_p, [_i32]),
+    "anova_last_error": (ctypes.c_char_p, []),
+    "anova_plan_window": (_i32, [_vp, _i32, _pf64, _pf64, _pf64, _pi32, _pi32, _pi32]),
+    "anova_debug_spread": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+    "anova_debug_diag": (_i32, [_vp, _i32, _pf64]),
+    "anova_set_profiling": (_i32, [_vp, _i32]),
+    "anova_stage_times": (_i32, [_vp, _pf64, _pi64, _i32]),
+}
+
+
+class AnovaError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        detail = lib().anova_last_error().decode()
+        super().__init__(f"{where}: {lib().anova_status_string(status).decode()} ({detail})")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status, where, allow=(OK,)):
+    if status not in allow:
+        raise AnovaError(status, where)
+    return status
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _require_cuda(t, name, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def windows_array(windows) -> np.ndarray:
+    out = -np.ones((len(windows), 3), dtype=np.int32)
+    for l, w in enumerate(windows):
+        out[l, :len(w)] = w
+    return out
+
+
+class Plan:
+    """Owning handle of an anova_plan (destroyed with the object)."""
+
+    def __init__(self, handle, N, d, P, precision):
+        self.handle = handle
+        self.N, self.d, self.P, self.precision = N, d, P, precision
+
+    def close(self):
+        if self.handle:
+            lib().anova_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def anova_fastsum_plan(points, windows, ell, n=None, m=6, sigma=2.0, eps_B=1.0 / 16, p=8,
+                       precision=FP64, weights=None, stream=None) -> Plan:
+    import torch
+    _require_cuda(points, "points", torch.float64)
+    N, d = points.shape
+    W = windows_array(windows) if not isinstance(windows, np.ndarray) else np.ascontiguousarray(windows, np.int32)
+    P = W.shape[0]
+    wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    nv = None if n is None else np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int32), (P,)), dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = lib().anova_fastsum_plan(
+        _ptr(points), N, d, d, W.ctypes.data_as(_pi32), P,
+        wts.ctypes.data_as(_pf64) if wts is not None else None, float(ell),
+        nv.ctypes.data_as(_pi32) if nv is not None else None, int(m), float(sigma), float(eps_B), int(p),
+        int(precision), _stream(stream), ctypes.byref(h))
+    _check(st, "anova_fastsum_plan")
+    return Plan(h, N, d, P, precision)
+
+
+def anova_matvec(plan: Plan, alpha, out, stream=None):
+    import torch
+    _require_cuda(alpha, "alpha")
+    _require_cuda(out, "out", alpha.dtype)
+    dtype = FP64 if alpha.dtype == torch.float64 else FP32 if alpha.dtype == torch.float32 else None
+    if dtype is None:
+        raise ValueError("alpha must be float64 or float32")
+    nrhs = 1 if alpha.dim() == 1 else alpha.shape[0]
+    ld = alpha.shape[-1]
+    _check(lib().anova_matvec(plan.handle, dtype, _ptr(alpha), _ptr(out), nrhs, ld, _stream(stream)),
+           "anova_matvec")
+    return out
+
+
+def krr_cg_solve(plan: Plan, lam, y, alpha, tol, maxit, stream=None):
+    """Returns (status, iterations per column, true relative residual per column)."""
+    import torch
+    _require_cuda(y, "y", torch.float64)
+    _require_cuda(alpha, "alpha", torch.float64)
+    nrhs = 1 if y.dim() == 1 else y.shape[0]
+    ld = y.shape[-1]
+    its = np.zeros(nrhs, dtype=np.int32)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    st = lib().krr_cg_solve(plan.handle, float(lam), _ptr(y), _ptr(alpha), nrhs, ld, float(tol), int(maxit),
+                            its.ctypes.data_as(_pi32), rel.ctypes.data_as(_pf64), _stream(stream))
+    _check(st, "krr_cg_solve", allow=(OK, ENOCONV))
+    return st, its, rel
+
+
+def krr_predict(plan: Plan, alpha, Z, out, stream=None):
+    import torch
+    _require_cuda(alpha, "alpha", torch.float64)
+    _require_cuda(Z, "Z", torch.float64)
+    _require_cuda(out, "out", torch.float64)
+    M = Z.shape[0]
+    _check(lib().krr_predict(plan.handle, _ptr(alpha), _ptr(Z), M, Z.shape[1], _ptr(out), _stream(stream)),
+           "krr_predict")
+    return out
+
+
+def anova_plan_window(plan: Plan, l: int) -> dict:
+    c = (ctypes.c_double * 3)()
+    s, e = ctypes.c_double(), ctypes.c_double()
+    dims, n, nos = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().anova_plan_window(plan.handle, l, c, ctypes.byref(s), ctypes.byref(e), ctypes.byref(dims),
+                                   ctypes.byref(n), ctypes.byref(nos)), "anova_plan_window")
+    return {"centre": np.array(c[:dims.value]), "scale": s.value, "ell_l": e.value, "dims": dims.value,
+            "n": n.value, "nos": nos.value}
+
+
+def anova_debug_spread(plan: Plan, l: int, alpha, grid, stream=None):
+    import torch
+    dtype = FP64 if alpha.dtype == torch.float64 else FP32
+    _check(lib().anova_debug_spread(plan.handle, l, dtype, _ptr(alpha), _ptr(grid), _stream(stream)),
+           "anova_debug_spread")
+    return grid
+
+
+def anova_debug_diag(plan: Plan, l: int) -> np.ndarray:
+    info = anova_plan_window(plan, l)
+    D = np.zeros(info["n"] ** info["dims"])
+    _check(lib().anova_debug_diag(plan.handle, l, D.ctypes.data_as(_pf64)), "anova_debug_diag")
+    return D.reshape((info["n"],) * info["dims"])
+
+
+def anova_set_profiling(plan: Plan, enable: bool):
+    _check(lib().anova_set_profiling(plan.handle, int(bool(enable))), "anova_set_profiling")
+
+
+def anova_stage_times(plan: Plan):
+    ms = (ctypes.c_double * 8)()
+    la = (ctypes.c_int64 * 8)()
+    k = lib().anova_stage_times(plan.handle, ms, la, 8)
+    return list(ms[:k]), list(la[:k])

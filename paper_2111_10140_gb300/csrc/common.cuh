@@ -1,0 +1,157 @@
+// common.cuh -- internal types and device helpers of libanova_gb300.
+//
+// Notation (arXiv 2111.10140, Sec. 4): window l has dA in {1,2,3} features,
+// bandwidth n, oversampled grid nos = sigma*n per axis, Kaiser-Bessel cutoff m.
+// Grid and frequency arrays use the centred index of I_M (value v stored at
+// v + M/2), last axis fastest.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/anova_gb300.h"
+
+namespace anova {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+#define ANOVA_CUDA_TRY(expr)                                                    \
+    do {                                                                        \
+        cudaError_t _e = (expr);                                                \
+        if (_e != cudaSuccess) {                                                \
+            ::anova::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+            return ANOVA_ECUDA;                                                 \
+        }                                                                       \
+    } while (0)
+#define ANOVA_TRY(expr)                       \
+    do {                                      \
+        anova_status _s = (expr);             \
+        if (_s != ANOVA_OK) return _s;        \
+    } while (0)
+#define ANOVA_CHECK_LAUNCH() ANOVA_CUDA_TRY(cudaGetLastError())
+
+// ------------------------------------------------------------- constants
+constexpr int kMaxDim = 3;
+constexpr int kMaxWindows = 256;
+constexpr int kMaxM = 12;
+constexpr int kSubChunk = 1024;        // points per spread/gather sub-problem
+constexpr int kThreads = 256;
+
+// Points of one window, binned and sorted (one for the training nodes X,
+// one per predict call for the test nodes Z).
+struct PointSet {
+    int64_t N = 0;
+    int32_t* perm = nullptr;       // sorted position -> original index
+    int32_t* cell = nullptr;       // dA x N cell index per axis in [0, nos)
+    double* frac64 = nullptr;      // dA x N, nos*x - floor(nos*x) in FP64
+    float* frac32 = nullptr;       // dA x N, same rounded to FP32
+    int32_t* bin_start = nullptr;  // nbins + 1 offsets of each bin in sorted order
+    int4* sub = nullptr;           // sub-problems: (bin, first, count, 0)
+    int32_t nsub = 0;
+};
+
+struct WindowPlan {
+    int dA = 0;
+    int feat[kMaxDim] = {-1, -1, -1};
+    int n = 0, nos = 0;
+    int T = 0;        // bin side in grid cells
+    int nb = 0;       // bins per axis, ceil(nos / T)
+    int R = 0;        // region side = T + 2m
+    int nbins = 0;    // nb^dA
+    double eta = 0.0;
+    double centre[kMaxDim] = {0, 0, 0};
+    double scale = 1.0, ell_l = 0.0;
+    double* D64 = nullptr;     // n^dA multiplier (FP64)
+    float* D32 = nullptr;      // same in FP32
+    double2* tw64 = nullptr;   // exp(-2 pi i r / nos), r = 0..nos-1
+    float2* tw32 = nullptr;
+    double* xw = nullptr;      // N x dA window coordinates (user units, original order)
+    PointSet X;
+};
+
+struct StageClock {
+    bool enabled = false;
+    static constexpr int kStages = 4;
+    std::vector<cudaEvent_t> ev;       // pairs (start, stop)
+    std::vector<int> stage_of_pair;
+    double ms[kStages] = {0, 0, 0, 0};
+    int64_t launches[kStages] = {0, 0, 0, 0};
+};
+
+}  // namespace anova
+
+struct anova_plan {
+    int64_t N = 0;
+    int d = 0, P = 0, m = 0, p = 0, precision = 0;
+    double sigma = 2.0, epsB = 1.0 / 16, ell = 0.0, b = 0.0;
+    double psi_norm = 1.0;              // m / sinh(b m): psi(t) = psi_norm * sinh(b s)/s
+    std::vector<anova::WindowPlan> win;
+    // shared work buffers (windows are processed one after another)
+    size_t grid_elems = 0, work_elems = 0;
+    void* grid = nullptr;               // real spread grid / inverse FFT output
+    void* work1 = nullptr;              // complex work arrays
+    void* work2 = nullptr;
+    void* tmp = nullptr;                // P x N per-window results (8 bytes each)
+    double* eta_dev = nullptr;          // P window weights on the device
+    // CG state
+    double* cg_vec = nullptr;           // r, p, q, a (FP64), each N
+    double* cg_scal = nullptr;          // scalars and per-iteration history
+    double* cg_part = nullptr;          // block partial sums
+    int cg_hist = 0;
+    anova::StageClock clock;
+    int sm_count = 0;
+};
+
+namespace anova {
+
+// ------------------------------------------------------------ device math
+// Kaiser-Bessel window normalised to psi(0) = 1 (grid units t):
+//   psi(t) = (m / sinh(b m)) * sinh(b s) / s,  s = sqrt(m^2 - t^2), |t| <= m,
+// with the limit (m / sinh(b m)) * b at |t| = m and 0 beyond.
+template <typename T>
+__device__ __forceinline__ T kb_psi(T t, T m, T b, T norm) {
+    T s2 = m * m - t * t;
+    if (s2 < T(0)) return T(0);
+    T s = sqrt(s2);
+    T r = (s > T(0)) ? sinh(b * s) / s : b;
+    return norm * r;
+}
+
+// ------------------------------------------------------------- host API
+anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
+                            int64_t ldc, const double* centre, double scale, PointSet& ps,
+                            cudaStream_t st);
+void free_pointset(PointSet& ps);
+anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M, WindowPlan& dst,
+                            cudaStream_t st);
+void window_release_reframed(WindowPlan& w);
+anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, const double* centre,
+                        double* rmax_host, cudaStream_t st);
+anova_status extract_window(anova_plan* plan, const double* Z, int64_t M, int64_t ldz,
+                            const WindowPlan& w, double* zw, cudaStream_t st);
+
+// window-level stages (matvec.cu / spread_gather.cu / fft.cu)
+template <typename T>
+anova_status spread_window(anova_plan* plan, const WindowPlan& w, const PointSet& ps,
+                           const void* alpha, int alpha_is_double, T* grid, cudaStream_t st);
+template <typename T>
+anova_status gather_window(anova_plan* plan, const WindowPlan& w, const PointSet& ps,
+                           const T* h, T* out, cudaStream_t st);
+template <typename T>
+anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid, cudaStream_t st);
+
+// stage clock helpers
+void clock_begin(anova_plan* plan, int stage, cudaStream_t st);
+void clock_end(anova_plan* plan, int stage, int launches, cudaStream_t st);
+
+inline int grid_for(int64_t n, int threads, int cap) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace anova

@@ -1,0 +1,564 @@
+// matvec.cu -- the ANOVA matrix-vector product, CG for kernel ridge regression
+// and prediction (arXiv 2111.10140):
+//
+//   K alpha = sum_l eta_l K_l alpha ~= sum_l eta_l Phi_l D_l Phi_l^* alpha
+//       (Sec. 4.3, Sec. 5: P fast summations, one per window, weighted sum)
+//   (K + lambda I) alpha = y by conjugate gradients (Sec. 2, Hestenes-Stiefel)
+//   s = sum_l eta_l Phi_{z,l} D_l Phi_l^* alpha at test points (Sec. 4.3)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace anova {
+
+// --------------------------------------------------------------- stage clock
+void clock_begin(anova_plan* plan, int stage, cudaStream_t st) {
+    StageClock& c = plan->clock;
+    if (!c.enabled) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    c.ev.push_back(a);
+    c.ev.push_back(b);
+    c.stage_of_pair.push_back(stage);
+}
+
+void clock_end(anova_plan* plan, int stage, int launches, cudaStream_t st) {
+    StageClock& c = plan->clock;
+    if (!c.enabled || c.ev.empty()) return;
+    cudaEventRecord(c.ev.back(), st);
+    c.launches[stage] += launches;
+}
+
+// ------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// deterministic block sum (blockDim.x == kThreads); result valid in all threads
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+// sum of nblk partials in a fixed order, inside every block
+__device__ double sum_partials(const double* __restrict__ part, int nblk, double* sh) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += part[i];
+    return block_sum(v, sh);
+}
+
+// ------------------------------------------------------------ window sum
+// out_i = sum_l eta_l tmp_l[i]
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kThreads)
+k_window_sum(const Tin* __restrict__ tmp, const double* __restrict__ eta, int P, int64_t N,
+             Tout* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < P; l++) acc += eta[l] * (double)tmp[l * N + i];
+        out[i] = (Tout)acc;
+    }
+}
+
+// -------------------------------------------------------------- matvec core
+// tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum)
+template <typename T>
+static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha_is_double, T* tmp,
+                                  cudaStream_t st) {
+    const int64_t N = plan->N;
+    T* grid = static_cast<T*>(plan->grid);
+    for (int l = 0; l < plan->P; l++) {
+        const WindowPlan& w = plan->win[l];
+        size_t ge = 1;
+        for (int t = 0; t < w.dA; t++) ge *= w.nos;
+        clock_begin(plan, 0, st);
+        ANOVA_CUDA_TRY(cudaMemsetAsync(grid, 0, ge * sizeof(T), st));
+        ANOVA_TRY(spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid, st));
+        clock_end(plan, 0, 2, st);
+        clock_begin(plan, 1, st);
+        ANOVA_TRY(fft_convolve_window<T>(plan, w, grid, st));
+        clock_end(plan, 1, 2 * w.dA, st);
+        clock_begin(plan, 2, st);
+        ANOVA_TRY(gather_window<T>(plan, w, w.X, grid, tmp + (int64_t)l * N, st));
+        clock_end(plan, 2, 1, st);
+    }
+    return ANOVA_OK;
+}
+
+static bool has_precision(const anova_plan* plan, int dtype) {
+    return (dtype == ANOVA_FP64 || dtype == ANOVA_FP32) && (plan->precision & dtype);
+}
+
+template <typename T>
+static anova_status matvec_one(anova_plan* plan, const T* alpha, T* out, cudaStream_t st) {
+    const int64_t N = plan->N;
+    if (N == 0) return ANOVA_OK;
+    T* tmp = static_cast<T*>(plan->tmp);
+    ANOVA_TRY(windows_apply<T>(plan, alpha, sizeof(T) == 8, tmp, st));
+    clock_begin(plan, 3, st);
+    k_window_sum<T, T><<<grid_for(N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+        tmp, plan->eta_dev, plan->P, N, out);
+    ANOVA_CHECK_LAUNCH();
+    clock_end(plan, 3, 1, st);
+    return ANOVA_OK;
+}
+
+// ================================================================== CG
+// Vectors (FP64): r, p, q, x stored in plan->cg_vec; scalars in cg_scal:
+//   [0] yy, [1] result scratch, [2 ...] rr history (one entry per iteration)
+__global__ void __launch_bounds__(kThreads)
+k_cg_init(const double* __restrict__ b, int64_t N, double* __restrict__ x, double* __restrict__ r,
+          double* __restrict__ p, int zero_x, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = b[i];
+        if (zero_x) x[i] = 0.0;
+        r[i] = v;
+        p[i] = v;
+        acc += v * v;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_reduce_to(const double* __restrict__ part, int nblk, double* __restrict__ dst) {
+    __shared__ double sh[32];
+    double v = sum_partials(part, nblk, sh);
+    if (threadIdx.x == 0) *dst = v;
+}
+
+// q = sum_l eta_l tmp_l + lambda p; partial sums of p.q
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cg_q(const T* __restrict__ tmp, const double* __restrict__ eta, int P, int64_t N, double lambda,
+       const double* __restrict__ p, double* __restrict__ q, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = lambda * p[i];
+        for (int l = 0; l < P; l++) v += eta[l] * (double)tmp[l * N + i];
+        q[i] = v;
+        acc += p[i] * v;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// a = rr / (p.q); x += a p; r -= a q; partial sums of r.r
+__global__ void __launch_bounds__(kThreads)
+k_cg_update(const double* __restrict__ part_pq, int nblk, const double* __restrict__ rr_now, int64_t N,
+            double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+            const double* __restrict__ q, double* __restrict__ part_rr) {
+    __shared__ double sh[32];
+    const double pq = sum_partials(part_pq, nblk, sh);
+    const double a = *rr_now / pq;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part_rr[blockIdx.x] = acc;
+}
+
+// b = rr_new / rr; p = r + b p; rr_next = rr_new
+__global__ void __launch_bounds__(kThreads)
+k_cg_pupdate(const double* __restrict__ part_rr, int nblk, const double* __restrict__ rr_now,
+             double* __restrict__ rr_next, int64_t N, const double* __restrict__ r, double* __restrict__ p) {
+    __shared__ double sh[32];
+    const double rr_new = sum_partials(part_rr, nblk, sh);
+    const double beta = rr_new / *rr_now;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = r[i] + beta * p[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rr_next = rr_new;
+}
+
+// r = b - q (q already holds (K + lambda I) x); partial sums of r.r
+__global__ void __launch_bounds__(kThreads)
+k_residual(const double* __restrict__ b, const double* __restrict__ q, int64_t N, double* __restrict__ r,
+           double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = b[i] - q[i];
+        r[i] = v;
+        acc += v * v;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_axpy(int64_t N, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+struct CgBuffers {
+    double *r, *p, *q, *x2, *scal, *part, *part2;
+    int nblk;
+};
+
+static anova_status cg_buffers(anova_plan* plan, int maxit, CgBuffers& B) {
+    const int64_t N = plan->N;
+    const int nblk = grid_for(N, kThreads, 2 * plan->sm_count);
+    if (!plan->cg_vec) ANOVA_CUDA_TRY(cudaMalloc(&plan->cg_vec, 4 * std::max<int64_t>(N, 1) * sizeof(double)));
+    if (!plan->cg_part) ANOVA_CUDA_TRY(cudaMalloc(&plan->cg_part, 2 * 2 * plan->sm_count * sizeof(double)));
+    if (plan->cg_hist < maxit + 8) {
+        cudaFree(plan->cg_scal);
+        plan->cg_scal = nullptr;
+        plan->cg_hist = maxit + 8;
+        ANOVA_CUDA_TRY(cudaMalloc(&plan->cg_scal, (plan->cg_hist + 4) * sizeof(double)));
+    }
+    B.r = plan->cg_vec;
+    B.p = plan->cg_vec + N;
+    B.q = plan->cg_vec + 2 * N;
+    B.x2 = plan->cg_vec + 3 * N;
+    B.scal = plan->cg_scal;
+    B.part = plan->cg_part;
+    B.part2 = plan->cg_part + 2 * plan->sm_count;
+    B.nblk = nblk;
+    return ANOVA_OK;
+}
+
+// q = (K + lambda I) v with the operator of precision T; partial sums of v.q in B.part
+template <typename T>
+static anova_status apply_shifted(anova_plan* plan, double lambda, const double* v, double* q,
+                                  const CgBuffers& B, cudaStream_t st) {
+    T* tmp = static_cast<T*>(plan->tmp);
+    ANOVA_TRY(windows_apply<T>(plan, v, 1, tmp, st));
+    clock_begin(plan, 3, st);
+    k_cg_q<T><<<B.nblk, kThreads, 0, st>>>(tmp, plan->eta_dev, plan->P, plan->N, lambda, v, q, B.part);
+    ANOVA_CHECK_LAUNCH();
+    clock_end(plan, 3, 1, st);
+    return ANOVA_OK;
+}
+
+static anova_status read_scalar(const double* d, double* h, cudaStream_t st) {
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    return ANOVA_OK;
+}
+
+// Plain CG on (K_T + lambda I) x = b, x_0 = 0 (FP64 vectors and scalars).
+// Stops when ||r|| <= tol * ||b||; returns iterations in *iters.
+template <typename T>
+static anova_status cg_run(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
+                           const CgBuffers& B, int* iters, double* bb_out, cudaStream_t st) {
+    const int64_t N = plan->N;
+    double* hist = B.scal + 2;
+    k_cg_init<<<B.nblk, kThreads, 0, st>>>(b, N, x, B.r, B.p, 1, B.part);
+    k_reduce_to<<<1, kThreads, 0, st>>>(B.part, B.nblk, hist);
+    ANOVA_CHECK_LAUNCH();
+    double bb = 0.0;
+    ANOVA_TRY(read_scalar(hist, &bb, st));
+    if (bb_out) *bb_out = bb;
+    int it = 0;
+    double rr = bb;
+    while (it < maxit && rr > tol * tol * bb && bb > 0.0) {
+        ANOVA_TRY(apply_shifted<T>(plan, lambda, B.p, B.q, B, st));
+        clock_begin(plan, 3, st);
+        k_cg_update<<<B.nblk, kThreads, 0, st>>>(B.part, B.nblk, hist + it, N, x, B.r, B.p, B.q, B.part2);
+        k_cg_pupdate<<<B.nblk, kThreads, 0, st>>>(B.part2, B.nblk, hist + it, hist + it + 1, N, B.r, B.p);
+        ANOVA_CHECK_LAUNCH();
+        clock_end(plan, 3, 2, st);
+        it++;
+        ANOVA_TRY(read_scalar(hist + it, &rr, st));
+        if (!std::isfinite(rr)) {
+            set_error("CG residual is not finite");
+            *iters = it;
+            return ANOVA_ERANGE;
+        }
+    }
+    *iters = it;
+    return ANOVA_OK;
+}
+
+// true relative residual ||b - (K_T + lambda I) x|| / ||b||
+template <typename T>
+static anova_status true_residual(anova_plan* plan, double lambda, const double* b, const double* x,
+                                  double bb, const CgBuffers& B, double* relres, cudaStream_t st) {
+    ANOVA_TRY(apply_shifted<T>(plan, lambda, x, B.q, B, st));
+    k_residual<<<B.nblk, kThreads, 0, st>>>(b, B.q, plan->N, B.r, B.part);
+    k_reduce_to<<<1, kThreads, 0, st>>>(B.part, B.nblk, B.scal + 1);
+    ANOVA_CHECK_LAUNCH();
+    double rr = 0.0;
+    ANOVA_TRY(read_scalar(B.scal + 1, &rr, st));
+    *relres = (bb > 0.0) ? std::sqrt(rr / bb) : 0.0;
+    return ANOVA_OK;
+}
+
+// Mixed precision: FP32-operator CG on the correction equation inside FP64
+// iterative refinement, x += CG32(r), r = b - (K64 + lambda I) x.
+static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
+                             const CgBuffers& B, int* iters, double* relres, cudaStream_t st) {
+    const int64_t N = plan->N;
+    const double inner_tol = 1e-4;
+    double* rhs = B.x2;            // current residual (right-hand side of the correction)
+    double* dx = static_cast<double*>(nullptr);
+    ANOVA_CUDA_TRY(cudaMalloc(&dx, std::max<int64_t>(N, 1) * sizeof(double)));
+    ANOVA_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double), st));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(rhs, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_cg_init<<<B.nblk, kThreads, 0, st>>>(b, N, B.q, B.r, B.p, 0, B.part);
+    k_reduce_to<<<1, kThreads, 0, st>>>(B.part, B.nblk, B.scal);
+    double bb = 0.0;
+    anova_status s = read_scalar(B.scal, &bb, st);
+    int total = 0;
+    double rel = 1.0;
+    while (s == ANOVA_OK && bb > 0.0 && total < maxit) {
+        int it = 0;
+        double rb = 0.0;
+        double tol_in = std::max(inner_tol, 0.5 * tol / std::max(rel, 1e-300));
+        s = cg_run<float>(plan, lambda, rhs, dx, std::min(tol_in, 0.5), maxit - total, B, &it, &rb, st);
+        if (s != ANOVA_OK) break;
+        total += std::max(it, 1);
+        k_axpy<<<grid_for(N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(N, 1.0, dx, x);
+        // FP64 residual of the original system
+        s = apply_shifted<double>(plan, lambda, x, B.q, B, st);
+        if (s != ANOVA_OK) break;
+        k_residual<<<B.nblk, kThreads, 0, st>>>(b, B.q, N, rhs, B.part);
+        k_reduce_to<<<1, kThreads, 0, st>>>(B.part, B.nblk, B.scal + 1);
+        double rr = 0.0;
+        s = read_scalar(B.scal + 1, &rr, st);
+        if (s != ANOVA_OK) break;
+        rel = std::sqrt(rr / bb);
+        if (!std::isfinite(rel)) {
+            set_error("refinement residual is not finite");
+            s = ANOVA_ERANGE;
+            break;
+        }
+        if (rel <= tol) break;
+    }
+    cudaFree(dx);
+    *iters = total;
+    *relres = (bb > 0.0) ? rel : 0.0;
+    if (s == ANOVA_OK && bb > 0.0 && rel > tol) s = ANOVA_ENOCONV;
+    return s;
+}
+
+// ------------------------------------------------------------ debug spread
+template <typename T>
+static anova_status debug_spread_t(anova_plan* plan, int l, const void* alpha, void* grid, cudaStream_t st) {
+    const WindowPlan& w = plan->win[l];
+    size_t ge = 1;
+    for (int t = 0; t < w.dA; t++) ge *= w.nos;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(grid, 0, ge * sizeof(T), st));
+    return spread_window<T>(plan, w, w.X, alpha, sizeof(T) == 8, static_cast<T*>(grid), st);
+}
+
+// ---------------------------------------------------------------- predict
+template <typename T>
+static anova_status predict_t(anova_plan* plan, const double* alpha, const double* Z, int64_t M, int64_t ldz,
+                              double* out, cudaStream_t st) {
+    const int P = plan->P;
+    T* grid = static_cast<T*>(plan->grid);
+    T* tmp = nullptr;
+    double* zw = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&tmp, std::max<int64_t>(M, 1) * P * sizeof(T)));
+    ANOVA_CUDA_TRY(cudaMalloc(&zw, std::max<int64_t>(M, 1) * 3 * sizeof(double)));
+    anova_status s = ANOVA_OK;
+    for (int l = 0; l < P && s == ANOVA_OK; l++) {
+        const WindowPlan& base = plan->win[l];
+        s = extract_window(plan, Z, M, ldz, base, zw, st);
+        double rmax = 0.0;
+        if (s == ANOVA_OK) s = max_radius(plan, zw, M, base.dA, base.centre, &rmax, st);
+        if (s != ANOVA_OK) break;
+        WindowPlan joint;
+        const bool reframe = base.scale * rmax > 0.25 - 0.5 * plan->epsB;
+        if (reframe) {
+            s = window_reframe(plan, l, zw, M, joint, st);
+            if (s != ANOVA_OK) {
+                window_release_reframed(joint);
+                break;
+            }
+        }
+        const WindowPlan& w = reframe ? joint : base;
+        PointSet zs;
+        WindowPlan wz = w;   // binning parameters of the window
+        s = build_pointset(plan, wz, zw, M, w.dA, w.centre, w.scale, zs, st);
+        size_t ge = 1;
+        for (int t = 0; t < w.dA; t++) ge *= w.nos;
+        if (s == ANOVA_OK && plan->N > 0) {
+            cudaMemsetAsync(grid, 0, ge * sizeof(T), st);
+            s = spread_window<T>(plan, w, w.X, alpha, 1, grid, st);
+            if (s == ANOVA_OK) s = fft_convolve_window<T>(plan, w, grid, st);
+            if (s == ANOVA_OK) s = gather_window<T>(plan, w, zs, grid, tmp + (int64_t)l * M, st);
+        } else if (s == ANOVA_OK) {
+            cudaMemsetAsync(tmp + (int64_t)l * M, 0, M * sizeof(T), st);
+        }
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (s == ANOVA_OK && e != cudaSuccess) {
+            set_error(std::string("predict: ") + cudaGetErrorString(e));
+            s = ANOVA_ECUDA;
+        }
+        free_pointset(zs);
+        wz.X = PointSet();
+        if (reframe) window_release_reframed(joint);
+    }
+    if (s == ANOVA_OK && M > 0) {
+        k_window_sum<T, double><<<grid_for(M, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            tmp, plan->eta_dev, P, M, out);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error(std::string("predict: ") + cudaGetErrorString(e));
+            s = ANOVA_ECUDA;
+        }
+    }
+    cudaFree(tmp);
+    cudaFree(zw);
+    return s;
+}
+
+}  // namespace anova
+
+using namespace anova;
+
+extern "C" {
+
+anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, void* out, int32_t nrhs,
+                          int64_t ld, void* stream) {
+    if (!plan || !has_precision(plan, dtype) || nrhs < 1 || ld < plan->N ||
+        (plan->N > 0 && (!alpha || !out))) {
+        set_error("anova_matvec: bad plan, dtype, pointers, nrhs or ld");
+        return ANOVA_EINVAL;
+    }
+    if (alpha == out) {
+        set_error("anova_matvec: out must not alias alpha");
+        return ANOVA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int r = 0; r < nrhs; r++) {
+        if (dtype == ANOVA_FP64)
+            ANOVA_TRY(matvec_one<double>(plan, static_cast<const double*>(alpha) + r * ld,
+                                         static_cast<double*>(out) + r * ld, st));
+        else
+            ANOVA_TRY(matvec_one<float>(plan, static_cast<const float*>(alpha) + r * ld,
+                                        static_cast<float*>(out) + r * ld, st));
+    }
+    return ANOVA_OK;
+}
+
+anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, double* alpha, int32_t nrhs,
+                          int64_t ld, double tol, int32_t maxit, int32_t* iters, double* relres,
+                          void* stream) {
+    if (!plan || !(lambda > 0.0) || !std::isfinite(lambda) || !(tol > 0.0) || maxit < 0 || nrhs < 1 ||
+        ld < plan->N || (plan->N > 0 && (!y || !alpha))) {
+        set_error("krr_cg_solve: bad plan, lambda, tol, maxit, nrhs, ld or pointers");
+        return ANOVA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    anova_status worst = ANOVA_OK;
+    if (plan->N == 0) {
+        for (int r = 0; r < nrhs; r++) {
+            if (iters) iters[r] = 0;
+            if (relres) relres[r] = 0.0;
+        }
+        return ANOVA_OK;
+    }
+    CgBuffers B;
+    ANOVA_TRY(cg_buffers(plan, maxit, B));
+    for (int c = 0; c < nrhs; c++) {
+        const double* b = y + c * ld;
+        double* x = alpha + c * ld;
+        int it = 0;
+        double rel = 0.0, bb = 0.0;
+        anova_status s;
+        if (plan->precision == ANOVA_MIXED) {
+            s = cg_mixed(plan, lambda, b, x, tol, maxit, B, &it, &rel, st);
+        } else if (plan->precision & ANOVA_FP64) {
+            s = cg_run<double>(plan, lambda, b, x, tol, maxit, B, &it, &bb, st);
+            if (s == ANOVA_OK) s = true_residual<double>(plan, lambda, b, x, bb, B, &rel, st);
+            if (s == ANOVA_OK && it >= maxit && rel > tol) s = ANOVA_ENOCONV;
+        } else {
+            s = cg_run<float>(plan, lambda, b, x, tol, maxit, B, &it, &bb, st);
+            if (s == ANOVA_OK) s = true_residual<float>(plan, lambda, b, x, bb, B, &rel, st);
+            if (s == ANOVA_OK && it >= maxit && rel > tol) s = ANOVA_ENOCONV;
+        }
+        if (iters) iters[c] = it;
+        if (relres) relres[c] = rel;
+        if (s != ANOVA_OK && s != ANOVA_ENOCONV) return s;
+        if (s == ANOVA_ENOCONV) worst = s;
+    }
+    return worst;
+}
+
+anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z, int64_t M, int64_t ldz,
+                         double* out, void* stream) {
+    if (!plan || M < 0 || M > INT32_MAX || ldz < plan->d || (M > 0 && (!Z || !out)) ||
+        (plan->N > 0 && !alpha)) {
+        set_error("krr_predict: bad plan, sizes or pointers");
+        return ANOVA_EINVAL;
+    }
+    if (M == 0) return ANOVA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->precision & ANOVA_FP64) return predict_t<double>(plan, alpha, Z, M, ldz, out, st);
+    return predict_t<float>(plan, alpha, Z, M, ldz, out, st);
+}
+
+anova_status anova_debug_spread(anova_plan* plan, int32_t l, int32_t dtype, const void* alpha, void* grid,
+                                void* stream) {
+    if (!plan || l < 0 || l >= plan->P || !has_precision(plan, dtype) || !grid ||
+        (plan->N > 0 && !alpha)) {
+        set_error("anova_debug_spread: bad arguments");
+        return ANOVA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == ANOVA_FP64) return debug_spread_t<double>(plan, l, alpha, grid, st);
+    return debug_spread_t<float>(plan, l, alpha, grid, st);
+}
+
+anova_status anova_set_profiling(anova_plan* plan, int32_t enable) {
+    if (!plan) return ANOVA_EINVAL;
+    plan->clock.enabled = enable != 0;
+    return ANOVA_OK;
+}
+
+int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap) {
+    if (!plan) return 0;
+    StageClock& c = plan->clock;
+    for (size_t i = 0; i + 1 < c.ev.size(); i += 2) {
+        cudaEventSynchronize(c.ev[i + 1]);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c.ev[i], c.ev[i + 1]) == cudaSuccess) c.ms[c.stage_of_pair[i / 2]] += t;
+        cudaEventDestroy(c.ev[i]);
+        cudaEventDestroy(c.ev[i + 1]);
+    }
+    c.ev.clear();
+    c.stage_of_pair.clear();
+    int k = std::min<int>(cap, StageClock::kStages);
+    for (int i = 0; i < k; i++) {
+        if (ms) ms[i] = c.ms[i];
+        if (launches) launches[i] = c.launches[i];
+        c.ms[i] = 0.0;
+        c.launches[i] = 0;
+    }
+    return k;
+}
+
+}  // extern "C"

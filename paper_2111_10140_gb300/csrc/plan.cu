@@ -1,0 +1,831 @@
+// plan.cu -- plan construction for the ANOVA fast summation (arXiv 2111.10140).
+//
+//   A0  node scaling: per window, centre = bounding-box midpoint and
+//       scale = (1/4 - eps_B/2) / max ||x - centre||, so scaled nodes lie in the
+//       ball that keeps all pairwise distances below 1/2 - eps_B (Sec. 4.2,
+//       "scaled nodes h^{-1} x", torus T = [-1/2, 1/2), Sec. 4.1).
+//   A1  binning: a stable counting sort of each window's nodes by spatial bin
+//       of T^dA grid cells, plus the list of sub-problems (bin, first, count)
+//       that the spread and gather kernels walk.
+//   A2  multiplier: b_k = n^{-dA} sum_{j in I_n} K_R(||j||/n) e^{-2 pi i k.j/n}
+//       (Sec. 4.2, Fourier coefficients from equispaced samples of the
+//       periodised kernel), divided by the squared Kaiser-Bessel transform
+//       per axis (the window deconvolution of the adjoint NFFT and the NFFT).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace anova {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// ===================================================================== A0
+// block-wide reductions over doubles (blockDim.x == kThreads)
+__device__ double block_reduce_min(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : INFINITY;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+__device__ double block_reduce_max(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : -INFINITY;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+// gather the window's columns: xw[i*dA + t] = X[i*ld + feat[t]]
+__global__ void k_extract(const double* __restrict__ X, int64_t N, int64_t ld, int dA, int f0,
+                          int f1, int f2, double* __restrict__ xw) {
+    int feat[3] = {f0, f1, f2};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int t = 0; t < dA; t++) xw[i * dA + t] = X[i * ld + feat[t]];
+}
+
+// per-block min/max per axis over two point sets (a: Na x dA, b: Nb x dA)
+__global__ void k_minmax(const double* __restrict__ a, int64_t Na, const double* __restrict__ b,
+                         int64_t Nb, int dA, double* __restrict__ part) {
+    __shared__ double sh[32];
+    for (int t = 0; t < dA; t++) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Na + Nb;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            double v = (i < Na) ? a[i * dA + t] : b[(i - Na) * dA + t];
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+        lo = block_reduce_min(lo, sh);
+        hi = block_reduce_max(hi, sh);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x * 6 + 2 * t] = lo;
+            part[blockIdx.x * 6 + 2 * t + 1] = hi;
+        }
+    }
+}
+
+// frame[0..2] = centre, frame[3] = scale (filled by k_maxnorm_final)
+__global__ void k_minmax_final(const double* __restrict__ part, int nblk, int dA,
+                               double* __restrict__ frame) {
+    __shared__ double sh[32];
+    for (int t = 0; t < 3; t++) {
+        double lo = INFINITY, hi = -INFINITY;
+        if (t < dA)
+            for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+                lo = fmin(lo, part[i * 6 + 2 * t]);
+                hi = fmax(hi, part[i * 6 + 2 * t + 1]);
+            }
+        lo = block_reduce_min(lo, sh);
+        hi = block_reduce_max(hi, sh);
+        if (threadIdx.x == 0) frame[t] = (t < dA) ? 0.5 * (lo + hi) : 0.0;
+    }
+}
+
+__global__ void k_maxnorm(const double* __restrict__ a, int64_t Na, const double* __restrict__ b,
+                          int64_t Nb, int dA, const double* __restrict__ frame,
+                          double* __restrict__ part) {
+    __shared__ double sh[32];
+    double c0 = frame[0], c1 = frame[1], c2 = frame[2];
+    double best = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Na + Nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double* x = (i < Na) ? a + i * dA : b + (i - Na) * dA;
+        double r2 = 0.0, df;
+        df = x[0] - c0;
+        r2 = df * df;
+        if (dA > 1) { df = x[1] - c1; r2 += df * df; }
+        if (dA > 2) { df = x[2] - c2; r2 += df * df; }
+        best = fmax(best, r2);
+    }
+    best = block_reduce_max(best, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+__global__ void k_maxnorm_final(const double* __restrict__ part, int nblk, double RB,
+                                double* __restrict__ frame) {
+    __shared__ double sh[32];
+    double best = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) best = fmax(best, part[i]);
+    best = block_reduce_max(best, sh);
+    if (threadIdx.x == 0) {
+        double r = sqrt(best);
+        frame[3] = (r > 0.0) ? RB / r : 1.0;
+        frame[4] = r;
+    }
+}
+
+// Frame of one window over one or two coordinate sets (device, n x dA each).
+// frame_host receives centre[3], scale, max radius.
+static anova_status compute_frame(anova_plan* plan, const double* a, int64_t Na, const double* b,
+                                  int64_t Nb, int dA, double* scratch, double* frame_host,
+                                  cudaStream_t st) {
+    const int nblk = grid_for(Na + Nb, kThreads, 2 * std::max(plan->sm_count, 1));
+    double* part = scratch;              // nblk * 6
+    double* frame = scratch + 6 * nblk;  // 5
+    k_minmax<<<nblk, kThreads, 0, st>>>(a, Na, b, Nb, dA, part);
+    k_minmax_final<<<1, kThreads, 0, st>>>(part, nblk, dA, frame);
+    k_maxnorm<<<nblk, kThreads, 0, st>>>(a, Na, b, Nb, dA, frame, part);
+    k_maxnorm_final<<<1, kThreads, 0, st>>>(part, nblk, 0.25 - 0.5 * plan->epsB, frame);
+    ANOVA_CHECK_LAUNCH();
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(frame_host, frame, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    return ANOVA_OK;
+}
+
+// ===================================================================== A1
+// Bins: a node in grid cell c (per axis) belongs to bin c / T.  Blocks of one
+// warp walk fixed chunks of nodes in order, which makes the sort stable.
+constexpr int kBinChunk = 8192;
+
+__device__ __forceinline__ void node_cell(const double* x, int dA, const double* c, double s,
+                                          int nos, int* cell, double* frac) {
+    for (int t = 0; t < dA; t++) {
+        double xt = s * (x[t] - c[t]);           // torus coordinate
+        double y = (double)nos * xt;             // grid units
+        double fl = floor(y);
+        frac[t] = y - fl;
+        int ci = (int)fl + nos / 2;
+        ci %= nos;
+        if (ci < 0) ci += nos;
+        cell[t] = ci;
+    }
+}
+
+__device__ __forceinline__ int bin_of(const int* cell, int dA, int T, int nb) {
+    int bin = 0;
+    for (int t = 0; t < dA; t++) bin = bin * nb + cell[t] / T;
+    return bin;
+}
+
+struct FrameArgs {
+    double c[3];
+    double s;
+};
+
+// per-chunk histograms, bin-major: hist[bin * nchunk + chunk]
+__global__ void k_bin_hist(const double* __restrict__ xw, int64_t N, int dA, FrameArgs fr, int nos,
+                           int T, int nb, int nbins, int nchunk, int32_t* __restrict__ hist) {
+    extern __shared__ int32_t sh_hist[];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) sh_hist[i] = 0;
+    __syncthreads();
+    int64_t lo = (int64_t)blockIdx.x * kBinChunk, hi = min(N, lo + kBinChunk);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        int cell[3];
+        double frac[3];
+        node_cell(xw + i * dA, dA, fr.c, fr.s, nos, cell, frac);
+        atomicAdd(&sh_hist[bin_of(cell, dA, T, nb)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+        hist[(int64_t)i * nchunk + blockIdx.x] = sh_hist[i];
+}
+
+// single-block exclusive scan of L int32 values in place; total -> *total
+__global__ void k_scan_exclusive(int32_t* __restrict__ v, int64_t L, int32_t* __restrict__ total) {
+    __shared__ int32_t sh[1024];
+    const int nt = blockDim.x;
+    int64_t per = (L + nt - 1) / nt;
+    int64_t lo = threadIdx.x * per, hi = min(L, lo + per);
+    int32_t sum = 0;
+    for (int64_t i = lo; i < hi; i++) sum += v[i];
+    sh[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int32_t add = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int32_t run = sh[threadIdx.x] - sum;
+    for (int64_t i = lo; i < hi; i++) {
+        int32_t x = v[i];
+        v[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == nt - 1 && total) *total = sh[nt - 1];
+}
+
+// stable scatter: one warp per chunk, ranks of equal bins via match_any
+template <typename T>
+__global__ void k_bin_scatter(const double* __restrict__ xw, int64_t N, int dA, FrameArgs fr,
+                              int nos, int T_, int nb, int nbins, int nchunk,
+                              const int32_t* __restrict__ off, int32_t* __restrict__ perm,
+                              int32_t* __restrict__ cellout, double* __restrict__ frac64,
+                              float* __restrict__ frac32) {
+    extern __shared__ int32_t cursor[];
+    for (int i = threadIdx.x; i < nbins; i += 32) cursor[i] = off[(int64_t)i * nchunk + blockIdx.x];
+    __syncwarp();
+    int64_t lo = (int64_t)blockIdx.x * kBinChunk, hi = min(N, lo + kBinChunk);
+    const unsigned lane = threadIdx.x;
+    for (int64_t base = lo; base < hi; base += 32) {
+        int64_t i = base + lane;
+        bool valid = i < hi;
+        int cell[3] = {0, 0, 0};
+        double frac[3] = {0, 0, 0};
+        int bin = -1 - (int)lane;  // distinct dummy keys for inactive lanes
+        if (valid) {
+            node_cell(xw + i * dA, dA, fr.c, fr.s, nos, cell, frac);
+            bin = bin_of(cell, dA, T_, nb);
+        }
+        unsigned peers = __match_any_sync(0xffffffffu, bin);
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        int leader = __ffs(peers) - 1;
+        int basepos = 0;
+        if (valid && (int)lane == leader) basepos = cursor[bin];
+        basepos = __shfl_sync(0xffffffffu, basepos, leader);
+        __syncwarp();
+        if (valid && (int)lane == leader) cursor[bin] = basepos + __popc(peers);
+        __syncwarp();
+        if (valid) {
+            int64_t pos = basepos + rank;
+            perm[pos] = (int32_t)i;
+            for (int t = 0; t < dA; t++) {
+                cellout[t * N + pos] = cell[t];
+                if (frac64) frac64[t * N + pos] = frac[t];
+                if (frac32) frac32[t * N + pos] = (float)frac[t];
+            }
+        }
+    }
+}
+
+// bin offsets from the scanned per-chunk histogram: bin_start[b] = off[b * nchunk]
+__global__ void k_bin_starts(const int32_t* __restrict__ off, int nbins, int nchunk, int64_t N,
+                             int32_t* __restrict__ bin_start, int32_t* __restrict__ nchunks_of_bin) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= nbins; b += gridDim.x * blockDim.x) {
+        int32_t s = (b < nbins) ? off[(int64_t)b * nchunk] : (int32_t)N;
+        bin_start[b] = s;
+        if (b < nbins) {
+            int32_t e = (b + 1 < nbins) ? off[(int64_t)(b + 1) * nchunk] : (int32_t)N;
+            nchunks_of_bin[b] = (e - s + kSubChunk - 1) / kSubChunk;
+        }
+    }
+}
+
+__global__ void k_sub_list(const int32_t* __restrict__ bin_start, const int32_t* __restrict__ sub_off,
+                           int nbins, int4* __restrict__ sub) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        int32_t s = bin_start[b], e = bin_start[b + 1];
+        int32_t k = sub_off[b];
+        for (int32_t f = s; f < e; f += kSubChunk) sub[k++] = make_int4(b, f, min(kSubChunk, e - f), 0);
+    }
+}
+
+void free_pointset(PointSet& ps) {
+    cudaFree(ps.perm);
+    cudaFree(ps.cell);
+    cudaFree(ps.frac64);
+    cudaFree(ps.frac32);
+    cudaFree(ps.bin_start);
+    cudaFree(ps.sub);
+    ps = PointSet();
+}
+
+// Bin and sort the nodes of one window.  coords: device N x dA (user units).
+anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
+                            int64_t /*ldc*/, const double* centre, double scale, PointSet& ps,
+                            cudaStream_t st) {
+    free_pointset(ps);
+    ps.N = N;
+    const int dA = w.dA;
+    const bool want64 = (plan->precision & ANOVA_FP64) != 0;
+    const bool want32 = (plan->precision & ANOVA_FP32) != 0;
+    if (N == 0) {
+        ANOVA_CUDA_TRY(cudaMalloc(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t)));
+        ANOVA_CUDA_TRY(cudaMemsetAsync(ps.bin_start, 0, (w.nbins + 1) * sizeof(int32_t), st));
+        return ANOVA_OK;
+    }
+    ANOVA_CUDA_TRY(cudaMalloc(&ps.perm, N * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(cudaMalloc(&ps.cell, N * dA * sizeof(int32_t)));
+    if (want64) ANOVA_CUDA_TRY(cudaMalloc(&ps.frac64, N * dA * sizeof(double)));
+    if (want32) ANOVA_CUDA_TRY(cudaMalloc(&ps.frac32, N * dA * sizeof(float)));
+    ANOVA_CUDA_TRY(cudaMalloc(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t)));
+
+    const int nchunk = (int)((N + kBinChunk - 1) / kBinChunk);
+    const int64_t L = (int64_t)w.nbins * nchunk;
+    int32_t *hist = nullptr, *nch = nullptr, *tot = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&hist, L * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(cudaMalloc(&nch, (w.nbins + 1) * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(cudaMalloc(&tot, 2 * sizeof(int32_t)));
+    FrameArgs fr;
+    for (int t = 0; t < 3; t++) fr.c[t] = centre[t];
+    fr.s = scale;
+    const size_t shb = w.nbins * sizeof(int32_t);
+    k_bin_hist<<<nchunk, kThreads, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk, hist);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(hist, L, tot);
+    k_bin_scatter<double><<<nchunk, 32, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk,
+                                                  hist, ps.perm, ps.cell, ps.frac64, ps.frac32);
+    k_bin_starts<<<grid_for(w.nbins + 1, kThreads, 1024), kThreads, 0, st>>>(hist, w.nbins, nchunk, N,
+                                                                              ps.bin_start, nch);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(nch, w.nbins, tot + 1);
+    ANOVA_CHECK_LAUNCH();
+    int32_t totals[2] = {0, 0};
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(totals, tot, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    ps.nsub = totals[1];
+    if (totals[0] != N) {
+        set_error("binning lost nodes");
+        return ANOVA_ECUDA;
+    }
+    ANOVA_CUDA_TRY(cudaMalloc(&ps.sub, std::max(ps.nsub, 1) * sizeof(int4)));
+    k_sub_list<<<grid_for(w.nbins, kThreads, 1024), kThreads, 0, st>>>(ps.bin_start, nch, w.nbins, ps.sub);
+    ANOVA_CHECK_LAUNCH();
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(hist);
+    cudaFree(nch);
+    cudaFree(tot);
+    return ANOVA_OK;
+}
+
+// ===================================================================== A2
+// Regularised kernel K_R(r) (Sec. 4.2): Gaussian for r <= a = 1/2 - eps_B,
+// two-point Taylor polynomial of degree 2p-1 on (a, 1/2] ending at the
+// constant c = K(1/2) with vanishing derivatives, c beyond 1/2.
+__device__ double gauss_dj(int j, double r, double ell) {
+    // d^j/dr^j exp(-(r/ell)^2) = (-1/ell)^j H_j(r/ell) exp(-(r/ell)^2)
+    double x = r / ell;
+    double h0 = 1.0, h1 = 2.0 * x, hj = (j == 0) ? h0 : h1;
+    for (int i = 1; i < j; i++) {
+        double h2 = 2.0 * x * h1 - 2.0 * i * h0;
+        h0 = h1;
+        h1 = h2;
+        hj = h2;
+    }
+    double sc = 1.0;
+    for (int i = 0; i < j; i++) sc *= -1.0 / ell;
+    return sc * hj * exp(-x * x);
+}
+
+__device__ double kreg_dev(double r, double ell, double epsB, int p) {
+    const double a = 0.5 - epsB, e = 0.5;
+    const double c = exp(-0.25 / (ell * ell));
+    if (r <= a) return exp(-(r * r) / (ell * ell));
+    if (r > e) return c;
+    // Hermite basis on [a, e] with u = (r-a)/(e-a), v = 1-u:
+    //   P(r) = sum_j [f^(j)(a) (r-a)^j/j! v^p S_j(u) + f^(j)(e) (r-e)^j/j! u^p S_j(v)],
+    //   S_j(z) = sum_{q=0}^{p-1-j} binom(p-1+q, q) z^q.
+    const double L = e - a, u = (r - a) / L, v = (e - r) / L;
+    double up = 1.0, vp = 1.0;
+    for (int i = 0; i < p; i++) { up *= u; vp *= v; }
+    double res = 0.0, jfact = 1.0, dra = 1.0;
+    for (int j = 0; j < p; j++) {
+        if (j > 0) { jfact *= j; dra *= (r - a); }
+        double S = 0.0, zq = 1.0, bq = 1.0;  // bq = binom(p-1+q, q)
+        for (int q = 0; q <= p - 1 - j; q++) {
+            S += bq * zq;
+            zq *= u;
+            bq = bq * (double)(p + q) / (double)(q + 1);
+        }
+        res += gauss_dj(j, a, ell) * dra / jfact * vp * S;
+    }
+    // the end point carries only the value c (its derivatives vanish)
+    double S0 = 0.0, zq = 1.0, bq = 1.0;
+    for (int q = 0; q <= p - 1; q++) {
+        S0 += bq * zq;
+        zq *= v;
+        bq = bq * (double)(p + q) / (double)(q + 1);
+    }
+    res += c * up * S0;
+    return res;
+}
+
+// f[idx] = K_R(||j|| / n), j in I_n^dA (centred index, last axis fastest)
+__global__ void k_sample_kreg(int dA, int n, double ell, double epsB, int p, double* __restrict__ f) {
+    int64_t tot = 1;
+    for (int t = 0; t < dA; t++) tot *= n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = idx;
+        double r2 = 0.0;
+        for (int t = 0; t < dA; t++) {
+            int j = (int)(rem % n) - n / 2;
+            rem /= n;
+            double v = (double)j / (double)n;
+            r2 += v * v;
+        }
+        f[idx] = kreg_dev(sqrt(r2), ell, epsB, p);
+    }
+}
+
+// One axis of the real cosine DFT of an even array (shape outer x n x inner):
+//   out[k] = sum_j in[j] cos(2 pi k j / n)   (the sine part cancels by symmetry)
+__global__ void k_cos_dft_axis(const double* __restrict__ in, double* __restrict__ out, int64_t outer,
+                               int n, int64_t inner) {
+    int64_t tot = outer * n * inner;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = idx % inner;
+        int64_t o = (idx / inner) % n;
+        int64_t o0 = idx / (inner * n);
+        int k = (int)o - n / 2;
+        double acc = 0.0;
+        for (int i = 0; i < n; i++) {
+            int j = i - n / 2;
+            int r = (k * j) % n;
+            if (r < 0) r += n;
+            acc += in[(o0 * n + i) * inner + s] * cospi(2.0 * (double)r / (double)n);
+        }
+        out[idx] = acc;
+    }
+}
+
+// D_k = b_k / prod_t psihat(k_t)^2, psihat = I0(m sqrt(b^2 - (2 pi k/nos)^2)) / phi(0),
+// phi(0) = sinh(b m) / (pi m): the transform of the window normalised to psi(0) = 1.
+__global__ void k_deconvolve(const double* __restrict__ f, int dA, int n, int nos, int m, double b,
+                             double* __restrict__ D64, float* __restrict__ D32) {
+    int64_t tot = 1;
+    for (int t = 0; t < dA; t++) tot *= n;
+    const double phi0 = sinh(b * m) / (M_PI * m);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = idx;
+        double den = 1.0;
+        for (int t = 0; t < dA; t++) {
+            int k = (int)(rem % n) - n / 2;
+            rem /= n;
+            double w = 2.0 * M_PI * (double)k / (double)nos;
+            double ph = cyl_bessel_i0((double)m * sqrt(b * b - w * w)) / phi0;
+            den *= ph * ph;
+        }
+        double v = f[idx] / (double)tot / den;
+        if (D64) D64[idx] = v;
+        if (D32) D32[idx] = (float)v;
+    }
+}
+
+// exp(-2 pi i r / nos)
+__global__ void k_twiddles(int nos, double2* __restrict__ tw64, float2* __restrict__ tw32) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nos; r += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)r / (double)nos, &s, &c);
+        if (tw64) tw64[r] = make_double2(c, -s);
+        if (tw32) tw32[r] = make_float2((float)c, (float)-s);
+    }
+}
+
+// ================================================================ set-up
+static void choose_bins(WindowPlan& w, int m) {
+    int T = (w.dA == 3) ? 4 : (w.dA == 2) ? 16 : 64;
+    T = std::min(T, w.nos);
+    auto nbins_of = [&](int t) {
+        int nb = (w.nos + t - 1) / t, nbins = 1;
+        for (int i = 0; i < w.dA; i++) nbins *= nb;
+        return nbins;
+    };
+    while (nbins_of(T) > 8192 && T < w.nos) T++;
+    auto region_bytes = [&](int t) {
+        int64_t r = t + 2 * m, v = 1;
+        for (int i = 0; i < w.dA; i++) v *= r;
+        return v * (int64_t)sizeof(double);
+    };
+    while (T > 1 && region_bytes(T) > 160 * 1024) T--;
+    w.T = T;
+    w.nb = (w.nos + T - 1) / T;
+    w.nbins = nbins_of(T);
+    w.R = T + 2 * m;
+}
+
+// Frame-dependent part of a window: scaled width, multiplier D_k, binned nodes.
+static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* frame,
+                                 double* scratch, cudaStream_t st) {
+    for (int t = 0; t < 3; t++) w.centre[t] = frame[t];
+    w.scale = frame[3];
+    w.ell_l = w.scale * plan->ell;
+    int64_t tk = 1;
+    for (int t = 0; t < w.dA; t++) tk *= w.n;
+    const bool want64 = (plan->precision & ANOVA_FP64) != 0;
+    const bool want32 = (plan->precision & ANOVA_FP32) != 0;
+    if (!w.D64) ANOVA_CUDA_TRY(cudaMalloc(&w.D64, tk * sizeof(double)));
+    if (want32 && !w.D32) ANOVA_CUDA_TRY(cudaMalloc(&w.D32, tk * sizeof(float)));
+    double* fa = scratch;
+    double* fb = scratch + tk;
+    const int g = grid_for(tk, kThreads, 4096);
+    k_sample_kreg<<<g, kThreads, 0, st>>>(w.dA, w.n, w.ell_l, plan->epsB, plan->p, fa);
+    for (int t = 0; t < w.dA; t++) {
+        int64_t outer = 1, inner = 1;
+        for (int i = 0; i < t; i++) outer *= w.n;
+        for (int i = t + 1; i < w.dA; i++) inner *= w.n;
+        k_cos_dft_axis<<<g, kThreads, 0, st>>>(fa, fb, outer, w.n, inner);
+        std::swap(fa, fb);
+    }
+    k_deconvolve<<<g, kThreads, 0, st>>>(fa, w.dA, w.n, w.nos, plan->m, plan->b, w.D64,
+                                         want32 ? w.D32 : nullptr);
+    ANOVA_CHECK_LAUNCH();
+    (void)want64;
+    return build_pointset(plan, w, w.xw, plan->N, w.dA, w.centre, w.scale, w.X, st);
+}
+
+static anova_status validate(int64_t N, int32_t d, int64_t ld, const int32_t* windows, int32_t P,
+                             const double* weights, double ell, const int32_t* n, int32_t m,
+                             double sigma, double eps_B, int32_t p, int32_t precision) {
+    auto bad = [](const std::string& s) {
+        set_error(s);
+        return ANOVA_EINVAL;
+    };
+    if (N < 0 || N > INT32_MAX) return bad("N must be in [0, 2^31)");
+    if (d < 1 || ld < d) return bad("need d >= 1 and ld >= d");
+    if (!windows || P < 1 || P > kMaxWindows) return bad("need 1 <= P <= 256 windows");
+    for (int l = 0; l < P; l++) {
+        int dA = 0;
+        while (dA < 3 && windows[3 * l + dA] >= 0) dA++;
+        if (dA == 0) return bad("empty window " + std::to_string(l));
+        for (int t = dA; t < 3; t++)
+            if (windows[3 * l + t] != -1) return bad("window padding must be -1 at the end");
+        for (int t = 0; t < dA; t++) {
+            if (windows[3 * l + t] >= d) return bad("feature index out of range in window " + std::to_string(l));
+            for (int u = 0; u < t; u++)
+                if (windows[3 * l + t] == windows[3 * l + u]) return bad("repeated feature in a window");
+        }
+        if (weights && !std::isfinite(weights[l])) return bad("non-finite weight");
+        int nl = n ? n[l] : 32;
+        if (nl < 4 || (nl & 1)) return bad("n must be even and >= 4");
+        double nosd = sigma * nl;
+        int nos = (int)std::lround(nosd);
+        if (std::fabs(nosd - nos) > 1e-9 || (nos & 1)) return bad("sigma*n must be an even integer");
+        if (2 * m + 2 > nos) return bad("need 2m+2 <= sigma*n");
+        int64_t big = 1;
+        for (int t = 0; t < dA; t++) big *= nos;
+        if (big > (int64_t)1 << 24) return bad("grid (sigma*n)^dims above 2^24 cells");
+    }
+    if (!(ell > 0.0) || !std::isfinite(ell)) return bad("ell must be positive and finite");
+    if (m < 1 || m > kMaxM) return bad("m must be in [1, 12]");
+    if (!(sigma >= 1.0) || sigma > 8.0) return bad("sigma must be in [1, 8]");
+    if (!(eps_B > 0.0 && eps_B < 0.5)) return bad("eps_B must be in (0, 1/2)");
+    if (p < 1 || p > 16) return bad("p must be in [1, 16]");
+    if (precision < 1 || precision > 3) return bad("precision must be ANOVA_FP64, ANOVA_FP32 or ANOVA_MIXED");
+    return ANOVA_OK;
+}
+
+static anova_status plan_build(const double* points, int64_t N, int32_t d, int64_t ld,
+                               const int32_t* windows, int32_t P, const double* weights, double ell,
+                               const int32_t* n, int32_t m, double sigma, double eps_B, int32_t p,
+                               int32_t precision, cudaStream_t st, anova_plan* plan) {
+    int dev = 0;
+    ANOVA_CUDA_TRY(cudaGetDevice(&dev));
+    ANOVA_CUDA_TRY(cudaDeviceGetAttribute(&plan->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    plan->N = N;
+    plan->d = d;
+    plan->P = P;
+    plan->m = m;
+    plan->p = p;
+    plan->precision = precision;
+    plan->sigma = sigma;
+    plan->epsB = eps_B;
+    plan->ell = ell;
+    plan->b = M_PI * (2.0 - 1.0 / sigma);
+    plan->psi_norm = (double)m / std::sinh(plan->b * m);
+    plan->win.resize(P);
+    size_t max_tk = 1;
+    for (int l = 0; l < P; l++) {
+        WindowPlan& w = plan->win[l];
+        w.dA = 0;
+        while (w.dA < 3 && windows[3 * l + w.dA] >= 0) {
+            w.feat[w.dA] = windows[3 * l + w.dA];
+            w.dA++;
+        }
+        w.n = n ? n[l] : 32;
+        w.nos = (int)std::lround(sigma * w.n);
+        w.eta = weights ? weights[l] : 1.0 / P;
+        choose_bins(w, m);
+        if (w.nbins > 8192) {
+            set_error("window " + std::to_string(l) + ": grid too fine for the binning (reduce n or m)");
+            return ANOVA_EINVAL;
+        }
+        size_t ge = 1, we = w.n, tk = 1;
+        for (int t = 0; t < w.dA; t++) { ge *= w.nos; tk *= w.n; }
+        for (int t = 1; t < w.dA; t++) we *= w.nos;
+        plan->grid_elems = std::max(plan->grid_elems, ge);
+        plan->work_elems = std::max(plan->work_elems, we);
+        max_tk = std::max(max_tk, tk);
+        ANOVA_CUDA_TRY(cudaMalloc(&w.tw64, w.nos * sizeof(double2)));
+        ANOVA_CUDA_TRY(cudaMalloc(&w.tw32, w.nos * sizeof(float2)));
+        k_twiddles<<<grid_for(w.nos, kThreads, 64), kThreads, 0, st>>>(w.nos, w.tw64, w.tw32);
+        ANOVA_CHECK_LAUNCH();
+        if (N > 0) {
+            ANOVA_CUDA_TRY(cudaMalloc(&w.xw, N * w.dA * sizeof(double)));
+            k_extract<<<grid_for(N, kThreads, 4 * plan->sm_count), kThreads, 0, st>>>(
+                points, N, ld, w.dA, w.feat[0], w.feat[1], w.feat[2], w.xw);
+            ANOVA_CHECK_LAUNCH();
+        }
+    }
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->grid, plan->grid_elems * sizeof(double)));
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->work1, plan->work_elems * sizeof(double2)));
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->work2, plan->work_elems * sizeof(double2)));
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->tmp, std::max<int64_t>(N, 1) * P * sizeof(double)));
+    {
+        std::vector<double> eta(P);
+        for (int l = 0; l < P; l++) eta[l] = plan->win[l].eta;
+        ANOVA_CUDA_TRY(cudaMalloc(&plan->eta_dev, P * sizeof(double)));
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->eta_dev, eta.data(), P * sizeof(double),
+                                       cudaMemcpyHostToDevice, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // scratch for frames and D_k set-up
+    const int nblk = grid_for(std::max<int64_t>(N, 1), kThreads, 2 * plan->sm_count);
+    size_t scratch_elems = std::max<size_t>(6 * nblk + 8, 2 * max_tk);
+    double* scratch = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&scratch, scratch_elems * sizeof(double)));
+    anova_status s = ANOVA_OK;
+    for (int l = 0; l < P && s == ANOVA_OK; l++) {
+        WindowPlan& w = plan->win[l];
+        double frame[5] = {0, 0, 0, 1.0, 0};
+        if (N > 0) s = compute_frame(plan, w.xw, N, nullptr, 0, w.dA, scratch, frame, st);
+        if (s == ANOVA_OK) s = window_setup(plan, w, frame, scratch, st);
+    }
+    if (s == ANOVA_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error(std::string("plan: ") + cudaGetErrorString(e));
+            s = ANOVA_ECUDA;
+        }
+    }
+    cudaFree(scratch);
+    return s;
+}
+
+// Rebuild window l of `dst` (a copy of the plan's window) in the frame spanned by
+// the training nodes and the extra coordinates zw (M x dA), for predictions
+// outside the plan's ball.
+anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M, WindowPlan& dst,
+                            cudaStream_t st) {
+    const WindowPlan& src = plan->win[l];
+    dst = WindowPlan();
+    dst.dA = src.dA;
+    for (int t = 0; t < 3; t++) dst.feat[t] = src.feat[t];
+    dst.n = src.n;
+    dst.nos = src.nos;
+    dst.T = src.T;
+    dst.nb = src.nb;
+    dst.R = src.R;
+    dst.nbins = src.nbins;
+    dst.eta = src.eta;
+    dst.tw64 = src.tw64;   // borrowed
+    dst.tw32 = src.tw32;   // borrowed
+    dst.xw = src.xw;       // borrowed
+    int64_t tk = 1;
+    for (int t = 0; t < src.dA; t++) tk *= src.n;
+    const int nblk = grid_for(plan->N + M, kThreads, 2 * plan->sm_count);
+    double* scratch = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&scratch, std::max<size_t>(6 * nblk + 8, 2 * tk) * sizeof(double)));
+    double frame[5];
+    anova_status s = compute_frame(plan, src.xw, plan->N, zw, M, src.dA, scratch, frame, st);
+    if (s == ANOVA_OK) s = window_setup(plan, dst, frame, scratch, st);
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    return s;
+}
+
+void window_release_reframed(WindowPlan& w) {
+    cudaFree(w.D64);
+    cudaFree(w.D32);
+    free_pointset(w.X);
+    w = WindowPlan();
+}
+
+// max ||z - centre|| over M coordinates (device M x dA)
+anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, const double* centre,
+                        double* rmax_host, cudaStream_t st) {
+    *rmax_host = 0.0;
+    if (M == 0) return ANOVA_OK;
+    const int nblk = grid_for(M, kThreads, 2 * plan->sm_count);
+    double* scratch = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&scratch, (nblk + 8) * sizeof(double)));
+    double* frame = scratch + nblk;
+    double hf[5] = {centre[0], centre[1], centre[2], 1.0, 0.0};
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(frame, hf, 5 * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_maxnorm<<<nblk, kThreads, 0, st>>>(zw, M, nullptr, 0, dA, frame, scratch);
+    k_maxnorm_final<<<1, kThreads, 0, st>>>(scratch, nblk, 1.0, frame);
+    ANOVA_CHECK_LAUNCH();
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(hf, frame, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(scratch);
+    *rmax_host = hf[4];
+    return ANOVA_OK;
+}
+
+// copy the window's feature columns of Z into zw (M x dA)
+anova_status extract_window(anova_plan* plan, const double* Z, int64_t M, int64_t ldz, const WindowPlan& w,
+                            double* zw, cudaStream_t st) {
+    if (M == 0) return ANOVA_OK;
+    k_extract<<<grid_for(M, kThreads, 4 * plan->sm_count), kThreads, 0, st>>>(
+        Z, M, ldz, w.dA, w.feat[0], w.feat[1], w.feat[2], zw);
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+}  // namespace anova
+
+using namespace anova;
+
+extern "C" {
+
+anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int64_t ld,
+                                const int32_t* windows, int32_t P, const double* weights,
+                                double ell, const int32_t* n, int32_t m, double sigma,
+                                double eps_B, int32_t p, int32_t precision, void* stream,
+                                anova_plan** out) {
+    set_error("");
+    if (!out) {
+        set_error("out is NULL");
+        return ANOVA_EINVAL;
+    }
+    *out = nullptr;
+    if (N > 0 && !points) {
+        set_error("points is NULL");
+        return ANOVA_EINVAL;
+    }
+    ANOVA_TRY(validate(N, d, ld, windows, P, weights, ell, n, m, sigma, eps_B, p, precision));
+    anova_plan* plan = new (std::nothrow) anova_plan();
+    if (!plan) return ANOVA_ENOMEM;
+    anova_status s = plan_build(points, N, d, ld, windows, P, weights, ell, n, m, sigma, eps_B, p,
+                                precision, (cudaStream_t)stream, plan);
+    if (s != ANOVA_OK) {
+        cudaGetLastError();
+        anova_plan_destroy(plan);
+        return s;
+    }
+    *out = plan;
+    return ANOVA_OK;
+}
+
+void anova_plan_destroy(anova_plan* plan) {
+    if (!plan) return;
+    for (auto& w : plan->win) {
+        cudaFree(w.D64);
+        cudaFree(w.D32);
+        cudaFree(w.tw64);
+        cudaFree(w.tw32);
+        cudaFree(w.xw);
+        free_pointset(w.X);
+    }
+    cudaFree(plan->grid);
+    cudaFree(plan->work1);
+    cudaFree(plan->work2);
+    cudaFree(plan->tmp);
+    cudaFree(plan->eta_dev);
+    cudaFree(plan->cg_vec);
+    cudaFree(plan->cg_scal);
+    cudaFree(plan->cg_part);
+    for (auto e : plan->clock.ev) cudaEventDestroy(e);
+    delete plan;
+}
+
+const char* anova_status_string(anova_status s) {
+    switch (s) {
+        case ANOVA_OK: return "ANOVA_OK: success";
+        case ANOVA_EINVAL: return "ANOVA_EINVAL: invalid argument";
+        case ANOVA_ENOMEM: return "ANOVA_ENOMEM: device allocation failed";
+        case ANOVA_ECUDA: return "ANOVA_ECUDA: CUDA call failed";
+        case ANOVA_ENOCONV: return "ANOVA_ENOCONV: CG reached maxit";
+        case ANOVA_ERANGE: return "ANOVA_ERANGE: input out of range";
+        case ANOVA_ETIMEOUT: return "ANOVA_ETIMEOUT: device wait expired";
+    }
+    return "unknown anova_status";
+}
+
+const char* anova_last_error(void) { return g_last_error.c_str(); }
+
+anova_status anova_plan_window(const anova_plan* plan, int32_t l, double* centre, double* scale,
+                               double* ell_l, int32_t* dims, int32_t* n, int32_t* nos) {
+    if (!plan || l < 0 || l >= plan->P) {
+        set_error("bad plan or window index");
+        return ANOVA_EINVAL;
+    }
+    const WindowPlan& w = plan->win[l];
+    if (centre) for (int t = 0; t < 3; t++) centre[t] = w.centre[t];
+    if (scale) *scale = w.scale;
+    if (ell_l) *ell_l = w.ell_l;
+    if (dims) *dims = w.dA;
+    if (n) *n = w.n;
+    if (nos) *nos = w.nos;
+    return ANOVA_OK;
+}
+
+anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host) {
+    if (!plan || l < 0 || l >= plan->P || !D_host) {
+        set_error("bad plan, window index or output");
+        return ANOVA_EINVAL;
+    }
+    const WindowPlan& w = plan->win[l];
+    int64_t tk = 1;
+    for (int t = 0; t < w.dA; t++) tk *= w.n;
+    ANOVA_CUDA_TRY(cudaMemcpy(D_host, w.D64, tk * sizeof(double), cudaMemcpyDeviceToHost));
+    return ANOVA_OK;
+}
+
+}  // extern "C"

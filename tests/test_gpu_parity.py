@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative 2-norm): FP64 path vs the same-parameter oracle fast
+summation 1e-12, FP32 path 1e-5; fast summation vs the direct sum 1e-5 where
+the parameters reach it.  The GPU window is the Kaiser-Bessel window scaled to
+psi(0) = 1, so its spread grid equals the oracle's divided by phi(0)^dims and
+its multiplier D_k the oracle's times phi(0)^(2 dims).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_10140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+B_KB = oracle.kb_b(2.0)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_10140_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def phi0(m):
+    return math.sinh(B_KB * m) / (math.pi * m)
+
+
+def make_plan(B, torch, w, precision):
+    X = torch.from_numpy(w.X).cuda()
+    return B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                precision=precision)
+
+
+def oracle_fast(w, Z=None, alpha=None):
+    return oracle.fastsum(Z, w.X, w.windows, w.eta, w.ell, w.n, w.m, w.alpha if alpha is None else alpha,
+                          sigma=w.sigma, epsB=w.epsB, p=w.p)
+
+
+CASES = {
+    "tiny_2d": lambda: W.plain_tiny(N=2000),
+    "small_3d": lambda: W.random_problem(3000, 6, [(0, 1, 2), (3, 4, 5)], 0.2, 16, 4, seed=21),
+    "mixed_dims_ragged": lambda: W.random_problem(2777, 7, [(0, 1, 2), (3, 4), (5,), (6,)], 0.25,
+                                                  [16, 32, 64, 32], 5, seed=22),
+    "overlapping": lambda: W.random_problem(1500, 4, [(0, 1, 2), (1, 2), (2, 3)], 0.3, 16, 3, seed=23),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_frame_and_multiplier_match_oracle(B, torch, case):
+    w = CASES[case]()
+    plan = make_plan(B, torch, w, B.FP64)
+    for l, win in enumerate(w.windows):
+        info = B.anova_plan_window(plan, l)
+        c, s = oracle.window_frame(w.X, win, 0.25 - w.epsB / 2)
+        np.testing.assert_allclose(info["centre"], c, rtol=0, atol=1e-15)
+        assert info["scale"] == pytest.approx(s, rel=1e-14)
+        dA, n, nos = len(win), w.n[l], 2 * w.n[l]
+        re, _ = oracle.kernel_coeffs(dA, n, s * w.ell, w.epsB, w.p)
+        D = oracle.diag(dA, n, nos, w.m, B_KB, re)
+        Dg = B.anova_debug_diag(plan, l) / phi0(w.m) ** (2 * dA)
+        assert rel(Dg, D) <= 1e-12
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_spread_grid_matches_oracle(B, torch, case):
+    w = CASES[case]()
+    plan = make_plan(B, torch, w, B.MIXED)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    for l, win in enumerate(w.windows):
+        c, s = oracle.window_frame(w.X, win, 0.25 - w.epsB / 2)
+        xt = s * (w.X[:, list(win)] - c)
+        dA, nos = len(win), 2 * w.n[l]
+        g_or = oracle.spread(xt, nos, w.m, B_KB, w.alpha) / phi0(w.m) ** dA
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            grid = torch.zeros((nos,) * dA, dtype=dt, device="cuda")
+            B.anova_debug_spread(plan, l, a64.to(dt), grid)
+            assert rel(grid.double().cpu().numpy(), g_or) <= tol, (l, dt)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_matvec_matches_oracle_fastsum(B, torch, case):
+    w = CASES[case]()
+    plan = make_plan(B, torch, w, B.MIXED)
+    ref = oracle_fast(w)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    out64 = torch.empty_like(a64)
+    B.anova_matvec(plan, a64, out64)
+    assert rel(out64.cpu().numpy(), ref) <= 1e-12
+    a32 = a64.float()
+    out32 = torch.empty_like(a32)
+    B.anova_matvec(plan, a32, out32)
+    assert rel(out32.cpu().numpy(), ref) <= 1e-5
+
+
+def test_matvec_matches_direct_sum(B, torch):
+    w = W.plain_tiny(N=2000)
+    plan = make_plan(B, torch, w, B.FP32)
+    direct = oracle.direct(w.X, w.X, w.windows, w.eta, w.ell, w.alpha)
+    a = torch.from_numpy(w.alpha).float().cuda()
+    out = torch.empty_like(a)
+    B.anova_matvec(plan, a, out)
+    assert rel(out.cpu().numpy(), direct) <= 1e-5
+
+
+def test_multiple_rhs_and_weights(B, torch):
+    w = W.random_problem(1200, 5, [(0, 1, 2), (3, 4)], 0.2, 16, 4, seed=31)
+    eta = np.array([0.3, 1.7])
+    X = torch.from_numpy(w.X).cuda()
+    plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, weights=eta, precision=B.FP64)
+    A = np.random.default_rng(2).standard_normal((3, w.N))
+    out = torch.empty((3, w.N), dtype=torch.float64, device="cuda")
+    B.anova_matvec(plan, torch.from_numpy(A).cuda(), out)
+    for r in range(3):
+        ref = oracle.fastsum(None, w.X, w.windows, eta, w.ell, w.n, w.m, A[r], epsB=w.epsB, p=w.p)
+        assert rel(out[r].cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 2, 31, 1025])
+def test_small_and_ragged_sizes(B, torch, N):
+    w = W.random_problem(N, 3, [(0, 1, 2)], 0.2, 8, 2, seed=N)
+    plan = make_plan(B, torch, w, B.FP64)
+    ref = oracle_fast(w)
+    a = torch.from_numpy(w.alpha).cuda()
+    out = torch.empty_like(a)
+    B.anova_matvec(plan, a, out)
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+
+
+def test_identical_points_degenerate_frame(B, torch):
+    """All nodes equal: the frame has radius 0 (scale 1) and K is the all-ones matrix."""
+    X = np.tile(np.array([[0.1, -0.2, 0.3]]), (50, 1))
+    alpha = np.random.default_rng(0).standard_normal(50)
+    plan = B.anova_fastsum_plan(torch.from_numpy(X).cuda(), [(0, 1, 2)], 0.2, n=16, m=4, precision=B.FP64)
+    out = torch.empty(50, dtype=torch.float64, device="cuda")
+    B.anova_matvec(plan, torch.from_numpy(alpha).cuda(), out)
+    ref = oracle.fastsum(None, X, [(0, 1, 2)], [1.0], 0.2, [16], 4, alpha)
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+    assert rel(out.cpu().numpy(), np.full(50, alpha.sum())) <= 1e-6
+
+
+def test_empty_problem(B, torch):
+    X = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    plan = B.anova_fastsum_plan(X, [(0, 1, 2)], 0.2, n=16, m=4, precision=B.MIXED)
+    a = torch.zeros(0, dtype=torch.float64, device="cuda")
+    out = torch.zeros(0, dtype=torch.float64, device="cuda")
+    B.anova_matvec(plan, a, out)
+    st, its, relres = B.krr_cg_solve(plan, 1e-2, a, out, 1e-8, 10)
+    assert st == B.OK and its[0] == 0
+
+
+def test_cg_matches_oracle_and_dense_solve(B, torch):
+    w = W.random_problem(400, 4, [(0, 1), (2, 3)], 0.15, 32, 4, seed=41)
+    lam = 1e-2
+    plan = make_plan(B, torch, w, B.FP64)
+    y = torch.from_numpy(w.y).cuda()
+    alpha = torch.zeros_like(y)
+    st, its, relres = B.krr_cg_solve(plan, lam, y, alpha, 1e-10, 1000)
+    assert st == B.OK and relres[0] <= 1e-10
+    a_or, it_or, rel_or = oracle.cg(w.X, w.windows, w.eta, w.ell, w.n, w.m, lam, w.y, 1e-10, 1000,
+                                    epsB=w.epsB, p=w.p)
+    assert abs(its[0] - it_or) <= 2
+    assert rel(alpha.cpu().numpy(), a_or) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["FP32", "MIXED"])
+def test_cg_reduced_precision_reaches_tolerance(B, torch, precision):
+    w = W.plain_tiny(N=2000)
+    plan = make_plan(B, torch, w, getattr(B, precision))
+    y = torch.from_numpy(w.y).cuda()
+    alpha = torch.zeros_like(y)
+    tol = 1e-8 if precision == "MIXED" else 1e-5
+    st, its, relres = B.krr_cg_solve(plan, w.lam, y, alpha, tol, 2000)
+    assert st == B.OK and relres[0] <= tol
+    # the FP64 oracle operator agrees that alpha solves the system
+    q = oracle_fast(w, alpha=alpha.cpu().numpy()) + w.lam * alpha.cpu().numpy()
+    assert rel(q, w.y) <= (2e-8 if precision == "MIXED" else 1e-4)
+
+
+@pytest.mark.parametrize("scale_z", [0.5, 1.7])
+def test_predict_matches_oracle(B, torch, scale_z):
+    w = W.random_problem(1500, 5, [(0, 1, 2), (3, 4)], 0.2, 16, 4, seed=51)
+    Z = W.random_problem(333, 5, [(0, 1, 2), (3, 4)], 0.2, 16, 4, seed=52).X * scale_z
+    plan = make_plan(B, torch, w, B.FP64)
+    out = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
+    B.krr_predict(plan, torch.from_numpy(w.alpha).cuda(), torch.from_numpy(Z).cuda(), out)
+    ref = oracle_fast(w, Z=Z)
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+    direct = oracle.direct(Z, w.X, w.windows, w.eta, w.ell, w.alpha)
+    assert rel(out.cpu().numpy(), direct) <= 1e-4
+
+
+def test_repeat_runs_agree(B, torch):
+    w = W.random_problem(5000, 3, [(0, 1, 2)], 0.2, 32, 6, seed=61)
+    plan = make_plan(B, torch, w, B.MIXED)
+    for dt, tol in ((torch.float64, 1e-14), (torch.float32, 1e-6)):
+        a = torch.from_numpy(w.alpha).to(dt).cuda()
+        o1, o2 = torch.empty_like(a), torch.empty_like(a)
+        B.anova_matvec(plan, a, o1)
+        B.anova_matvec(plan, a, o2)
+        assert rel(o1.cpu().numpy(), o2.cpu().numpy()) <= tol
+
+
+@pytest.mark.slow
+def test_full_mid_workload_parity(B, torch):
+    """N = 1e5, three 3-D windows (n = 32, m = 6): every output against the oracle."""
+    w = W.plain_mid()
+    plan = make_plan(B, torch, w, B.MIXED)
+    ref = oracle_fast(w)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    out = torch.empty_like(a64)
+    B.anova_matvec(plan, a64, out)
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+    a32 = a64.float()
+    out32 = torch.empty_like(a32)
+    B.anova_matvec(plan, a32, out32)
+    assert rel(out32.cpu().numpy(), ref) <= 1e-5
+    idx = np.random.default_rng(7).choice(w.N, 500, replace=False)
+    direct = oracle.direct(w.X[idx], w.X, w.windows, w.eta, w.ell, w.alpha)
+    assert rel(out32.cpu().numpy()[idx], direct) <= 1e-5
