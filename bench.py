@@ -1,0 +1,308 @@
+"""Benchmark: ANOVA fast-summation matvec throughput (Gpts/s) on the mid
+workload (N = 1e5, d = 9, three 3-D windows, n = 32, m = 6, sigma = 2), plus
+KRR CG solves/s and p50/p99 step latency.
+
+A step is one full ANOVA matvec K alpha (all windows: spread, FFT, multiply,
+inverse FFT, gather, weighted window sum) in FP32 through the C ABI, inputs
+resident in HBM.  L2 is flushed before every step (256 MB write outside the
+per-step events).  With --gpus N (torchrun) every rank runs an independent
+replica (the path has no exchange step); value = points of all ranks / max
+time over ranks.
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method used for parity) on the same workload on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ANOVA fastsum matvec Gpts/s & KRR solves/s at rel err 1e-5; p50/p99 latency"
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+
+
+def fp32_peak_tflops():
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args):
+    """Time the FP64 CPU oracle's fast summation on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2111_10140_gb300 import workloads as W
+    oracle.build()
+    w = W.plain_mid()
+    ns = args.ref_sample
+    Xs, alpha = w.X[:ns], w.alpha[:ns]
+    cores = len(os.sched_getaffinity(0))
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.fastsum(None, Xs, w.windows, w.eta, w.ell, w.n, w.m, alpha, sigma=w.sigma, epsB=w.epsB, p=w.p)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = ns / t / 1e9
+    sample = f"oracle fast summation on the first {ns} of {w.N} points (same windows, n, m, sigma, eps_B)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "windows": "3x3D", "n": 32, "m": 6, "sigma": 2.0,
+                       "eps_B": w.epsB, "ell": w.ell},
+            "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(ns):
+    """One timed oracle fast summation on a bounded sample (about 10-30 s of CPU work)."""
+    import oracle
+    from paper_2111_10140_gb300 import workloads as W
+    oracle.build()
+    w = W.plain_mid()
+    t0 = time.perf_counter()
+    oracle.fastsum(None, w.X[:ns], w.windows, w.eta, w.ell, w.n, w.m, w.alpha[:ns], sigma=w.sigma,
+                   epsB=w.epsB, p=w.p)
+    t = time.perf_counter() - t0
+    return {"value": ns / t / 1e9, "unit": "Gpts/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"one oracle fast summation (FP64, OpenMP) on the first {ns} of {w.N} points, "
+                      f"same windows/n/m/sigma/eps_B; {t:.2f} s"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    from paper_2111_10140_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(B.lib_path()):
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+
+    # the CPU baseline runs before any kernel work (rank 0, N = 1 only)
+    cpu = cpu_baseline(args.cpu_sample) if (rank == 0 and ws == 1 and not args.skip_cpu) else None
+
+    w = W.plain_mid(seed=1 + rank)
+    N = w.N
+    X = torch.from_numpy(w.X).to(dev)
+    plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                precision=B.MIXED)
+    alpha = torch.from_numpy(w.alpha).to(dev).float()
+    out = torch.empty_like(alpha)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.anova_matvec(plan, alpha, out)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # stage breakdown from a second, profiled pass (events between the stages)
+    B.anova_set_profiling(plan, True)
+    B.anova_stage_times(plan)   # reset
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
+    stage_ms, stage_launch = B.anova_stage_times(plan)
+    B.anova_set_profiling(plan, False)
+    total_ms = sum(step_ms)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * N * args.steps / (total_ms * 1e-3) / 1e9
+    launches = int(sum(stage_launch))
+
+    # dominant kernel: spread (stage 0) or gather (stage 2); one launch per window per step
+    taps = (2 * w.m + 1) ** 3
+    dom = 0 if stage_ms[0] >= stage_ms[2] else 2
+    dom_name = "k_spread<float,3>" if dom == 0 else "k_gather<float,3>"
+    per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
+    flops_per_launch = 2.0 * taps * N   # one multiply-add per tap and node, one window
+    achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived FP32 FMA peak ({FP32_PEAK_NOTE})",
+                "per_launch_ms": per_launch_ms,
+                "stage_ms_per_step": {k: v / args.steps for k, v in
+                                      zip(["spread", "fft", "gather", "window_sum"], stage_ms)}}
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    a_host = torch.from_numpy(w.alpha.astype(np.float32)).pin_memory()
+    o_host = torch.empty(N, dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        alpha.copy_(a_host, non_blocking=True)
+        step()
+        o_host.copy_(out, non_blocking=True)
+        e_ev.record(stream)
+        e_ev.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(s_ev.elapsed_time(e_ev))
+    e2e_t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * N * args.steps / (float(e2e_t.item()) * 1e-3) / 1e9
+
+    # KRR solves/s (mixed precision: FP32 inner CG, FP64 refinement) to the workload's tolerance
+    krr = None
+    if not args.skip_krr:
+        y = torch.from_numpy(w.y).to(dev)
+        sol = torch.zeros_like(y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, its, rel = B.krr_cg_solve(plan, w.lam, y, sol, w.tol, 5000)
+        t = time.perf_counter() - t0
+        krr = {"solves_per_s": 1.0 / t, "seconds": t, "iterations": int(its[0]), "relres": float(rel[0]),
+               "status": int(st), "precision": "mixed (FP32 inner CG, FP64 refinement)", "tol": w.tol,
+               "lambda": w.lam}
+
+    q = sorted(step_ms)
+    lat = {"p50": q[len(q) // 2], "p99": q[min(len(q) - 1, int(0.99 * len(q)))], "unit": "ms"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "N": N, "d": 9, "windows": "3x3D", "n": 32, "m": 6,
+                           "sigma": 2.0, "eps_B": w.epsB, "ell": w.ell, "precision": "fp32 operator",
+                           "l2": "flushed before every step (256 MB write outside the step events)",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": 4 * N,
+                        "d2h_bytes_per_step": 4 * N},
+                "gpu_launches": launches, "latency_ms": lat, "krr": krr, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--ref-sample", type=int, default=10_000)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-krr", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

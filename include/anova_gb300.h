@@ -178,8 +178,8 @@ anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host)
  * stream around each stage of the fast summation; anova_stage_times returns
  * the accumulated milliseconds and kernel launch counts per stage since the
  * last call (which resets them):
- *   0 grid clearing and spreading, 1 forward FFT, multiply by D, inverse FFT,
- *   2 gathering, 3 window sum and CG vector kernels.
+ *   0 spreading, 1 forward FFT, multiply by D, inverse FFT, 2 gathering,
+ *   3 window sum and CG vector kernels (grid clearing is a memset, not timed).
  * `ms` and `launches` are host arrays of `cap` entries; returns the number of
  * stages written.  Reading synchronises the recorded events.
  */

@@ -88,10 +88,10 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
         const WindowPlan& w = plan->win[l];
         size_t ge = 1;
         for (int t = 0; t < w.dA; t++) ge *= w.nos;
-        clock_begin(plan, 0, st);
         ANOVA_CUDA_TRY(cudaMemsetAsync(grid, 0, ge * sizeof(T), st));
+        clock_begin(plan, 0, st);
         ANOVA_TRY(spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid, st));
-        clock_end(plan, 0, 2, st);
+        clock_end(plan, 0, 1, st);
         clock_begin(plan, 1, st);
         ANOVA_TRY(fft_convolve_window<T>(plan, w, grid, st));
         clock_end(plan, 1, 2 * w.dA, st);
@@ -448,7 +448,7 @@ anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, vo
         set_error("anova_matvec: bad plan, dtype, pointers, nrhs or ld");
         return ANOVA_EINVAL;
     }
-    if (alpha == out) {
+    if (plan->N > 0 && alpha == out) {
         set_error("anova_matvec: out must not alias alpha");
         return ANOVA_EINVAL;
     }
