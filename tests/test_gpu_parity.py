@@ -199,7 +199,7 @@ def test_cg_reduced_precision_reaches_tolerance(B, torch, precision):
     assert st == B.OK and relres[0] <= (tol if precision == "MIXED" else 2 * tol)
     # the FP64 oracle operator agrees that alpha solves the system
     q = oracle_fast(w, alpha=alpha.cpu().numpy()) + w.lam * alpha.cpu().numpy()
-    assert rel(q, w.y) <= (2e-8 if precision == "MIXED" else 1e-4)
+    assert rel(q, w.y) <= (2e-8 if precision == "MIXED" else 3 * tol)
 
 
 @pytest.mark.parametrize("scale_z", [0.5, 1.7])
