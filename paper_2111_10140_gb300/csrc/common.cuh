@@ -39,6 +39,7 @@ constexpr int kMaxWindows = 256;
 constexpr int kMaxM = 12;
 constexpr int kSubChunk = 1024;        // points per spread/gather sub-problem
 constexpr int kThreads = 256;
+constexpr int kMaxBins = 32768;        // bins per window (shared histogram of the sort)
 
 // Points of one window, binned and sorted (one for the training nodes X,
 // one per predict call for the test nodes Z).
@@ -61,6 +62,7 @@ struct WindowPlan {
     int nb = 0;       // bins per axis, ceil(nos / T)
     int R = 0;        // region side = T + 2m
     int nbins = 0;    // nb^dA
+    bool dense = false;  // 3-D window on the dense tensor-product kernels (dense3.cu)
     double eta = 0.0;
     double centre[kMaxDim] = {0, 0, 0};
     double scale = 1.0, ell_l = 0.0;
@@ -140,6 +142,12 @@ anova_status spread_window(anova_plan* plan, const WindowPlan& w, const PointSet
 template <typename T>
 anova_status gather_window(anova_plan* plan, const WindowPlan& w, const PointSet& ps,
                            const T* h, T* out, cudaStream_t st);
+template <typename T>
+anova_status spread3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
+                           int alpha_double, T* grid, cudaStream_t st);
+template <typename T>
+anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
+                           cudaStream_t st);
 template <typename T>
 anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid, cudaStream_t st);
 

@@ -1,0 +1,266 @@
+// dense3.cu -- spreading and gathering for 3-D windows as dense tensor-product
+// sums over a bin's region (the window steps of the adjoint NFFT, Eq. adjnfft,
+// and of the NFFT, Eq. nfft, in the fast summation of Sec. 4.2).
+//
+// Bins are Tb^3 grid cells (Tb = 2 or 4), so every node of a bin touches only the
+// region of R = Tb + 2m <= 16 cells per axis starting at (bin * Tb - m).  Per node the window
+// weights are zero-padded to that region:
+//     wx[r] = psi(off_x + m + f_x - r),  r in [0, R)   (zero where |t| > m)
+// so a node's contribution to the region is the outer product wx (x) wy (x) wz.
+//
+//   gather: one lane per node, the region of h staged in shared memory with a
+//           row pitch of 16 along the last axis; every row is read with
+//           broadcast 128-bit loads and contracted against the lane's own
+//           weights:  s = sum_a wx[a] sum_b wy[b] sum_c wz[c] h[a][b][c].
+//   spread: one thread per (a, pair of b, half of c) block of the region keeps
+//           2 x 8 accumulators in registers and adds alpha_j wx wy wz for the
+//           nodes of the sub-problem, whose weights are staged in shared
+//           memory; the region is added to the global grid once at the end.
+//
+// Both loops are plain FP32 (or FP64) multiply-adds: no atomics per tap.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace anova {
+
+constexpr int kPitch = 16;        // shared row pitch along the last axis (elements)
+constexpr int kGatherThreads = 256;
+constexpr int kSpreadChunk = 64;  // nodes whose weights are staged at once
+
+__device__ __forceinline__ int wrap_idx(int u, int nos) {
+    u %= nos;
+    return u < 0 ? u + nos : u;
+}
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    __device__ static __forceinline__ void load(const float* p, float* v) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    __device__ static __forceinline__ void load(const double* p, double* v) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+// ------------------------------------------------------------------ gather
+template <typename T, int R>
+__global__ void __launch_bounds__(kGatherThreads)
+k_gather3_dense(const int4* __restrict__ sub, const int32_t* __restrict__ perm,
+                const int32_t* __restrict__ cell, const T* __restrict__ frac, int64_t N,
+                const T* __restrict__ h, int nos, int Tb, int nb, int m, T b, T norm, T* __restrict__ out) {
+    static_assert(R <= kPitch, "region wider than the row pitch");
+    __shared__ __align__(16) T reg[R * R * kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
+    for (int i = threadIdx.x; i < R * R * kPitch; i += blockDim.x) {
+        const int c = i % kPitch, ab = i / kPitch;
+        const int bb = ab % R, a = ab / R;
+        T v = T(0);
+        if (c < R)
+            v = h[((int64_t)wrap_idx(ox + a, nos) * nos + wrap_idx(oy + bb, nos)) * nos + wrap_idx(oz + c, nos)];
+        reg[i] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const T mm = (T)m;
+    for (int base = threadIdx.x - lane; base < sp.z; base += blockDim.x) {
+        const int q = base + lane;
+        const bool valid = q < sp.z;
+        const int64_t pos = (int64_t)sp.y + (valid ? q : sp.z - 1);
+        const T fx = frac[pos], fy = frac[N + pos], fz = frac[2 * N + pos];
+        const T tx = (T)(cell[pos] - Tb * bx) + mm + fx;
+        const T ty = (T)(cell[N + pos] - Tb * by) + mm + fy;
+        const T tz = (T)(cell[2 * N + pos] - Tb * bz) + mm + fz;
+        T wy[R], wz[kPitch];
+#pragma unroll
+        for (int r = 0; r < R; r++) wy[r] = kb_psi<T>(ty - (T)r, mm, b, norm);
+#pragma unroll
+        for (int r = 0; r < kPitch; r++) wz[r] = (r < R) ? kb_psi<T>(tz - (T)r, mm, b, norm) : T(0);
+        T acc = T(0);
+#pragma unroll 1
+        for (int a = 0; a < R; a++) {
+            const T wa = kb_psi<T>(tx - (T)a, mm, b, norm);
+            const T* rows = reg + a * R * kPitch;
+            T sa = T(0);
+#pragma unroll
+            for (int bb = 0; bb < R; bb++) {
+                const T* row = rows + bb * kPitch;
+                T s = T(0);
+#pragma unroll
+                for (int c4 = 0; c4 < (R + 3) / 4; c4++) {
+                    T v[4];
+                    Vec4<T>::load(row + 4 * c4, v);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (4 * c4 + k < R) s = fma(wz[4 * c4 + k], v[k], s);
+                }
+                sa = fma(wy[bb], s, sa);
+            }
+            acc = fma(wa, sa, acc);
+        }
+        if (valid) out[perm[pos]] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ spread
+template <typename T, int R>
+__global__ void __launch_bounds__(R * (R / 2 + R % 2) * 2)
+k_spread3_dense(const int4* __restrict__ sub, const int32_t* __restrict__ perm,
+                const int32_t* __restrict__ cell, const T* __restrict__ frac, int64_t N,
+                const void* __restrict__ alpha, int alpha_double, T* __restrict__ grid, int nos, int Tb,
+                int nb, int m, T b, T norm) {
+    static_assert(R <= kPitch, "region wider than the row pitch");
+    constexpr int BP = R / 2 + R % 2;          // pairs of b rows
+    constexpr int NT = R * BP * 2;             // threads: a x b-pair x c-half
+    __shared__ __align__(16) T wxs[kSpreadChunk][R];
+    __shared__ __align__(16) T wys[kSpreadChunk][kPitch];
+    __shared__ __align__(16) T wzs[kSpreadChunk][kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int tid = threadIdx.x;
+    const int ch = tid & 1, bp = (tid >> 1) % BP, a = (tid >> 1) / BP;
+    const int b0 = 2 * bp, c0 = 8 * ch;
+    const T mm = (T)m;
+    T acc[2][8];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[i][k] = T(0);
+
+    for (int first = 0; first < sp.z; first += kSpreadChunk) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        __syncthreads();
+        // stage the weights of `cnt` nodes: 3 axes x kPitch entries each
+        for (int i = tid; i < cnt * 3 * kPitch; i += NT) {
+            const int r = i % kPitch, ax = (i / kPitch) % 3, p = i / (3 * kPitch);
+            const int64_t pos = (int64_t)sp.y + first + p;
+            const int bcoord = (ax == 0) ? bx : (ax == 1) ? by : bz;
+            const T t = (T)(cell[ax * N + pos] - Tb * bcoord) + mm + frac[ax * N + pos] - (T)r;
+            T w = (r < R) ? kb_psi<T>(t, mm, b, norm) : T(0);
+            if (ax == 0) {
+                if (r < R) {
+                    const int32_t src = perm[pos];
+                    const T al = alpha_double ? (T)(static_cast<const double*>(alpha)[src])
+                                              : (T)(static_cast<const float*>(alpha)[src]);
+                    wxs[p][r] = al * w;
+                }
+            } else if (ax == 1) {
+                wys[p][r] = w;
+            } else {
+                wzs[p][r] = w;
+            }
+        }
+        __syncthreads();
+        if (a < R) {
+            for (int p = 0; p < cnt; p++) {
+                const T wa = wxs[p][a];
+                const T w0 = wa * wys[p][b0];
+                const T w1 = wa * wys[p][b0 + 1];
+                T z[8];
+                Vec4<T>::load(&wzs[p][c0], z);
+                Vec4<T>::load(&wzs[p][c0 + 4], z + 4);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    acc[0][k] = fma(w0, z[k], acc[0][k]);
+                    acc[1][k] = fma(w1, z[k], acc[1][k]);
+                }
+            }
+        }
+    }
+    if (a < R) {
+        const int ga = wrap_idx(Tb * bx - m + a, nos);
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int bb = b0 + i;
+            if (bb >= R) continue;
+            const int64_t rowbase = ((int64_t)ga * nos + wrap_idx(Tb * by - m + bb, nos)) * nos;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int c = c0 + k;
+                if (c < R) atomicAdd(&grid[rowbase + wrap_idx(Tb * bz - m + c, nos)], acc[i][k]);
+            }
+        }
+    }
+}
+
+template <typename T>
+static const T* frac_of3(const PointSet& ps);
+template <>
+const double* frac_of3<double>(const PointSet& ps) { return ps.frac64; }
+template <>
+const float* frac_of3<float>(const PointSet& ps) { return ps.frac32; }
+
+
+template <typename T, int R>
+static void launch_spread(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
+                          int alpha_double, T* grid, cudaStream_t st) {
+    constexpr int NT = R * (R / 2 + R % 2) * 2;
+    k_spread3_dense<T, R><<<ps.nsub, NT, 0, st>>>(ps.sub, ps.perm, ps.cell, frac_of3<T>(ps), ps.N, alpha,
+                                                  alpha_double, grid, w.nos, w.T, w.nb, plan->m, (T)plan->b,
+                                                  (T)plan->psi_norm);
+}
+
+template <typename T, int R>
+static void launch_gather(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
+                          cudaStream_t st) {
+    k_gather3_dense<T, R><<<ps.nsub, kGatherThreads, 0, st>>>(ps.sub, ps.perm, ps.cell, frac_of3<T>(ps), ps.N,
+                                                              h, w.nos, w.T, w.nb, plan->m, (T)plan->b,
+                                                              (T)plan->psi_norm, out);
+}
+
+template <typename T>
+anova_status spread3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
+                           int alpha_double, T* grid, cudaStream_t st) {
+    if (ps.nsub == 0) return ANOVA_OK;
+    switch (w.R) {
+        case 4: launch_spread<T, 4>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        case 6: launch_spread<T, 6>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        case 8: launch_spread<T, 8>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        case 10: launch_spread<T, 10>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        case 12: launch_spread<T, 12>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        case 14: launch_spread<T, 14>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        case 16: launch_spread<T, 16>(plan, w, ps, alpha, alpha_double, grid, st); break;
+        default: set_error("dense 3-D spread: unsupported region size"); return ANOVA_EINVAL;
+    }
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+template <typename T>
+anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
+                           cudaStream_t st) {
+    if (ps.nsub == 0) return ANOVA_OK;
+    switch (w.R) {
+        case 4: launch_gather<T, 4>(plan, w, ps, h, out, st); break;
+        case 6: launch_gather<T, 6>(plan, w, ps, h, out, st); break;
+        case 8: launch_gather<T, 8>(plan, w, ps, h, out, st); break;
+        case 10: launch_gather<T, 10>(plan, w, ps, h, out, st); break;
+        case 12: launch_gather<T, 12>(plan, w, ps, h, out, st); break;
+        case 14: launch_gather<T, 14>(plan, w, ps, h, out, st); break;
+        case 16: launch_gather<T, 16>(plan, w, ps, h, out, st); break;
+        default: set_error("dense 3-D gather: unsupported region size"); return ANOVA_EINVAL;
+    }
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+template anova_status spread3_dense<float>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,
+                                           float*, cudaStream_t);
+template anova_status spread3_dense<double>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,
+                                            double*, cudaStream_t);
+template anova_status gather3_dense<float>(anova_plan*, const WindowPlan&, const PointSet&, const float*, float*,
+                                           cudaStream_t);
+template anova_status gather3_dense<double>(anova_plan*, const WindowPlan&, const PointSet&, const double*,
+                                            double*, cudaStream_t);
+
+}  // namespace anova

@@ -326,6 +326,12 @@ anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coord
     for (int t = 0; t < 3; t++) fr.c[t] = centre[t];
     fr.s = scale;
     const size_t shb = w.nbins * sizeof(int32_t);
+    static bool attrs = [] {
+        cudaFuncSetAttribute(k_bin_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4);
+        cudaFuncSetAttribute(k_bin_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4);
+        return true;
+    }();
+    (void)attrs;
     k_bin_hist<<<nchunk, kThreads, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk, hist);
     k_scan_exclusive<<<1, 1024, 0, st>>>(hist, L, tot);
     k_bin_scatter<double><<<nchunk, 32, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk,
@@ -480,6 +486,21 @@ __global__ void k_twiddles(int nos, double2* __restrict__ tw64, float2* __restri
 
 // ================================================================ set-up
 static void choose_bins(WindowPlan& w, int m) {
+    if (w.dA == 3) {
+        // dense tensor-product kernels: bins of Tb^3 cells, region Tb + 2m <= 16
+        for (int Tb = 2; Tb <= 4; Tb += 2) {
+            const int nb = (w.nos + Tb - 1) / Tb;
+            if (Tb + 2 * m <= 16 && nb * nb * nb <= kMaxBins) {
+                w.dense = true;
+                w.T = Tb;
+                w.nb = nb;
+                w.nbins = nb * nb * nb;
+                w.R = Tb + 2 * m;
+                return;
+            }
+        }
+    }
+    w.dense = false;
     int T = (w.dA == 3) ? 4 : (w.dA == 2) ? 16 : 64;
     T = std::min(T, w.nos);
     auto nbins_of = [&](int t) {
@@ -487,7 +508,7 @@ static void choose_bins(WindowPlan& w, int m) {
         for (int i = 0; i < w.dA; i++) nbins *= nb;
         return nbins;
     };
-    while (nbins_of(T) > 8192 && T < w.nos) T++;
+    while (nbins_of(T) > kMaxBins && T < w.nos) T++;
     auto region_bytes = [&](int t) {
         int64_t r = t + 2 * m, v = 1;
         for (int i = 0; i < w.dA; i++) v *= r;
@@ -602,7 +623,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
         w.nos = (int)std::lround(sigma * w.n);
         w.eta = weights ? weights[l] : 1.0 / P;
         choose_bins(w, m);
-        if (w.nbins > 8192) {
+        if (w.nbins > kMaxBins) {
             set_error("window " + std::to_string(l) + ": grid too fine for the binning (reduce n or m)");
             return ANOVA_EINVAL;
         }
