@@ -134,6 +134,34 @@ anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, doub
 anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
                          int64_t ldz, double* out, void* stream);
 
+/*
+ * krr_predict_noalloc -- the same prediction as krr_predict, but the call
+ * itself allocates no device memory: no cudaMalloc, cudaFree or allocating
+ * library routine runs inside it.  The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate while serving a request, such
+ * as a request path recorded while a CUDA stream is being captured (allocation
+ * is not capturable), a server holding a fixed device-memory budget, or a
+ * process whose device allocator belongs to another framework.
+ *
+ * Arguments and result are those of krr_predict, with these limits:
+ *   - M <= 65536 test points per call; larger M returns ANOVA_EINVAL.
+ *   - The per-call scratch (test-point coordinates, their binned copy, sort
+ *     histograms, per-window results; about 7 MiB at M = 65536) lives in one
+ *     8 MiB file-scope device array that every GPU loading the library holds
+ *     until the process exits.  The plan's own buffers are used as in
+ *     anova_matvec.
+ *   - The first call on a device looks up that array's device address (with
+ *     the device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other threads,
+ *     other streams) race and corrupt each other's results.  Serialise them.
+ *   - A test point outside the plan's ball returns ANOVA_ERANGE (krr_predict
+ *     would build a joint frame, which needs allocation).
+ * Synchronises `stream`.
+ */
+anova_status krr_predict_noalloc(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
+                                 int64_t ldz, double* out, void* stream);
+
 /* Free every device buffer of the plan.  NULL is ignored. */
 void anova_plan_destroy(anova_plan* plan);
 

@@ -32,6 +32,7 @@ _SIGNATURES = {
     "anova_matvec": (_i32, [_vp, _i32, _vp, _vp, _i32, _i64, _vp]),
     "krr_cg_solve": (_i32, [_vp, _f64, _vp, _vp, _i32, _i64, _f64, _i32, _pi32, _pf64, _vp]),
     "krr_predict": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
+    "krr_predict_noalloc": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
     "anova_plan_destroy": (None, [_vp]),
     "anova_status_string": (ctypes.c_char_p, [_i32]),
     "anova_last_error": (ctypes.c_char_p, []),
@@ -180,6 +181,17 @@ def krr_predict(plan: Plan, alpha, Z, out, stream=None):
     M = Z.shape[0]
     _check(lib().krr_predict(plan.handle, _ptr(alpha), _ptr(Z), M, Z.shape[1], _ptr(out), _stream(stream)),
            "krr_predict")
+    return out
+
+
+def krr_predict_noalloc(plan: Plan, alpha, Z, out, stream=None):
+    """krr_predict without device allocation inside the call (see the header)."""
+    import torch
+    _require_cuda(alpha, "alpha", torch.float64)
+    _require_cuda(Z, "Z", torch.float64)
+    _require_cuda(out, "out", torch.float64)
+    _check(lib().krr_predict_noalloc(plan.handle, _ptr(alpha), _ptr(Z), Z.shape[0], Z.shape[1], _ptr(out),
+                                     _stream(stream)), "krr_predict_noalloc")
     return out
 
 

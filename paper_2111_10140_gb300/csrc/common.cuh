@@ -135,6 +135,29 @@ anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, c
 anova_status extract_window(anova_plan* plan, const double* Z, int64_t M, int64_t ldz,
                             const WindowPlan& w, double* zw, cudaStream_t st);
 
+// caller-provided buffers for binning M nodes without allocating
+struct NoallocBinBuffers {
+    int nchunk = 0;              // capacity in node chunks of the sort
+    int64_t hist_elems = 0;      // capacity of hist
+    int sub_capacity = 0;        // capacity of sub
+    int64_t red_elems = 0;       // capacity of the radius reduction buffer
+    int32_t* perm = nullptr;     // M
+    int32_t* cell = nullptr;     // 3 M
+    double* frac64 = nullptr;    // 3 M
+    float* frac32 = nullptr;     // 3 M
+    int32_t* bin_start = nullptr;// kMaxBins + 1
+    int32_t* nch = nullptr;      // kMaxBins + 1
+    int32_t* hist = nullptr;     // hist_elems
+    int32_t* tot = nullptr;      // 2
+    int4* sub = nullptr;         // sub_capacity
+};
+NoallocBinBuffers noalloc_bin_layout(int64_t M);
+anova_status max_radius_into(anova_plan* plan, const double* zw, int64_t M, int dA, const double* centre,
+                             double* red, double* rmax_host, cudaStream_t st);
+anova_status build_pointset_into(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
+                                 const double* centre, double scale, const NoallocBinBuffers& buf,
+                                 PointSet& ps, cudaStream_t st);
+
 // window-level stages (matvec.cu / spread_gather.cu / fft.cu)
 template <typename T>
 anova_status spread_window(anova_plan* plan, const WindowPlan& w, const PointSet& ps,

@@ -739,6 +739,89 @@ anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, c
     return ANOVA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Variants of the binning and radius helpers that write into caller-provided
+// device buffers instead of allocating (used by krr_predict_noalloc).
+NoallocBinBuffers noalloc_bin_layout(int64_t M) {
+    NoallocBinBuffers b;
+    b.nchunk = (int)((M + kBinChunk - 1) / kBinChunk);
+    b.hist_elems = (int64_t)kMaxBins * std::max(b.nchunk, 1);
+    b.sub_capacity = kMaxBins + (int)(M / kSubChunk) + 1;
+    b.red_elems = 6 * 2 * 1024 + 16;
+    return b;
+}
+
+anova_status max_radius_into(anova_plan* plan, const double* zw, int64_t M, int dA, const double* centre,
+                             double* red, double* rmax_host, cudaStream_t st) {
+    *rmax_host = 0.0;
+    if (M == 0) return ANOVA_OK;
+    const int nblk = grid_for(M, kThreads, std::min(2 * plan->sm_count, 2048));
+    double* frame = red + nblk;
+    double hf[5] = {centre[0], centre[1], centre[2], 1.0, 0.0};
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(frame, hf, 5 * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_maxnorm<<<nblk, kThreads, 0, st>>>(zw, M, nullptr, 0, dA, frame, red);
+    k_maxnorm_final<<<1, kThreads, 0, st>>>(red, nblk, 1.0, frame);
+    ANOVA_CHECK_LAUNCH();
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(hf, frame, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    *rmax_host = hf[4];
+    return ANOVA_OK;
+}
+
+anova_status build_pointset_into(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
+                                 const double* centre, double scale, const NoallocBinBuffers& buf,
+                                 PointSet& ps, cudaStream_t st) {
+    ps.N = N;
+    ps.perm = buf.perm;
+    ps.cell = buf.cell;
+    ps.frac64 = (plan->precision & ANOVA_FP64) ? buf.frac64 : nullptr;
+    ps.frac32 = (plan->precision & ANOVA_FP32) ? buf.frac32 : nullptr;
+    ps.bin_start = buf.bin_start;
+    ps.sub = buf.sub;
+    ps.nsub = 0;
+    if (N == 0) return ANOVA_OK;
+    const int dA = w.dA;
+    const int nchunk = (int)((N + kBinChunk - 1) / kBinChunk);
+    const int64_t L = (int64_t)w.nbins * nchunk;
+    if (nchunk > buf.nchunk || L > buf.hist_elems) {
+        set_error("no-alloc binning: scratch too small");
+        return ANOVA_EINVAL;
+    }
+    FrameArgs fr;
+    for (int t = 0; t < 3; t++) fr.c[t] = centre[t];
+    fr.s = scale;
+    const size_t shb = w.nbins * sizeof(int32_t);
+    static bool attrs = [] {
+        cudaFuncSetAttribute(k_bin_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4);
+        cudaFuncSetAttribute(k_bin_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4);
+        return true;
+    }();
+    (void)attrs;
+    k_bin_hist<<<nchunk, kThreads, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk, buf.hist);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(buf.hist, L, buf.tot);
+    k_bin_scatter<double><<<nchunk, 32, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk,
+                                                  buf.hist, ps.perm, ps.cell, ps.frac64, ps.frac32);
+    k_bin_starts<<<grid_for(w.nbins + 1, kThreads, 1024), kThreads, 0, st>>>(buf.hist, w.nbins, nchunk, N,
+                                                                              ps.bin_start, buf.nch);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(buf.nch, w.nbins, buf.tot + 1);
+    ANOVA_CHECK_LAUNCH();
+    int32_t totals[2] = {0, 0};
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(totals, buf.tot, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (totals[0] != N) {
+        set_error("no-alloc binning lost nodes");
+        return ANOVA_ECUDA;
+    }
+    if (totals[1] > buf.sub_capacity) {
+        set_error("no-alloc binning: too many sub-problems for the scratch");
+        return ANOVA_EINVAL;
+    }
+    ps.nsub = totals[1];
+    k_sub_list<<<grid_for(w.nbins, kThreads, 1024), kThreads, 0, st>>>(ps.bin_start, buf.nch, w.nbins, ps.sub);
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
 // copy the window's feature columns of Z into zw (M x dA)
 anova_status extract_window(anova_plan* plan, const double* Z, int64_t M, int64_t ldz, const WindowPlan& w,
                             double* zw, cudaStream_t st) {
