@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -37,7 +38,7 @@ void set_error(const std::string& msg);
 constexpr int kMaxDim = 3;
 constexpr int kMaxWindows = 256;
 constexpr int kMaxM = 12;
-constexpr int kSubChunk = 1024;        // points per spread/gather sub-problem
+constexpr int kSubChunk = 256;         // points per spread/gather sub-problem
 constexpr int kThreads = 256;
 constexpr int kMaxBins = 32768;        // bins per window (shared histogram of the sort)
 
@@ -71,7 +72,20 @@ struct WindowPlan {
     double2* tw64 = nullptr;   // exp(-2 pi i r / nos), r = 0..nos-1
     float2* tw32 = nullptr;
     double* xw = nullptr;      // N x dA window coordinates (user units, original order)
+    size_t grid_off = 0;       // element offset of this window's grid in plan->grid
+    size_t work_off = 0;       // element offset of this window's FFT work arrays
     PointSet X;
+};
+
+// Per-window arguments of the batched dense 3-D kernels (one launch, all windows).
+struct DenseWin {
+    const int32_t* perm;
+    const int32_t* cell;
+    const void* frac;          // FP32 or FP64, as the launch
+    void* grid;                // this window's grid
+    void* out;                 // gather output (this window's slice of plan->tmp)
+    int64_t N;
+    int nos, Tb, nb, pad;
 };
 
 struct StageClock {
@@ -91,11 +105,17 @@ struct anova_plan {
     double sigma = 2.0, epsB = 1.0 / 16, ell = 0.0, b = 0.0;
     double psi_norm = 1.0;              // m / sinh(b m): psi(t) = psi_norm * sinh(b s)/s
     std::vector<anova::WindowPlan> win;
-    // shared work buffers (windows are processed one after another)
-    size_t grid_elems = 0, work_elems = 0;
-    void* grid = nullptr;               // real spread grid / inverse FFT output
+    // work buffers: every window has its own grid and FFT work arrays (offsets in WindowPlan)
+    size_t grid_elems = 0, work_elems = 0;  // totals over the windows
+    void* grid = nullptr;               // real spread grids / inverse FFT outputs
     void* work1 = nullptr;              // complex work arrays
     void* work2 = nullptr;
+    // batched dense 3-D windows: merged sub-problem list (bin, first, count, window)
+    int4* dense_sub = nullptr;
+    int dense_nsub = 0;
+    std::vector<int> dense_windows;     // indices of the dense windows, in launch order
+    std::vector<std::array<int, 3>> dense_groups;  // (region size R, first sub, count) per launch
+    anova::DenseWin* dense_desc = nullptr;  // device, 2 x dense_windows.size(): FP64 then FP32
     void* tmp = nullptr;                // P x N per-window results (8 bytes each)
     double* eta_dev = nullptr;          // P window weights on the device
     // CG state
@@ -173,6 +193,15 @@ anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet
                            cudaStream_t st);
 template <typename T>
 anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid, cudaStream_t st);
+template <typename T>
+anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st);
+template <typename T>
+anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st);
+
+template <typename T>
+inline T* grid_of(anova_plan* plan, const WindowPlan& w) {
+    return static_cast<T*>(plan->grid) + w.grid_off;
+}
 
 // stage clock helpers
 void clock_begin(anova_plan* plan, int stage, cudaStream_t st);

@@ -54,12 +54,19 @@ struct Vec4<double> {
 // ------------------------------------------------------------------ gather
 template <typename T, int R>
 __global__ void __launch_bounds__(kGatherThreads)
-k_gather3_dense(const int4* __restrict__ sub, const int32_t* __restrict__ perm,
-                const int32_t* __restrict__ cell, const T* __restrict__ frac, int64_t N,
-                const T* __restrict__ h, int nos, int Tb, int nb, int m, T b, T norm, T* __restrict__ out) {
+k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, DenseWin one, int m, T b,
+                T norm) {
     static_assert(R <= kPitch, "region wider than the row pitch");
     __shared__ __align__(16) T reg[R * R * kPitch];
     const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs ? descs[sp.w] : one;
+    const int32_t* __restrict__ perm = W.perm;
+    const int32_t* __restrict__ cell = W.cell;
+    const T* __restrict__ frac = static_cast<const T*>(W.frac);
+    const T* __restrict__ h = static_cast<const T*>(W.grid);
+    T* __restrict__ out = static_cast<T*>(W.out);
+    const int64_t N = W.N;
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
     const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
     for (int i = threadIdx.x; i < R * R * kPitch; i += blockDim.x) {
@@ -115,10 +122,8 @@ k_gather3_dense(const int4* __restrict__ sub, const int32_t* __restrict__ perm,
 // ------------------------------------------------------------------ spread
 template <typename T, int R>
 __global__ void __launch_bounds__(R * (R / 2 + R % 2) * 2)
-k_spread3_dense(const int4* __restrict__ sub, const int32_t* __restrict__ perm,
-                const int32_t* __restrict__ cell, const T* __restrict__ frac, int64_t N,
-                const void* __restrict__ alpha, int alpha_double, T* __restrict__ grid, int nos, int Tb,
-                int nb, int m, T b, T norm) {
+k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, DenseWin one,
+                const void* __restrict__ alpha, int alpha_double, int m, T b, T norm) {
     static_assert(R <= kPitch, "region wider than the row pitch");
     constexpr int BP = R / 2 + R % 2;          // pairs of b rows
     constexpr int NT = R * BP * 2;             // threads: a x b-pair x c-half
@@ -126,6 +131,13 @@ k_spread3_dense(const int4* __restrict__ sub, const int32_t* __restrict__ perm,
     __shared__ __align__(16) T wys[kSpreadChunk][kPitch];
     __shared__ __align__(16) T wzs[kSpreadChunk][kPitch];
     const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs ? descs[sp.w] : one;
+    const int32_t* __restrict__ perm = W.perm;
+    const int32_t* __restrict__ cell = W.cell;
+    const T* __restrict__ frac = static_cast<const T*>(W.frac);
+    T* __restrict__ grid = static_cast<T*>(W.grid);
+    const int64_t N = W.N;
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
     const int tid = threadIdx.x;
     const int ch = tid & 1, bp = (tid >> 1) % BP, a = (tid >> 1) / BP;
@@ -200,36 +212,33 @@ const double* frac_of3<double>(const PointSet& ps) { return ps.frac64; }
 template <>
 const float* frac_of3<float>(const PointSet& ps) { return ps.frac32; }
 
-
 template <typename T, int R>
-static void launch_spread(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
-                          int alpha_double, T* grid, cudaStream_t st) {
+static void launch_spread(anova_plan* plan, const int4* sub, int nsub, const DenseWin* descs, const DenseWin& one,
+                          const void* alpha, int alpha_double, cudaStream_t st) {
     constexpr int NT = R * (R / 2 + R % 2) * 2;
-    k_spread3_dense<T, R><<<ps.nsub, NT, 0, st>>>(ps.sub, ps.perm, ps.cell, frac_of3<T>(ps), ps.N, alpha,
-                                                  alpha_double, grid, w.nos, w.T, w.nb, plan->m, (T)plan->b,
-                                                  (T)plan->psi_norm);
+    k_spread3_dense<T, R><<<nsub, NT, 0, st>>>(sub, descs, one, alpha, alpha_double, plan->m, (T)plan->b,
+                                               (T)plan->psi_norm);
 }
 
 template <typename T, int R>
-static void launch_gather(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
+static void launch_gather(anova_plan* plan, const int4* sub, int nsub, const DenseWin* descs, const DenseWin& one,
                           cudaStream_t st) {
-    k_gather3_dense<T, R><<<ps.nsub, kGatherThreads, 0, st>>>(ps.sub, ps.perm, ps.cell, frac_of3<T>(ps), ps.N,
-                                                              h, w.nos, w.T, w.nb, plan->m, (T)plan->b,
-                                                              (T)plan->psi_norm, out);
+    k_gather3_dense<T, R><<<nsub, kGatherThreads, 0, st>>>(sub, descs, one, plan->m, (T)plan->b,
+                                                           (T)plan->psi_norm);
 }
 
 template <typename T>
-anova_status spread3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
-                           int alpha_double, T* grid, cudaStream_t st) {
-    if (ps.nsub == 0) return ANOVA_OK;
-    switch (w.R) {
-        case 4: launch_spread<T, 4>(plan, w, ps, alpha, alpha_double, grid, st); break;
-        case 6: launch_spread<T, 6>(plan, w, ps, alpha, alpha_double, grid, st); break;
-        case 8: launch_spread<T, 8>(plan, w, ps, alpha, alpha_double, grid, st); break;
-        case 10: launch_spread<T, 10>(plan, w, ps, alpha, alpha_double, grid, st); break;
-        case 12: launch_spread<T, 12>(plan, w, ps, alpha, alpha_double, grid, st); break;
-        case 14: launch_spread<T, 14>(plan, w, ps, alpha, alpha_double, grid, st); break;
-        case 16: launch_spread<T, 16>(plan, w, ps, alpha, alpha_double, grid, st); break;
+static anova_status spread_dispatch(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
+                                    const DenseWin& one, const void* alpha, int alpha_double, cudaStream_t st) {
+    if (nsub == 0) return ANOVA_OK;
+    switch (R) {
+        case 4: launch_spread<T, 4>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
+        case 6: launch_spread<T, 6>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
+        case 8: launch_spread<T, 8>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
+        case 10: launch_spread<T, 10>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
+        case 12: launch_spread<T, 12>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
+        case 14: launch_spread<T, 14>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
+        case 16: launch_spread<T, 16>(plan, sub, nsub, descs, one, alpha, alpha_double, st); break;
         default: set_error("dense 3-D spread: unsupported region size"); return ANOVA_EINVAL;
     }
     ANOVA_CHECK_LAUNCH();
@@ -237,23 +246,77 @@ anova_status spread3_dense(anova_plan* plan, const WindowPlan& w, const PointSet
 }
 
 template <typename T>
-anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
-                           cudaStream_t st) {
-    if (ps.nsub == 0) return ANOVA_OK;
-    switch (w.R) {
-        case 4: launch_gather<T, 4>(plan, w, ps, h, out, st); break;
-        case 6: launch_gather<T, 6>(plan, w, ps, h, out, st); break;
-        case 8: launch_gather<T, 8>(plan, w, ps, h, out, st); break;
-        case 10: launch_gather<T, 10>(plan, w, ps, h, out, st); break;
-        case 12: launch_gather<T, 12>(plan, w, ps, h, out, st); break;
-        case 14: launch_gather<T, 14>(plan, w, ps, h, out, st); break;
-        case 16: launch_gather<T, 16>(plan, w, ps, h, out, st); break;
+static anova_status gather_dispatch(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
+                                    const DenseWin& one, cudaStream_t st) {
+    if (nsub == 0) return ANOVA_OK;
+    switch (R) {
+        case 4: launch_gather<T, 4>(plan, sub, nsub, descs, one, st); break;
+        case 6: launch_gather<T, 6>(plan, sub, nsub, descs, one, st); break;
+        case 8: launch_gather<T, 8>(plan, sub, nsub, descs, one, st); break;
+        case 10: launch_gather<T, 10>(plan, sub, nsub, descs, one, st); break;
+        case 12: launch_gather<T, 12>(plan, sub, nsub, descs, one, st); break;
+        case 14: launch_gather<T, 14>(plan, sub, nsub, descs, one, st); break;
+        case 16: launch_gather<T, 16>(plan, sub, nsub, descs, one, st); break;
         default: set_error("dense 3-D gather: unsupported region size"); return ANOVA_EINVAL;
     }
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
 }
 
+static DenseWin single_desc(const WindowPlan& w, const PointSet& ps, const void* frac, void* grid, void* out) {
+    DenseWin d;
+    d.perm = ps.perm;
+    d.cell = ps.cell;
+    d.frac = frac;
+    d.grid = grid;
+    d.out = out;
+    d.N = ps.N;
+    d.nos = w.nos;
+    d.Tb = w.T;
+    d.nb = w.nb;
+    d.pad = 0;
+    return d;
+}
+
+// one window, any node set (used by prediction and the debug entry point)
+template <typename T>
+anova_status spread3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
+                           int alpha_double, T* grid, cudaStream_t st) {
+    const DenseWin one = single_desc(w, ps, frac_of3<T>(ps), grid, nullptr);
+    return spread_dispatch<T>(plan, w.R, ps.sub, ps.nsub, nullptr, one, alpha, alpha_double, st);
+}
+
+template <typename T>
+anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
+                           cudaStream_t st) {
+    const DenseWin one = single_desc(w, ps, frac_of3<T>(ps), const_cast<T*>(h), out);
+    return gather_dispatch<T>(plan, w.R, ps.sub, ps.nsub, nullptr, one, st);
+}
+
+// all dense windows of the plan on their training nodes, one launch per region size
+template <typename T>
+anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st) {
+    const int nd = (int)plan->dense_windows.size();
+    const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
+    for (const auto& g : plan->dense_groups)
+        ANOVA_TRY(spread_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), alpha,
+                                     alpha_double, st));
+    return ANOVA_OK;
+}
+
+template <typename T>
+anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
+    const int nd = (int)plan->dense_windows.size();
+    const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
+    for (const auto& g : plan->dense_groups)
+        ANOVA_TRY(gather_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), st));
+    return ANOVA_OK;
+}
+
+template anova_status dense3_spread_all<float>(anova_plan*, const void*, int, cudaStream_t);
+template anova_status dense3_spread_all<double>(anova_plan*, const void*, int, cudaStream_t);
+template anova_status dense3_gather_all<float>(anova_plan*, cudaStream_t);
+template anova_status dense3_gather_all<double>(anova_plan*, cudaStream_t);
 template anova_status spread3_dense<float>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,
                                            float*, cudaStream_t);
 template anova_status spread3_dense<double>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,

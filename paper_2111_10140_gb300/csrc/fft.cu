@@ -93,7 +93,8 @@ anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid,
     const int dA = w.dA, n = w.n, nos = w.nos;
     const auto* tw = tw_of<T>(w);
     const T* D = D_of<T>(w);
-    void* bufs[2] = {plan->work1, plan->work2};
+    using C = typename Cplx<T>::type;
+    void* bufs[2] = {static_cast<C*>(plan->work1) + w.work_off, static_cast<C*>(plan->work2) + w.work_off};
     int cur = 0;
     const int cap = 8 * plan->sm_count;
     // extents per axis: axes < t already transformed (n), axes >= t not yet (nos)

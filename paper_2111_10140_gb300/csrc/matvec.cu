@@ -78,27 +78,47 @@ k_window_sum(const Tin* __restrict__ tmp, const double* __restrict__ eta, int P,
 }
 
 // -------------------------------------------------------------- matvec core
-// tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum)
+// tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum).
+// `tmp` must be plan->tmp: the batched dense kernels write their slices of it.
 template <typename T>
 static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha_is_double, T* tmp,
                                   cudaStream_t st) {
     const int64_t N = plan->N;
-    T* grid = static_cast<T*>(plan->grid);
+    ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(T), st));
+    int nl = 0;
+    clock_begin(plan, 0, st);
+    if (!plan->dense_windows.empty()) {
+        ANOVA_TRY(dense3_spread_all<T>(plan, alpha, alpha_is_double, st));
+        nl += (int)plan->dense_groups.size();
+    }
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];
-        size_t ge = 1;
-        for (int t = 0; t < w.dA; t++) ge *= w.nos;
-        ANOVA_CUDA_TRY(cudaMemsetAsync(grid, 0, ge * sizeof(T), st));
-        clock_begin(plan, 0, st);
-        ANOVA_TRY(spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid, st));
-        clock_end(plan, 0, 1, st);
-        clock_begin(plan, 1, st);
-        ANOVA_TRY(fft_convolve_window<T>(plan, w, grid, st));
-        clock_end(plan, 1, 2 * w.dA, st);
-        clock_begin(plan, 2, st);
-        ANOVA_TRY(gather_window<T>(plan, w, w.X, grid, tmp + (int64_t)l * N, st));
-        clock_end(plan, 2, 1, st);
+        if (w.dense) continue;
+        ANOVA_TRY(spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid_of<T>(plan, w), st));
+        nl++;
     }
+    clock_end(plan, 0, nl, st);
+    nl = 0;
+    clock_begin(plan, 1, st);
+    for (int l = 0; l < plan->P; l++) {
+        const WindowPlan& w = plan->win[l];
+        ANOVA_TRY(fft_convolve_window<T>(plan, w, grid_of<T>(plan, w), st));
+        nl += 2 * w.dA;
+    }
+    clock_end(plan, 1, nl, st);
+    nl = 0;
+    clock_begin(plan, 2, st);
+    if (!plan->dense_windows.empty()) {
+        ANOVA_TRY(dense3_gather_all<T>(plan, st));
+        nl += (int)plan->dense_groups.size();
+    }
+    for (int l = 0; l < plan->P; l++) {
+        const WindowPlan& w = plan->win[l];
+        if (w.dense) continue;
+        ANOVA_TRY(gather_window<T>(plan, w, w.X, grid_of<T>(plan, w), tmp + (int64_t)l * N, st));
+        nl++;
+    }
+    clock_end(plan, 2, nl, st);
     return ANOVA_OK;
 }
 
@@ -376,7 +396,6 @@ template <typename T>
 static anova_status predict_t(anova_plan* plan, const double* alpha, const double* Z, int64_t M, int64_t ldz,
                               double* out, cudaStream_t st) {
     const int P = plan->P;
-    T* grid = static_cast<T*>(plan->grid);
     T* tmp = nullptr;
     double* zw = nullptr;
     ANOVA_CUDA_TRY(cudaMalloc(&tmp, std::max<int64_t>(M, 1) * P * sizeof(T)));
@@ -403,6 +422,7 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
         s = build_pointset(plan, wz, zw, M, w.dA, w.centre, w.scale, zs, st);
         size_t ge = 1;
         for (int t = 0; t < w.dA; t++) ge *= w.nos;
+        T* grid = grid_of<T>(plan, w);
         if (s == ANOVA_OK && plan->N > 0) {
             cudaMemsetAsync(grid, 0, ge * sizeof(T), st);
             s = spread_window<T>(plan, w, w.X, alpha, 1, grid, st);

@@ -92,7 +92,6 @@ static anova_status predict_noalloc_t(anova_plan* plan, const double* alpha, con
         set_error("krr_predict_noalloc: scratch layout exceeds the static array");
         return ANOVA_EINVAL;
     }
-    T* grid = static_cast<T*>(plan->grid);
     const double RB = 0.25 - 0.5 * plan->epsB;
     for (int l = 0; l < plan->P; l++) {
         WindowPlan& w = plan->win[l];
@@ -108,6 +107,7 @@ static anova_status predict_noalloc_t(anova_plan* plan, const double* alpha, con
         ANOVA_TRY(build_pointset_into(plan, w, zw, M, w.centre, w.scale, buf, zs, st));
         size_t ge = 1;
         for (int t = 0; t < w.dA; t++) ge *= w.nos;
+        T* grid = grid_of<T>(plan, w);
         if (plan->N > 0) {
             ANOVA_CUDA_TRY(cudaMemsetAsync(grid, 0, ge * sizeof(T), st));
             ANOVA_TRY(spread_window<T>(plan, w, w.X, alpha, 1, grid, st));

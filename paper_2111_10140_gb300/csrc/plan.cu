@@ -551,6 +551,65 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
     return build_pointset(plan, w, w.xw, plan->N, w.dA, w.centre, w.scale, w.X, st);
 }
 
+// tag the sub-problems of window slot w and append them to the merged list
+__global__ void k_tag_subs(const int4* __restrict__ src, int n, int slot, int4* __restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int4 v = src[i];
+        v.w = slot;
+        dst[i] = v;
+    }
+}
+
+// Merged sub-problem list and per-window descriptors for the batched dense kernels.
+static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
+    plan->dense_windows.clear();
+    plan->dense_groups.clear();
+    int total = 0;
+    for (int R = 1; R <= 16; R++) {        // windows grouped by region size (one launch each)
+        const int first = total;
+        for (int l = 0; l < plan->P; l++)
+            if (plan->win[l].dense && plan->win[l].R == R && plan->win[l].X.nsub > 0) {
+                plan->dense_windows.push_back(l);
+                total += plan->win[l].X.nsub;
+            }
+        if (total > first) plan->dense_groups.push_back({R, first, total - first});
+    }
+    plan->dense_nsub = total;
+    const int nd = (int)plan->dense_windows.size();
+    if (nd == 0) return ANOVA_OK;
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_sub, total * sizeof(int4)));
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_desc, 2 * nd * sizeof(DenseWin)));
+    std::vector<DenseWin> desc(2 * nd);
+    int at = 0;
+    for (int k = 0; k < nd; k++) {
+        const WindowPlan& w = plan->win[plan->dense_windows[k]];
+        k_tag_subs<<<grid_for(w.X.nsub, kThreads, 256), kThreads, 0, st>>>(w.X.sub, w.X.nsub, k,
+                                                                          plan->dense_sub + at);
+        at += w.X.nsub;
+        for (int prec = 0; prec < 2; prec++) {
+            DenseWin& d = desc[prec * nd + k];
+            d.perm = w.X.perm;
+            d.cell = w.X.cell;
+            d.frac = prec == 0 ? (const void*)w.X.frac64 : (const void*)w.X.frac32;
+            d.grid = prec == 0 ? (void*)(static_cast<double*>(plan->grid) + w.grid_off)
+                               : (void*)(static_cast<float*>(plan->grid) + w.grid_off);
+            const int l = plan->dense_windows[k];
+            d.out = prec == 0 ? (void*)(static_cast<double*>(plan->tmp) + (int64_t)l * plan->N)
+                              : (void*)(static_cast<float*>(plan->tmp) + (int64_t)l * plan->N);
+            d.N = w.X.N;
+            d.nos = w.nos;
+            d.Tb = w.T;
+            d.nb = w.nb;
+            d.pad = 0;
+        }
+    }
+    ANOVA_CHECK_LAUNCH();
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->dense_desc, desc.data(), 2 * nd * sizeof(DenseWin),
+                                   cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    return ANOVA_OK;
+}
+
 static anova_status validate(int64_t N, int32_t d, int64_t ld, const int32_t* windows, int32_t P,
                              const double* weights, double ell, const int32_t* n, int32_t m,
                              double sigma, double eps_B, int32_t p, int32_t precision) {
@@ -630,8 +689,10 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
         size_t ge = 1, we = w.n, tk = 1;
         for (int t = 0; t < w.dA; t++) { ge *= w.nos; tk *= w.n; }
         for (int t = 1; t < w.dA; t++) we *= w.nos;
-        plan->grid_elems = std::max(plan->grid_elems, ge);
-        plan->work_elems = std::max(plan->work_elems, we);
+        w.grid_off = plan->grid_elems;
+        w.work_off = plan->work_elems;
+        plan->grid_elems += (ge + 63) / 64 * 64;
+        plan->work_elems += (we + 63) / 64 * 64;
         max_tk = std::max(max_tk, tk);
         ANOVA_CUDA_TRY(cudaMalloc(&w.tw64, w.nos * sizeof(double2)));
         ANOVA_CUDA_TRY(cudaMalloc(&w.tw32, w.nos * sizeof(float2)));
@@ -668,6 +729,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
         if (N > 0) s = compute_frame(plan, w.xw, N, nullptr, 0, w.dA, scratch, frame, st);
         if (s == ANOVA_OK) s = window_setup(plan, w, frame, scratch, st);
     }
+    if (s == ANOVA_OK) s = build_dense_batch(plan, st);
     if (s == ANOVA_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
@@ -694,6 +756,9 @@ anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M
     dst.nb = src.nb;
     dst.R = src.R;
     dst.nbins = src.nbins;
+    dst.dense = src.dense;
+    dst.grid_off = src.grid_off;
+    dst.work_off = src.work_off;
     dst.eta = src.eta;
     dst.tw64 = src.tw64;   // borrowed
     dst.tw32 = src.tw32;   // borrowed
@@ -882,6 +947,8 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->work2);
     cudaFree(plan->tmp);
     cudaFree(plan->eta_dev);
+    cudaFree(plan->dense_sub);
+    cudaFree(plan->dense_desc);
     cudaFree(plan->cg_vec);
     cudaFree(plan->cg_scal);
     cudaFree(plan->cg_part);
