@@ -217,12 +217,17 @@ def run_ours(args):
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e9
     launches = int(sum(stage_launch))
 
-    # dominant kernel: spread (stage 0) or gather (stage 2); one launch per window per step
+    # dominant kernel: spread (stage 0) or gather (stage 2); the dense 3-D kernels
+    # cover all windows of the step in one launch
     taps = (2 * w.m + 1) ** 3
+    P = len(w.windows)
     dom = 0 if stage_ms[0] >= stage_ms[2] else 2
-    dom_name = "k_spread<float,3>" if dom == 0 else "k_gather<float,3>"
+    R = 2 + 2 * w.m
+    dom_name = f"k_spread3_dense<float,{R}>" if dom == 0 else f"k_gather3_dense<float,{R}>"
     per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
-    flops_per_launch = 2.0 * taps * N   # one multiply-add per tap and node, one window
+    launches_per_step = max(1, stage_launch[dom] // args.steps)
+    # algorithmic work: one multiply-add (2 flop) per tap, node and window
+    flops_per_launch = 2.0 * taps * N * P / launches_per_step
     achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -74,7 +74,20 @@ struct WindowPlan {
     double* xw = nullptr;      // N x dA window coordinates (user units, original order)
     size_t grid_off = 0;       // element offset of this window's grid in plan->grid
     size_t work_off = 0;       // element offset of this window's FFT work arrays
+    int box_lo[kMaxDim] = {0, 0, 0};   // grid cells touched by the training nodes: start (may be < 0)
+    int box_ext[kMaxDim] = {0, 0, 0};  // and extent per axis (<= nos)
     PointSet X;
+};
+
+// Per-window arguments of the batched box-restricted 3-D FFT (fft3.cu).
+struct Fft3Win {
+    void* grid;                // real grid, nos^3
+    void* buf1;                // complex work arrays
+    void* buf2;
+    const void* tw;            // e^{-2 pi i r/nos}
+    const void* D;             // n^3 multiplier
+    int lo[3], B[3];           // box start and extent per axis
+    int n, nos;
 };
 
 // Per-window arguments of the batched dense 3-D kernels (one launch, all windows).
@@ -116,6 +129,8 @@ struct anova_plan {
     std::vector<int> dense_windows;     // indices of the dense windows, in launch order
     std::vector<std::array<int, 3>> dense_groups;  // (region size R, first sub, count) per launch
     anova::DenseWin* dense_desc = nullptr;  // device, 2 x dense_windows.size(): FP64 then FP32
+    std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
+    anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
     void* tmp = nullptr;                // P x N per-window results (8 bytes each)
     double* eta_dev = nullptr;          // P window weights on the device
     // CG state
@@ -193,6 +208,9 @@ anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet
                            cudaStream_t st);
 template <typename T>
 anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid, cudaStream_t st);
+template <typename T>
+anova_status fft3_box_all(anova_plan* plan, cudaStream_t st);
+bool fft3_box_supported(const WindowPlan& w);
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st);
 template <typename T>

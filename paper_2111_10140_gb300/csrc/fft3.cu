@@ -1,0 +1,271 @@
+// fft3.cu -- the FFT / multiply / inverse-FFT middle of the fast summation
+// for 3-D windows, restricted to the box of grid cells the nodes touch and
+// batched over windows (arXiv 2111.10140, Sec. 4.2 Eq. fastsum, Sec. 4.3):
+//
+//   G_k = sum_{u in box} g_u e^{-2 pi i k.u/nos},  k in I_n^3
+//   h_u = Re sum_{k in I_n^3} D_k G_k e^{+2 pi i k.u/nos},  u in box
+//
+// Spreading writes only inside the box and gathering reads only inside it,
+// so every other grid cell contributes nothing and is never needed.  The box
+// is the union of the regions of the occupied bins (or the whole torus when
+// that union would wrap onto itself).  Passes, with box extents Bx, By, Bz:
+//   F1  z -> kz:   (Bx, By, Bz) real      -> (Bx, By, n)  complex
+//   F2  y -> ky:   (Bx, By, n)            -> (Bx, n, n)
+//   M   x -> kx, multiply by D, kx -> x:  (Bx, n, n) -> (Bx, n, n)
+//   I2  ky -> y:   (Bx, n, n)             -> (Bx, By, n)
+//   I3  kz -> z:   (Bx, By, n)            -> (Bx, By, Bz), real part into the grid
+//
+// Twiddles: consecutive box cells have consecutive values modulo nos, so the
+// table index (k u mod nos) advances by a constant step along every loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace anova {
+
+template <typename T>
+struct C2;
+template <>
+struct C2<double> { using type = double2; };
+template <>
+struct C2<float> { using type = float2; };
+
+__device__ __forceinline__ int modp(int v, int p) {
+    v %= p;
+    return v < 0 ? v + p : v;
+}
+
+// centred value of box coordinate 0 on an axis starting at grid index lo
+__device__ __forceinline__ int box_value0(int lo, int nos) { return modp(lo, nos) - nos / 2; }
+
+// acc += v * w (complex), with conj(w) when inverse
+template <typename C, typename T>
+__device__ __forceinline__ void cmac(const C& v, C w, int inverse, T& ar, T& ai) {
+    if (inverse) w.y = -w.y;
+    ar = fma(v.x, w.x, fma(-v.y, w.y, ar));
+    ai = fma(v.x, w.y, fma(v.y, w.x, ai));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft3_f1(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    const Fft3Win W = wins[blockIdx.y];
+    const T* __restrict__ g = static_cast<const T*>(W.grid);
+    C* __restrict__ A = static_cast<C*>(W.buf1);
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    const int n = W.n, nos = W.nos;
+    const int64_t tot = (int64_t)W.B[0] * W.B[1] * n;
+    const int z0v = box_value0(W.lo[2], nos);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % n) - n / 2;
+        const int y = (int)((idx / n) % W.B[1]);
+        const int x = (int)(idx / ((int64_t)n * W.B[1]));
+        const int64_t row = ((int64_t)modp(W.lo[0] + x, nos) * nos + modp(W.lo[1] + y, nos)) * nos;
+        int r = modp(kz * z0v, nos);
+        const int step = modp(kz, nos);
+        int gz = modp(W.lo[2], nos);
+        T ar = T(0), ai = T(0);
+        for (int z = 0; z < W.B[2]; z++) {
+            const T v = g[row + gz];
+            const C w = tw[r];
+            ar = fma(v, w.x, ar);
+            ai = fma(v, w.y, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+            if (++gz == nos) gz = 0;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        A[idx] = o;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    const Fft3Win W = wins[blockIdx.y];
+    const C* __restrict__ A = static_cast<const C*>(W.buf1);
+    C* __restrict__ Bo = static_cast<C*>(W.buf2);
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    const int n = W.n, nos = W.nos, By = W.B[1];
+    const int64_t tot = (int64_t)W.B[0] * n * n;
+    const int y0v = box_value0(W.lo[1], nos);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % n);
+        const int ky = (int)((idx / n) % n) - n / 2;
+        const int x = (int)(idx / ((int64_t)n * n));
+        int r = modp(ky * y0v, nos);
+        const int step = modp(ky, nos);
+        T ar = T(0), ai = T(0);
+        const C* a = A + (int64_t)x * By * n + kz;
+        for (int y = 0; y < By; y++) {
+            cmac(a[(int64_t)y * n], tw[r], 0, ar, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        Bo[idx] = o;
+    }
+}
+
+// Fused middle pass along x for up to 32 consecutive kz of one ky per block:
+// H[kx] = D[kx] sum_x B[x] e^{-2 pi i kx x/nos}, then C[x] = sum_kx H[kx] e^{+...}.
+constexpr int kMidLanes = 32, kMidWarps = 8, kMaxN3 = 64, kMaxBox3 = 256;
+template <typename T>
+__global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    __shared__ C sH[kMaxN3][kMidLanes];
+    const Fft3Win W = wins[blockIdx.y];
+    const int n = W.n, nos = W.nos, Bx = W.B[0];
+    const int lines_per_ky = (n + kMidLanes - 1) / kMidLanes;
+    if ((int)blockIdx.x >= n * lines_per_ky) return;
+    const int lane = threadIdx.x % kMidLanes, warp = threadIdx.x / kMidLanes;
+    const int ky = blockIdx.x / lines_per_ky;
+    const int kz = (blockIdx.x % lines_per_ky) * kMidLanes + lane;
+    const bool ok = kz < n;
+    const C* __restrict__ Bi = static_cast<const C*>(W.buf2);
+    C* __restrict__ Co = static_cast<C*>(W.buf1);
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    const T* __restrict__ D = static_cast<const T*>(W.D);
+    const int x0v = box_value0(W.lo[0], nos);
+    for (int kx = warp; kx < n; kx += kMidWarps) {
+        const int kxv = kx - n / 2;
+        int r = modp(kxv * x0v, nos);
+        const int step = modp(kxv, nos);
+        T ar = T(0), ai = T(0);
+        for (int x = 0; x < Bx; x++) {
+            C v;
+            v.x = T(0);
+            v.y = T(0);
+            if (ok) v = Bi[((int64_t)x * n + ky) * n + kz];
+            cmac(v, tw[r], 0, ar, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        const T dk = ok ? D[((int64_t)kx * n + ky) * n + kz] : T(0);
+        C h;
+        h.x = ar * dk;
+        h.y = ai * dk;
+        sH[kx][lane] = h;
+    }
+    __syncthreads();
+    for (int x = warp; x < Bx; x += kMidWarps) {
+        const int xv = modp(W.lo[0] + x, nos) - nos / 2;
+        int r = modp((-n / 2) * xv, nos);
+        const int step = modp(xv, nos);
+        T ar = T(0), ai = T(0);
+        for (int kx = 0; kx < n; kx++) {
+            cmac(sH[kx][lane], tw[r], 1, ar, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        if (ok) {
+            C o;
+            o.x = ar;
+            o.y = ai;
+            Co[((int64_t)x * n + ky) * n + kz] = o;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft3_i2(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    const Fft3Win W = wins[blockIdx.y];
+    const C* __restrict__ Ci = static_cast<const C*>(W.buf1);
+    C* __restrict__ E = static_cast<C*>(W.buf2);
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    const int n = W.n, nos = W.nos, By = W.B[1];
+    const int64_t tot = (int64_t)W.B[0] * By * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % n);
+        const int y = (int)((idx / n) % By);
+        const int x = (int)(idx / ((int64_t)n * By));
+        const int yv = modp(W.lo[1] + y, nos) - nos / 2;
+        int r = modp((-n / 2) * yv, nos);
+        const int step = modp(yv, nos);
+        T ar = T(0), ai = T(0);
+        const C* c = Ci + (int64_t)x * n * n + kz;
+        for (int ky = 0; ky < n; ky++) {
+            cmac(c[(int64_t)ky * n], tw[r], 1, ar, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        E[idx] = o;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft3_i3(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    const Fft3Win W = wins[blockIdx.y];
+    const C* __restrict__ E = static_cast<const C*>(W.buf2);
+    T* __restrict__ g = static_cast<T*>(W.grid);
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
+    const int64_t tot = (int64_t)W.B[0] * By * Bz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(idx % Bz);
+        const int y = (int)((idx / Bz) % By);
+        const int x = (int)(idx / ((int64_t)Bz * By));
+        const int gz = modp(W.lo[2] + z, nos);
+        const int zv = gz - nos / 2;
+        int r = modp((-n / 2) * zv, nos);
+        const int step = modp(zv, nos);
+        const C* e = E + ((int64_t)x * By + y) * n;
+        T ar = T(0);
+        for (int kz = 0; kz < n; kz++) {
+            const C v = e[kz];
+            const C w = tw[r];
+            // real part of v * conj(w)
+            ar = fma(v.x, w.x, fma(v.y, w.y, ar));
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        g[((int64_t)modp(W.lo[0] + x, nos) * nos + modp(W.lo[1] + y, nos)) * nos + gz] = ar;
+    }
+}
+
+bool fft3_box_supported(const WindowPlan& w) {
+    return w.dA == 3 && w.n <= kMaxN3 && w.box_ext[0] <= kMaxBox3;
+}
+
+// every batched window: one launch per pass for all of them
+template <typename T>
+anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
+    const int nw = (int)plan->fft3_windows.size();
+    if (nw == 0) return ANOVA_OK;
+    const Fft3Win* wins = plan->fft3_desc + (sizeof(T) == 8 ? 0 : nw);
+    const int cap = 4 * plan->sm_count;
+    int64_t t1 = 0, t2 = 0, t3 = 0;
+    int nmax = 0;
+    for (int k = 0; k < nw; k++) {
+        const WindowPlan& w = plan->win[plan->fft3_windows[k]];
+        t1 = std::max<int64_t>(t1, (int64_t)w.box_ext[0] * w.box_ext[1] * w.n);
+        t2 = std::max<int64_t>(t2, (int64_t)w.box_ext[0] * w.n * w.n);
+        t3 = std::max<int64_t>(t3, (int64_t)w.box_ext[0] * w.box_ext[1] * w.box_ext[2]);
+        nmax = std::max(nmax, w.n);
+    }
+    const dim3 g1(grid_for(t1, kThreads, cap), nw), g2(grid_for(t2, kThreads, cap), nw);
+    const dim3 gm(nmax * ((nmax + kMidLanes - 1) / kMidLanes), nw), g3(grid_for(t3, kThreads, cap), nw);
+    k_fft3_f1<T><<<g1, kThreads, 0, st>>>(wins);
+    k_fft3_f2<T><<<g2, kThreads, 0, st>>>(wins);
+    k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, 0, st>>>(wins);
+    k_fft3_i2<T><<<g1, kThreads, 0, st>>>(wins);
+    k_fft3_i3<T><<<g3, kThreads, 0, st>>>(wins);
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+template anova_status fft3_box_all<float>(anova_plan*, cudaStream_t);
+template anova_status fft3_box_all<double>(anova_plan*, cudaStream_t);
+
+}  // namespace anova

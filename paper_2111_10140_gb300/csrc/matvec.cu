@@ -100,8 +100,13 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
     clock_end(plan, 0, nl, st);
     nl = 0;
     clock_begin(plan, 1, st);
+    if (!plan->fft3_windows.empty()) {
+        ANOVA_TRY(fft3_box_all<T>(plan, st));
+        nl += 5;
+    }
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];
+        if (fft3_box_supported(w)) continue;
         ANOVA_TRY(fft_convolve_window<T>(plan, w, grid_of<T>(plan, w), st));
         nl += 2 * w.dA;
     }

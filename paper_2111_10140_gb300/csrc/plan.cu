@@ -521,6 +521,59 @@ static void choose_bins(WindowPlan& w, int m) {
     w.R = T + 2 * m;
 }
 
+// min / max cell index per axis over the binned nodes (ints: min at 2t, max at 2t+1)
+__global__ void k_cell_range(const int32_t* __restrict__ cell, int64_t N, int dA, int* __restrict__ mm) {
+    int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {-1, -1, -1};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int t = 0; t < dA; t++) {
+            const int c = cell[t * N + i];
+            lo[t] = min(lo[t], c);
+            hi[t] = max(hi[t], c);
+        }
+    for (int t = 0; t < dA; t++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[t] = min(lo[t], __shfl_xor_sync(0xffffffffu, lo[t], o));
+            hi[t] = max(hi[t], __shfl_xor_sync(0xffffffffu, hi[t], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[2 * t], lo[t]);
+            atomicMax(&mm[2 * t + 1], hi[t]);
+        }
+    }
+}
+
+// Box of grid cells that spreading writes and gathering reads: the union of
+// the regions [bin*T - m, bin*T + T + m) of the occupied bins, per axis.
+static anova_status window_box(anova_plan* plan, WindowPlan& w, cudaStream_t st) {
+    for (int t = 0; t < 3; t++) {
+        w.box_lo[t] = 0;
+        w.box_ext[t] = (t < w.dA) ? w.nos : 1;
+    }
+    if (w.X.N == 0) return ANOVA_OK;
+    int* mm = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&mm, 6 * sizeof(int)));
+    int init[6] = {INT32_MAX, -1, INT32_MAX, -1, INT32_MAX, -1};
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    k_cell_range<<<grid_for(w.X.N, kThreads, 2 * plan->sm_count), kThreads, 0, st>>>(w.X.cell, w.X.N, w.dA, mm);
+    ANOVA_CHECK_LAUNCH();
+    int h[6];
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(mm);
+    for (int t = 0; t < w.dA; t++) {
+        const int blo = h[2 * t] / w.T, bhi = h[2 * t + 1] / w.T;
+        const int ext = (bhi - blo + 1) * w.T + 2 * plan->m;
+        if (ext >= w.nos) {
+            w.box_lo[t] = 0;
+            w.box_ext[t] = w.nos;
+        } else {
+            w.box_lo[t] = blo * w.T - plan->m;
+            w.box_ext[t] = ext;
+        }
+    }
+    return ANOVA_OK;
+}
+
 // Frame-dependent part of a window: scaled width, multiplier D_k, binned nodes.
 static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* frame,
                                  double* scratch, cudaStream_t st) {
@@ -548,7 +601,8 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
                                          want32 ? w.D32 : nullptr);
     ANOVA_CHECK_LAUNCH();
     (void)want64;
-    return build_pointset(plan, w, w.xw, plan->N, w.dA, w.centre, w.scale, w.X, st);
+    ANOVA_TRY(build_pointset(plan, w, w.xw, plan->N, w.dA, w.centre, w.scale, w.X, st));
+    return window_box(plan, w, st);
 }
 
 // tag the sub-problems of window slot w and append them to the merged list
@@ -605,6 +659,46 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
     }
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->dense_desc, desc.data(), 2 * nd * sizeof(DenseWin),
+                                   cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    return ANOVA_OK;
+}
+
+// Descriptors of the 3-D windows that use the batched box FFT.
+static anova_status build_fft3_batch(anova_plan* plan, cudaStream_t st) {
+    plan->fft3_windows.clear();
+    for (int l = 0; l < plan->P; l++)
+        if (fft3_box_supported(plan->win[l])) plan->fft3_windows.push_back(l);
+    const int nw = (int)plan->fft3_windows.size();
+    if (nw == 0) return ANOVA_OK;
+    std::vector<Fft3Win> desc(2 * nw);
+    for (int k = 0; k < nw; k++) {
+        const WindowPlan& w = plan->win[plan->fft3_windows[k]];
+        for (int prec = 0; prec < 2; prec++) {
+            Fft3Win& d = desc[prec * nw + k];
+            if (prec == 0) {
+                d.grid = static_cast<double*>(plan->grid) + w.grid_off;
+                d.buf1 = static_cast<double2*>(plan->work1) + w.work_off;
+                d.buf2 = static_cast<double2*>(plan->work2) + w.work_off;
+                d.tw = w.tw64;
+                d.D = w.D64;
+            } else {
+                d.grid = static_cast<float*>(plan->grid) + w.grid_off;
+                d.buf1 = static_cast<float2*>(plan->work1) + w.work_off;
+                d.buf2 = static_cast<float2*>(plan->work2) + w.work_off;
+                d.tw = w.tw32;
+                d.D = w.D32;
+            }
+            for (int t = 0; t < 3; t++) {
+                d.lo[t] = w.box_lo[t];
+                d.B[t] = w.box_ext[t];
+            }
+            d.n = w.n;
+            d.nos = w.nos;
+        }
+    }
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->fft3_desc, 2 * nw * sizeof(Fft3Win)));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->fft3_desc, desc.data(), 2 * nw * sizeof(Fft3Win),
                                    cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     return ANOVA_OK;
@@ -730,6 +824,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
         if (s == ANOVA_OK) s = window_setup(plan, w, frame, scratch, st);
     }
     if (s == ANOVA_OK) s = build_dense_batch(plan, st);
+    if (s == ANOVA_OK) s = build_fft3_batch(plan, st);
     if (s == ANOVA_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
@@ -949,6 +1044,7 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->eta_dev);
     cudaFree(plan->dense_sub);
     cudaFree(plan->dense_desc);
+    cudaFree(plan->fft3_desc);
     cudaFree(plan->cg_vec);
     cudaFree(plan->cg_scal);
     cudaFree(plan->cg_part);
