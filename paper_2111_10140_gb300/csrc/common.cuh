@@ -41,6 +41,8 @@ constexpr int kMaxM = 12;
 constexpr int kSubChunk = 256;         // points per spread/gather sub-problem
 constexpr int kThreads = 256;
 constexpr int kMaxBins = 32768;        // bins per window (shared histogram of the sort)
+constexpr int kPsiDeg = 8;             // degree of the per-interval window polynomials (FP32 path)
+constexpr int kPsiStride = kPsiDeg + 1;
 
 // Points of one window, binned and sorted (one for the training nodes X,
 // one per predict call for the test nodes Z).
@@ -117,6 +119,7 @@ struct anova_plan {
     int d = 0, P = 0, m = 0, p = 0, precision = 0;
     double sigma = 2.0, epsB = 1.0 / 16, ell = 0.0, b = 0.0;
     double psi_norm = 1.0;              // m / sinh(b m): psi(t) = psi_norm * sinh(b s)/s
+    float* psi_poly = nullptr;          // 2m x kPsiStride: psi(q - m + f) ~ sum_k c_k (f - 1/2)^k
     std::vector<anova::WindowPlan> win;
     // work buffers: every window has its own grid and FFT work arrays (offsets in WindowPlan)
     size_t grid_elems = 0, work_elems = 0;  // totals over the windows
@@ -155,6 +158,20 @@ __device__ __forceinline__ T kb_psi(T t, T m, T b, T norm) {
     T s = sqrt(s2);
     T r = (s > T(0)) ? sinh(b * s) / s : b;
     return norm * r;
+}
+
+// FP32 window weight from the per-interval polynomials: t = j + f with integer
+// j and f in [0, 1); zero outside [-m, m) (the single point t = m, where psi is
+// about 1e-7 of its peak or less, is dropped in FP32).
+__device__ __forceinline__ float psi_poly_eval(const float* __restrict__ P, int j, float f, int m) {
+    const int q = j + m;
+    if (q < 0 || q >= 2 * m) return 0.f;
+    const float* c = P + q * kPsiStride;
+    const float u = f - 0.5f;
+    float acc = c[kPsiDeg];
+#pragma unroll
+    for (int k = kPsiDeg - 1; k >= 0; k--) acc = fmaf(acc, u, c[k]);
+    return acc;
 }
 
 // ------------------------------------------------------------- host API

@@ -20,6 +20,8 @@
 // Both loops are plain FP32 (or FP64) multiply-adds: no atomics per tap.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace anova {
@@ -55,9 +57,13 @@ struct Vec4<double> {
 template <typename T, int R>
 __global__ void __launch_bounds__(kGatherThreads)
 k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, DenseWin one, int m, T b,
-                T norm) {
+                T norm, const float* __restrict__ poly) {
     static_assert(R <= kPitch, "region wider than the row pitch");
+    constexpr bool kPoly = std::is_same<T, float>::value;
     __shared__ __align__(16) T reg[R * R * kPitch];
+    __shared__ float sP[2 * 8 * kPsiStride];
+    if (kPoly)
+        for (int i = threadIdx.x; i < 2 * m * kPsiStride; i += blockDim.x) sP[i] = poly[i];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs ? descs[sp.w] : one;
     const int32_t* __restrict__ perm = W.perm;
@@ -85,18 +91,20 @@ k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
         const bool valid = q < sp.z;
         const int64_t pos = (int64_t)sp.y + (valid ? q : sp.z - 1);
         const T fx = frac[pos], fy = frac[N + pos], fz = frac[2 * N + pos];
-        const T tx = (T)(cell[pos] - Tb * bx) + mm + fx;
-        const T ty = (T)(cell[N + pos] - Tb * by) + mm + fy;
-        const T tz = (T)(cell[2 * N + pos] - Tb * bz) + mm + fz;
+        const int jx = cell[pos] - Tb * bx + m, jy = cell[N + pos] - Tb * by + m, jz = cell[2 * N + pos] - Tb * bz + m;
+        const T tx = (T)jx + fx, ty = (T)jy + fy, tz = (T)jz + fz;
         T wy[R], wz[kPitch];
 #pragma unroll
-        for (int r = 0; r < R; r++) wy[r] = kb_psi<T>(ty - (T)r, mm, b, norm);
+        for (int r = 0; r < R; r++)
+            wy[r] = kPoly ? (T)psi_poly_eval(sP, jy - r, (float)fy, m) : kb_psi<T>(ty - (T)r, mm, b, norm);
 #pragma unroll
-        for (int r = 0; r < kPitch; r++) wz[r] = (r < R) ? kb_psi<T>(tz - (T)r, mm, b, norm) : T(0);
+        for (int r = 0; r < kPitch; r++)
+            wz[r] = (r < R) ? (kPoly ? (T)psi_poly_eval(sP, jz - r, (float)fz, m) : kb_psi<T>(tz - (T)r, mm, b, norm))
+                            : T(0);
         T acc = T(0);
 #pragma unroll 1
         for (int a = 0; a < R; a++) {
-            const T wa = kb_psi<T>(tx - (T)a, mm, b, norm);
+            const T wa = kPoly ? (T)psi_poly_eval(sP, jx - a, (float)fx, m) : kb_psi<T>(tx - (T)a, mm, b, norm);
             const T* rows = reg + a * R * kPitch;
             T sa = T(0);
 #pragma unroll
@@ -123,7 +131,10 @@ k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
 template <typename T, int R>
 __global__ void __launch_bounds__(R * (R / 2 + R % 2) * 2)
 k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, DenseWin one,
-                const void* __restrict__ alpha, int alpha_double, int m, T b, T norm) {
+                const void* __restrict__ alpha, int alpha_double, int m, T b, T norm,
+                const float* __restrict__ poly) {
+    constexpr bool kPoly = std::is_same<T, float>::value;
+    __shared__ float sP[2 * 8 * kPsiStride];
     static_assert(R <= kPitch, "region wider than the row pitch");
     constexpr int BP = R / 2 + R % 2;          // pairs of b rows
     constexpr int NT = R * BP * 2;             // threads: a x b-pair x c-half
@@ -149,6 +160,8 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
 #pragma unroll
         for (int k = 0; k < 8; k++) acc[i][k] = T(0);
 
+    if (kPoly)
+        for (int i = tid; i < 2 * m * kPsiStride; i += NT) sP[i] = poly[i];
     for (int first = 0; first < sp.z; first += kSpreadChunk) {
         const int cnt = min(kSpreadChunk, sp.z - first);
         __syncthreads();
@@ -157,8 +170,10 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
             const int r = i % kPitch, ax = (i / kPitch) % 3, p = i / (3 * kPitch);
             const int64_t pos = (int64_t)sp.y + first + p;
             const int bcoord = (ax == 0) ? bx : (ax == 1) ? by : bz;
-            const T t = (T)(cell[ax * N + pos] - Tb * bcoord) + mm + frac[ax * N + pos] - (T)r;
-            T w = (r < R) ? kb_psi<T>(t, mm, b, norm) : T(0);
+            const int j = cell[ax * N + pos] - Tb * bcoord + m - r;
+            const T f = frac[ax * N + pos];
+            T w = T(0);
+            if (r < R) w = kPoly ? (T)psi_poly_eval(sP, j, (float)f, m) : kb_psi<T>((T)j + f, mm, b, norm);
             if (ax == 0) {
                 if (r < R) {
                     const int32_t src = perm[pos];
@@ -217,14 +232,14 @@ static void launch_spread(anova_plan* plan, const int4* sub, int nsub, const Den
                           const void* alpha, int alpha_double, cudaStream_t st) {
     constexpr int NT = R * (R / 2 + R % 2) * 2;
     k_spread3_dense<T, R><<<nsub, NT, 0, st>>>(sub, descs, one, alpha, alpha_double, plan->m, (T)plan->b,
-                                               (T)plan->psi_norm);
+                                               (T)plan->psi_norm, plan->psi_poly);
 }
 
 template <typename T, int R>
 static void launch_gather(anova_plan* plan, const int4* sub, int nsub, const DenseWin* descs, const DenseWin& one,
                           cudaStream_t st) {
     k_gather3_dense<T, R><<<nsub, kGatherThreads, 0, st>>>(sub, descs, one, plan->m, (T)plan->b,
-                                                           (T)plan->psi_norm);
+                                                           (T)plan->psi_norm, plan->psi_poly);
 }
 
 template <typename T>

@@ -474,6 +474,55 @@ __global__ void k_deconvolve(const double* __restrict__ f, int dA, int n, int no
     }
 }
 
+// Per-interval polynomials of the normalised window for the FP32 kernels:
+// on t in [q - m, q - m + 1), psi(t) is interpolated at kPsiDeg+1 Chebyshev
+// points in f = t - (q - m) and rewritten in powers of u = f - 1/2 (FP64).
+__global__ void k_psi_poly_fit(int m, double b, double norm, float* __restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 2 * m) return;
+    constexpr int D = kPsiDeg, K = kPsiDeg + 1;
+    double val[K], cheb[K];
+    for (int k = 0; k < K; k++) {
+        const double f = 0.5 + 0.5 * cospi((k + 0.5) / K);
+        const double t = (double)(q - m) + f;
+        const double s2 = (double)m * m - t * t;
+        double v = 0.0;
+        if (s2 > 0.0) {
+            const double s = sqrt(s2);
+            v = norm * sinh(b * s) / s;
+        } else if (s2 == 0.0) {
+            v = norm * b;
+        }
+        val[k] = v;
+    }
+    for (int i = 0; i < K; i++) {       // Chebyshev coefficients in x = 2u
+        double a = 0.0;
+        for (int k = 0; k < K; k++) a += val[k] * cospi(i * (k + 0.5) / K);
+        cheb[i] = a * 2.0 / K;
+    }
+    cheb[0] *= 0.5;
+    // sum_i cheb_i T_i(x) in powers of x, via T_{i+1} = 2x T_i - T_{i-1}
+    double mono[K], tm[K], tc[K], tn[K];
+    for (int k = 0; k < K; k++) { mono[k] = 0.0; tm[k] = 0.0; tc[k] = 0.0; }
+    tm[0] = 1.0;                        // T_0
+    tc[1] = 1.0;                        // T_1
+    mono[0] += cheb[0];
+    if (D >= 1) mono[1] += cheb[1];
+    for (int i = 2; i <= D; i++) {
+        for (int k = 0; k < K; k++) tn[k] = -tm[k] + ((k > 0) ? 2.0 * tc[k - 1] : 0.0);
+        for (int k = 0; k < K; k++) {
+            mono[k] += cheb[i] * tn[k];
+            tm[k] = tc[k];
+            tc[k] = tn[k];
+        }
+    }
+    double sc = 1.0;                    // x^k = 2^k u^k
+    for (int k = 0; k < K; k++) {
+        out[q * kPsiStride + k] = (float)(mono[k] * sc);
+        sc *= 2.0;
+    }
+}
+
 // exp(-2 pi i r / nos)
 __global__ void k_twiddles(int nos, double2* __restrict__ tw64, float2* __restrict__ tw32) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nos; r += gridDim.x * blockDim.x) {
@@ -764,6 +813,9 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     plan->b = M_PI * (2.0 - 1.0 / sigma);
     plan->psi_norm = (double)m / std::sinh(plan->b * m);
     plan->win.resize(P);
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->psi_poly, 2 * m * kPsiStride * sizeof(float)));
+    k_psi_poly_fit<<<1, 64, 0, st>>>(m, plan->b, plan->psi_norm, plan->psi_poly);
+    ANOVA_CHECK_LAUNCH();
     size_t max_tk = 1;
     for (int l = 0; l < P; l++) {
         WindowPlan& w = plan->win[l];
@@ -1045,6 +1097,7 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->dense_sub);
     cudaFree(plan->dense_desc);
     cudaFree(plan->fft3_desc);
+    cudaFree(plan->psi_poly);
     cudaFree(plan->cg_vec);
     cudaFree(plan->cg_scal);
     cudaFree(plan->cg_part);
