@@ -76,6 +76,7 @@ struct WindowPlan {
     double* xw = nullptr;      // N x dA window coordinates (user units, original order)
     size_t grid_off = 0;       // element offset of this window's grid in plan->grid
     size_t work_off = 0;       // element offset of this window's FFT work arrays
+    float* wtab = nullptr;     // dense 3-D windows, FP32 plans: N x 3 x 16 zero-padded window weights (sorted order)
     int box_lo[kMaxDim] = {0, 0, 0};   // grid cells touched by the training nodes: start (may be < 0)
     int box_ext[kMaxDim] = {0, 0, 0};  // and extent per axis (<= nos)
     PointSet X;
@@ -97,6 +98,7 @@ struct DenseWin {
     const int32_t* perm;
     const int32_t* cell;
     const void* frac;          // FP32 or FP64, as the launch
+    const float* wtab;         // FP32 weight table (N x 48) or null
     void* grid;                // this window's grid
     void* out;                 // gather output (this window's slice of plan->tmp)
     int64_t N;

@@ -220,6 +220,161 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
     }
 }
 
+// --------------------------------------------------- FP32 with weight table
+// Packed FP32 multiply-add on (x, y) pairs.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+    unsigned long long rc = *reinterpret_cast<unsigned long long*>(&c);
+    unsigned long long rd;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    return *reinterpret_cast<float2*>(&rd);
+}
+
+// Gather, FP32, weights read from the plan's table.  For every x-row a the
+// lane accumulates t[c] = sum_b wy[b] h[a][b][c] as c-pairs (packed FMA), then
+// s += wx[a] * sum_c wz[c] t[c].
+template <int R>
+__global__ void __launch_bounds__(kGatherThreads)
+k_gather3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
+    static_assert(R <= kPitch && R % 2 == 0, "even region up to the row pitch");
+    constexpr int RP = R / 2;                      // c-pairs per row
+    __shared__ __align__(16) float reg[R * R * kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    const float* __restrict__ h = static_cast<const float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
+    for (int i = threadIdx.x; i < R * R * kPitch; i += blockDim.x) {
+        const int c = i % kPitch, ab = i / kPitch;
+        const int bb = ab % R, a = ab / R;
+        float v = 0.f;
+        if (c < R)
+            v = h[((int64_t)wrap_idx(ox + a, nos) * nos + wrap_idx(oy + bb, nos)) * nos + wrap_idx(oz + c, nos)];
+        reg[i] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float* __restrict__ out = static_cast<float*>(W.out);
+    for (int base = threadIdx.x - lane; base < sp.z; base += blockDim.x) {
+        const int q = base + lane;
+        const bool valid = q < sp.z;
+        const int64_t pos = (int64_t)sp.y + (valid ? q : sp.z - 1);
+        const float4* __restrict__ wp = reinterpret_cast<const float4*>(W.wtab + pos * 48);
+        float wy[16];
+        float2 wz[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float4 v = wp[4 + k];
+            wy[4 * k] = v.x; wy[4 * k + 1] = v.y; wy[4 * k + 2] = v.z; wy[4 * k + 3] = v.w;
+            const float4 z = wp[8 + k];
+            wz[2 * k] = make_float2(z.x, z.y);
+            wz[2 * k + 1] = make_float2(z.z, z.w);
+        }
+        const float* __restrict__ wx = W.wtab + pos * 48;
+        float acc = 0.f;
+#pragma unroll 1
+        for (int a = 0; a < R; a++) {
+            const float4* rows = reinterpret_cast<const float4*>(reg + a * R * kPitch);
+            float2 t[RP];
+#pragma unroll
+            for (int k = 0; k < RP; k++) t[k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int bb = 0; bb < R; bb++) {
+                const float2 wb = make_float2(wy[bb], wy[bb]);
+#pragma unroll
+                for (int c4 = 0; c4 < (R + 3) / 4; c4++) {
+                    const float4 v = rows[bb * (kPitch / 4) + c4];
+                    if (2 * c4 < RP) t[2 * c4] = ffma2(wb, make_float2(v.x, v.y), t[2 * c4]);
+                    if (2 * c4 + 1 < RP) t[2 * c4 + 1] = ffma2(wb, make_float2(v.z, v.w), t[2 * c4 + 1]);
+                }
+            }
+            float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < RP; k++) s2 = ffma2(wz[k], t[k], s2);
+            acc = fmaf(__ldg(wx + a), s2.x + s2.y, acc);
+        }
+        if (valid) out[W.perm[pos]] = acc;
+    }
+}
+
+// Spread, FP32, weights read from the plan's table.  Thread (a, b-pair,
+// c-half) keeps its 2 x 8 region cells as packed pairs.
+template <int R>
+__global__ void __launch_bounds__(R * (R / 2) * 2)
+k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, const void* __restrict__ alpha,
+              int alpha_double, int m) {
+    static_assert(R <= kPitch && R % 2 == 0, "even region up to the row pitch");
+    constexpr int BP = R / 2;
+    constexpr int NT = R * BP * 2;
+    __shared__ __align__(16) float wxs[kSpreadChunk][kPitch];
+    __shared__ __align__(16) float wys[kSpreadChunk][kPitch];
+    __shared__ __align__(16) float wzs[kSpreadChunk][kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    float* __restrict__ grid = static_cast<float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int tid = threadIdx.x;
+    const int ch = tid & 1, bp = (tid >> 1) % BP, a = (tid >> 1) / BP;
+    const int b0 = 2 * bp, c0 = 8 * ch;
+    float2 acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc[i][k] = make_float2(0.f, 0.f);
+    for (int first = 0; first < sp.z; first += kSpreadChunk) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        __syncthreads();
+        // 12 float4 per node: x row scaled by alpha, then y and z rows
+        for (int i = tid; i < cnt * 12; i += NT) {
+            const int p = i / 12, k = i % 12;
+            const int64_t pos = (int64_t)sp.y + first + p;
+            float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
+            if (k < 4) {
+                const int32_t src = W.perm[pos];
+                const float al = alpha_double ? (float)(static_cast<const double*>(alpha)[src])
+                                              : static_cast<const float*>(alpha)[src];
+                v.x *= al; v.y *= al; v.z *= al; v.w *= al;
+                reinterpret_cast<float4*>(wxs[p])[k] = v;
+            } else if (k < 8) {
+                reinterpret_cast<float4*>(wys[p])[k - 4] = v;
+            } else {
+                reinterpret_cast<float4*>(wzs[p])[k - 8] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int p = 0; p < cnt; p++) {
+            const float wa = wxs[p][a];
+            const float2 wyp = *reinterpret_cast<const float2*>(&wys[p][b0]);
+            const float4 z0 = *reinterpret_cast<const float4*>(&wzs[p][c0]);
+            const float4 z1 = *reinterpret_cast<const float4*>(&wzs[p][c0 + 4]);
+            const float w0 = wa * wyp.x, w1 = wa * wyp.y;
+            const float2 W0 = make_float2(w0, w0), W1 = make_float2(w1, w1);
+            const float2 z[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
+                                 make_float2(z1.z, z1.w)};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                acc[0][k] = ffma2(W0, z[k], acc[0][k]);
+                acc[1][k] = ffma2(W1, z[k], acc[1][k]);
+            }
+        }
+    }
+    const int ga = wrap_idx(Tb * bx - m + a, nos);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int64_t rowbase = ((int64_t)ga * nos + wrap_idx(Tb * by - m + b0 + i, nos)) * nos;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int c = c0 + 2 * k;
+            if (c < R) atomicAdd(&grid[rowbase + wrap_idx(Tb * bz - m + c, nos)], acc[i][k].x);
+            if (c + 1 < R) atomicAdd(&grid[rowbase + wrap_idx(Tb * bz - m + c + 1, nos)], acc[i][k].y);
+        }
+    }
+}
+
 template <typename T>
 static const T* frac_of3(const PointSet& ps);
 template <>
@@ -283,6 +438,7 @@ static DenseWin single_desc(const WindowPlan& w, const PointSet& ps, const void*
     d.perm = ps.perm;
     d.cell = ps.cell;
     d.frac = frac;
+    d.wtab = nullptr;
     d.grid = grid;
     d.out = out;
     d.N = ps.N;
@@ -309,13 +465,52 @@ anova_status gather3_dense(anova_plan* plan, const WindowPlan& w, const PointSet
 }
 
 // all dense windows of the plan on their training nodes, one launch per region size
+// FP32 windows with a weight table and an even region use the packed kernels
+static bool table_kernels(const anova_plan* plan, int R) {
+    return (plan->precision & ANOVA_FP32) && R % 2 == 0 && R >= 4 && R <= 16;
+}
+
+static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
+                                 const void* alpha, int alpha_double, cudaStream_t st) {
+    if (nsub == 0) return ANOVA_OK;
+    switch (R) {
+#define ANOVA_SPREAD_T(R_) \
+    case R_: k_spread3_f32<R_><<<nsub, R_ * (R_ / 2) * 2, 0, st>>>(sub, descs, alpha, alpha_double, plan->m); break;
+        ANOVA_SPREAD_T(4) ANOVA_SPREAD_T(6) ANOVA_SPREAD_T(8) ANOVA_SPREAD_T(10) ANOVA_SPREAD_T(12)
+        ANOVA_SPREAD_T(14) ANOVA_SPREAD_T(16)
+#undef ANOVA_SPREAD_T
+        default: set_error("dense 3-D spread: unsupported region size"); return ANOVA_EINVAL;
+    }
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
+                                 cudaStream_t st) {
+    if (nsub == 0) return ANOVA_OK;
+    switch (R) {
+#define ANOVA_GATHER_T(R_) \
+    case R_: k_gather3_f32<R_><<<nsub, kGatherThreads, 0, st>>>(sub, descs, plan->m); break;
+        ANOVA_GATHER_T(4) ANOVA_GATHER_T(6) ANOVA_GATHER_T(8) ANOVA_GATHER_T(10) ANOVA_GATHER_T(12)
+        ANOVA_GATHER_T(14) ANOVA_GATHER_T(16)
+#undef ANOVA_GATHER_T
+        default: set_error("dense 3-D gather: unsupported region size"); return ANOVA_EINVAL;
+    }
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
-    for (const auto& g : plan->dense_groups)
-        ANOVA_TRY(spread_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), alpha,
-                                     alpha_double, st));
+    for (const auto& g : plan->dense_groups) {
+        if (sizeof(T) == 4 && table_kernels(plan, g[0]))
+            ANOVA_TRY(spread_table(plan, g[0], plan->dense_sub + g[1], g[2], descs, alpha, alpha_double, st));
+        else
+            ANOVA_TRY(spread_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), alpha,
+                                         alpha_double, st));
+    }
     return ANOVA_OK;
 }
 
@@ -323,8 +518,12 @@ template <typename T>
 anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
-    for (const auto& g : plan->dense_groups)
-        ANOVA_TRY(gather_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), st));
+    for (const auto& g : plan->dense_groups) {
+        if (sizeof(T) == 4 && table_kernels(plan, g[0]))
+            ANOVA_TRY(gather_table(plan, g[0], plan->dense_sub + g[1], g[2], descs, st));
+        else
+            ANOVA_TRY(gather_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), st));
+    }
     return ANOVA_OK;
 }
 

@@ -591,6 +591,43 @@ __global__ void k_cell_range(const int32_t* __restrict__ cell, int64_t N, int dA
     }
 }
 
+// FP32 weight table of a dense 3-D window: for sorted node pos and axis t,
+// wtab[(pos*3 + t)*16 + r] = psi(c_t - (bin_t*T - m) - r + f_t) for r < R, 0 for
+// R <= r < 16, evaluated in FP64 from the node's FP64 coordinates.
+__global__ void k_weight_table(const double* __restrict__ xw, const int32_t* __restrict__ perm, int64_t N,
+                               FrameArgs fr, int nos, int Tb, int R, int m, double b, double norm,
+                               float* __restrict__ wtab) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * 3;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pos = idx / 3;
+        const int t = (int)(idx % 3);
+        const int64_t i = perm[pos];
+        const double xt = fr.s * (xw[i * 3 + t] - fr.c[t]);
+        const double y = (double)nos * xt;
+        const double fl = floor(y);
+        const double f = y - fl;
+        int c = (int)fl + nos / 2;
+        c %= nos;
+        if (c < 0) c += nos;
+        const int j0 = c - (c / Tb) * Tb + m;
+        float* out = wtab + idx * 16;
+        for (int r = 0; r < 16; r++) {
+            double w = 0.0;
+            if (r < R) {
+                const double tt = (double)(j0 - r) + f;
+                const double s2 = (double)m * m - tt * tt;
+                if (s2 > 0.0) {
+                    const double sq = sqrt(s2);
+                    w = norm * sinh(b * sq) / sq;
+                } else if (s2 == 0.0) {
+                    w = norm * b;
+                }
+            }
+            out[r] = (float)w;
+        }
+    }
+}
+
 // Box of grid cells that spreading writes and gathering reads: the union of
 // the regions [bin*T - m, bin*T + T + m) of the occupied bins, per axis.
 static anova_status window_box(anova_plan* plan, WindowPlan& w, cudaStream_t st) {
@@ -651,6 +688,17 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
     ANOVA_CHECK_LAUNCH();
     (void)want64;
     ANOVA_TRY(build_pointset(plan, w, w.xw, plan->N, w.dA, w.centre, w.scale, w.X, st));
+    if (w.dense && want32 && plan->N > 0) {
+        cudaFree(w.wtab);
+        w.wtab = nullptr;
+        ANOVA_CUDA_TRY(cudaMalloc(&w.wtab, plan->N * 48 * sizeof(float)));
+        FrameArgs fr;
+        for (int t = 0; t < 3; t++) fr.c[t] = w.centre[t];
+        fr.s = w.scale;
+        k_weight_table<<<grid_for(plan->N * 3, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            w.xw, w.X.perm, plan->N, fr, w.nos, w.T, w.R, plan->m, plan->b, plan->psi_norm, w.wtab);
+        ANOVA_CHECK_LAUNCH();
+    }
     return window_box(plan, w, st);
 }
 
@@ -694,6 +742,7 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
             d.perm = w.X.perm;
             d.cell = w.X.cell;
             d.frac = prec == 0 ? (const void*)w.X.frac64 : (const void*)w.X.frac32;
+            d.wtab = prec == 0 ? nullptr : w.wtab;
             d.grid = prec == 0 ? (void*)(static_cast<double*>(plan->grid) + w.grid_off)
                                : (void*)(static_cast<float*>(plan->grid) + w.grid_off);
             const int l = plan->dense_windows[k];
@@ -924,6 +973,7 @@ anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M
 }
 
 void window_release_reframed(WindowPlan& w) {
+    cudaFree(w.wtab);
     cudaFree(w.D64);
     cudaFree(w.D32);
     free_pointset(w.X);
@@ -1082,6 +1132,7 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
 void anova_plan_destroy(anova_plan* plan) {
     if (!plan) return;
     for (auto& w : plan->win) {
+        cudaFree(w.wtab);
         cudaFree(w.D64);
         cudaFree(w.D32);
         cudaFree(w.tw64);
