@@ -234,7 +234,7 @@ def run_ours(args):
     P = len(w.windows)
     dom = 0 if stage_ms[0] >= stage_ms[2] else 2
     R = 2 + 2 * w.m
-    dom_name = f"k_spread3_dense<float,{R}>" if dom == 0 else f"k_gather3_dense<float,{R}>"
+    dom_name = f"k_spread3_f32<{R}>" if dom == 0 else f"k_gather3_f32<{R}>"
     per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
     launches_per_step = max(1, stage_launch[dom] // args.steps)
     # algorithmic work: one multiply-add (2 flop) per tap, node and window
