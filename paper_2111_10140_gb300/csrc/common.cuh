@@ -136,6 +136,7 @@ struct anova_plan {
     anova::DenseWin* dense_desc = nullptr;  // device, 2 x dense_windows.size(): FP64 then FP32
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
+    bool fft3_slab = false;             // every batched 3-D window fits the slab kernels
     void* tmp = nullptr;                // P x N per-window results (8 bytes each)
     double* eta_dev = nullptr;          // P window weights on the device
     // CG state
@@ -230,6 +231,7 @@ anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid,
 template <typename T>
 anova_status fft3_box_all(anova_plan* plan, cudaStream_t st);
 bool fft3_box_supported(const WindowPlan& w);
+bool fft3_slab_supported(const WindowPlan& w);
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st);
 template <typename T>

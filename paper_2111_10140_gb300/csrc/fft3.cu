@@ -234,8 +234,143 @@ __global__ void __launch_bounds__(kThreads) k_fft3_i3(const Fft3Win* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- slab form
+// For boxes up to kSlab cells per axis: one CTA per x-slab runs F1 and F2 in
+// shared memory (forward), one CTA per x-slab runs I2 and I3 (inverse); the
+// middle pass is k_fft3_mid.  Three launches instead of five, and every line
+// sum reads shared memory.
+constexpr int kSlab = 64;
+constexpr int kSlabThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    const Fft3Win W = wins[blockIdx.y];
+    const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
+    const int x = blockIdx.x;
+    if (x >= W.B[0]) return;
+    C* stw = reinterpret_cast<C*>(slab_raw);                  // nos twiddles
+    T* P = reinterpret_cast<T*>(stw + nos);                   // By x Bz real plane
+    C* Q = reinterpret_cast<C*>(P + ((By * Bz + 1) & ~1));    // By x n
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    for (int i = threadIdx.x; i < nos; i += blockDim.x) stw[i] = tw[i];
+    const T* __restrict__ g = static_cast<const T*>(W.grid);
+    const int gx = modp(W.lo[0] + x, nos);
+    for (int i = threadIdx.x; i < By * Bz; i += blockDim.x) {
+        const int y = i / Bz, z = i % Bz;
+        P[i] = g[((int64_t)gx * nos + modp(W.lo[1] + y, nos)) * nos + modp(W.lo[2] + z, nos)];
+    }
+    __syncthreads();
+    const int z0v = box_value0(W.lo[2], nos), y0v = box_value0(W.lo[1], nos);
+    for (int i = threadIdx.x; i < By * n; i += blockDim.x) {      // F1: z -> kz
+        const int y = i / n, kz = i % n - n / 2;
+        int r = modp(kz * z0v, nos);
+        const int step = modp(kz, nos);
+        T ar = T(0), ai = T(0);
+        const T* prow = P + y * Bz;
+        for (int z = 0; z < Bz; z++) {
+            const C w = stw[r];
+            ar = fma(prow[z], w.x, ar);
+            ai = fma(prow[z], w.y, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        Q[i] = o;
+    }
+    __syncthreads();
+    C* __restrict__ Bo = static_cast<C*>(W.buf2);
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {       // F2: y -> ky
+        const int ky = i / n - n / 2, kz = i % n;
+        int r = modp(ky * y0v, nos);
+        const int step = modp(ky, nos);
+        T ar = T(0), ai = T(0);
+        for (int y = 0; y < By; y++) {
+            cmac(Q[y * n + kz], stw[r], 0, ar, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        Bo[(int64_t)x * n * n + i] = o;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* __restrict__ wins) {
+    using C = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    const Fft3Win W = wins[blockIdx.y];
+    const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
+    const int x = blockIdx.x;
+    if (x >= W.B[0]) return;
+    C* stw = reinterpret_cast<C*>(slab_raw);       // nos twiddles
+    C* Cs = stw + nos;                             // n x n
+    C* E = Cs + n * n;                             // By x n
+    const C* __restrict__ tw = static_cast<const C*>(W.tw);
+    for (int i = threadIdx.x; i < nos; i += blockDim.x) stw[i] = tw[i];
+    const C* __restrict__ Ci = static_cast<const C*>(W.buf1) + (int64_t)x * n * n;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Cs[i] = Ci[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < By * n; i += blockDim.x) {      // I2: ky -> y
+        const int y = i / n, kz = i % n;
+        const int yv = modp(W.lo[1] + y, nos) - nos / 2;
+        int r = modp((-n / 2) * yv, nos);
+        const int step = modp(yv, nos);
+        T ar = T(0), ai = T(0);
+        for (int ky = 0; ky < n; ky++) {
+            cmac(Cs[ky * n + kz], stw[r], 1, ar, ai);
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        E[i] = o;
+    }
+    __syncthreads();
+    T* __restrict__ g = static_cast<T*>(W.grid);
+    const int gx = modp(W.lo[0] + x, nos);
+    for (int i = threadIdx.x; i < By * Bz; i += blockDim.x) {     // I3: kz -> z, real part
+        const int y = i / Bz, z = i % Bz;
+        const int gz = modp(W.lo[2] + z, nos);
+        const int zv = gz - nos / 2;
+        int r = modp((-n / 2) * zv, nos);
+        const int step = modp(zv, nos);
+        T ar = T(0);
+        const C* e = E + y * n;
+        for (int kz = 0; kz < n; kz++) {
+            const C v = e[kz];
+            const C w = stw[r];
+            ar = fma(v.x, w.x, fma(v.y, w.y, ar));
+            r += step;
+            if (r >= nos) r -= nos;
+        }
+        g[((int64_t)gx * nos + modp(W.lo[1] + y, nos)) * nos + gz] = ar;
+    }
+}
+
+template <typename T>
+static size_t slab_fwd_bytes(int nos, int By, int Bz, int n) {
+    using C = typename C2<T>::type;
+    return nos * sizeof(C) + ((By * Bz + 1) & ~1) * sizeof(T) + (size_t)By * n * sizeof(C);
+}
+template <typename T>
+static size_t slab_inv_bytes(int nos, int By, int n) {
+    using C = typename C2<T>::type;
+    return (nos + (size_t)n * n + (size_t)By * n) * sizeof(C);
+}
+
 bool fft3_box_supported(const WindowPlan& w) {
     return w.dA == 3 && w.n <= kMaxN3 && w.box_ext[0] <= kMaxBox3;
+}
+
+bool fft3_slab_supported(const WindowPlan& w) {
+    return fft3_box_supported(w) && w.box_ext[1] <= kSlab && w.box_ext[2] <= kSlab && w.nos <= 4 * kSlab;
 }
 
 // every batched window: one launch per pass for all of them
@@ -256,6 +391,30 @@ anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
     }
     const dim3 g1(grid_for(t1, kThreads, cap), nw), g2(grid_for(t2, kThreads, cap), nw);
     const dim3 gm(nmax * ((nmax + kMidLanes - 1) / kMidLanes), nw), g3(grid_for(t3, kThreads, cap), nw);
+    if (plan->fft3_slab) {
+        int bxmax = 0, nosmax = 0, bymax = 0, bzmax = 0;
+        for (int k = 0; k < nw; k++) {
+            const WindowPlan& w = plan->win[plan->fft3_windows[k]];
+            bxmax = std::max(bxmax, w.box_ext[0]);
+            bymax = std::max(bymax, w.box_ext[1]);
+            bzmax = std::max(bzmax, w.box_ext[2]);
+            nosmax = std::max(nosmax, w.nos);
+        }
+        const size_t shf = slab_fwd_bytes<T>(nosmax, bymax, bzmax, nmax);
+        const size_t shi = slab_inv_bytes<T>(nosmax, bymax, nmax);
+        static bool attrs = [] {
+            cudaFuncSetAttribute(k_fft3_slab_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_fft3_slab_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            return true;
+        }();
+        (void)attrs;
+        const dim3 gs(bxmax, nw);
+        k_fft3_slab_fwd<T><<<gs, kSlabThreads, shf, st>>>(wins);
+        k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, 0, st>>>(wins);
+        k_fft3_slab_inv<T><<<gs, kSlabThreads, shi, st>>>(wins);
+        ANOVA_CHECK_LAUNCH();
+        return ANOVA_OK;
+    }
     k_fft3_f1<T><<<g1, kThreads, 0, st>>>(wins);
     k_fft3_f2<T><<<g2, kThreads, 0, st>>>(wins);
     k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, 0, st>>>(wins);

@@ -102,7 +102,7 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
     clock_begin(plan, 1, st);
     if (!plan->fft3_windows.empty()) {
         ANOVA_TRY(fft3_box_all<T>(plan, st));
-        nl += 5;
+        nl += plan->fft3_slab ? 3 : 5;
     }
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];

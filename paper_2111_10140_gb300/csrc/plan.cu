@@ -769,6 +769,8 @@ static anova_status build_fft3_batch(anova_plan* plan, cudaStream_t st) {
         if (fft3_box_supported(plan->win[l])) plan->fft3_windows.push_back(l);
     const int nw = (int)plan->fft3_windows.size();
     if (nw == 0) return ANOVA_OK;
+    plan->fft3_slab = true;
+    for (int l : plan->fft3_windows) plan->fft3_slab = plan->fft3_slab && fft3_slab_supported(plan->win[l]);
     std::vector<Fft3Win> desc(2 * nw);
     for (int k = 0; k < nw; k++) {
         const WindowPlan& w = plan->win[plan->fft3_windows[k]];
