@@ -231,14 +231,25 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return *reinterpret_cast<float2*>(&rd);
 }
 
-// Gather, FP32, weights read from the plan's table.  For every x-row a the
-// lane accumulates t[c] = sum_b wy[b] h[a][b][c] as c-pairs (packed FMA), then
-// s += wx[a] * sum_c wz[c] t[c].
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+    unsigned long long rd;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2*>(&rd);
+}
+
+// Gather, FP32, weights read from the plan's table.  Every lane handles two
+// nodes of the bin; each row h[a][b][:] is read once (broadcast) and
+// contracted against both nodes' z weights (packed FMA), then
+// s += wx[a] wy[b] (row . wz) per node.
+constexpr int kGather2Threads = 128;
 template <int R>
-__global__ void __launch_bounds__(kGatherThreads)
+__global__ void __launch_bounds__(kGather2Threads, 3)
 k_gather3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
     static_assert(R <= kPitch && R % 2 == 0, "even region up to the row pitch");
     constexpr int RP = R / 2;                      // c-pairs per row
+    constexpr int NV = (R + 3) / 4;                // float4 per row
     __shared__ __align__(16) float reg[R * R * kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
@@ -255,52 +266,72 @@ k_gather3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
         reg[i] = v;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* __restrict__ out = static_cast<float*>(W.out);
-    for (int base = threadIdx.x - lane; base < sp.z; base += blockDim.x) {
-        const int q = base + lane;
-        const bool valid = q < sp.z;
-        const int64_t pos = (int64_t)sp.y + (valid ? q : sp.z - 1);
-        const float4* __restrict__ wp = reinterpret_cast<const float4*>(W.wtab + pos * 48);
-        float wy[16];
-        float2 wz[8];
+    for (int base = warp * 64; base < sp.z; base += (kGather2Threads / 32) * 64) {
+        const int q0 = base + lane, q1 = base + 32 + lane;
+        const bool v0 = q0 < sp.z, v1 = q1 < sp.z;
+        const int64_t p0 = (int64_t)sp.y + (v0 ? q0 : sp.z - 1);
+        const int64_t p1 = (int64_t)sp.y + (v1 ? q1 : sp.z - 1);
+        float wy0[R], wy1[R];
+        float2 wz0[RP], wz1[RP];
+        {
+            const float* a0 = W.wtab + p0 * 48;
+            const float* a1 = W.wtab + p1 * 48;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float4 v = wp[4 + k];
-            wy[4 * k] = v.x; wy[4 * k + 1] = v.y; wy[4 * k + 2] = v.z; wy[4 * k + 3] = v.w;
-            const float4 z = wp[8 + k];
-            wz[2 * k] = make_float2(z.x, z.y);
-            wz[2 * k + 1] = make_float2(z.z, z.w);
+            for (int k = 0; k < NV; k++) {
+                const float4 y0 = reinterpret_cast<const float4*>(a0 + 16)[k];
+                const float4 y1 = reinterpret_cast<const float4*>(a1 + 16)[k];
+                const float4 z0 = reinterpret_cast<const float4*>(a0 + 32)[k];
+                const float4 z1 = reinterpret_cast<const float4*>(a1 + 32)[k];
+                const float ya[4] = {y0.x, y0.y, y0.z, y0.w}, yb[4] = {y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (4 * k + e < R) { wy0[4 * k + e] = ya[e]; wy1[4 * k + e] = yb[e]; }
+                if (2 * k < RP) { wz0[2 * k] = make_float2(z0.x, z0.y); wz1[2 * k] = make_float2(z1.x, z1.y); }
+                if (2 * k + 1 < RP) { wz0[2 * k + 1] = make_float2(z0.z, z0.w); wz1[2 * k + 1] = make_float2(z1.z, z1.w); }
+            }
         }
-        const float* __restrict__ wx = W.wtab + pos * 48;
-        float acc = 0.f;
+        const float* __restrict__ wx0 = W.wtab + p0 * 48;
+        const float* __restrict__ wx1 = W.wtab + p1 * 48;
+        float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll 1
         for (int a = 0; a < R; a++) {
             const float4* rows = reinterpret_cast<const float4*>(reg + a * R * kPitch);
-            float2 t[RP];
-#pragma unroll
-            for (int k = 0; k < RP; k++) t[k] = make_float2(0.f, 0.f);
+            float sa0 = 0.f, sa1 = 0.f;
 #pragma unroll
             for (int bb = 0; bb < R; bb++) {
-                const float2 wb = make_float2(wy[bb], wy[bb]);
+                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c4 = 0; c4 < (R + 3) / 4; c4++) {
+                for (int c4 = 0; c4 < NV; c4++) {
                     const float4 v = rows[bb * (kPitch / 4) + c4];
-                    if (2 * c4 < RP) t[2 * c4] = ffma2(wb, make_float2(v.x, v.y), t[2 * c4]);
-                    if (2 * c4 + 1 < RP) t[2 * c4 + 1] = ffma2(wb, make_float2(v.z, v.w), t[2 * c4 + 1]);
+                    if (2 * c4 < RP) {
+                        const float2 hv = make_float2(v.x, v.y);
+                        s0 = ffma2(wz0[2 * c4], hv, s0);
+                        s1 = ffma2(wz1[2 * c4], hv, s1);
+                    }
+                    if (2 * c4 + 1 < RP) {
+                        const float2 hv = make_float2(v.z, v.w);
+                        s0 = ffma2(wz0[2 * c4 + 1], hv, s0);
+                        s1 = ffma2(wz1[2 * c4 + 1], hv, s1);
+                    }
                 }
+                sa0 = fmaf(wy0[bb], s0.x + s0.y, sa0);
+                sa1 = fmaf(wy1[bb], s1.x + s1.y, sa1);
             }
-            float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < RP; k++) s2 = ffma2(wz[k], t[k], s2);
-            acc = fmaf(__ldg(wx + a), s2.x + s2.y, acc);
+            acc0 = fmaf(__ldg(wx0 + a), sa0, acc0);
+            acc1 = fmaf(__ldg(wx1 + a), sa1, acc1);
         }
-        if (valid) out[W.perm[pos]] = acc;
+        if (v0) out[W.perm[p0]] = acc0;
+        if (v1) out[W.perm[p1]] = acc1;
     }
 }
 
 // Spread, FP32, weights read from the plan's table.  Thread (a, b-pair,
-// c-half) keeps its 2 x 8 region cells as packed pairs.
+// c-half) keeps its 2 x 8 region cells as packed pairs.  x and y weights are
+// staged as duplicated pairs so that the per-node products are packed
+// multiplies; the next chunk's table rows are fetched into registers while
+// the current chunk is accumulated.
 template <int R>
 __global__ void __launch_bounds__(R * (R / 2) * 2)
 k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, const void* __restrict__ alpha,
@@ -308,8 +339,9 @@ k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     static_assert(R <= kPitch && R % 2 == 0, "even region up to the row pitch");
     constexpr int BP = R / 2;
     constexpr int NT = R * BP * 2;
-    __shared__ __align__(16) float wxs[kSpreadChunk][kPitch];
-    __shared__ __align__(16) float wys[kSpreadChunk][kPitch];
+    constexpr int PER = (kSpreadChunk * 12 + NT - 1) / NT;   // float4 table entries per thread per chunk
+    __shared__ __align__(16) float2 wxs[kSpreadChunk][kPitch];   // (alpha wx, alpha wx)
+    __shared__ __align__(16) float2 wys[kSpreadChunk][kPitch];   // (wy, wy)
     __shared__ __align__(16) float wzs[kSpreadChunk][kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
@@ -324,35 +356,66 @@ k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int k = 0; k < 4; k++) acc[i][k] = make_float2(0.f, 0.f);
+
+    float4 pre[PER];
+    float pal[PER];
+    auto fetch = [&](int first) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int i = tid + u * NT;
+            pre[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pal[u] = 0.f;
+            if (i < cnt * 12) {
+                const int p = i / 12, k = i % 12;
+                const int64_t pos = (int64_t)sp.y + first + p;
+                pre[u] = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
+                if (k < 4) {
+                    const int32_t src = W.perm[pos];
+                    pal[u] = alpha_double ? (float)(static_cast<const double*>(alpha)[src])
+                                          : static_cast<const float*>(alpha)[src];
+                }
+            }
+        }
+    };
+    auto stage = [&](int first) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int i = tid + u * NT;
+            if (i < cnt * 12) {
+                const int p = i / 12, k = i % 12;
+                float4 v = pre[u];
+                if (k < 4) {
+                    const float al = pal[u];
+                    float4* d = reinterpret_cast<float4*>(&wxs[p][4 * k]);
+                    d[0] = make_float4(al * v.x, al * v.x, al * v.y, al * v.y);
+                    d[1] = make_float4(al * v.z, al * v.z, al * v.w, al * v.w);
+                } else if (k < 8) {
+                    float4* d = reinterpret_cast<float4*>(&wys[p][4 * (k - 4)]);
+                    d[0] = make_float4(v.x, v.x, v.y, v.y);
+                    d[1] = make_float4(v.z, v.z, v.w, v.w);
+                } else {
+                    reinterpret_cast<float4*>(wzs[p])[k - 8] = v;
+                }
+            }
+        }
+    };
+    fetch(0);
     for (int first = 0; first < sp.z; first += kSpreadChunk) {
         const int cnt = min(kSpreadChunk, sp.z - first);
         __syncthreads();
-        // 12 float4 per node: x row scaled by alpha, then y and z rows
-        for (int i = tid; i < cnt * 12; i += NT) {
-            const int p = i / 12, k = i % 12;
-            const int64_t pos = (int64_t)sp.y + first + p;
-            float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
-            if (k < 4) {
-                const int32_t src = W.perm[pos];
-                const float al = alpha_double ? (float)(static_cast<const double*>(alpha)[src])
-                                              : static_cast<const float*>(alpha)[src];
-                v.x *= al; v.y *= al; v.z *= al; v.w *= al;
-                reinterpret_cast<float4*>(wxs[p])[k] = v;
-            } else if (k < 8) {
-                reinterpret_cast<float4*>(wys[p])[k - 4] = v;
-            } else {
-                reinterpret_cast<float4*>(wzs[p])[k - 8] = v;
-            }
-        }
+        stage(first);
         __syncthreads();
+        if (first + kSpreadChunk < sp.z) fetch(first + kSpreadChunk);
 #pragma unroll 2
         for (int p = 0; p < cnt; p++) {
-            const float wa = wxs[p][a];
-            const float2 wyp = *reinterpret_cast<const float2*>(&wys[p][b0]);
+            const float2 wa = wxs[p][a];
+            const float4 wy = *reinterpret_cast<const float4*>(&wys[p][b0]);
             const float4 z0 = *reinterpret_cast<const float4*>(&wzs[p][c0]);
             const float4 z1 = *reinterpret_cast<const float4*>(&wzs[p][c0 + 4]);
-            const float w0 = wa * wyp.x, w1 = wa * wyp.y;
-            const float2 W0 = make_float2(w0, w0), W1 = make_float2(w1, w1);
+            const float2 W0 = fmul2(wa, make_float2(wy.x, wy.y));
+            const float2 W1 = fmul2(wa, make_float2(wy.z, wy.w));
             const float2 z[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
                                  make_float2(z1.z, z1.w)};
 #pragma unroll
@@ -490,7 +553,7 @@ static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int n
     if (nsub == 0) return ANOVA_OK;
     switch (R) {
 #define ANOVA_GATHER_T(R_) \
-    case R_: k_gather3_f32<R_><<<nsub, kGatherThreads, 0, st>>>(sub, descs, plan->m); break;
+    case R_: k_gather3_f32<R_><<<nsub, kGather2Threads, 0, st>>>(sub, descs, plan->m); break;
         ANOVA_GATHER_T(4) ANOVA_GATHER_T(6) ANOVA_GATHER_T(8) ANOVA_GATHER_T(10) ANOVA_GATHER_T(12)
         ANOVA_GATHER_T(14) ANOVA_GATHER_T(16)
 #undef ANOVA_GATHER_T
