@@ -30,9 +30,12 @@ constexpr int kPitch = 16;        // shared row pitch along the last axis (eleme
 constexpr int kGatherThreads = 256;
 constexpr int kSpreadChunk = 64;  // nodes whose weights are staged at once
 
+// Region cells bin*Tb - m + r lie in [-m, nos + Tb + m - 2], inside [-nos, 2 nos)
+// because bin*Tb < nos, r < Tb + 2m and 2m + 2 <= nos, so one conditional add
+// or subtract wraps them onto the torus.
 __device__ __forceinline__ int wrap_idx(int u, int nos) {
-    u %= nos;
-    return u < 0 ? u + nos : u;
+    u += (u < 0) ? nos : 0;
+    return u - ((u >= nos) ? nos : 0);
 }
 
 template <typename T>
@@ -221,23 +224,9 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
 }
 
 // --------------------------------------------------- FP32 with weight table
-// Packed FP32 multiply-add on (x, y) pairs.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
-    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
-    unsigned long long rc = *reinterpret_cast<unsigned long long*>(&c);
-    unsigned long long rd;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
-    return *reinterpret_cast<float2*>(&rd);
-}
-
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
-    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
-    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
-    unsigned long long rd;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    return *reinterpret_cast<float2*>(&rd);
-}
+// Packed FP32 multiply-add / multiply on (x, y) pairs (Blackwell f32x2 instructions).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // Gather, FP32, weights read from the plan's table.  Every lane handles two
 // nodes of the bin; each row h[a][b][:] is read once (broadcast) and
@@ -257,13 +246,16 @@ k_gather3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
     const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
-    for (int i = threadIdx.x; i < R * R * kPitch; i += blockDim.x) {
-        const int c = i % kPitch, ab = i / kPitch;
-        const int bb = ab % R, a = ab / R;
-        float v = 0.f;
-        if (c < R)
-            v = h[((int64_t)wrap_idx(ox + a, nos) * nos + wrap_idx(oy + bb, nos)) * nos + wrap_idx(oz + c, nos)];
-        reg[i] = v;
+    {
+        // thread -> (row, c) with c fastest: one wrapped row base per row
+        const int c = threadIdx.x % kPitch;
+        const int gz = wrap_idx(oz + c, nos);
+        for (int ab = threadIdx.x / kPitch; ab < R * R; ab += blockDim.x / kPitch) {
+            const int a = ab / R, bb = ab - a * R;
+            float v = 0.f;
+            if (c < R) v = h[(wrap_idx(ox + a, nos) * nos + wrap_idx(oy + bb, nos)) * nos + gz];
+            reg[ab * kPitch + c] = v;
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
