@@ -99,6 +99,7 @@ struct DenseWin {
     const int32_t* cell;
     const void* frac;          // FP32 or FP64, as the launch
     const float* wtab;         // FP32 weight table (N x 48) or null
+    float* asort;              // FP32 coefficients in this window's sorted order (filled per matvec)
     void* grid;                // this window's grid
     void* out;                 // gather output (this window's slice of plan->tmp)
     int64_t N;
@@ -134,6 +135,7 @@ struct anova_plan {
     std::vector<int> dense_windows;     // indices of the dense windows, in launch order
     std::vector<std::array<int, 3>> dense_groups;  // (region size R, first sub, count) per launch
     anova::DenseWin* dense_desc = nullptr;  // device, 2 x dense_windows.size(): FP64 then FP32
+    float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
     bool fft3_slab = false;             // every batched 3-D window fits the slab kernels

@@ -319,6 +319,21 @@ k_gather3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     }
 }
 
+// asort_w[pos] = alpha[perm_w[pos]] for every dense window (one launch), so
+// that the spread reads its coefficients contiguously with the weight rows.
+__global__ void k_sort_alpha(const DenseWin* __restrict__ descs, int nd, int64_t N, const void* __restrict__ alpha,
+                             int alpha_double) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * nd;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(idx / N);
+        const int64_t pos = idx - (int64_t)w * N;
+        const DenseWin& W = descs[w];
+        const int32_t src = W.perm[pos];
+        W.asort[pos] = alpha_double ? (float)(static_cast<const double*>(alpha)[src])
+                                    : static_cast<const float*>(alpha)[src];
+    }
+}
+
 // Spread, FP32, weights read from the plan's table.  Thread (a, b-pair,
 // c-half) keeps its 2 x 8 region cells as packed pairs.  x and y weights are
 // staged as duplicated pairs so that the per-node products are packed
@@ -362,11 +377,7 @@ k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
                 const int p = i / 12, k = i % 12;
                 const int64_t pos = (int64_t)sp.y + first + p;
                 pre[u] = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
-                if (k < 4) {
-                    const int32_t src = W.perm[pos];
-                    pal[u] = alpha_double ? (float)(static_cast<const double*>(alpha)[src])
-                                          : static_cast<const float*>(alpha)[src];
-                }
+                if (k < 4) pal[u] = W.asort[pos];
             }
         }
     };
@@ -494,6 +505,7 @@ static DenseWin single_desc(const WindowPlan& w, const PointSet& ps, const void*
     d.cell = ps.cell;
     d.frac = frac;
     d.wtab = nullptr;
+    d.asort = nullptr;
     d.grid = grid;
     d.out = out;
     d.N = ps.N;
@@ -559,6 +571,11 @@ template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
+    if (sizeof(T) == 4 && plan->dense_asort) {
+        k_sort_alpha<<<grid_for(plan->N * nd, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            descs, nd, plan->N, alpha, alpha_double);
+        ANOVA_CHECK_LAUNCH();
+    }
     for (const auto& g : plan->dense_groups) {
         if (sizeof(T) == 4 && table_kernels(plan, g[0]))
             ANOVA_TRY(spread_table(plan, g[0], plan->dense_sub + g[1], g[2], descs, alpha, alpha_double, st));

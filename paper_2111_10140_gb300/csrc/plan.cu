@@ -730,6 +730,8 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
     if (nd == 0) return ANOVA_OK;
     ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_sub, total * sizeof(int4)));
     ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_desc, 2 * nd * sizeof(DenseWin)));
+    if (plan->precision & ANOVA_FP32)
+        ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_asort, (size_t)nd * plan->N * sizeof(float)));
     std::vector<DenseWin> desc(2 * nd);
     int at = 0;
     for (int k = 0; k < nd; k++) {
@@ -743,6 +745,7 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
             d.cell = w.X.cell;
             d.frac = prec == 0 ? (const void*)w.X.frac64 : (const void*)w.X.frac32;
             d.wtab = prec == 0 ? nullptr : w.wtab;
+            d.asort = (prec == 0 || !plan->dense_asort) ? nullptr : plan->dense_asort + (size_t)k * plan->N;
             d.grid = prec == 0 ? (void*)(static_cast<double*>(plan->grid) + w.grid_off)
                                : (void*)(static_cast<float*>(plan->grid) + w.grid_off);
             const int l = plan->dense_windows[k];
@@ -1149,6 +1152,7 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->eta_dev);
     cudaFree(plan->dense_sub);
     cudaFree(plan->dense_desc);
+    cudaFree(plan->dense_asort);
     cudaFree(plan->fft3_desc);
     cudaFree(plan->psi_poly);
     cudaFree(plan->cg_vec);
