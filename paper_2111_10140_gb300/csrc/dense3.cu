@@ -441,6 +441,131 @@ k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     }
 }
 
+// ------------------------------------------------- tensor-core spread (TF32)
+// The spread of one sub-problem is the product C[(b,c), a] = sum_p A[(b,c), p]
+// B[p, a] with A = wy (x) wz and B = alpha wx: a dense contraction over the
+// nodes of the bin, run on mma.sync m16n8k8 TF32.  FP32 accuracy comes from
+// splitting every operand into a TF32 head and a TF32 tail and accumulating
+// head*head + head*tail + tail*head in FP32 (the dropped tail*tail term is
+// 2^-22 relative).  Warp w owns the M-tiles b = 2w, 2w+1 (16 c-rows each) and
+// both N-tiles (a = 0..7, 8..15).
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_of(x);
+    lo = tf32_of(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kTcPitch = 24;   // shared row pitch: rows p and p+1..3 land in distinct bank groups
+template <int R>
+__global__ void __launch_bounds__(32 * ((R + 1) / 2))
+k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
+    static_assert(R <= kPitch && R % 2 == 0, "even region up to 16");
+    constexpr int NW = R / 2;                  // warps, two b rows each
+    constexpr int NT = 32 * NW;
+    __shared__ __align__(16) uint32_t sxh[kSpreadChunk][kTcPitch];   // alpha wx, TF32 head
+    __shared__ __align__(16) uint32_t sxl[kSpreadChunk][kTcPitch];   // and tail
+    __shared__ __align__(16) float sy[kSpreadChunk][kTcPitch];
+    __shared__ __align__(16) float sz[kSpreadChunk][kTcPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    float* __restrict__ grid = static_cast<float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
+    for (int first = 0; first < sp.z; first += kSpreadChunk) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        const int cnt8 = (cnt + 7) & ~7;
+        __syncthreads();
+        for (int i = tid; i < cnt8 * 12; i += NT) {
+            const int p = i / 12, k = i % 12;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float al = 0.f;
+            if (p < cnt) {
+                const int64_t pos = (int64_t)sp.y + first + p;
+                v = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
+                if (k < 4) al = W.asort[pos];
+            }
+            if (k < 4) {
+                const float xs[4] = {al * v.x, al * v.y, al * v.z, al * v.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    uint32_t hi, lo;
+                    tf32_split(xs[e], hi, lo);
+                    sxh[p][4 * k + e] = hi;
+                    sxl[p][4 * k + e] = lo;
+                }
+            } else if (k < 8) {
+                *reinterpret_cast<float4*>(&sy[p][4 * (k - 4)]) = v;
+            } else {
+                *reinterpret_cast<float4*>(&sz[p][4 * (k - 8)]) = v;
+            }
+        }
+        __syncthreads();
+        for (int p0 = 0; p0 < cnt8; p0 += 8) {
+            const int pa = p0 + t, pb = p0 + t + 4;
+            const float z0 = sz[pa][g], z1 = sz[pa][g + 8], z2 = sz[pb][g], z3 = sz[pb][g + 8];
+            uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                bh[nt][0] = sxh[pa][8 * nt + g];
+                bl[nt][0] = sxl[pa][8 * nt + g];
+                bh[nt][1] = sxh[pb][8 * nt + g];
+                bl[nt][1] = sxl[pb][8 * nt + g];
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int b = 2 * warp + i;
+                const float y0 = sy[pa][b], y1 = sy[pb][b];
+                uint32_t ah[4], alo[4];
+                tf32_split(y0 * z0, ah[0], alo[0]);
+                tf32_split(y0 * z1, ah[1], alo[1]);
+                tf32_split(y1 * z2, ah[2], alo[2]);
+                tf32_split(y1 * z3, ah[3], alo[3]);
+#pragma unroll
+                for (int nt = 0; nt < 2; nt++) {
+                    mma_tf32(acc[i][nt], ah, bh[nt][0], bh[nt][1]);
+                    mma_tf32(acc[i][nt], ah, bl[nt][0], bl[nt][1]);
+                    mma_tf32(acc[i][nt], alo, bh[nt][0], bh[nt][1]);
+                }
+            }
+        }
+    }
+    // acc[i][nt] holds C rows c = g, g+8 and columns a = 8 nt + 2t, 8 nt + 2t + 1
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int b = 2 * warp + i;
+        const int gb = wrap_idx(Tb * by - m + b, nos);
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int c = g + 8 * (e >> 1);
+                const int a = 8 * nt + 2 * t + (e & 1);
+                if (a < R && c < R) {
+                    const int ga = wrap_idx(Tb * bx - m + a, nos);
+                    atomicAdd(&grid[(ga * nos + gb) * nos + wrap_idx(Tb * bz - m + c, nos)], acc[i][nt][e]);
+                }
+            }
+    }
+}
+
 template <typename T>
 static const T* frac_of3(const PointSet& ps);
 template <>
@@ -540,6 +665,16 @@ static bool table_kernels(const anova_plan* plan, int R) {
 static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  const void* alpha, int alpha_double, cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
+    if (plan->spread_tc) {
+        switch (R) {
+#define ANOVA_SPREAD_TC(R_) \
+    case R_: k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, plan->m); ANOVA_CHECK_LAUNCH(); return ANOVA_OK;
+            ANOVA_SPREAD_TC(4) ANOVA_SPREAD_TC(6) ANOVA_SPREAD_TC(8) ANOVA_SPREAD_TC(10) ANOVA_SPREAD_TC(12)
+            ANOVA_SPREAD_TC(14) ANOVA_SPREAD_TC(16)
+#undef ANOVA_SPREAD_TC
+            default: break;
+        }
+    }
     switch (R) {
 #define ANOVA_SPREAD_T(R_) \
     case R_: k_spread3_f32<R_><<<nsub, R_ * (R_ / 2) * 2, 0, st>>>(sub, descs, alpha, alpha_double, plan->m); break;
