@@ -137,6 +137,7 @@ struct anova_plan {
     anova::DenseWin* dense_desc = nullptr;  // device, 2 x dense_windows.size(): FP64 then FP32
     float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
+    bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
     bool fft3_slab = false;             // every batched 3-D window fits the slab kernels

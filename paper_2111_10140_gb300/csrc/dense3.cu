@@ -566,6 +566,110 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
     }
 }
 
+// ------------------------------------------------- tensor-core gather (TF32)
+// Per warp, 16 nodes j of the bin: U[j][(a,b)] = sum_c wz_j[c] h[a][b][c] on
+// mma.sync m16n8k8 TF32 (A = the nodes' z weights, B = rows of the staged
+// region, 3xTF32 for FP32 accuracy), then s_j = sum_a wx_j[a] sum_b wy_j[b]
+// U[j][(a,b)] on the accumulator fragments and a reduction over the 4 lanes
+// that share a node.  The region is staged once per CTA as TF32 heads and
+// tails with a 20-float row pitch (conflict-free fragment loads).
+constexpr int kTcRowPitch = 20;
+constexpr int kGatherTcThreads = 128;
+template <int R>
+__global__ void __launch_bounds__(kGatherTcThreads)
+k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
+    static_assert(R <= kPitch && R % 2 == 0, "even region up to 16");
+    __shared__ __align__(16) uint32_t rh[R * R * kTcRowPitch];
+    __shared__ __align__(16) uint32_t rl[R * R * kTcRowPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    const float* __restrict__ h = static_cast<const float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
+    {
+        const int c = threadIdx.x % kPitch;
+        const int gz = wrap_idx(oz + c, nos);
+        for (int ab = threadIdx.x / kPitch; ab < R * R; ab += blockDim.x / kPitch) {
+            const int a = ab / R, bb = ab - a * R;
+            float v = 0.f;
+            if (c < R) v = h[(wrap_idx(ox + a, nos) * nos + wrap_idx(oy + bb, nos)) * nos + gz];
+            uint32_t hi, lo;
+            tf32_split(v, hi, lo);
+            rh[ab * kTcRowPitch + c] = hi;
+            rl[ab * kTcRowPitch + c] = lo;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    float* __restrict__ out = static_cast<float*>(W.out);
+    for (int base = warp * 16; base < sp.z; base += (kGatherTcThreads / 32) * 16) {
+        const int j0 = base + g, j1 = base + g + 8;
+        const bool v0 = j0 < sp.z, v1 = j1 < sp.z;
+        const int64_t p0 = (int64_t)sp.y + (v0 ? j0 : sp.z - 1);
+        const int64_t p1 = (int64_t)sp.y + (v1 ? j1 : sp.z - 1);
+        const float* w0 = W.wtab + p0 * 48;
+        const float* w1 = W.wtab + p1 * 48;
+        // A fragments for the two k-steps (c = 0..7, 8..15): a0 (j0, t), a1 (j1, t), a2 (j0, t+4), a3 (j1, t+4)
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+            tf32_split(v0 ? __ldg(w0 + 32 + 8 * ks + t) : 0.f, ah[ks][0], al[ks][0]);
+            tf32_split(v1 ? __ldg(w1 + 32 + 8 * ks + t) : 0.f, ah[ks][1], al[ks][1]);
+            tf32_split(v0 ? __ldg(w0 + 32 + 8 * ks + t + 4) : 0.f, ah[ks][2], al[ks][2]);
+            tf32_split(v1 ? __ldg(w1 + 32 + 8 * ks + t + 4) : 0.f, ah[ks][3], al[ks][3]);
+        }
+        // y weights at the fragment columns b = 8 nt + 2t, 8 nt + 2t + 1
+        float y0[2][2], y1[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int b = 8 * nt + 2 * t + e;
+                y0[nt][e] = (b < R) ? __ldg(w0 + 16 + b) : 0.f;
+                y1[nt][e] = (b < R) ? __ldg(w1 + 16 + b) : 0.f;
+            }
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 1
+        for (int a = 0; a < R; a++) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                const int brow = a * R + 8 * nt + g;          // B column n = b = 8 nt + g
+                const bool brow_ok = 8 * nt + g < R;
+#pragma unroll
+                for (int ks = 0; ks < 2; ks++) {
+                    uint32_t bh0 = 0, bh1 = 0, bl0 = 0, bl1 = 0;
+                    if (brow_ok) {
+                        const int o = brow * kTcRowPitch + 8 * ks + t;
+                        bh0 = rh[o];
+                        bh1 = rh[o + 4];
+                        bl0 = rl[o];
+                        bl1 = rl[o + 4];
+                    }
+                    mma_tf32(c, ah[ks], bh0, bh1);
+                    mma_tf32(c, ah[ks], bl0, bl1);
+                    mma_tf32(c, al[ks], bh0, bh1);
+                }
+                s0 = fmaf(y0[nt][0], c[0], fmaf(y0[nt][1], c[1], s0));
+                s1 = fmaf(y1[nt][0], c[2], fmaf(y1[nt][1], c[3], s1));
+            }
+            acc0 = fmaf(__ldg(w0 + a), s0, acc0);
+            acc1 = fmaf(__ldg(w1 + a), s1, acc1);
+        }
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, 2);
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, 2);
+        if (t == 0) {
+            if (v0) out[W.perm[p0]] = acc0;
+            if (v1) out[W.perm[p1]] = acc1;
+        }
+    }
+}
+
 template <typename T>
 static const T* frac_of3(const PointSet& ps);
 template <>
@@ -690,6 +794,16 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
 static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
+    if (plan->gather_tc) {
+        switch (R) {
+#define ANOVA_GATHER_TC(R_) \
+    case R_: k_gather3_tc<R_><<<nsub, kGatherTcThreads, 0, st>>>(sub, descs, plan->m); ANOVA_CHECK_LAUNCH(); return ANOVA_OK;
+            ANOVA_GATHER_TC(4) ANOVA_GATHER_TC(6) ANOVA_GATHER_TC(8) ANOVA_GATHER_TC(10) ANOVA_GATHER_TC(12)
+            ANOVA_GATHER_TC(14) ANOVA_GATHER_TC(16)
+#undef ANOVA_GATHER_TC
+            default: break;
+        }
+    }
     switch (R) {
 #define ANOVA_GATHER_T(R_) \
     case R_: k_gather3_f32<R_><<<nsub, kGather2Threads, 0, st>>>(sub, descs, plan->m); break;
