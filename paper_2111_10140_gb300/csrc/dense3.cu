@@ -620,8 +620,8 @@ k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
             tf32_split(v0 ? __ldg(w0 + 32 + 8 * ks + t + 4) : 0.f, ah[ks][2], al[ks][2]);
             tf32_split(v1 ? __ldg(w1 + 32 + 8 * ks + t + 4) : 0.f, ah[ks][3], al[ks][3]);
         }
-        // y weights at the fragment columns b = 8 nt + 2t, 8 nt + 2t + 1
-        float y0[2][2], y1[2][2];
+        // y weights at the fragment columns b = 8 nt + 2t, 8 nt + 2t + 1; x weights of both nodes
+        float y0[2][2], y1[2][2], x0[R], x1[R];
 #pragma unroll
         for (int nt = 0; nt < 2; nt++)
 #pragma unroll
@@ -630,13 +630,20 @@ k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
                 y0[nt][e] = (b < R) ? __ldg(w0 + 16 + b) : 0.f;
                 y1[nt][e] = (b < R) ? __ldg(w1 + 16 + b) : 0.f;
             }
+#pragma unroll
+        for (int a = 0; a < R; a++) {
+            x0[a] = __ldg(w0 + a);
+            x1[a] = __ldg(w1 + a);
+        }
         float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll 1
+#pragma unroll
         for (int a = 0; a < R; a++) {
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll
             for (int nt = 0; nt < 2; nt++) {
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                if (8 * nt >= R) continue;
+                // head*head and the two correction products accumulate separately
+                float ch[4] = {0.f, 0.f, 0.f, 0.f}, cx[4] = {0.f, 0.f, 0.f, 0.f};
                 const int brow = a * R + 8 * nt + g;          // B column n = b = 8 nt + g
                 const bool brow_ok = 8 * nt + g < R;
 #pragma unroll
@@ -649,15 +656,15 @@ k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
                         bl0 = rl[o];
                         bl1 = rl[o + 4];
                     }
-                    mma_tf32(c, ah[ks], bh0, bh1);
-                    mma_tf32(c, ah[ks], bl0, bl1);
-                    mma_tf32(c, al[ks], bh0, bh1);
+                    mma_tf32(ch, ah[ks], bh0, bh1);
+                    mma_tf32(cx, ah[ks], bl0, bl1);
+                    mma_tf32(cx, al[ks], bh0, bh1);
                 }
-                s0 = fmaf(y0[nt][0], c[0], fmaf(y0[nt][1], c[1], s0));
-                s1 = fmaf(y1[nt][0], c[2], fmaf(y1[nt][1], c[3], s1));
+                s0 = fmaf(y0[nt][0], ch[0] + cx[0], fmaf(y0[nt][1], ch[1] + cx[1], s0));
+                s1 = fmaf(y1[nt][0], ch[2] + cx[2], fmaf(y1[nt][1], ch[3] + cx[3], s1));
             }
-            acc0 = fmaf(__ldg(w0 + a), s0, acc0);
-            acc1 = fmaf(__ldg(w1 + a), s1, acc1);
+            acc0 = fmaf(x0[a], s0, acc0);
+            acc1 = fmaf(x1[a], s1, acc1);
         }
         acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
         acc0 += __shfl_xor_sync(0xffffffffu, acc0, 2);
