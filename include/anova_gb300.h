@@ -94,7 +94,11 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
  *   alpha  device, nrhs columns of N entries, column r at alpha + r*ld.
  *   out    device, same layout; overwritten.  Must not alias alpha.
  *   nrhs   >= 1; ld >= N.
- * Asynchronous on `stream`.  Errors: EINVAL.
+ * Asynchronous on `stream`.  With nrhs = 1 the plan records the call's launch
+ * sequence as a CUDA graph the second time it sees the same (dtype, alpha,
+ * out) and replays it from then on (at most 8 such graphs per plan).  Calls on
+ * one plan must not overlap on the GPU: they share the plan's work buffers.
+ * Errors: EINVAL.
  */
 anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, void* out,
                           int32_t nrhs, int64_t ld, void* stream);

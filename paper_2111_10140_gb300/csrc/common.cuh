@@ -150,6 +150,17 @@ struct anova_plan {
     int cg_hist = 0;
     anova::StageClock clock;
     int sm_count = 0;
+    // replayable launch sequences of anova_matvec, keyed by (dtype, alpha, out)
+    struct GraphEntry {
+        int dtype;
+        const void* alpha;
+        void* out;
+        int uses;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
+    bool use_graphs = true;
 };
 
 namespace anova {

@@ -116,10 +116,13 @@ __global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict_
 // Fused middle pass along x for up to 32 consecutive kz of one ky per block:
 // H[kx] = D[kx] sum_x B[x] e^{-2 pi i kx x/nos}, then C[x] = sum_kx H[kx] e^{+...}.
 constexpr int kMidLanes = 32, kMidWarps = 8, kMaxN3 = 64, kMaxBox3 = 256;
+// Dynamic shared memory: H (n x 32), the staged lines (Bx x 32) when Bx <= kMidStage, twiddles (nos).
+constexpr int kMidStage = 64;
 template <typename T>
 __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
-    __shared__ C sH[kMaxN3][kMidLanes];
+    extern __shared__ __align__(16) unsigned char mid_raw[];
+    C (*sH)[kMidLanes] = reinterpret_cast<C (*)[kMidLanes]>(mid_raw);
     const Fft3Win W = wins[blockIdx.y];
     const int n = W.n, nos = W.nos, Bx = W.B[0];
     const int lines_per_ky = (n + kMidLanes - 1) / kMidLanes;
@@ -133,6 +136,19 @@ __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Wi
     const C* __restrict__ tw = static_cast<const C*>(W.tw);
     const T* __restrict__ D = static_cast<const T*>(W.D);
     const int x0v = box_value0(W.lo[0], nos);
+    const bool staged = Bx <= kMidStage;
+    C (*sBx)[kMidLanes] = sH + kMaxN3;              // the block's 32 lines, x < Bx
+    C* stw = reinterpret_cast<C*>(sBx + kMidStage); // twiddles
+    for (int i = threadIdx.x; i < nos; i += blockDim.x) stw[i] = tw[i];
+    if (staged)
+        for (int x = warp; x < Bx; x += kMidWarps) {
+            C v;
+            v.x = T(0);
+            v.y = T(0);
+            if (ok) v = Bi[((int64_t)x * n + ky) * n + kz];
+            sBx[x][lane] = v;
+        }
+    __syncthreads();
     for (int kx = warp; kx < n; kx += kMidWarps) {
         const int kxv = kx - n / 2;
         int r = modp(kxv * x0v, nos);
@@ -140,10 +156,14 @@ __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Wi
         T ar = T(0), ai = T(0);
         for (int x = 0; x < Bx; x++) {
             C v;
-            v.x = T(0);
-            v.y = T(0);
-            if (ok) v = Bi[((int64_t)x * n + ky) * n + kz];
-            cmac(v, tw[r], 0, ar, ai);
+            if (staged) {
+                v = sBx[x][lane];
+            } else {
+                v.x = T(0);
+                v.y = T(0);
+                if (ok) v = Bi[((int64_t)x * n + ky) * n + kz];
+            }
+            cmac(v, stw[r], 0, ar, ai);
             r += step;
             if (r >= nos) r -= nos;
         }
@@ -160,7 +180,7 @@ __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Wi
         const int step = modp(xv, nos);
         T ar = T(0), ai = T(0);
         for (int kx = 0; kx < n; kx++) {
-            cmac(sH[kx][lane], tw[r], 1, ar, ai);
+            cmac(sH[kx][lane], stw[r], 1, ar, ai);
             r += step;
             if (r >= nos) r -= nos;
         }
@@ -240,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_fft3_i3(const Fft3Win* __restrict_
 // middle pass is k_fft3_mid.  Three launches instead of five, and every line
 // sum reads shared memory.
 constexpr int kSlab = 64;
-constexpr int kSlabThreads = 256;
+constexpr int kSlabThreads = 1024;
 
 template <typename T>
 __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* __restrict__ wins) {
@@ -373,9 +393,20 @@ bool fft3_slab_supported(const WindowPlan& w) {
     return fft3_box_supported(w) && w.box_ext[1] <= kSlab && w.box_ext[2] <= kSlab && w.nos <= 4 * kSlab;
 }
 
+template <typename T>
+static size_t mid_bytes() {
+    using C = typename C2<T>::type;
+    return ((size_t)(kMaxN3 + kMidStage) * kMidLanes + 4 * kMaxN3) * sizeof(C);
+}
+
 // every batched window: one launch per pass for all of them
 template <typename T>
 anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
+    static bool mid_attr = [] {
+        cudaFuncSetAttribute(k_fft3_mid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_bytes<T>());
+        return true;
+    }();
+    (void)mid_attr;
     const int nw = (int)plan->fft3_windows.size();
     if (nw == 0) return ANOVA_OK;
     const Fft3Win* wins = plan->fft3_desc + (sizeof(T) == 8 ? 0 : nw);
@@ -410,14 +441,14 @@ anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
         (void)attrs;
         const dim3 gs(bxmax, nw);
         k_fft3_slab_fwd<T><<<gs, kSlabThreads, shf, st>>>(wins);
-        k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, 0, st>>>(wins);
+        k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, mid_bytes<T>(), st>>>(wins);
         k_fft3_slab_inv<T><<<gs, kSlabThreads, shi, st>>>(wins);
         ANOVA_CHECK_LAUNCH();
         return ANOVA_OK;
     }
     k_fft3_f1<T><<<g1, kThreads, 0, st>>>(wins);
     k_fft3_f2<T><<<g2, kThreads, 0, st>>>(wins);
-    k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, 0, st>>>(wins);
+    k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, mid_bytes<T>(), st>>>(wins);
     k_fft3_i2<T><<<g1, kThreads, 0, st>>>(wins);
     k_fft3_i3<T><<<g3, kThreads, 0, st>>>(wins);
     ANOVA_CHECK_LAUNCH();

@@ -478,6 +478,50 @@ anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, vo
         return ANOVA_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (nrhs == 1 && plan->use_graphs && !plan->clock.enabled && plan->N > 0) {
+        // replay the captured launch sequence for this (dtype, alpha, out); the
+        // first call with a new key runs directly, the second one captures
+        for (auto& g : plan->graphs)
+            if (g.dtype == dtype && g.alpha == alpha && g.out == out) {
+                if (g.exec) {
+                    ANOVA_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+                    return ANOVA_OK;
+                }
+                if (!plan->capture_stream)
+                    ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking));
+                cudaGraph_t graph = nullptr;
+                ANOVA_CUDA_TRY(cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal));
+                anova_status cs = (dtype == ANOVA_FP64)
+                                      ? matvec_one<double>(plan, static_cast<const double*>(alpha),
+                                                           static_cast<double*>(out), plan->capture_stream)
+                                      : matvec_one<float>(plan, static_cast<const float*>(alpha),
+                                                          static_cast<float*>(out), plan->capture_stream);
+                cudaError_t ce = cudaStreamEndCapture(plan->capture_stream, &graph);
+                if (cs != ANOVA_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return cs;
+                }
+                if (ce != cudaSuccess) {
+                    set_error(std::string("anova_matvec: graph capture: ") + cudaGetErrorString(ce));
+                    return ANOVA_ECUDA;
+                }
+                cudaGraphExec_t exec = nullptr;
+                ce = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ce != cudaSuccess) {
+                    set_error(std::string("anova_matvec: graph instantiate: ") + cudaGetErrorString(ce));
+                    return ANOVA_ECUDA;
+                }
+                g.exec = exec;
+                ANOVA_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+                return ANOVA_OK;
+            }
+        if (plan->graphs.size() >= 8) {
+            if (plan->graphs.front().exec) cudaGraphExecDestroy(plan->graphs.front().exec);
+            plan->graphs.erase(plan->graphs.begin());
+        }
+        plan->graphs.push_back({dtype, alpha, out, 1, nullptr});
+    }
     for (int r = 0; r < nrhs; r++) {
         if (dtype == ANOVA_FP64)
             ANOVA_TRY(matvec_one<double>(plan, static_cast<const double*>(alpha) + r * ld,

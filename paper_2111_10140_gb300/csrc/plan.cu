@@ -1159,6 +1159,9 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->cg_scal);
     cudaFree(plan->cg_part);
     for (auto e : plan->clock.ev) cudaEventDestroy(e);
+    for (auto& g : plan->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
     delete plan;
 }
 
