@@ -244,3 +244,37 @@ def test_full_mid_workload_parity(B, torch):
     idx = np.random.default_rng(7).choice(w.N, 500, replace=False)
     direct = oracle.direct(w.X[idx], w.X, w.windows, w.eta, w.ell, w.alpha)
     assert rel(out32.cpu().numpy()[idx], direct) <= 1e-5
+
+
+@pytest.mark.parametrize("n,m", [(64, 6), (16, 7), (16, 5), (16, 3), (8, 1)])
+def test_dense_region_sizes(B, torch, n, m):
+    """3-D windows on the dense kernels with other region sizes R = Tb + 2m:
+    n = 64 (bin side 4, R = 16), m = 7 (R = 16), m = 5 (R = 12), m = 3 (R = 8), m = 1 (R = 4)."""
+    w = W.random_problem(4000, 3, [(0, 1, 2)], 0.25, n, m, seed=80 + m + n)
+    w.epsB = 0.25
+    plan = make_plan(B, torch, w, B.MIXED)
+    ref = oracle_fast(w)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    out64 = torch.empty_like(a64)
+    B.anova_matvec(plan, a64, out64)
+    assert rel(out64.cpu().numpy(), ref) <= 1e-12
+    a32 = a64.float()
+    out32 = torch.empty_like(a32)
+    B.anova_matvec(plan, a32, out32)
+    assert rel(out32.cpu().numpy(), ref) <= 1e-5
+
+
+def test_graph_replay_matches_direct_calls(B, torch):
+    """anova_matvec replays a captured launch sequence from the second call on;
+    new inputs in the same buffers must give new results."""
+    w = W.random_problem(3000, 6, [(0, 1, 2), (3, 4, 5)], 0.2, 16, 4, seed=91)
+    plan = make_plan(B, torch, w, B.MIXED)
+    a = torch.from_numpy(w.alpha).float().cuda()
+    out = torch.empty_like(a)
+    rng = np.random.default_rng(3)
+    for call in range(4):
+        vals = rng.standard_normal(w.N)
+        a.copy_(torch.from_numpy(vals).float())
+        B.anova_matvec(plan, a, out)
+        ref = oracle_fast(w, alpha=vals)
+        assert rel(out.cpu().numpy(), ref) <= 1e-5, call
