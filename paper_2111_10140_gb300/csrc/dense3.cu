@@ -677,6 +677,169 @@ k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
     }
 }
 
+// ------------------------------------------------ 2-D and 1-D windows, FP32
+// Same binning and weight table as the 3-D kernels (rows of 16 floats per axis),
+// regions R x R (2-D, bins of 2x2 cells) and R (1-D).  The work per node is small
+// (R^2 or R multiply-adds), so one warp accumulates a sub-problem's region in
+// registers and adds it to the grid once, and the gather is one thread per node.
+
+// 2-D spread: lane (a = lane/2, half h) keeps cells (a, 8h .. 8h+7).
+template <int R>
+__global__ void __launch_bounds__(32) k_spread2_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
+                                                    int m) {
+    static_assert(R <= kPitch, "region up to 16");
+    __shared__ __align__(16) float sx[kSpreadChunk][kPitch];
+    __shared__ __align__(16) float sy[kSpreadChunk][kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    float* __restrict__ grid = static_cast<float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int by = sp.x % nb, bx = sp.x / nb;
+    const int lane = threadIdx.x, a = lane >> 1, h = lane & 1;
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) acc[k] = 0.f;
+    for (int first = 0; first < sp.z; first += kSpreadChunk) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        __syncwarp();
+        for (int i = lane; i < cnt * 8; i += 32) {
+            const int p = i >> 3, k = i & 7;
+            const int64_t pos = (int64_t)sp.y + first + p;
+            float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 32)[k];
+            if (k < 4) {
+                const float al = W.asort[pos];
+                v.x *= al; v.y *= al; v.z *= al; v.w *= al;
+                reinterpret_cast<float4*>(sx[p])[k] = v;
+            } else {
+                reinterpret_cast<float4*>(sy[p])[k - 4] = v;
+            }
+        }
+        __syncwarp();
+        if (a < R)
+            for (int p = 0; p < cnt; p++) {
+                const float wa = sx[p][a];
+                const float4 y0 = *reinterpret_cast<const float4*>(&sy[p][8 * h]);
+                const float4 y1 = *reinterpret_cast<const float4*>(&sy[p][8 * h + 4]);
+                acc[0] = fmaf(wa, y0.x, acc[0]); acc[1] = fmaf(wa, y0.y, acc[1]);
+                acc[2] = fmaf(wa, y0.z, acc[2]); acc[3] = fmaf(wa, y0.w, acc[3]);
+                acc[4] = fmaf(wa, y1.x, acc[4]); acc[5] = fmaf(wa, y1.y, acc[5]);
+                acc[6] = fmaf(wa, y1.z, acc[6]); acc[7] = fmaf(wa, y1.w, acc[7]);
+            }
+    }
+    if (a < R) {
+        const int ga = wrap_idx(Tb * bx - m + a, nos);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int c = 8 * h + k;
+            if (c < R) atomicAdd(&grid[ga * nos + wrap_idx(Tb * by - m + c, nos)], acc[k]);
+        }
+    }
+}
+
+// 2-D gather: one thread per node.
+template <int R>
+__global__ void __launch_bounds__(128) k_gather2_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
+                                                     int m) {
+    static_assert(R <= kPitch, "region up to 16");
+    __shared__ __align__(16) float reg[R * kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    const float* __restrict__ h = static_cast<const float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int by = sp.x % nb, bx = sp.x / nb;
+    for (int i = threadIdx.x; i < R * kPitch; i += blockDim.x) {
+        const int a = i / kPitch, c = i % kPitch;
+        reg[i] = (c < R) ? h[wrap_idx(Tb * bx - m + a, nos) * nos + wrap_idx(Tb * by - m + c, nos)] : 0.f;
+    }
+    __syncthreads();
+    float* __restrict__ out = static_cast<float*>(W.out);
+    for (int q = threadIdx.x; q < sp.z; q += blockDim.x) {
+        const int64_t pos = (int64_t)sp.y + q;
+        const float4* wp = reinterpret_cast<const float4*>(W.wtab + pos * 32);
+        float wx[16], wy[16];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float4 x = wp[k], y = wp[4 + k];
+            wx[4 * k] = x.x; wx[4 * k + 1] = x.y; wx[4 * k + 2] = x.z; wx[4 * k + 3] = x.w;
+            wy[4 * k] = y.x; wy[4 * k + 1] = y.y; wy[4 * k + 2] = y.z; wy[4 * k + 3] = y.w;
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < R; a++) {
+            float s = 0.f;
+#pragma unroll
+            for (int c4 = 0; c4 < (R + 3) / 4; c4++) {
+                const float4 v = *reinterpret_cast<const float4*>(&reg[a * kPitch + 4 * c4]);
+                const float hv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (4 * c4 + e < R) s = fmaf(wy[4 * c4 + e], hv[e], s);
+            }
+            acc = fmaf(wx[a], s, acc);
+        }
+        out[W.perm[pos]] = acc;
+    }
+}
+
+// 1-D spread: lane a < R keeps cell a.
+template <int R>
+__global__ void __launch_bounds__(32) k_spread1_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
+                                                    int m) {
+    static_assert(R <= kPitch, "region up to 16");
+    __shared__ __align__(16) float sx[kSpreadChunk][kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    float* __restrict__ grid = static_cast<float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb;
+    const int bx = sp.x;
+    const int lane = threadIdx.x;
+    float acc = 0.f;
+    for (int first = 0; first < sp.z; first += kSpreadChunk) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        __syncwarp();
+        for (int i = lane; i < cnt * 4; i += 32) {
+            const int p = i >> 2, k = i & 3;
+            const int64_t pos = (int64_t)sp.y + first + p;
+            float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 16)[k];
+            const float al = W.asort[pos];
+            v.x *= al; v.y *= al; v.z *= al; v.w *= al;
+            reinterpret_cast<float4*>(sx[p])[k] = v;
+        }
+        __syncwarp();
+        if (lane < R)
+            for (int p = 0; p < cnt; p++) acc += sx[p][lane];
+    }
+    if (lane < R) atomicAdd(&grid[wrap_idx(Tb * bx - m + lane, nos)], acc);
+}
+
+// 1-D gather: one thread per node.
+template <int R>
+__global__ void __launch_bounds__(128) k_gather1_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
+                                                     int m) {
+    static_assert(R <= kPitch, "region up to 16");
+    __shared__ __align__(16) float reg[kPitch];
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    const float* __restrict__ h = static_cast<const float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb;
+    const int bx = sp.x;
+    if (threadIdx.x < kPitch) reg[threadIdx.x] = (threadIdx.x < R) ? h[wrap_idx(Tb * bx - m + threadIdx.x, nos)] : 0.f;
+    __syncthreads();
+    float* __restrict__ out = static_cast<float*>(W.out);
+    for (int q = threadIdx.x; q < sp.z; q += blockDim.x) {
+        const int64_t pos = (int64_t)sp.y + q;
+        const float4* wp = reinterpret_cast<const float4*>(W.wtab + pos * 16);
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float4 x = wp[k];
+            const float4 v = *reinterpret_cast<const float4*>(&reg[4 * k]);
+            acc = fmaf(x.x, v.x, fmaf(x.y, v.y, fmaf(x.z, v.z, fmaf(x.w, v.w, acc))));
+        }
+        out[W.perm[pos]] = acc;
+    }
+}
+
 template <typename T>
 static const T* frac_of3(const PointSet& ps);
 template <>
@@ -833,11 +996,33 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
         ANOVA_CHECK_LAUNCH();
     }
     for (const auto& g : plan->dense_groups) {
-        if (sizeof(T) == 4 && table_kernels(plan, g[0]))
-            ANOVA_TRY(spread_table(plan, g[0], plan->dense_sub + g[1], g[2], descs, alpha, alpha_double, st));
+        const int dA = g[0] / 100, R = g[0] % 100;
+        const int4* sub = plan->dense_sub + g[1];
+        const int nsub = g[2];
+        if (dA < 3) {
+            if (sizeof(T) != 4 || !plan->dense_asort) continue;   // FP64: generic kernels per window
+            if (dA == 2) {
+                switch (R) {
+#define ANOVA_S2(R_) case R_: k_spread2_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, plan->m); break;
+                    ANOVA_S2(4) ANOVA_S2(6) ANOVA_S2(8) ANOVA_S2(10) ANOVA_S2(12) ANOVA_S2(14) ANOVA_S2(16)
+#undef ANOVA_S2
+                    default: set_error("dense 2-D spread: unsupported region size"); return ANOVA_EINVAL;
+                }
+            } else {
+                switch (R) {
+#define ANOVA_S1(R_) case R_: k_spread1_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, plan->m); break;
+                    ANOVA_S1(4) ANOVA_S1(6) ANOVA_S1(8) ANOVA_S1(10) ANOVA_S1(12) ANOVA_S1(14) ANOVA_S1(16)
+#undef ANOVA_S1
+                    default: set_error("dense 1-D spread: unsupported region size"); return ANOVA_EINVAL;
+                }
+            }
+            ANOVA_CHECK_LAUNCH();
+            continue;
+        }
+        if (sizeof(T) == 4 && table_kernels(plan, R))
+            ANOVA_TRY(spread_table(plan, R, sub, nsub, descs, alpha, alpha_double, st));
         else
-            ANOVA_TRY(spread_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), alpha,
-                                         alpha_double, st));
+            ANOVA_TRY(spread_dispatch<T>(plan, R, sub, nsub, descs, DenseWin(), alpha, alpha_double, st));
     }
     return ANOVA_OK;
 }
@@ -847,10 +1032,33 @@ anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
     for (const auto& g : plan->dense_groups) {
-        if (sizeof(T) == 4 && table_kernels(plan, g[0]))
-            ANOVA_TRY(gather_table(plan, g[0], plan->dense_sub + g[1], g[2], descs, st));
+        const int dA = g[0] / 100, R = g[0] % 100;
+        const int4* sub = plan->dense_sub + g[1];
+        const int nsub = g[2];
+        if (dA < 3) {
+            if (sizeof(T) != 4 || !plan->dense_asort) continue;
+            if (dA == 2) {
+                switch (R) {
+#define ANOVA_G2(R_) case R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, plan->m); break;
+                    ANOVA_G2(4) ANOVA_G2(6) ANOVA_G2(8) ANOVA_G2(10) ANOVA_G2(12) ANOVA_G2(14) ANOVA_G2(16)
+#undef ANOVA_G2
+                    default: set_error("dense 2-D gather: unsupported region size"); return ANOVA_EINVAL;
+                }
+            } else {
+                switch (R) {
+#define ANOVA_G1(R_) case R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, plan->m); break;
+                    ANOVA_G1(4) ANOVA_G1(6) ANOVA_G1(8) ANOVA_G1(10) ANOVA_G1(12) ANOVA_G1(14) ANOVA_G1(16)
+#undef ANOVA_G1
+                    default: set_error("dense 1-D gather: unsupported region size"); return ANOVA_EINVAL;
+                }
+            }
+            ANOVA_CHECK_LAUNCH();
+            continue;
+        }
+        if (sizeof(T) == 4 && table_kernels(plan, R))
+            ANOVA_TRY(gather_table(plan, R, sub, nsub, descs, st));
         else
-            ANOVA_TRY(gather_dispatch<T>(plan, g[0], plan->dense_sub + g[1], g[2], descs, DenseWin(), st));
+            ANOVA_TRY(gather_dispatch<T>(plan, R, sub, nsub, descs, DenseWin(), st));
     }
     return ANOVA_OK;
 }

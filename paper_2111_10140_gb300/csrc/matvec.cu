@@ -91,9 +91,12 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
         ANOVA_TRY(dense3_spread_all<T>(plan, alpha, alpha_is_double, st));
         nl += (int)plan->dense_groups.size();
     }
+    // windows not on the batched dense kernels: generic kernels, one window at a time
+    // (FP64 runs the dense 1-D / 2-D windows here too)
+    auto generic = [&](const WindowPlan& w) { return !w.dense || (sizeof(T) == 8 && w.dA < 3); };
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];
-        if (w.dense) continue;
+        if (!generic(w)) continue;
         ANOVA_TRY(spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid_of<T>(plan, w), st));
         nl++;
     }
@@ -119,7 +122,7 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
     }
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];
-        if (w.dense) continue;
+        if (!generic(w)) continue;
         ANOVA_TRY(gather_window<T>(plan, w, w.X, grid_of<T>(plan, w), tmp + (int64_t)l * N, st));
         nl++;
     }

@@ -535,6 +535,22 @@ __global__ void k_twiddles(int nos, double2* __restrict__ tw64, float2* __restri
 
 // ================================================================ set-up
 static void choose_bins(WindowPlan& w, int m) {
+    if (w.dA <= 2 && 2 * m + 2 <= 16) {
+        // dense small-region kernels: 2-D bins of 2x2 cells (R = 2m + 2); 1-D bins of 16 - 2m cells
+        // (R = 16) when the region cells bin*Tb - m + r stay inside [-nos, 2 nos), else 2 cells
+        int Tb = 2;
+        if (w.dA == 1 && (16 - 2 * m) + m - 2 < w.nos) Tb = 16 - 2 * m;
+        const int nb = (w.nos + Tb - 1) / Tb;
+        const int nbins = (w.dA == 2) ? nb * nb : nb;
+        if (nbins <= kMaxBins) {
+            w.dense = true;
+            w.T = Tb;
+            w.nb = nb;
+            w.nbins = nbins;
+            w.R = Tb + 2 * m;
+            return;
+        }
+    }
     if (w.dA == 3) {
         // dense tensor-product kernels: bins of Tb^3 cells, region Tb + 2m <= 16
         for (int Tb = 2; Tb <= 4; Tb += 2) {
@@ -591,18 +607,18 @@ __global__ void k_cell_range(const int32_t* __restrict__ cell, int64_t N, int dA
     }
 }
 
-// FP32 weight table of a dense 3-D window: for sorted node pos and axis t,
-// wtab[(pos*3 + t)*16 + r] = psi(c_t - (bin_t*T - m) - r + f_t) for r < R, 0 for
+// FP32 weight table of a dense window: for sorted node pos and axis t < dA,
+// wtab[(pos*dA + t)*16 + r] = psi(c_t - (bin_t*T - m) - r + f_t) for r < R, 0 for
 // R <= r < 16, evaluated in FP64 from the node's FP64 coordinates.
 __global__ void k_weight_table(const double* __restrict__ xw, const int32_t* __restrict__ perm, int64_t N,
-                               FrameArgs fr, int nos, int Tb, int R, int m, double b, double norm,
+                               int dA, FrameArgs fr, int nos, int Tb, int R, int m, double b, double norm,
                                float* __restrict__ wtab) {
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * 3;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * dA;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pos = idx / 3;
-        const int t = (int)(idx % 3);
+        const int64_t pos = idx / dA;
+        const int t = (int)(idx % dA);
         const int64_t i = perm[pos];
-        const double xt = fr.s * (xw[i * 3 + t] - fr.c[t]);
+        const double xt = fr.s * (xw[i * dA + t] - fr.c[t]);
         const double y = (double)nos * xt;
         const double fl = floor(y);
         const double f = y - fl;
@@ -691,12 +707,12 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
     if (w.dense && want32 && plan->N > 0) {
         cudaFree(w.wtab);
         w.wtab = nullptr;
-        ANOVA_CUDA_TRY(cudaMalloc(&w.wtab, plan->N * 48 * sizeof(float)));
+        ANOVA_CUDA_TRY(cudaMalloc(&w.wtab, plan->N * 16 * w.dA * sizeof(float)));
         FrameArgs fr;
         for (int t = 0; t < 3; t++) fr.c[t] = w.centre[t];
         fr.s = w.scale;
-        k_weight_table<<<grid_for(plan->N * 3, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
-            w.xw, w.X.perm, plan->N, fr, w.nos, w.T, w.R, plan->m, plan->b, plan->psi_norm, w.wtab);
+        k_weight_table<<<grid_for(plan->N * w.dA, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            w.xw, w.X.perm, plan->N, w.dA, fr, w.nos, w.T, w.R, plan->m, plan->b, plan->psi_norm, w.wtab);
         ANOVA_CHECK_LAUNCH();
     }
     return window_box(plan, w, st);
@@ -716,15 +732,16 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
     plan->dense_windows.clear();
     plan->dense_groups.clear();
     int total = 0;
-    for (int R = 1; R <= 16; R++) {        // windows grouped by region size (one launch each)
-        const int first = total;
-        for (int l = 0; l < plan->P; l++)
-            if (plan->win[l].dense && plan->win[l].R == R && plan->win[l].X.nsub > 0) {
-                plan->dense_windows.push_back(l);
-                total += plan->win[l].X.nsub;
-            }
-        if (total > first) plan->dense_groups.push_back({R, first, total - first});
-    }
+    for (int dA = 1; dA <= 3; dA++)          // windows grouped by dimension and region size (one launch each)
+        for (int R = 1; R <= 16; R++) {
+            const int first = total;
+            for (int l = 0; l < plan->P; l++)
+                if (plan->win[l].dense && plan->win[l].dA == dA && plan->win[l].R == R && plan->win[l].X.nsub > 0) {
+                    plan->dense_windows.push_back(l);
+                    total += plan->win[l].X.nsub;
+                }
+            if (total > first) plan->dense_groups.push_back({dA * 100 + R, first, total - first});
+        }
     plan->dense_nsub = total;
     const int nd = (int)plan->dense_windows.size();
     if (nd == 0) return ANOVA_OK;

@@ -177,7 +177,7 @@ template <typename T>
 anova_status spread_window(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const void* alpha,
                            int alpha_is_double, T* grid, cudaStream_t st) {
     if (ps.nsub == 0) return ANOVA_OK;
-    if (w.dense) return spread3_dense<T>(plan, w, ps, alpha, alpha_is_double, grid, st);
+    if (w.dense && w.dA == 3) return spread3_dense<T>(plan, w, ps, alpha, alpha_is_double, grid, st);
     const size_t sh = (size_t)region_elems(w) * sizeof(T);
     const T b = (T)plan->b, norm = (T)plan->psi_norm;
     const T* frac = frac_of<T>(ps);
@@ -199,7 +199,7 @@ template <typename T>
 anova_status gather_window(anova_plan* plan, const WindowPlan& w, const PointSet& ps, const T* h, T* out,
                            cudaStream_t st) {
     if (ps.nsub == 0) return ANOVA_OK;
-    if (w.dense) return gather3_dense<T>(plan, w, ps, h, out, st);
+    if (w.dense && w.dA == 3) return gather3_dense<T>(plan, w, ps, h, out, st);
     const size_t sh = (size_t)region_elems(w) * sizeof(T);
     const T b = (T)plan->b, norm = (T)plan->psi_norm;
     const T* frac = frac_of<T>(ps);

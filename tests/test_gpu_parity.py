@@ -278,3 +278,20 @@ def test_graph_replay_matches_direct_calls(B, torch):
         B.anova_matvec(plan, a, out)
         ref = oracle_fast(w, alpha=vals)
         assert rel(out.cpu().numpy(), ref) <= 1e-5, call
+
+
+@pytest.mark.parametrize("n,m", [(4, 1), (8, 3), (32, 6), (64, 7)])
+def test_dense_small_windows(B, torch, n, m):
+    """1-D and 2-D windows on the dense FP32 kernels (and the generic FP64 ones)."""
+    w = W.random_problem(5000, 3, [(0,), (1, 2)], 0.25, n, m, seed=100 + n + m)
+    w.epsB = 0.25
+    plan = make_plan(B, torch, w, B.MIXED)
+    ref = oracle_fast(w)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    out64 = torch.empty_like(a64)
+    B.anova_matvec(plan, a64, out64)
+    assert rel(out64.cpu().numpy(), ref) <= 1e-12
+    a32 = a64.float()
+    out32 = torch.empty_like(a32)
+    B.anova_matvec(plan, a32, out32)
+    assert rel(out32.cpu().numpy(), ref) <= 1e-5
