@@ -294,10 +294,15 @@ static anova_status read_scalar(const double* d, double* h, cudaStream_t st) {
 }
 
 // Plain CG on (K_T + lambda I) x = b, x_0 = 0 (FP64 vectors and scalars).
-// Stops when ||r|| <= tol * ||b||; returns iterations in *iters.
+// Stops when ||r|| <= tol * ||b|| (checked every kCheckEvery iterations, which
+// are queued without a host round trip in between), after maxit iterations, or
+// -- when `stagnation` is set -- when the best residual of the last
+// kStallWindow iterations is not below half the best one before them.
+constexpr int kCheckEvery = 4;
+constexpr int kStallWindow = 64;
 template <typename T>
 static anova_status cg_run(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
-                           const CgBuffers& B, int* iters, double* bb_out, cudaStream_t st) {
+                           const CgBuffers& B, int* iters, double* bb_out, cudaStream_t st, bool stagnation = false) {
     const int64_t N = plan->N;
     double* hist = B.scal + 2;
     k_cg_init<<<B.nblk, kThreads, 0, st>>>(b, N, x, B.r, B.p, 1, B.part);
@@ -308,19 +313,36 @@ static anova_status cg_run(anova_plan* plan, double lambda, const double* b, dou
     if (bb_out) *bb_out = bb;
     int it = 0;
     double rr = bb;
+    double best = bb, best_at_window = bb;
+    int window_start = 0;
+    std::vector<double> hbuf(kCheckEvery);
     while (it < maxit && rr > tol * tol * bb && bb > 0.0) {
-        ANOVA_TRY(apply_shifted<T>(plan, lambda, B.p, B.q, B, st));
-        clock_begin(plan, 3, st);
-        k_cg_update<<<B.nblk, kThreads, 0, st>>>(B.part, B.nblk, hist + it, N, x, B.r, B.p, B.q, B.part2);
-        k_cg_pupdate<<<B.nblk, kThreads, 0, st>>>(B.part2, B.nblk, hist + it, hist + it + 1, N, B.r, B.p);
-        ANOVA_CHECK_LAUNCH();
-        clock_end(plan, 3, 2, st);
-        it++;
-        ANOVA_TRY(read_scalar(hist + it, &rr, st));
-        if (!std::isfinite(rr)) {
-            set_error("CG residual is not finite");
-            *iters = it;
-            return ANOVA_ERANGE;
+        const int batch = std::min(kCheckEvery, maxit - it);
+        for (int k = 0; k < batch; k++) {
+            ANOVA_TRY(apply_shifted<T>(plan, lambda, B.p, B.q, B, st));
+            clock_begin(plan, 3, st);
+            k_cg_update<<<B.nblk, kThreads, 0, st>>>(B.part, B.nblk, hist + it, N, x, B.r, B.p, B.q, B.part2);
+            k_cg_pupdate<<<B.nblk, kThreads, 0, st>>>(B.part2, B.nblk, hist + it, hist + it + 1, N, B.r, B.p);
+            ANOVA_CHECK_LAUNCH();
+            clock_end(plan, 3, 2, st);
+            it++;
+        }
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), hist + it - batch + 1, batch * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int k = 0; k < batch; k++) {
+            if (!std::isfinite(hbuf[k])) {
+                set_error("CG residual is not finite");
+                *iters = it;
+                return ANOVA_ERANGE;
+            }
+            best = std::min(best, hbuf[k]);
+        }
+        rr = hbuf[batch - 1];
+        if (stagnation && it - window_start >= kStallWindow) {
+            if (best > 0.25 * best_at_window) break;    // residual norm not halved over the window
+            best_at_window = best;
+            window_start = it;
         }
     }
     *iters = it;
@@ -346,7 +368,7 @@ static anova_status true_residual(anova_plan* plan, double lambda, const double*
 static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
                              const CgBuffers& B, int* iters, double* relres, cudaStream_t st) {
     const int64_t N = plan->N;
-    const double inner_tol = 1e-4;
+    const double inner_floor = 1e-7;   // about what an FP32 operator supports
     double* rhs = B.x2;            // current residual (right-hand side of the correction)
     double* dx = static_cast<double*>(nullptr);
     ANOVA_CUDA_TRY(cudaMalloc(&dx, std::max<int64_t>(N, 1) * sizeof(double)));
@@ -361,8 +383,9 @@ static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, d
     while (s == ANOVA_OK && bb > 0.0 && total < maxit) {
         int it = 0;
         double rb = 0.0;
-        double tol_in = std::max(inner_tol, 0.5 * tol / std::max(rel, 1e-300));
-        s = cg_run<float>(plan, lambda, rhs, dx, std::min(tol_in, 0.5), maxit - total, B, &it, &rb, st);
+        // aim the correction directly at the target; stop early when FP32 stagnates
+        double tol_in = std::max(inner_floor, 0.5 * tol / std::max(rel, 1e-300));
+        s = cg_run<float>(plan, lambda, rhs, dx, std::min(tol_in, 0.5), maxit - total, B, &it, &rb, st, true);
         if (s != ANOVA_OK) break;
         total += std::max(it, 1);
         k_axpy<<<grid_for(N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(N, 1.0, dx, x);
