@@ -384,7 +384,7 @@ static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, d
         int it = 0;
         double rb = 0.0;
         double tol_in = std::max(inner_tol, 0.5 * tol / std::max(rel, 1e-300));
-        s = cg_run<float>(plan, lambda, rhs, dx, std::min(tol_in, 0.5), maxit - total, B, &it, &rb, st, true);
+        s = cg_run<float>(plan, lambda, rhs, dx, std::min(tol_in, 0.5), maxit - total, B, &it, &rb, st);
         if (s != ANOVA_OK) break;
         total += std::max(it, 1);
         k_axpy<<<grid_for(N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(N, 1.0, dx, x);
