@@ -96,7 +96,8 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
  *   nrhs   >= 1; ld >= N.
  * Asynchronous on `stream`.  With nrhs = 1 the plan records the call's launch
  * sequence as a CUDA graph the second time it sees the same (dtype, alpha,
- * out) and replays it from then on (at most 8 such graphs per plan).  Calls on
+ * out) and replays it from then on (at most 16 graphs per plan, shared with
+ * the CG solver, which replays its operator application the same way).  Calls on
  * one plan must not overlap on the GPU: they share the plan's work buffers.
  * Errors: EINVAL.
  */

@@ -152,10 +152,11 @@ struct anova_plan {
     int sm_count = 0;
     // replayable launch sequences of anova_matvec, keyed by (dtype, alpha, out)
     struct GraphEntry {
+        int kind;            // 0: anova_matvec, 1: CG operator application
         int dtype;
         const void* alpha;
         void* out;
-        int uses;
+        double lambda;
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graphs;

@@ -274,17 +274,66 @@ static anova_status cg_buffers(anova_plan* plan, int maxit, CgBuffers& B) {
     return ANOVA_OK;
 }
 
+// Replay a captured launch sequence keyed by (kind, dtype, input, output,
+// lambda): the first call with a key runs `launch` directly (so that one-time
+// kernel attributes are set outside any capture), the second captures it into
+// a CUDA graph, later calls replay that graph.  At most 16 graphs per plan.
+template <typename F>
+static anova_status run_cached(anova_plan* plan, int kind, int dtype, const void* in, void* out, double lambda,
+                               cudaStream_t st, F&& launch) {
+    if (!plan->use_graphs || plan->clock.enabled) return launch(st);
+    for (auto& g : plan->graphs) {
+        if (g.kind != kind || g.dtype != dtype || g.alpha != in || g.out != out || g.lambda != lambda) continue;
+        if (g.exec) {
+            ANOVA_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+            return ANOVA_OK;
+        }
+        if (!plan->capture_stream)
+            ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        ANOVA_CUDA_TRY(cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal));
+        anova_status cs = launch(plan->capture_stream);
+        cudaError_t ce = cudaStreamEndCapture(plan->capture_stream, &graph);
+        if (cs != ANOVA_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cs;
+        }
+        if (ce != cudaSuccess) {
+            set_error(std::string("graph capture: ") + cudaGetErrorString(ce));
+            return ANOVA_ECUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce));
+            return ANOVA_ECUDA;
+        }
+        g.exec = exec;
+        ANOVA_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+        return ANOVA_OK;
+    }
+    if (plan->graphs.size() >= 16) {
+        if (plan->graphs.front().exec) cudaGraphExecDestroy(plan->graphs.front().exec);
+        plan->graphs.erase(plan->graphs.begin());
+    }
+    plan->graphs.push_back({kind, dtype, in, out, lambda, nullptr});
+    return launch(st);
+}
+
 // q = (K + lambda I) v with the operator of precision T; partial sums of v.q in B.part
 template <typename T>
 static anova_status apply_shifted(anova_plan* plan, double lambda, const double* v, double* q,
                                   const CgBuffers& B, cudaStream_t st) {
     T* tmp = static_cast<T*>(plan->tmp);
-    ANOVA_TRY(windows_apply<T>(plan, v, 1, tmp, st));
-    clock_begin(plan, 3, st);
-    k_cg_q<T><<<B.nblk, kThreads, 0, st>>>(tmp, plan->eta_dev, plan->P, plan->N, lambda, v, q, B.part);
-    ANOVA_CHECK_LAUNCH();
-    clock_end(plan, 3, 1, st);
-    return ANOVA_OK;
+    return run_cached(plan, 1, (int)sizeof(T), v, q, lambda, st, [&](cudaStream_t s) -> anova_status {
+        ANOVA_TRY(windows_apply<T>(plan, v, 1, tmp, s));
+        clock_begin(plan, 3, s);
+        k_cg_q<T><<<B.nblk, kThreads, 0, s>>>(tmp, plan->eta_dev, plan->P, plan->N, lambda, v, q, B.part);
+        ANOVA_CHECK_LAUNCH();
+        clock_end(plan, 3, 1, s);
+        return ANOVA_OK;
+    });
 }
 
 static anova_status read_scalar(const double* d, double* h, cudaStream_t st) {
@@ -503,50 +552,12 @@ anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, vo
         return ANOVA_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (nrhs == 1 && plan->use_graphs && !plan->clock.enabled && plan->N > 0) {
-        // replay the captured launch sequence for this (dtype, alpha, out); the
-        // first call with a new key runs directly, the second one captures
-        for (auto& g : plan->graphs)
-            if (g.dtype == dtype && g.alpha == alpha && g.out == out) {
-                if (g.exec) {
-                    ANOVA_CUDA_TRY(cudaGraphLaunch(g.exec, st));
-                    return ANOVA_OK;
-                }
-                if (!plan->capture_stream)
-                    ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking));
-                cudaGraph_t graph = nullptr;
-                ANOVA_CUDA_TRY(cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal));
-                anova_status cs = (dtype == ANOVA_FP64)
-                                      ? matvec_one<double>(plan, static_cast<const double*>(alpha),
-                                                           static_cast<double*>(out), plan->capture_stream)
-                                      : matvec_one<float>(plan, static_cast<const float*>(alpha),
-                                                          static_cast<float*>(out), plan->capture_stream);
-                cudaError_t ce = cudaStreamEndCapture(plan->capture_stream, &graph);
-                if (cs != ANOVA_OK) {
-                    if (graph) cudaGraphDestroy(graph);
-                    return cs;
-                }
-                if (ce != cudaSuccess) {
-                    set_error(std::string("anova_matvec: graph capture: ") + cudaGetErrorString(ce));
-                    return ANOVA_ECUDA;
-                }
-                cudaGraphExec_t exec = nullptr;
-                ce = cudaGraphInstantiate(&exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ce != cudaSuccess) {
-                    set_error(std::string("anova_matvec: graph instantiate: ") + cudaGetErrorString(ce));
-                    return ANOVA_ECUDA;
-                }
-                g.exec = exec;
-                ANOVA_CUDA_TRY(cudaGraphLaunch(g.exec, st));
-                return ANOVA_OK;
-            }
-        if (plan->graphs.size() >= 8) {
-            if (plan->graphs.front().exec) cudaGraphExecDestroy(plan->graphs.front().exec);
-            plan->graphs.erase(plan->graphs.begin());
-        }
-        plan->graphs.push_back({dtype, alpha, out, 1, nullptr});
-    }
+    if (nrhs == 1 && plan->N > 0)
+        return run_cached(plan, 0, dtype, alpha, out, 0.0, st, [&](cudaStream_t s) -> anova_status {
+            if (dtype == ANOVA_FP64)
+                return matvec_one<double>(plan, static_cast<const double*>(alpha), static_cast<double*>(out), s);
+            return matvec_one<float>(plan, static_cast<const float*>(alpha), static_cast<float*>(out), s);
+        });
     for (int r = 0; r < nrhs; r++) {
         if (dtype == ANOVA_FP64)
             ANOVA_TRY(matvec_one<double>(plan, static_cast<const double*>(alpha) + r * ld,
