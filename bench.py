@@ -273,6 +273,17 @@ def run_ours(args):
                 "stage_ms_per_step": {k: v / args.steps for k, v in
                                       zip(["spread", "fft", "gather", "window_sum"], stage_ms)}}
 
+    # accuracy of the timed operator: FP32 fast matvec vs the direct sum on sampled rows (GPU, exact FP64 kernel)
+    rows = torch.from_numpy(np.sort(np.random.default_rng(7).choice(N, args.check_rows, replace=False))).to(dev)
+    dref = torch.empty(args.check_rows, dtype=torch.float64, device=dev)
+    B.anova_direct_matvec(X[rows].contiguous(), X, w.windows, w.ell, torch.from_numpy(w.alpha).to(dev), dref,
+                          dtype=B.FP64)
+    step()
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(out.double()[rows] - dref) / torch.linalg.norm(dref)).item()
+    accuracy = {"rel_err_vs_direct": err, "sample_rows": args.check_rows, "direct": "anova_direct_matvec FP64",
+                "target": 1e-5, "meets_target": bool(err <= 1e-5)}
+
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     a_host = torch.from_numpy(w.alpha.astype(np.float32)).pin_memory()
     o_host = torch.empty(N, dtype=torch.float32).pin_memory()
@@ -344,12 +355,51 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": 4 * N,
                         "d2h_bytes_per_step": 4 * N},
-                "gpu_launches": launches, "latency_ms": lat, "krr": krr, "krr_plain_fp64": krr64,
+                "gpu_launches": launches, "latency_ms": lat, "accuracy": accuracy, "krr": krr, "krr_plain_fp64": krr64,
                 "clocks": dict(clk.summary(), window="0.6 s busy lead-in, timed steps, e2e steps and the KRR solve")}
         print(json.dumps(line), flush=True)
     plan.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_crossover(args):
+    """Direct O(N^2 P) GPU sum vs the fast summation on the mid workload's shape."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    from paper_2111_10140_gb300 import workloads as W
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    for N in [1000, 3000, 10_000, 30_000, 100_000, 300_000, 1_000_000]:
+        w = W.plain_mid(N=N)
+        X = torch.from_numpy(w.X).to(dev)
+        a64 = torch.from_numpy(w.alpha).to(dev)
+        plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                    precision=B.FP32)
+        a32, o32 = a64.float(), torch.empty(N, dtype=torch.float32, device=dev)
+        od = torch.empty(N, dtype=torch.float64, device=dev)
+
+        def timeit(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_fast = timeit(lambda: B.anova_matvec(plan, a32, o32), 20)
+        reps = 3 if N <= 300_000 else 1
+        t_dir = timeit(lambda: B.anova_direct_matvec(X, X, w.windows, w.ell, a64, od, dtype=B.FP32), reps)
+        err = (torch.linalg.norm(o32.double() - od) / torch.linalg.norm(od)).item()
+        print(json.dumps({"crossover": True, "N": N, "fast_ms": t_fast, "direct_fp32_ms": t_dir,
+                          "speedup": t_dir / t_fast, "rel_diff": err}), flush=True)
+        plan.close()
 
 
 def main():
@@ -363,11 +413,16 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-krr", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--check-rows", type=int, default=2048)
+    ap.add_argument("--crossover", action="store_true",
+                    help="direct vs fast matvec time over N (the paper's Fig. 1 on synthetic data); prints one line per N")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.crossover:
+        run_crossover(args)
     else:
         run_ours(args)
 

@@ -167,6 +167,25 @@ anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z,
 anova_status krr_predict_noalloc(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
                                  int64_t ldz, double* out, void* stream);
 
+/*
+ * anova_direct_matvec -- the exact kernel sum, no fast summation (Sec. 2
+ * Eq. mult_with_K; Sec. 4.2 Eq. kernelsum with Z != X), O(M N P) work:
+ *   out_i = sum_l eta_l sum_j alpha_j exp(-||z_i^{W_l} - x_j^{W_l}||^2 / ell^2).
+ *
+ *   Z      device FP64, M x d row-major (ldz >= d); pass X for K alpha.
+ *   X      device FP64, N x d row-major (ldx >= d).
+ *   windows, weights, ell as in anova_fastsum_plan (weights may be NULL).
+ *   dtype  ANOVA_FP64 (all in double) or ANOVA_FP32 (coordinates, exponentials
+ *          and per-tile partial sums in float, tile sums in double; relative
+ *          error around 1e-6).
+ *   alpha  device FP64, N entries; out device FP64, M entries.
+ * Allocates nothing; asynchronous on `stream`.  Errors: EINVAL.
+ */
+anova_status anova_direct_matvec(const double* Z, int64_t M, int64_t ldz, const double* X, int64_t N,
+                                 int64_t ldx, int32_t d, const int32_t* windows, int32_t P,
+                                 const double* weights, double ell, int32_t dtype, const double* alpha,
+                                 double* out, void* stream);
+
 /* Free every device buffer of the plan.  NULL is ignored. */
 void anova_plan_destroy(anova_plan* plan);
 

@@ -33,6 +33,8 @@ _SIGNATURES = {
     "krr_cg_solve": (_i32, [_vp, _f64, _vp, _vp, _i32, _i64, _f64, _i32, _pi32, _pf64, _vp]),
     "krr_predict": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
     "krr_predict_noalloc": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
+    "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
+                                   _vp, _vp]),
     "anova_plan_destroy": (None, [_vp]),
     "anova_status_string": (ctypes.c_char_p, [_i32]),
     "anova_last_error": (ctypes.c_char_p, []),
@@ -192,6 +194,20 @@ def krr_predict_noalloc(plan: Plan, alpha, Z, out, stream=None):
     _require_cuda(out, "out", torch.float64)
     _check(lib().krr_predict_noalloc(plan.handle, _ptr(alpha), _ptr(Z), Z.shape[0], Z.shape[1], _ptr(out),
                                      _stream(stream)), "krr_predict_noalloc")
+    return out
+
+
+def anova_direct_matvec(Z, X, windows, ell, alpha, out, weights=None, dtype=FP64, stream=None):
+    """Exact kernel sum out = sum_l eta_l sum_j alpha_j kappa_l(z_i, x_j) on the GPU."""
+    import torch
+    for t, nm in ((Z, "Z"), (X, "X"), (alpha, "alpha"), (out, "out")):
+        _require_cuda(t, nm, torch.float64)
+    W = windows_array(windows) if not isinstance(windows, np.ndarray) else np.ascontiguousarray(windows, np.int32)
+    wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    _check(lib().anova_direct_matvec(_ptr(Z), Z.shape[0], Z.shape[1], _ptr(X), X.shape[0], X.shape[1], X.shape[1],
+                                     W.ctypes.data_as(_pi32), W.shape[0],
+                                     wts.ctypes.data_as(_pf64) if wts is not None else None, float(ell),
+                                     int(dtype), _ptr(alpha), _ptr(out), _stream(stream)), "anova_direct_matvec")
     return out
 
 

@@ -295,3 +295,15 @@ def test_dense_small_windows(B, torch, n, m):
     out32 = torch.empty_like(a32)
     B.anova_matvec(plan, a32, out32)
     assert rel(out32.cpu().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [("FP64", 1e-12), ("FP32", 1e-5)])
+def test_direct_matvec_matches_oracle_direct(B, torch, dtype, tol):
+    w = W.random_problem(1500, 7, [(0, 1, 2), (3, 4), (5,), (6,)], 0.2, 16, 4, seed=111)
+    Z = W.random_problem(700, 7, [(0, 1, 2), (3, 4), (5,), (6,)], 0.2, 16, 4, seed=112).X
+    eta = np.array([0.1, 0.2, 0.3, 0.4])
+    out = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
+    B.anova_direct_matvec(torch.from_numpy(Z).cuda(), torch.from_numpy(w.X).cuda(), w.windows, w.ell,
+                          torch.from_numpy(w.alpha).cuda(), out, weights=eta, dtype=getattr(B, dtype))
+    ref = oracle.direct(Z, w.X, w.windows, eta, w.ell, w.alpha)
+    assert rel(out.cpu().numpy(), ref) <= tol
