@@ -402,6 +402,68 @@ def run_crossover(args):
         plan.close()
 
 
+def run_serve(args):
+    """Serving form: models of the mid workload's shape stay resident in a
+    request server; predictions of `--serve-rows` test points arrive as a
+    Poisson stream at `--serve-rate` requests/s (a fit of a fresh model joins
+    the stream every `--serve-fit-every` requests).  Prints one line with the
+    latency percentiles and the served throughput."""
+    import time
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    from paper_2111_10140_gb300 import workloads as W
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(7)
+    n_models, rows, rate = 4, args.serve_rows, args.serve_rate
+    probs = [W.plain_mid(N=args.serve_n) for _ in range(n_models)]
+    for k, w in enumerate(probs):      # distinct targets per model
+        w.y = np.random.default_rng(100 + k).standard_normal(w.X.shape[0])
+    Xs = [torch.from_numpy(w.X).to(dev) for w in probs]
+    ys = [torch.from_numpy(w.y).to(dev) for w in probs]
+    Zpool = torch.from_numpy(rng.uniform(probs[0].X.min(0), probs[0].X.max(0),
+                                         size=(16 * rows, probs[0].X.shape[1]))).to(dev)
+    torch.cuda.synchronize()
+    sv = B.Server(n_workers=args.serve_workers, hbm_budget_bytes=64 << 30)
+    lam, tol = probs[0].lam, 1e-6
+    t_fit0 = time.perf_counter()
+    models = [sv.submit_fit(X, w.windows, w.ell, y, lam, n=w.n, m=w.m, eps_B=w.epsB, tol=tol)
+              for w, X, y in zip(probs, Xs, ys)]
+    fit_info = [sv.wait(t) for t in models]
+    t_fit = time.perf_counter() - t_fit0
+    outs = [torch.empty(rows, dtype=torch.float64, device=dev) for _ in range(args.serve_requests)]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_requests))
+    tickets, fits = [], []
+    t0 = time.perf_counter()
+    for i, ta in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        if args.serve_fit_every and i % args.serve_fit_every == args.serve_fit_every - 1:
+            k = int(rng.integers(n_models))
+            fits.append(sv.submit_fit(Xs[k], probs[k].windows, probs[k].ell, ys[k], lam, n=probs[k].n,
+                                      m=probs[k].m, eps_B=probs[k].epsB, tol=tol))
+        b = int(rng.integers(16))
+        tickets.append(sv.submit_predict(models[int(rng.integers(n_models))], Zpool[b * rows:(b + 1) * rows],
+                                         outs[i]))
+    lat = np.array([sv.wait(t)["latency_ms"] for t in tickets])
+    t_all = time.perf_counter() - t0
+    fit_lat = [sv.wait(t)["latency_ms"] for t in fits]
+    sv.close()
+    print(json.dumps({
+        "serve": True, "workload": f"plain_mid shape, N={args.serve_n}, d=9, 8 windows x 2 features",
+        "workers": args.serve_workers, "models": n_models, "rows_per_request": rows,
+        "offered_rate_rps": rate, "requests": len(tickets), "fits_in_stream": len(fits),
+        "predict_p50_ms": float(np.percentile(lat, 50)), "predict_p99_ms": float(np.percentile(lat, 99)),
+        "achieved_rps": len(tickets) / t_all, "rows_per_s": len(tickets) * rows / t_all,
+        "fit_latency_ms": [round(x, 1) for x in fit_lat],
+        "initial_fits_s": t_fit, "initial_fit_iters": [f["iterations"] for f in fit_info]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,6 +478,14 @@ def main():
     ap.add_argument("--check-rows", type=int, default=2048)
     ap.add_argument("--crossover", action="store_true",
                     help="direct vs fast matvec time over N (the paper's Fig. 1 on synthetic data); prints one line per N")
+    ap.add_argument("--serve", action="store_true",
+                    help="Poisson stream of prediction (and fit) requests through the request server")
+    ap.add_argument("--serve-n", type=int, default=100_000)
+    ap.add_argument("--serve-rows", type=int, default=4096)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-fit-every", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -423,6 +493,8 @@ def main():
         run_reference(args)
     elif args.crossover:
         run_crossover(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

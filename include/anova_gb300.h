@@ -186,6 +186,55 @@ anova_status anova_direct_matvec(const double* Z, int64_t M, int64_t ldz, const 
                                  const double* weights, double ell, int32_t dtype, const double* alpha,
                                  double* out, void* stream);
 
+/* ----------------------------------------------------------------------------
+ * Request server: kernel ridge regression fits (anova_fastsum_plan with
+ * ANOVA_MIXED + krr_cg_solve) and predictions (krr_predict) served by worker
+ * threads, each on its own CUDA stream.  Requests are admitted in arrival order
+ * as soon as a worker is free and their device memory fits the budget (a
+ * request that alone exceeds the budget runs when nothing else does); work of
+ * different requests overlaps on the GPU.  Fitted models stay on the device
+ * until released.  The paper serves no requests; this is the serving form of
+ * its fit (Sec. 2) and predict (Sec. 4.3) operations.
+ * ------------------------------------------------------------------------- */
+typedef struct anova_server anova_server;
+
+/* n_workers in 1..64; hbm_budget_bytes > 0. */
+anova_status anova_server_create(int32_t n_workers, int64_t hbm_budget_bytes, anova_server** out);
+
+/*
+ * Queue a fit.  points (device, N x d row-major, ld = d) and y (device, N) must
+ * stay valid until anova_server_wait on the returned ticket has returned.
+ * windows / n (host, copied), ell, m, eps_B as in anova_fastsum_plan (sigma 2,
+ * p 8); lambda, tol, maxit as in krr_cg_solve.  The ticket also names the model.
+ */
+anova_status anova_server_submit_fit(anova_server* server, const double* points, int64_t N, int32_t d,
+                                     const int32_t* windows, int32_t P, double ell, const int32_t* n,
+                                     int32_t m, double eps_B, double lambda, const double* y, double tol,
+                                     int32_t maxit, int64_t* ticket);
+
+/* Queue a prediction at M test points Z (device, M x d) into out (device, M)
+ * with the model of fit ticket `model` (waits for that fit if needed). */
+anova_status anova_server_submit_predict(anova_server* server, int64_t model, const double* Z, int64_t M,
+                                         double* out, int64_t* ticket);
+
+/* Block until the request is done; result receives its status, latency_ms the
+ * time from submission to completion; iterations / relres the CG figures of a
+ * fit.  Output pointers may be NULL. */
+anova_status anova_server_wait(anova_server* server, int64_t ticket, anova_status* result, double* latency_ms,
+                               int32_t* iterations, double* relres);
+
+/* Drop a fitted model and return its memory to the budget. */
+anova_status anova_server_release(anova_server* server, int64_t model);
+
+/* Latency percentiles of the completed requests, their number, and the budgeted
+ * bytes currently held (resident models and running requests). */
+anova_status anova_server_stats(anova_server* server, double* p50_ms, double* p99_ms, int64_t* completed,
+                                int64_t* bytes_in_use);
+
+/* Stop the workers and free every model.  Queued requests that have not started
+ * are dropped; call this only after every anova_server_wait has returned. */
+void anova_server_destroy(anova_server* server);
+
 /* Free every device buffer of the plan.  NULL is ignored. */
 void anova_plan_destroy(anova_plan* plan);
 

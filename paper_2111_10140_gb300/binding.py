@@ -35,6 +35,14 @@ _SIGNATURES = {
     "krr_predict_noalloc": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
+    "anova_server_create": (_i32, [_i32, _i64, ctypes.POINTER(_vp)]),
+    "anova_server_submit_fit": (_i32, [_vp, _vp, _i64, _i32, _pi32, _i32, _f64, _pi32, _i32, _f64, _f64, _vp,
+                                       _f64, _i32, _pi64]),
+    "anova_server_submit_predict": (_i32, [_vp, _i64, _vp, _i64, _vp, _pi64]),
+    "anova_server_wait": (_i32, [_vp, _i64, _pi32, _pf64, _pi32, _pf64]),
+    "anova_server_release": (_i32, [_vp, _i64]),
+    "anova_server_stats": (_i32, [_vp, _pf64, _pf64, _pi64, _pi64]),
+    "anova_server_destroy": (None, [_vp]),
     "anova_plan_destroy": (None, [_vp]),
     "anova_status_string": (ctypes.c_char_p, [_i32]),
     "anova_last_error": (ctypes.c_char_p, []),
@@ -245,3 +253,69 @@ def anova_stage_times(plan: Plan):
     la = (ctypes.c_int64 * 8)()
     k = lib().anova_stage_times(plan.handle, ms, la, 8)
     return list(ms[:k]), list(la[:k])
+
+
+class Server:
+    """Handle of an anova_server (see the header); tensors passed in must stay
+    alive until the corresponding wait() has returned."""
+
+    def __init__(self, n_workers=4, hbm_budget_bytes=150 << 30):
+        h = ctypes.c_void_p()
+        _check(lib().anova_server_create(int(n_workers), int(hbm_budget_bytes), ctypes.byref(h)),
+               "anova_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit_fit(self, points, windows, ell, y, lam, n=None, m=6, eps_B=1.0 / 16, tol=1e-6, maxit=5000):
+        import torch
+        _require_cuda(points, "points", torch.float64)
+        _require_cuda(y, "y", torch.float64)
+        W = windows_array(windows)
+        P = W.shape[0]
+        nv = None if n is None else np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int32), (P,)), np.int32)
+        t = ctypes.c_int64()
+        _check(lib().anova_server_submit_fit(self.handle, _ptr(points), points.shape[0], points.shape[1],
+                                             W.ctypes.data_as(_pi32), P, float(ell),
+                                             nv.ctypes.data_as(_pi32) if nv is not None else None, int(m),
+                                             float(eps_B), float(lam), _ptr(y), float(tol), int(maxit),
+                                             ctypes.byref(t)), "anova_server_submit_fit")
+        self._keep[t.value] = (points, y)
+        return t.value
+
+    def submit_predict(self, model, Z, out):
+        import torch
+        _require_cuda(Z, "Z", torch.float64)
+        _require_cuda(out, "out", torch.float64)
+        t = ctypes.c_int64()
+        _check(lib().anova_server_submit_predict(self.handle, int(model), _ptr(Z), Z.shape[0], _ptr(out),
+                                                 ctypes.byref(t)), "anova_server_submit_predict")
+        self._keep[t.value] = (Z, out)
+        return t.value
+
+    def wait(self, ticket):
+        st, lat, it, rr = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().anova_server_wait(self.handle, int(ticket), ctypes.byref(st), ctypes.byref(lat),
+                                       ctypes.byref(it), ctypes.byref(rr)), "anova_server_wait")
+        self._keep.pop(ticket, None)
+        return {"status": st.value, "latency_ms": lat.value, "iterations": it.value, "relres": rr.value}
+
+    def release(self, model):
+        _check(lib().anova_server_release(self.handle, int(model)), "anova_server_release")
+
+    def stats(self):
+        p50, p99 = ctypes.c_double(), ctypes.c_double()
+        n, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().anova_server_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n),
+                                        ctypes.byref(b)), "anova_server_stats")
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "completed": n.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if self.handle:
+            lib().anova_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

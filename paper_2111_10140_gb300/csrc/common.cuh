@@ -198,6 +198,7 @@ anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coord
                             int64_t ldc, const double* centre, double scale, PointSet& ps,
                             cudaStream_t st);
 void free_pointset(PointSet& ps);
+void free_pointset_async(PointSet& ps, cudaStream_t st);
 anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M, WindowPlan& dst,
                             cudaStream_t st);
 void window_release_reframed(WindowPlan& w);

@@ -420,7 +420,7 @@ static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, d
     const double inner_tol = 1e-4;     // per refinement pass (tighter FP32 passes converge slowly near the floor)
     double* rhs = B.x2;            // current residual (right-hand side of the correction)
     double* dx = static_cast<double*>(nullptr);
-    ANOVA_CUDA_TRY(cudaMalloc(&dx, std::max<int64_t>(N, 1) * sizeof(double)));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&dx, std::max<int64_t>(N, 1) * sizeof(double), st));
     ANOVA_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double), st));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(rhs, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_cg_init<<<B.nblk, kThreads, 0, st>>>(b, N, B.q, B.r, B.p, 0, B.part);
@@ -453,7 +453,7 @@ static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, d
         }
         if (rel <= tol) break;
     }
-    cudaFree(dx);
+    cudaFreeAsync(dx, st);
     *iters = total;
     *relres = (bb > 0.0) ? rel : 0.0;
     if (s == ANOVA_OK && bb > 0.0 && rel > tol) s = ANOVA_ENOCONV;
@@ -477,8 +477,8 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
     const int P = plan->P;
     T* tmp = nullptr;
     double* zw = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&tmp, std::max<int64_t>(M, 1) * P * sizeof(T)));
-    ANOVA_CUDA_TRY(cudaMalloc(&zw, std::max<int64_t>(M, 1) * 3 * sizeof(double)));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&tmp, std::max<int64_t>(M, 1) * P * sizeof(T), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&zw, std::max<int64_t>(M, 1) * 3 * sizeof(double), st));
     anova_status s = ANOVA_OK;
     for (int l = 0; l < P && s == ANOVA_OK; l++) {
         const WindowPlan& base = plan->win[l];
@@ -515,7 +515,7 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
             set_error(std::string("predict: ") + cudaGetErrorString(e));
             s = ANOVA_ECUDA;
         }
-        free_pointset(zs);
+        free_pointset_async(zs, st);
         wz.X = PointSet();
         if (reframe) window_release_reframed(joint);
     }
@@ -529,8 +529,8 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
             s = ANOVA_ECUDA;
         }
     }
-    cudaFree(tmp);
-    cudaFree(zw);
+    cudaFreeAsync(tmp, st);
+    cudaFreeAsync(zw, st);
     return s;
 }
 

@@ -286,6 +286,17 @@ __global__ void k_sub_list(const int32_t* __restrict__ bin_start, const int32_t*
     }
 }
 
+// stream-ordered release (no device-wide synchronisation)
+void free_pointset_async(PointSet& ps, cudaStream_t st) {
+    cudaFreeAsync(ps.perm, st);
+    cudaFreeAsync(ps.cell, st);
+    cudaFreeAsync(ps.frac64, st);
+    cudaFreeAsync(ps.frac32, st);
+    cudaFreeAsync(ps.bin_start, st);
+    cudaFreeAsync(ps.sub, st);
+    ps = PointSet();
+}
+
 void free_pointset(PointSet& ps) {
     cudaFree(ps.perm);
     cudaFree(ps.cell);
@@ -306,22 +317,22 @@ anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coord
     const bool want64 = (plan->precision & ANOVA_FP64) != 0;
     const bool want32 = (plan->precision & ANOVA_FP32) != 0;
     if (N == 0) {
-        ANOVA_CUDA_TRY(cudaMalloc(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t)));
+        ANOVA_CUDA_TRY(cudaMallocAsync(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t), st));
         ANOVA_CUDA_TRY(cudaMemsetAsync(ps.bin_start, 0, (w.nbins + 1) * sizeof(int32_t), st));
         return ANOVA_OK;
     }
-    ANOVA_CUDA_TRY(cudaMalloc(&ps.perm, N * sizeof(int32_t)));
-    ANOVA_CUDA_TRY(cudaMalloc(&ps.cell, N * dA * sizeof(int32_t)));
-    if (want64) ANOVA_CUDA_TRY(cudaMalloc(&ps.frac64, N * dA * sizeof(double)));
-    if (want32) ANOVA_CUDA_TRY(cudaMalloc(&ps.frac32, N * dA * sizeof(float)));
-    ANOVA_CUDA_TRY(cudaMalloc(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.perm, N * sizeof(int32_t), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.cell, N * dA * sizeof(int32_t), st));
+    if (want64) ANOVA_CUDA_TRY(cudaMallocAsync(&ps.frac64, N * dA * sizeof(double), st));
+    if (want32) ANOVA_CUDA_TRY(cudaMallocAsync(&ps.frac32, N * dA * sizeof(float), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t), st));
 
     const int nchunk = (int)((N + kBinChunk - 1) / kBinChunk);
     const int64_t L = (int64_t)w.nbins * nchunk;
     int32_t *hist = nullptr, *nch = nullptr, *tot = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&hist, L * sizeof(int32_t)));
-    ANOVA_CUDA_TRY(cudaMalloc(&nch, (w.nbins + 1) * sizeof(int32_t)));
-    ANOVA_CUDA_TRY(cudaMalloc(&tot, 2 * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&hist, L * sizeof(int32_t), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&nch, (w.nbins + 1) * sizeof(int32_t), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&tot, 2 * sizeof(int32_t), st));
     FrameArgs fr;
     for (int t = 0; t < 3; t++) fr.c[t] = centre[t];
     fr.s = scale;
@@ -348,13 +359,13 @@ anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coord
         set_error("binning lost nodes");
         return ANOVA_ECUDA;
     }
-    ANOVA_CUDA_TRY(cudaMalloc(&ps.sub, std::max(ps.nsub, 1) * sizeof(int4)));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.sub, std::max(ps.nsub, 1) * sizeof(int4), st));
     k_sub_list<<<grid_for(w.nbins, kThreads, 1024), kThreads, 0, st>>>(ps.bin_start, nch, w.nbins, ps.sub);
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(hist);
-    cudaFree(nch);
-    cudaFree(tot);
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(nch, st);
+    cudaFreeAsync(tot, st);
     return ANOVA_OK;
 }
 

@@ -1,0 +1,400 @@
+// server.cu -- a request server for kernel ridge regression with the ANOVA
+// fast summation (fit = plan + CG solve of Sec. 2; predict = the test-point
+// summation of Sec. 4.3).
+//
+// Worker threads, each with its own CUDA stream, take requests from one
+// queue in arrival order as soon as a worker is idle and the request's device
+// memory fits under the budget (continuous admission: a request never waits
+// for a batch to fill).  Work of different requests overlaps on the GPU.
+// Fitted models -- plan, coefficients -- stay resident on the device until
+// released.  Host code only; every computation is a call of the library's
+// entry points on the worker's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace anova {
+
+struct ServerRequest {
+    int64_t ticket = 0;
+    int kind = 0;                 // 0 fit, 1 predict
+    // fit
+    const double* points = nullptr;
+    int64_t N = 0;
+    int32_t d = 0;
+    std::vector<int32_t> windows;
+    int32_t P = 0;
+    double ell = 0, eps_B = 0, lambda = 0, tol = 0;
+    std::vector<int32_t> n;
+    int32_t m = 0, maxit = 0;
+    const double* y = nullptr;
+    // predict
+    int64_t model = 0;
+    const double* Z = nullptr;
+    int64_t M = 0;
+    double* out = nullptr;
+    // bookkeeping
+    int64_t bytes = 0;
+    std::chrono::steady_clock::time_point submitted;
+    double latency_ms = 0.0;
+    anova_status status = ANOVA_OK;
+    int32_t iterations = 0;
+    double relres = 0.0;
+    std::string error;            // the worker's error text, handed to the waiting thread
+    bool done = false;
+};
+
+struct ServerModel {
+    anova_plan* plan = nullptr;
+    double* alpha = nullptr;      // device, N
+    int64_t N = 0, bytes = 0;
+    int32_t d = 0;
+    bool ready = false;
+    bool busy = false;            // a prediction is running: the plan's grids are in use
+    bool releasing = false;       // released while busy: freed when that prediction ends
+};
+
+}  // namespace anova
+
+struct anova_server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<anova::ServerRequest>> queue;
+    std::map<int64_t, std::shared_ptr<anova::ServerRequest>> requests;
+    std::map<int64_t, anova::ServerModel> models;
+    std::vector<std::thread> workers;
+    std::vector<double> latencies;
+    int64_t next_ticket = 1;
+    int64_t budget = 0, in_use = 0;
+    bool stop = false;
+    int device = 0;
+    int running = 0;
+    std::chrono::steady_clock::time_point t0;
+};
+
+namespace anova {
+
+// device bytes of a fitted model: the plan's node arrays, weight tables,
+// grids and work buffers, the CG vectors and the coefficients
+static int64_t fit_bytes(int64_t N, const std::vector<int32_t>& windows, int32_t P, const std::vector<int32_t>& n) {
+    int64_t b = 0;
+    for (int l = 0; l < P; l++) {
+        int dA = 0;
+        while (dA < 3 && windows[3 * l + dA] >= 0) dA++;
+        int64_t nos = 2 * (n.empty() ? 32 : n[l]), grid = 1;
+        for (int t = 0; t < dA; t++) grid *= nos;
+        b += N * (8 * dA + 4 + 4 * dA + 8 * dA + 4 * dA + 64 * dA + 8 + 4) + grid * 8 * 3;
+    }
+    return b + N * (8 * 5) + (64 << 20);
+}
+
+static int64_t predict_bytes(int64_t M, int32_t P) { return M * (P * 8 + 3 * 8 + 48) + (16 << 20); }
+
+static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
+    if (r.kind == 0) {
+        ServerModel mdl;
+        mdl.N = r.N;
+        mdl.d = r.d;
+        anova_status s = anova_fastsum_plan(r.points, r.N, r.d, r.d, r.windows.data(), r.P, nullptr, r.ell,
+                                            r.n.empty() ? nullptr : r.n.data(), r.m, 2.0, r.eps_B, 8,
+                                            ANOVA_MIXED, st, &mdl.plan);
+        if (s == ANOVA_OK) {
+            if (cudaMalloc(&mdl.alpha, std::max<int64_t>(r.N, 1) * sizeof(double)) != cudaSuccess) s = ANOVA_ENOMEM;
+        }
+        if (s == ANOVA_OK)
+            s = krr_cg_solve(mdl.plan, r.lambda, r.y, mdl.alpha, 1, r.N, r.tol, r.maxit, &r.iterations, &r.relres, st);
+        std::lock_guard<std::mutex> lock(sv->mu);
+        if (s == ANOVA_OK || s == ANOVA_ENOCONV) {
+            mdl.bytes = r.bytes;
+            mdl.ready = true;
+            sv->models[r.ticket] = mdl;
+        } else {
+            if (mdl.plan) anova_plan_destroy(mdl.plan);
+            cudaFree(mdl.alpha);
+            sv->in_use -= r.bytes;
+        }
+        r.status = s;
+        if (s != ANOVA_OK) r.error = anova_last_error();
+        return;
+    }
+    ServerModel mdl;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->models.find(r.model);
+        if (it == sv->models.end() || !it->second.ready || !it->second.busy) {
+            sv->in_use -= r.bytes;
+            r.status = ANOVA_EINVAL;
+            r.error = "anova_server: the model of this prediction failed to fit or was released";
+            return;
+        }
+        mdl = it->second;
+    }
+    anova_status s = krr_predict(mdl.plan, mdl.alpha, r.Z, r.M, mdl.d, r.out, st);
+    if (s != ANOVA_OK) r.error = anova_last_error();
+    bool free_now = false;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->in_use -= r.bytes;
+        r.status = s;
+        auto it = sv->models.find(r.model);
+        it->second.busy = false;
+        if (it->second.releasing) {
+            sv->in_use -= it->second.bytes;
+            sv->models.erase(it);
+            free_now = true;
+        }
+    }
+    if (free_now) {
+        anova_plan_destroy(mdl.plan);
+        cudaFree(mdl.alpha);
+    }
+}
+
+static void worker_main(anova_server* sv) {
+    cudaSetDevice(sv->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+        std::shared_ptr<ServerRequest> r;
+        {
+            std::unique_lock<std::mutex> lock(sv->mu);
+            for (;;) {
+                if (sv->stop) {
+                    lock.unlock();
+                    cudaStreamDestroy(st);
+                    return;
+                }
+                // admit the oldest request whose memory fits; a prediction waits
+                // while its model is still being fitted or serves another
+                // prediction (one plan's grids serve one request at a time)
+                auto pick = sv->queue.end();
+                for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+                    const auto& q = *it;
+                    if (q->kind == 1) {
+                        auto m = sv->models.find(q->model);
+                        if (m == sv->models.end()) {
+                            auto rq = sv->requests.find(q->model);
+                            const bool fit_over = rq != sv->requests.end() && rq->second->done;
+                            if (!fit_over) continue;   // fit still queued or running
+                        } else if (!m->second.ready || m->second.busy || m->second.releasing) {
+                            continue;
+                        }
+                    }
+                    if (sv->in_use + q->bytes <= sv->budget || sv->running == 0) {
+                        pick = it;
+                        break;
+                    }
+                    break;   // keep arrival order for memory admission
+                }
+                if (pick != sv->queue.end()) {
+                    r = *pick;
+                    sv->queue.erase(pick);
+                    sv->in_use += r->bytes;
+                    sv->running++;
+                    if (r->kind == 1) {
+                        auto m = sv->models.find(r->model);
+                        if (m != sv->models.end()) m->second.busy = true;
+                    }
+                    break;
+                }
+                sv->cv_work.wait(lock);
+            }
+        }
+        run_request(sv, *r, st);
+        // completion means the result is in device memory
+        const cudaError_t se = cudaStreamSynchronize(st);
+        if (se != cudaSuccess && r->status == ANOVA_OK) {
+            r->status = ANOVA_ECUDA;
+            r->error = std::string("anova_server: ") + cudaGetErrorString(se);
+        }
+        const auto t1 = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> lock(sv->mu);
+            r->latency_ms = std::chrono::duration<double, std::milli>(t1 - r->submitted).count();
+            r->done = true;
+            sv->running--;
+            if (r->status == ANOVA_OK || r->status == ANOVA_ENOCONV) sv->latencies.push_back(r->latency_ms);
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+}
+
+static anova_status enqueue(anova_server* sv, std::shared_ptr<ServerRequest> r, int64_t* ticket) {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    r->ticket = sv->next_ticket++;
+    r->submitted = std::chrono::steady_clock::now();
+    sv->requests[r->ticket] = r;
+    sv->queue.push_back(r);
+    *ticket = r->ticket;
+    sv->cv_work.notify_all();
+    return ANOVA_OK;
+}
+
+}  // namespace anova
+
+using namespace anova;
+
+extern "C" {
+
+anova_status anova_server_create(int32_t n_workers, int64_t hbm_budget_bytes, anova_server** out) {
+    if (!out || n_workers < 1 || n_workers > 64 || hbm_budget_bytes <= 0) {
+        set_error("anova_server_create: need 1..64 workers, a positive budget and an output pointer");
+        return ANOVA_EINVAL;
+    }
+    anova_server* sv = new (std::nothrow) anova_server();
+    if (!sv) return ANOVA_ENOMEM;
+    cudaGetDevice(&sv->device);
+    sv->budget = hbm_budget_bytes;
+    sv->t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n_workers; i++) sv->workers.emplace_back(worker_main, sv);
+    *out = sv;
+    return ANOVA_OK;
+}
+
+anova_status anova_server_submit_fit(anova_server* sv, const double* points, int64_t N, int32_t d,
+                                     const int32_t* windows, int32_t P, double ell, const int32_t* n, int32_t m,
+                                     double eps_B, double lambda, const double* y, double tol, int32_t maxit,
+                                     int64_t* ticket) {
+    if (!sv || !ticket || !windows || P < 1 || P > kMaxWindows || N < 0) {
+        set_error("anova_server_submit_fit: bad arguments");
+        return ANOVA_EINVAL;
+    }
+    auto r = std::make_shared<ServerRequest>();
+    r->kind = 0;
+    r->points = points;
+    r->N = N;
+    r->d = d;
+    r->windows.assign(windows, windows + 3 * P);
+    r->P = P;
+    r->ell = ell;
+    if (n) r->n.assign(n, n + P);
+    r->m = m;
+    r->eps_B = eps_B;
+    r->lambda = lambda;
+    r->y = y;
+    r->tol = tol;
+    r->maxit = maxit;
+    r->bytes = fit_bytes(N, r->windows, P, r->n);
+    return enqueue(sv, r, ticket);
+}
+
+anova_status anova_server_submit_predict(anova_server* sv, int64_t model, const double* Z, int64_t M, double* out,
+                                         int64_t* ticket) {
+    if (!sv || !ticket || M < 0) {
+        set_error("anova_server_submit_predict: bad arguments");
+        return ANOVA_EINVAL;
+    }
+    int32_t P = 1;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto rq = sv->requests.find(model);
+        if (rq == sv->requests.end() || rq->second->kind != 0) {
+            set_error("anova_server_submit_predict: unknown model ticket");
+            return ANOVA_EINVAL;
+        }
+        P = rq->second->P;
+    }
+    auto r = std::make_shared<ServerRequest>();
+    r->kind = 1;
+    r->model = model;
+    r->Z = Z;
+    r->M = M;
+    r->out = out;
+    r->bytes = predict_bytes(M, P);
+    return enqueue(sv, r, ticket);
+}
+
+anova_status anova_server_wait(anova_server* sv, int64_t ticket, anova_status* result, double* latency_ms,
+                               int32_t* iterations, double* relres) {
+    if (!sv) return ANOVA_EINVAL;
+    std::unique_lock<std::mutex> lock(sv->mu);
+    auto it = sv->requests.find(ticket);
+    if (it == sv->requests.end()) {
+        set_error("anova_server_wait: unknown ticket");
+        return ANOVA_EINVAL;
+    }
+    auto r = it->second;
+    sv->cv_done.wait(lock, [&] { return r->done; });
+    if (result) *result = r->status;
+    if (latency_ms) *latency_ms = r->latency_ms;
+    if (iterations) *iterations = r->iterations;
+    if (relres) *relres = r->relres;
+    if (r->status != ANOVA_OK) set_error(r->error);
+    if (r->kind == 1) sv->requests.erase(it);   // a fit's record names its model and stays
+    return ANOVA_OK;
+}
+
+anova_status anova_server_release(anova_server* sv, int64_t model) {
+    if (!sv) return ANOVA_EINVAL;
+    ServerModel mdl;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->models.find(model);
+        if (it == sv->models.end()) {
+            set_error("anova_server_release: unknown model");
+            return ANOVA_EINVAL;
+        }
+        if (it->second.busy) {
+            it->second.releasing = true;   // freed by the running prediction
+            return ANOVA_OK;
+        }
+        mdl = it->second;
+        sv->models.erase(it);
+        sv->in_use -= mdl.bytes;
+    }
+    anova_plan_destroy(mdl.plan);
+    cudaFree(mdl.alpha);
+    sv->cv_work.notify_all();
+    return ANOVA_OK;
+}
+
+anova_status anova_server_stats(anova_server* sv, double* p50_ms, double* p99_ms, int64_t* completed,
+                                int64_t* bytes_in_use) {
+    if (!sv) return ANOVA_EINVAL;
+    std::lock_guard<std::mutex> lock(sv->mu);
+    std::vector<double> v = sv->latencies;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double f) { return v.empty() ? 0.0 : v[std::min<size_t>(v.size() - 1, (size_t)(f * v.size()))]; };
+    if (p50_ms) *p50_ms = q(0.50);
+    if (p99_ms) *p99_ms = q(0.99);
+    if (completed) *completed = (int64_t)v.size();
+    if (bytes_in_use) *bytes_in_use = sv->in_use;
+    return ANOVA_OK;
+}
+
+void anova_server_destroy(anova_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+        for (auto& q : sv->queue) {
+            q->status = ANOVA_EINVAL;
+            q->error = "anova_server: the server stopped before this request ran";
+            q->done = true;
+        }
+        sv->queue.clear();
+    }
+    sv->cv_work.notify_all();
+    sv->cv_done.notify_all();
+    for (auto& t : sv->workers) t.join();
+    for (auto& kv : sv->models) {
+        anova_plan_destroy(kv.second.plan);
+        cudaFree(kv.second.alpha);
+    }
+    delete sv;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+"""The request server: fits and predictions served concurrently by worker
+threads give the results that the same calls give one at a time.
+
+Each model is fitted (mixed-precision CG of Sec. 2 to tol 1e-8) and evaluated
+at test points (Sec. 4.3) once through the plain entry points on one stream,
+then again through a server where all fits and many small prediction batches
+are in flight together.  The FP32 spread of the mixed operator sums with
+atomics, so two runs agree to rounding, not bit for bit: predictions must match
+to 1e-6 relative (the CG tolerance times the conditioning margin of these
+problems), iteration counts within a few.
+"""
+import numpy as np
+import pytest
+
+from paper_2111_10140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_10140_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def problems():
+    out = []
+    specs = [
+        (6000, 6, [(0, 1, 2), (3, 4, 5)], 0.2, 16, 4, 31),
+        (9000, 4, [(0, 1), (2, 3), (1, 2)], 0.15, 32, 5, 32),
+        (4000, 5, [(0, 1, 2), (2, 3), (4,)], 0.25, 16, 5, 33),
+    ]
+    for N, d, wins, ell, n, m, seed in specs:
+        w = W.random_problem(N, d, wins, ell, n, m, seed=seed)
+        rng = np.random.default_rng(seed + 100)
+        Z = rng.uniform(w.X.min(0), w.X.max(0), size=(3000, d))
+        out.append((w, Z))
+    return out
+
+
+LAM, TOL = 1.0, 1e-8
+
+
+def serial_results(B, torch, probs):
+    res = []
+    for w, Z in probs:
+        X = torch.from_numpy(w.X).cuda()
+        y = torch.from_numpy(w.y).cuda()
+        plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, precision=B.MIXED)
+        alpha = torch.zeros_like(y)
+        st, its, _ = B.krr_cg_solve(plan, LAM, y, alpha, TOL, 5000)
+        Zt = torch.from_numpy(Z).cuda()
+        pred = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
+        B.krr_predict(plan, alpha, Zt, pred)
+        torch.cuda.synchronize()
+        res.append((int(its[0]), pred.cpu().numpy()))
+        plan.close()
+    return res
+
+
+def test_server_matches_serial_calls(B, torch):
+    probs = problems()
+    ref = serial_results(B, torch, probs)
+    sv = B.Server(n_workers=4, hbm_budget_bytes=8 << 30)
+    try:
+        dev = []
+        for w, Z in probs:
+            dev.append((torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda(), torch.from_numpy(Z).cuda()))
+        torch.cuda.synchronize()
+        fits = [sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
+                for (w, _), (X, y, _) in zip(probs, dev)]
+        # predictions in batches of 500 rows, interleaved over the models,
+        # submitted while the fits are still running
+        outs, tickets = [], []
+        for k in range(6):
+            for i, (_, _, Zt) in enumerate(dev):
+                o = torch.full((500,), float("nan"), dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                tickets.append((i, k, sv.submit_predict(fits[i], Zt[500 * k:500 * (k + 1)], o)))
+                outs.append(o)
+        fit_info = [sv.wait(t) for t in fits]
+        got = [np.empty(3000) for _ in probs]
+        for (i, k, t), o in zip(tickets, outs):
+            r = sv.wait(t)
+            assert r["status"] == B.OK
+            got[i][500 * k:500 * (k + 1)] = o.cpu().numpy()
+        for (its, pred), fi, g in zip(ref, fit_info, got):
+            assert fi["status"] == B.OK
+            assert abs(fi["iterations"] - its) <= max(3, its // 10)
+            err = np.max(np.abs(g - pred)) / np.max(np.abs(pred))
+            assert err < 1e-6, err
+        s = sv.stats()
+        assert s["completed"] == len(fits) + len(tickets)
+        assert 0 < s["p50_ms"] <= s["p99_ms"]
+        for f in fits:
+            sv.release(f)
+        assert sv.stats()["bytes_in_use"] == 0
+    finally:
+        sv.close()
+
+
+def test_server_budget_serialises_and_reports_errors(B, torch):
+    """A budget below every request runs them one at a time; a fit with a bad
+    window fails with EINVAL and so do predictions on it; a released model
+    takes no more predictions."""
+    w, Z = problems()[0]
+    sv = B.Server(n_workers=3, hbm_budget_bytes=1)
+    try:
+        X = torch.from_numpy(w.X).cuda()
+        y = torch.from_numpy(w.y).cuda()
+        Zt = torch.from_numpy(Z[:700]).cuda()
+        torch.cuda.synchronize()
+        good = sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
+        bad = sv.submit_fit(X, [(0, 1, 99)], w.ell, y, LAM, m=w.m, eps_B=w.epsB, tol=TOL)
+        o1 = torch.empty(700, dtype=torch.float64, device="cuda")
+        o2 = torch.empty(700, dtype=torch.float64, device="cuda")
+        o3 = torch.empty(700, dtype=torch.float64, device="cuda")
+        t1 = sv.submit_predict(good, Zt, o1)
+        t2 = sv.submit_predict(bad, Zt, o2)
+        t3 = sv.submit_predict(good, Zt, o3)
+        assert sv.wait(good)["status"] == B.OK
+        assert sv.wait(bad)["status"] == B.EINVAL
+        assert sv.wait(t1)["status"] == B.OK
+        assert sv.wait(t2)["status"] == B.EINVAL
+        assert sv.wait(t3)["status"] == B.OK
+        assert torch.equal(o1, o3) or torch.allclose(o1, o3, rtol=0, atol=1e-12 * float(o1.abs().max()))
+        sv.release(good)
+        t4 = sv.submit_predict(good, Zt, o2)
+        assert sv.wait(t4)["status"] == B.EINVAL
+        with pytest.raises(B.AnovaError):
+            sv.submit_predict(12345, Zt, o2)
+        assert sv.stats()["bytes_in_use"] == 0
+    finally:
+        sv.close()
