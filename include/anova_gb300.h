@@ -97,8 +97,12 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
  * Asynchronous on `stream`.  With nrhs = 1 the plan records the call's launch
  * sequence as a CUDA graph the second time it sees the same (dtype, alpha,
  * out) and replays it from then on (at most 16 graphs per plan, shared with
- * the CG solver, which replays its operator application the same way).  Calls on
- * one plan must not overlap on the GPU: they share the plan's work buffers.
+ * the CG solver, which replays its operator application the same way).  While
+ * a call captures, no other host thread may synchronise the whole device
+ * (cudaDeviceSynchronize, torch.cuda.synchronize): CUDA refuses that while any
+ * stream captures.  Multi-threaded callers switch capture off with
+ * anova_plan_set_graphs.  Calls on one plan must not overlap on the GPU: they
+ * share the plan's work buffers.
  * Errors: EINVAL.
  */
 anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, void* out,
@@ -285,6 +289,11 @@ anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host)
  * stages written.  Reading synchronises the recorded events.
  */
 anova_status anova_set_profiling(anova_plan* plan, int32_t enable);
+
+/* Graph capture and replay of anova_matvec / krr_cg_solve on (enable != 0,
+ * the default) or off; switching off drops the captured graphs.  The paper has
+ * no counterpart: this is a launch-overhead setting. */
+anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable);
 int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap);
 
 #ifdef __cplusplus

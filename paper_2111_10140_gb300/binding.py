@@ -35,6 +35,7 @@ _SIGNATURES = {
     "krr_predict_noalloc": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
+    "anova_plan_set_graphs": (_i32, [_vp, _i32]),
     "anova_server_create": (_i32, [_i32, _i64, ctypes.POINTER(_vp)]),
     "anova_server_submit_fit": (_i32, [_vp, _vp, _i64, _i32, _pi32, _i32, _f64, _pi32, _i32, _f64, _f64, _vp,
                                        _f64, _i32, _pi64]),
@@ -246,6 +247,10 @@ def anova_debug_diag(plan: Plan, l: int) -> np.ndarray:
 
 def anova_set_profiling(plan: Plan, enable: bool):
     _check(lib().anova_set_profiling(plan.handle, int(bool(enable))), "anova_set_profiling")
+
+
+def anova_plan_set_graphs(plan: Plan, enable: bool):
+    _check(lib().anova_plan_set_graphs(plan.handle, 1 if enable else 0), "anova_plan_set_graphs")
 
 
 def anova_stage_times(plan: Plan):

@@ -644,6 +644,17 @@ anova_status anova_set_profiling(anova_plan* plan, int32_t enable) {
     return ANOVA_OK;
 }
 
+anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable) {
+    if (!plan) return ANOVA_EINVAL;
+    plan->use_graphs = enable != 0;
+    if (!plan->use_graphs) {
+        for (auto& g : plan->graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        plan->graphs.clear();
+    }
+    return ANOVA_OK;
+}
+
 int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap) {
     if (!plan) return 0;
     StageClock& c = plan->clock;

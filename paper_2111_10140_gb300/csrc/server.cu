@@ -110,6 +110,9 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
         anova_status s = anova_fastsum_plan(r.points, r.N, r.d, r.d, r.windows.data(), r.P, nullptr, r.ell,
                                             r.n.empty() ? nullptr : r.n.data(), r.m, 2.0, r.eps_B, 8,
                                             ANOVA_MIXED, st, &mdl.plan);
+        // no graph capture in server plans: a capture in one worker would make
+        // device-wide synchronisation in any other thread of the process fail
+        if (s == ANOVA_OK) s = anova_plan_set_graphs(mdl.plan, 0);
         if (s == ANOVA_OK) {
             if (cudaMalloc(&mdl.alpha, std::max<int64_t>(r.N, 1) * sizeof(double)) != cudaSuccess) s = ANOVA_ENOMEM;
         }
