@@ -403,11 +403,15 @@ def run_crossover(args):
 
 
 def run_serve(args):
-    """Serving form: models of the mid workload's shape stay resident in a
-    request server; predictions of `--serve-rows` test points arrive as a
-    Poisson stream at `--serve-rate` requests/s (a fit of a fresh model joins
-    the stream every `--serve-fit-every` requests).  Prints one line with the
-    latency percentiles and the served throughput."""
+    """Serving form: a Poisson stream of requests (mean `--serve-rate` per s),
+    70 % predictions of M test points (log-uniform in [1e2, 1e5]) against a
+    resident model (N log-uniform in [1e4, 1e6]) and 30 % fits of new problems
+    (N log-uniform in [1e3, 1e6]), d 9..28, 3..9 windows, served by the
+    library's request server under a 150 GB budget (FP32 bulk, FP64
+    refinement to residual 1e-6).  Fitted stream models are released as soon
+    as their fit is done.  Prints one line with latency percentiles per kind
+    and the served throughput."""
+    import threading
     import time
 
     import numpy as np
@@ -418,50 +422,92 @@ def run_serve(args):
     from paper_2111_10140_gb300 import workloads as W
     __graft_entry__.build()
     dev = torch.device("cuda", 0)
-    rng = np.random.default_rng(7)
-    n_models, rows, rate = 4, args.serve_rows, args.serve_rate
-    probs = [W.plain_mid(N=args.serve_n) for _ in range(n_models)]
-    for k, w in enumerate(probs):      # distinct targets per model
-        w.y = np.random.default_rng(100 + k).standard_normal(w.X.shape[0])
-    Xs = [torch.from_numpy(w.X).to(dev) for w in probs]
-    ys = [torch.from_numpy(w.y).to(dev) for w in probs]
-    Zpool = torch.from_numpy(rng.uniform(probs[0].X.min(0), probs[0].X.max(0),
-                                         size=(16 * rows, probs[0].X.shape[1]))).to(dev)
+    rng = np.random.default_rng(5)
+    logu = lambda lo, hi: int(round(10 ** rng.uniform(np.log10(lo), np.log10(hi))))
+
+    def to_dev(w):
+        return (torch.from_numpy(w.X).to(dev), torch.from_numpy(w.y).to(dev))
+
+    # resident models (fitted before the stream starts) with held-out test rows
+    res_N = [logu(1e4, 1e6) for _ in range(args.serve_models)]
+    res = [W.serving_problem(N, seed=1000 + k, M_test=100_000) for k, N in enumerate(res_N)]
+    res_dev = [to_dev(w) + (torch.from_numpy(w.meta["Z"]).to(dev),) for w in res]
+    fit_pool = [W.serving_problem(logu(1e3, 1e6), seed=2000 + k) for k in range(args.serve_fit_pool)]
+    fit_dev = [to_dev(w) for w in fit_pool]
     torch.cuda.synchronize()
-    sv = B.Server(n_workers=args.serve_workers, hbm_budget_bytes=64 << 30)
-    lam, tol = probs[0].lam, 1e-6
-    t_fit0 = time.perf_counter()
-    models = [sv.submit_fit(X, w.windows, w.ell, y, lam, n=w.n, m=w.m, eps_B=w.epsB, tol=tol)
-              for w, X, y in zip(probs, Xs, ys)]
-    fit_info = [sv.wait(t) for t in models]
-    t_fit = time.perf_counter() - t_fit0
-    outs = [torch.empty(rows, dtype=torch.float64, device=dev) for _ in range(args.serve_requests)]
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_requests))
-    tickets, fits = [], []
+    sv = B.Server(n_workers=args.serve_workers, hbm_budget_bytes=150 << 30)
     t0 = time.perf_counter()
-    for i, ta in enumerate(arrivals):
+    models = [sv.submit_fit(X, w.windows, w.ell, y, w.lam, n=w.n, m=w.m, eps_B=w.epsB, tol=w.tol)
+              for w, (X, y, _) in zip(res, res_dev)]
+    init = [sv.wait(t) for t in models]
+    t_init = time.perf_counter() - t0
+    # the stream
+    n_req = int(args.serve_rate * args.serve_seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_req))
+    kinds = rng.uniform(size=n_req) < 0.7
+    fit_tickets, pred = [], []
+    done_fits = []
+
+    def releaser():
+        k = 0
+        while True:
+            while k >= len(fit_tickets):
+                if stop.is_set() and k >= len(fit_tickets):
+                    return
+                time.sleep(0.002)
+            r = sv.wait(fit_tickets[k][0])
+            done_fits.append((fit_tickets[k][1], r))
+            if r["status"] in (B.OK, B.ENOCONV):
+                sv.release(fit_tickets[k][0])
+            k += 1
+
+    stop = threading.Event()
+    th = threading.Thread(target=releaser)
+    th.start()
+    outs = []
+    rows = 0
+    t0 = time.perf_counter()
+    for i in range(n_req):
         now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        if args.serve_fit_every and i % args.serve_fit_every == args.serve_fit_every - 1:
-            k = int(rng.integers(n_models))
-            fits.append(sv.submit_fit(Xs[k], probs[k].windows, probs[k].ell, ys[k], lam, n=probs[k].n,
-                                      m=probs[k].m, eps_B=probs[k].epsB, tol=tol))
-        b = int(rng.integers(16))
-        tickets.append(sv.submit_predict(models[int(rng.integers(n_models))], Zpool[b * rows:(b + 1) * rows],
-                                         outs[i]))
-    lat = np.array([sv.wait(t)["latency_ms"] for t in tickets])
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        if kinds[i]:
+            k = int(rng.integers(len(res)))
+            M = logu(1e2, 1e5)
+            Zt = res_dev[k][2]
+            off = int(rng.integers(0, Zt.shape[0] - M + 1))
+            o = torch.empty(M, dtype=torch.float64, device=dev)
+            outs.append(o)
+            pred.append((sv.submit_predict(models[k], Zt[off:off + M], o), M))
+            rows += M
+        else:
+            k = int(rng.integers(len(fit_pool)))
+            w, (X, y) = fit_pool[k], fit_dev[k]
+            fit_tickets.append((sv.submit_fit(X, w.windows, w.ell, y, w.lam, n=w.n, m=w.m, eps_B=w.epsB,
+                                              tol=w.tol), w.N))
+    t_sub = time.perf_counter() - t0
+    plat = np.array([sv.wait(t)["latency_ms"] for t, _ in pred])
+    stop.set()
+    th.join()
     t_all = time.perf_counter() - t0
-    fit_lat = [sv.wait(t)["latency_ms"] for t in fits]
+    flat = np.array([r["latency_ms"] for _, r in done_fits])
+    fitted = sum(N for N, r in done_fits)
+    bad = sum(r["status"] not in (B.OK, B.ENOCONV) for _, r in done_fits)
     sv.close()
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     print(json.dumps({
-        "serve": True, "workload": f"plain_mid shape, N={args.serve_n}, d=9, 8 windows x 2 features",
-        "workers": args.serve_workers, "models": n_models, "rows_per_request": rows,
-        "offered_rate_rps": rate, "requests": len(tickets), "fits_in_stream": len(fits),
-        "predict_p50_ms": float(np.percentile(lat, 50)), "predict_p99_ms": float(np.percentile(lat, 99)),
-        "achieved_rps": len(tickets) / t_all, "rows_per_s": len(tickets) * rows / t_all,
-        "fit_latency_ms": [round(x, 1) for x in fit_lat],
-        "initial_fits_s": t_fit, "initial_fit_iters": [f["iterations"] for f in fit_info]}), flush=True)
+        "serve": True,
+        "workload": "Poisson stream, 70% predict (M log-uniform 1e2..1e5) on resident models, "
+                    "30% fit (N log-uniform 1e3..1e6); d 9..28, 3..9 windows of 1-3 features",
+        "offered_rate_rps": args.serve_rate, "seconds_offered": args.serve_seconds, "workers": args.serve_workers,
+        "resident_models_N": res_N, "initial_fits_s": round(t_init, 3),
+        "initial_fit_iters": [r["iterations"] for r in init],
+        "requests": n_req, "predicts": len(pred), "fits": len(done_fits), "failed_fits": int(bad),
+        "predict_p50_ms": pct(plat, 50), "predict_p99_ms": pct(plat, 99),
+        "fit_p50_ms": pct(flat, 50), "fit_p99_ms": pct(flat, 99),
+        "submit_s": round(t_sub, 3), "drain_s": round(t_all, 3),
+        "achieved_rps": n_req / t_all, "predicted_rows_per_s": rows / t_all, "fitted_points_per_s": fitted / t_all,
+    }), flush=True)
 
 
 def main():
@@ -480,12 +526,11 @@ def main():
                     help="direct vs fast matvec time over N (the paper's Fig. 1 on synthetic data); prints one line per N")
     ap.add_argument("--serve", action="store_true",
                     help="Poisson stream of prediction (and fit) requests through the request server")
-    ap.add_argument("--serve-n", type=int, default=100_000)
-    ap.add_argument("--serve-rows", type=int, default=4096)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-fit-every", type=int, default=0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-models", type=int, default=4)
+    ap.add_argument("--serve-fit-pool", type=int, default=6)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -191,6 +191,38 @@ anova_status anova_direct_matvec(const double* Z, int64_t M, int64_t ldz, const 
                                  double* out, void* stream);
 
 /* ----------------------------------------------------------------------------
+ * Fitted models (Sec. 4.3).  For fixed coefficients alpha the factor
+ * D_l Phi_{X,l}^* alpha of the test-point summation -- alpha spread onto window
+ * l's grid and convolved with the kernel's Fourier multiplier -- does not
+ * depend on the test points.  krr_model_create computes it once per window;
+ * krr_model_predict then bins the test points and gathers from those grids.
+ * Same kernels and precision as krr_predict (FP64 when the plan holds FP64).
+ * The paper has no model object: this caches a factor of its prediction.
+ * ------------------------------------------------------------------------- */
+typedef struct krr_model krr_model;
+
+/* plan: must outlive the model and must not change its points; alpha: device,
+ * N entries, copied (the caller may free it afterwards).  Synchronous on
+ * `stream`; uses the plan's work buffers, so no other call on the plan may run
+ * meanwhile.  Errors: EINVAL, ENOMEM, ECUDA. */
+anova_status krr_model_create(anova_plan* plan, const double* alpha, void* stream, krr_model** out);
+
+/*
+ * out (device, M) <- the model's prediction at Z (device, M rows of ld ldz >=
+ * d).  Returns when out is written.  Calls on one model may run concurrently
+ * from several host threads on different streams: they read the model's grids
+ * and allocate their own scratch (stream-ordered).  A call whose test points
+ * leave the plan's ball in some window runs krr_predict (re-framed) on the
+ * plan's grids instead, one such call per model at a time.
+ * Errors: EINVAL, ECUDA.
+ */
+anova_status krr_model_predict(krr_model* model, const double* Z, int64_t M, int64_t ldz, double* out,
+                               void* stream);
+
+/* Free the model's grids and coefficients.  NULL is ignored. */
+void krr_model_destroy(krr_model* model);
+
+/* ----------------------------------------------------------------------------
  * Request server: kernel ridge regression fits (anova_fastsum_plan with
  * ANOVA_MIXED + krr_cg_solve) and predictions (krr_predict) served by worker
  * threads, each on its own CUDA stream.  Requests are admitted in arrival order

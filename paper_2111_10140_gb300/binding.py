@@ -36,6 +36,9 @@ _SIGNATURES = {
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
+    "krr_model_create": (_i32, [_vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "krr_model_predict": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
+    "krr_model_destroy": (None, [_vp]),
     "anova_server_create": (_i32, [_i32, _i64, ctypes.POINTER(_vp)]),
     "anova_server_submit_fit": (_i32, [_vp, _vp, _i64, _i32, _pi32, _i32, _f64, _pi32, _i32, _f64, _f64, _vp,
                                        _f64, _i32, _pi64]),
@@ -91,7 +94,7 @@ def _check(status, where, allow=(OK,)):
 
 def _stream(stream):
     if stream is not None:
-        return ctypes.c_void_p(int(stream))
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -258,6 +261,38 @@ def anova_stage_times(plan: Plan):
     la = (ctypes.c_int64 * 8)()
     k = lib().anova_stage_times(plan.handle, ms, la, 8)
     return list(ms[:k]), list(la[:k])
+
+
+class Model:
+    """A fitted model (krr_model_create): the plan must outlive it."""
+
+    def __init__(self, plan: Plan, alpha, stream=None):
+        import torch
+        _require_cuda(alpha, "alpha", torch.float64)
+        h = ctypes.c_void_p()
+        _check(lib().krr_model_create(plan.handle, _ptr(alpha), _stream(stream), ctypes.byref(h)),
+               "krr_model_create")
+        self.handle = h
+        self.plan = plan
+
+    def predict(self, Z, out, stream=None):
+        import torch
+        _require_cuda(Z, "Z", torch.float64)
+        _require_cuda(out, "out", torch.float64)
+        _check(lib().krr_model_predict(self.handle, _ptr(Z), Z.shape[0], Z.shape[1], _ptr(out), _stream(stream)),
+               "krr_model_predict")
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().krr_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -201,6 +201,10 @@ void free_pointset(PointSet& ps);
 void free_pointset_async(PointSet& ps, cudaStream_t st);
 anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M, WindowPlan& dst,
                             cudaStream_t st);
+template <typename T>
+anova_status predict_window(anova_plan* plan, int l, const double* alpha, const double* zw, int64_t M, T* out,
+                            cudaStream_t st);
+anova_status window_widened(anova_plan* plan, int l, double rho, WindowPlan& dst, cudaStream_t st);
 void window_release_reframed(WindowPlan& w);
 anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, const double* centre,
                         double* rmax_host, cudaStream_t st);

@@ -471,6 +471,57 @@ static anova_status debug_spread_t(anova_plan* plan, int l, const void* alpha, v
 }
 
 // ---------------------------------------------------------------- predict
+// Window l's part of the test-point summation (Sec. 4.3) at M test
+// coordinates zw (device, this window's features): out = K_l(Z, X) alpha.
+// Test points outside the plan's ball are summed in the joint frame of nodes
+// and test points (window_reframe).  Uses the plan's grid of the window.
+template <typename T>
+anova_status predict_window(anova_plan* plan, int l, const double* alpha, const double* zw, int64_t M, T* out,
+                            cudaStream_t st) {
+    const WindowPlan& base = plan->win[l];
+    double rmax = 0.0;
+    ANOVA_TRY(max_radius(plan, zw, M, base.dA, base.centre, &rmax, st));
+    WindowPlan joint;
+    const bool reframe = base.scale * rmax > 0.25 - 0.5 * plan->epsB;
+    anova_status s = ANOVA_OK;
+    if (reframe) {
+        s = window_reframe(plan, l, zw, M, joint, st);
+        if (s != ANOVA_OK) {
+            window_release_reframed(joint);
+            return s;
+        }
+    }
+    const WindowPlan& w = reframe ? joint : base;
+    PointSet zs;
+    WindowPlan wz = w;   // binning parameters of the window
+    s = build_pointset(plan, wz, zw, M, w.dA, w.centre, w.scale, zs, st);
+    size_t ge = 1;
+    for (int t = 0; t < w.dA; t++) ge *= w.nos;
+    T* grid = grid_of<T>(plan, w);
+    if (s == ANOVA_OK && plan->N > 0) {
+        cudaMemsetAsync(grid, 0, ge * sizeof(T), st);
+        s = spread_window<T>(plan, w, w.X, alpha, 1, grid, st);
+        if (s == ANOVA_OK) s = fft_convolve_window<T>(plan, w, grid, st);
+        if (s == ANOVA_OK) s = gather_window<T>(plan, w, zs, grid, out, st);
+    } else if (s == ANOVA_OK) {
+        cudaMemsetAsync(out, 0, M * sizeof(T), st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == ANOVA_OK && e != cudaSuccess) {
+        set_error(std::string("predict: ") + cudaGetErrorString(e));
+        s = ANOVA_ECUDA;
+    }
+    free_pointset_async(zs, st);
+    wz.X = PointSet();
+    if (reframe) window_release_reframed(joint);
+    return s;
+}
+
+template anova_status predict_window<double>(anova_plan*, int, const double*, const double*, int64_t, double*,
+                                             cudaStream_t);
+template anova_status predict_window<float>(anova_plan*, int, const double*, const double*, int64_t, float*,
+                                            cudaStream_t);
+
 template <typename T>
 static anova_status predict_t(anova_plan* plan, const double* alpha, const double* Z, int64_t M, int64_t ldz,
                               double* out, cudaStream_t st) {
@@ -481,43 +532,8 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
     ANOVA_CUDA_TRY(cudaMallocAsync(&zw, std::max<int64_t>(M, 1) * 3 * sizeof(double), st));
     anova_status s = ANOVA_OK;
     for (int l = 0; l < P && s == ANOVA_OK; l++) {
-        const WindowPlan& base = plan->win[l];
-        s = extract_window(plan, Z, M, ldz, base, zw, st);
-        double rmax = 0.0;
-        if (s == ANOVA_OK) s = max_radius(plan, zw, M, base.dA, base.centre, &rmax, st);
-        if (s != ANOVA_OK) break;
-        WindowPlan joint;
-        const bool reframe = base.scale * rmax > 0.25 - 0.5 * plan->epsB;
-        if (reframe) {
-            s = window_reframe(plan, l, zw, M, joint, st);
-            if (s != ANOVA_OK) {
-                window_release_reframed(joint);
-                break;
-            }
-        }
-        const WindowPlan& w = reframe ? joint : base;
-        PointSet zs;
-        WindowPlan wz = w;   // binning parameters of the window
-        s = build_pointset(plan, wz, zw, M, w.dA, w.centre, w.scale, zs, st);
-        size_t ge = 1;
-        for (int t = 0; t < w.dA; t++) ge *= w.nos;
-        T* grid = grid_of<T>(plan, w);
-        if (s == ANOVA_OK && plan->N > 0) {
-            cudaMemsetAsync(grid, 0, ge * sizeof(T), st);
-            s = spread_window<T>(plan, w, w.X, alpha, 1, grid, st);
-            if (s == ANOVA_OK) s = fft_convolve_window<T>(plan, w, grid, st);
-            if (s == ANOVA_OK) s = gather_window<T>(plan, w, zs, grid, tmp + (int64_t)l * M, st);
-        } else if (s == ANOVA_OK) {
-            cudaMemsetAsync(tmp + (int64_t)l * M, 0, M * sizeof(T), st);
-        }
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (s == ANOVA_OK && e != cudaSuccess) {
-            set_error(std::string("predict: ") + cudaGetErrorString(e));
-            s = ANOVA_ECUDA;
-        }
-        free_pointset_async(zs, st);
-        wz.X = PointSet();
-        if (reframe) window_release_reframed(joint);
+        s = extract_window(plan, Z, M, ldz, plan->win[l], zw, st);
+        if (s == ANOVA_OK) s = predict_window<T>(plan, l, alpha, zw, M, tmp + (int64_t)l * M, st);
     }
     if (s == ANOVA_OK && M > 0) {
         k_window_sum<T, double><<<grid_for(M, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(

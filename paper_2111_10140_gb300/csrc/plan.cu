@@ -1005,6 +1005,38 @@ anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M
     return s;
 }
 
+// Window l in the frame of the plan's own, with the same centre and the scale
+// divided by rho >= 1: every point within rho times the nodes' radius of the
+// centre maps into the ball.  Same buffers as window_reframe.
+anova_status window_widened(anova_plan* plan, int l, double rho, WindowPlan& dst, cudaStream_t st) {
+    const WindowPlan& src = plan->win[l];
+    dst = WindowPlan();
+    dst.dA = src.dA;
+    for (int t = 0; t < 3; t++) dst.feat[t] = src.feat[t];
+    dst.n = src.n;
+    dst.nos = src.nos;
+    dst.T = src.T;
+    dst.nb = src.nb;
+    dst.R = src.R;
+    dst.nbins = src.nbins;
+    dst.dense = src.dense;
+    dst.grid_off = src.grid_off;
+    dst.work_off = src.work_off;
+    dst.eta = src.eta;
+    dst.tw64 = src.tw64;   // borrowed
+    dst.tw32 = src.tw32;   // borrowed
+    dst.xw = src.xw;       // borrowed
+    int64_t tk = 1;
+    for (int t = 0; t < src.dA; t++) tk *= src.n;
+    double* scratch = nullptr;
+    ANOVA_CUDA_TRY(cudaMalloc(&scratch, std::max<size_t>(16, 2 * tk) * sizeof(double)));
+    const double frame[5] = {src.centre[0], src.centre[1], src.centre[2], src.scale / rho, 0.0};
+    anova_status s = window_setup(plan, dst, frame, scratch, st);
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    return s;
+}
+
 void window_release_reframed(WindowPlan& w) {
     cudaFree(w.wtab);
     cudaFree(w.D64);
@@ -1020,7 +1052,7 @@ anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, c
     if (M == 0) return ANOVA_OK;
     const int nblk = grid_for(M, kThreads, 2 * plan->sm_count);
     double* scratch = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&scratch, (nblk + 8) * sizeof(double)));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&scratch, (nblk + 8) * sizeof(double), st));
     double* frame = scratch + nblk;
     double hf[5] = {centre[0], centre[1], centre[2], 1.0, 0.0};
     ANOVA_CUDA_TRY(cudaMemcpyAsync(frame, hf, 5 * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1029,7 +1061,7 @@ anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, c
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaMemcpyAsync(hf, frame, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(scratch);
+    cudaFreeAsync(scratch, st);
     *rmax_host = hf[4];
     return ANOVA_OK;
 }

@@ -6,8 +6,9 @@
 // queue in arrival order as soon as a worker is idle and the request's device
 // memory fits under the budget (continuous admission: a request never waits
 // for a batch to fill).  Work of different requests overlaps on the GPU.
-// Fitted models -- plan, coefficients -- stay resident on the device until
-// released.  Host code only; every computation is a call of the library's
+// Fitted models -- plan and krr_model, whose convolved grids make a
+// prediction a binning and a gather -- stay resident on the device until
+// released; predictions on one model run concurrently.  Host code only; every computation is a call of the library's
 // entry points on the worker's stream.
 #include <cuda_runtime.h>
 
@@ -58,12 +59,12 @@ struct ServerRequest {
 
 struct ServerModel {
     anova_plan* plan = nullptr;
-    double* alpha = nullptr;      // device, N
+    krr_model* model = nullptr;   // the fitted predictor (its own grids and alpha)
     int64_t N = 0, bytes = 0;
     int32_t d = 0;
     bool ready = false;
-    bool busy = false;            // a prediction is running: the plan's grids are in use
-    bool releasing = false;       // released while busy: freed when that prediction ends
+    int inflight = 0;             // predictions running on this model
+    bool releasing = false;       // released while predictions ran: freed by the last
 };
 
 }  // namespace anova
@@ -87,7 +88,8 @@ struct anova_server {
 namespace anova {
 
 // device bytes of a fitted model: the plan's node arrays, weight tables,
-// grids and work buffers, the CG vectors and the coefficients
+// grids and work buffers, the CG vectors, the coefficients and the model's
+// convolved grids
 static int64_t fit_bytes(int64_t N, const std::vector<int32_t>& windows, int32_t P, const std::vector<int32_t>& n) {
     int64_t b = 0;
     for (int l = 0; l < P; l++) {
@@ -95,7 +97,7 @@ static int64_t fit_bytes(int64_t N, const std::vector<int32_t>& windows, int32_t
         while (dA < 3 && windows[3 * l + dA] >= 0) dA++;
         int64_t nos = 2 * (n.empty() ? 32 : n[l]), grid = 1;
         for (int t = 0; t < dA; t++) grid *= nos;
-        b += N * (8 * dA + 4 + 4 * dA + 8 * dA + 4 * dA + 64 * dA + 8 + 4) + grid * 8 * 3;
+        b += N * (8 * dA + 4 + 4 * dA + 8 * dA + 4 * dA + 64 * dA + 8 + 4) + grid * 8 * 4;
     }
     return b + N * (8 * 5) + (64 << 20);
 }
@@ -113,19 +115,26 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
         // no graph capture in server plans: a capture in one worker would make
         // device-wide synchronisation in any other thread of the process fail
         if (s == ANOVA_OK) s = anova_plan_set_graphs(mdl.plan, 0);
+        double* alpha = nullptr;
         if (s == ANOVA_OK) {
-            if (cudaMalloc(&mdl.alpha, std::max<int64_t>(r.N, 1) * sizeof(double)) != cudaSuccess) s = ANOVA_ENOMEM;
+            if (cudaMallocAsync(&alpha, std::max<int64_t>(r.N, 1) * sizeof(double), st) != cudaSuccess)
+                s = ANOVA_ENOMEM;
         }
         if (s == ANOVA_OK)
-            s = krr_cg_solve(mdl.plan, r.lambda, r.y, mdl.alpha, 1, r.N, r.tol, r.maxit, &r.iterations, &r.relres, st);
+            s = krr_cg_solve(mdl.plan, r.lambda, r.y, alpha, 1, r.N, r.tol, r.maxit, &r.iterations, &r.relres, st);
+        if (s == ANOVA_OK || s == ANOVA_ENOCONV) {
+            const anova_status sm = krr_model_create(mdl.plan, alpha, st, &mdl.model);
+            if (sm != ANOVA_OK) s = sm;
+        }
+        if (alpha) cudaFreeAsync(alpha, st);
         std::lock_guard<std::mutex> lock(sv->mu);
         if (s == ANOVA_OK || s == ANOVA_ENOCONV) {
             mdl.bytes = r.bytes;
             mdl.ready = true;
             sv->models[r.ticket] = mdl;
         } else {
+            krr_model_destroy(mdl.model);
             if (mdl.plan) anova_plan_destroy(mdl.plan);
-            cudaFree(mdl.alpha);
             sv->in_use -= r.bytes;
         }
         r.status = s;
@@ -136,7 +145,7 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lock(sv->mu);
         auto it = sv->models.find(r.model);
-        if (it == sv->models.end() || !it->second.ready || !it->second.busy) {
+        if (it == sv->models.end() || !it->second.ready || it->second.inflight == 0) {
             sv->in_use -= r.bytes;
             r.status = ANOVA_EINVAL;
             r.error = "anova_server: the model of this prediction failed to fit or was released";
@@ -144,7 +153,7 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
         }
         mdl = it->second;
     }
-    anova_status s = krr_predict(mdl.plan, mdl.alpha, r.Z, r.M, mdl.d, r.out, st);
+    anova_status s = krr_model_predict(mdl.model, r.Z, r.M, mdl.d, r.out, st);
     if (s != ANOVA_OK) r.error = anova_last_error();
     bool free_now = false;
     {
@@ -152,16 +161,16 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
         sv->in_use -= r.bytes;
         r.status = s;
         auto it = sv->models.find(r.model);
-        it->second.busy = false;
-        if (it->second.releasing) {
+        it->second.inflight--;
+        if (it->second.releasing && it->second.inflight == 0) {
             sv->in_use -= it->second.bytes;
             sv->models.erase(it);
             free_now = true;
         }
     }
     if (free_now) {
+        krr_model_destroy(mdl.model);
         anova_plan_destroy(mdl.plan);
-        cudaFree(mdl.alpha);
     }
 }
 
@@ -180,8 +189,7 @@ static void worker_main(anova_server* sv) {
                     return;
                 }
                 // admit the oldest request whose memory fits; a prediction waits
-                // while its model is still being fitted or serves another
-                // prediction (one plan's grids serve one request at a time)
+                // while its model is still being fitted
                 auto pick = sv->queue.end();
                 for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
                     const auto& q = *it;
@@ -191,7 +199,7 @@ static void worker_main(anova_server* sv) {
                             auto rq = sv->requests.find(q->model);
                             const bool fit_over = rq != sv->requests.end() && rq->second->done;
                             if (!fit_over) continue;   // fit still queued or running
-                        } else if (!m->second.ready || m->second.busy || m->second.releasing) {
+                        } else if (!m->second.ready || m->second.releasing) {
                             continue;
                         }
                     }
@@ -208,7 +216,7 @@ static void worker_main(anova_server* sv) {
                     sv->running++;
                     if (r->kind == 1) {
                         auto m = sv->models.find(r->model);
-                        if (m != sv->models.end()) m->second.busy = true;
+                        if (m != sv->models.end()) m->second.inflight++;
                     }
                     break;
                 }
@@ -350,16 +358,16 @@ anova_status anova_server_release(anova_server* sv, int64_t model) {
             set_error("anova_server_release: unknown model");
             return ANOVA_EINVAL;
         }
-        if (it->second.busy) {
-            it->second.releasing = true;   // freed by the running prediction
+        if (it->second.inflight > 0) {
+            it->second.releasing = true;   // freed by the last running prediction
             return ANOVA_OK;
         }
         mdl = it->second;
         sv->models.erase(it);
         sv->in_use -= mdl.bytes;
     }
+    krr_model_destroy(mdl.model);
     anova_plan_destroy(mdl.plan);
-    cudaFree(mdl.alpha);
     sv->cv_work.notify_all();
     return ANOVA_OK;
 }
@@ -394,8 +402,8 @@ void anova_server_destroy(anova_server* sv) {
     sv->cv_done.notify_all();
     for (auto& t : sv->workers) t.join();
     for (auto& kv : sv->models) {
+        krr_model_destroy(kv.second.model);
         anova_plan_destroy(kv.second.plan);
-        cudaFree(kv.second.alpha);
     }
     delete sv;
 }

@@ -134,3 +134,30 @@ def random_problem(N, d, windows, ell, n, m, seed, dist="normal"):
 
 
 CONFIGS = {"plain_tiny": plain_tiny, "plain_mid": plain_mid, "precision_form": precision_form}
+
+
+def serving_problem(N, seed, M_test=0):
+    """One problem of the serving stream: d uniform in 9..28 standard normal
+    features, 3..9 windows of 1-3 distinct features (n = 32 for 3-D windows,
+    64 otherwise, m = 6, eps_B = 0.25), ell = 0.25, lambda = 1e-2, y a sum of
+    per-window smooth functions plus noise.  With M_test > 0 another M_test
+    rows are drawn with the training rows and min-max mapped together with
+    them (a held-out split); they are returned in meta["Z"]."""
+    rng = np.random.default_rng(seed)
+    d = int(rng.integers(9, 29))
+    P = int(rng.integers(3, 10))
+    feats = list(rng.permutation(d))
+    windows = []
+    while len(windows) < P and feats:
+        k = min(int(rng.integers(1, 4)), len(feats))
+        windows.append(tuple(sorted(int(f) for f in feats[:k])))
+        feats = feats[k:]
+    raw = rng.standard_normal((N + M_test, d))
+    Xall = _minmax_into_ball(raw, windows)
+    u = _unit(raw[:N])
+    y = sum(np.sin(2 * np.pi * u[:, list(w)].mean(axis=1)) for w in windows) + 0.05 * rng.standard_normal(N)
+    P = len(windows)
+    n = [32 if len(w) == 3 else 64 for w in windows]
+    return Workload(f"serving_N{N}_d{d}_P{P}", np.ascontiguousarray(Xall[:N]), windows, np.full(P, 1.0 / P), 0.25,
+                    n, 6, 2.0, rng.standard_normal(N), y, 1e-2, 1e-6, epsB=0.25,
+                    meta={"Z": np.ascontiguousarray(Xall[N:])})

@@ -216,6 +216,111 @@ def test_predict_matches_oracle(B, torch, scale_z):
     assert rel(out.cpu().numpy(), direct) <= 1e-5
 
 
+def wide_rho(fr):
+    """rho of a model's wide frame: largest value <= 2 with the Gaussian's
+    Fourier transform at the band edge, exp(-(pi ell_l n / (2 rho))^2), below 1e-12."""
+    return min(2.0, math.pi * fr["ell_l"] * fr["n"] / (2 * math.sqrt(math.log(1e12))))
+
+
+def wide_frame_rows(w, frames):
+    """Rows that make the oracle's joint frame (bounding-box midpoint, scale
+    R_B / max radius of nodes and test points, Sec. 4.2) equal to the
+    widened frame of each window: centre unchanged, scale / rho.  Every
+    feature sits at its window's centre except one, moved by the wide radius
+    along one axis of one window."""
+    RB = 0.25 - 0.5 * w.epsB
+    base = np.zeros(w.d)
+    for win, fr in zip(w.windows, frames):
+        base[list(win)] = fr["centre"]
+    rows = []
+    for win, fr in zip(w.windows, frames):
+        r = wide_rho(fr) * RB / fr["scale"]
+        for t, f in enumerate(win):
+            for sgn in (-1.0, 1.0):
+                row = base.copy()
+                row[f] = fr["centre"][t] + sgn * r
+                rows.append(row)
+    return np.array(rows)
+
+
+def radial_scaled(Z, w, frames, targets):
+    """Z with each (disjoint) window's features scaled about the window centre
+    so that the window's largest test-point radius equals targets[l]."""
+    Z = Z.copy()
+    for win, fr, tr in zip(w.windows, frames, targets):
+        dz = Z[:, list(win)] - fr["centre"]
+        Z[:, list(win)] = fr["centre"] + dz * (tr / np.linalg.norm(dz, axis=1).max())
+    return Z
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+def test_model_predict_matches_oracle(B, torch, precision):
+    """krr_model: the convolved grids computed once give the oracle's fast
+    summation (FP64 1e-12, FP32 1e-5) for test points inside the nodes' ball
+    (plan frame), for points beyond it but inside rho times its radius (wide
+    frame: the oracle's joint frame is pinned to it by extra rows) and for
+    points further out (per-window summation in the joint frame, as
+    krr_predict); all three within 1e-5 of the direct sum.  Several host
+    threads on their own streams predicting on one model give the serial
+    results."""
+    import threading
+    wins = [(0, 1, 2), (3, 4), (5,)]
+    w = W.random_problem(2500, 6, wins, 0.3, 32, 6, seed=53)
+    w.epsB = 0.25
+    Zraw = W.random_problem(777, 6, wins, 0.3, 32, 6, seed=54).X
+    plan = make_plan(B, torch, w, getattr(B, precision))
+    frames = [B.anova_plan_window(plan, l) for l in range(len(wins))]
+    RB = 0.25 - 0.5 * w.epsB
+    rX = [RB / fr["scale"] for fr in frames]              # nodes' largest radius per window
+    rho = [wide_rho(fr) for fr in frames]
+    assert min(rho) > 1.2
+    alpha = torch.from_numpy(w.alpha).cuda()
+    model = B.Model(plan, alpha)
+    del alpha                                 # the model holds its own copy
+    tol = 1e-12 if precision == "FP64" else 1e-5
+    cases = [
+        (radial_scaled(Zraw, w, frames, [0.9 * r for r in rX]), None),
+        (radial_scaled(Zraw, w, frames, [0.5 * (1 + q) * r for q, r in zip(rho, rX)]),
+         wide_frame_rows(w, frames)),
+        (radial_scaled(Zraw, w, frames, [1.3 * q * r for q, r in zip(rho, rX)]), None),
+    ]
+    for Z, extra in cases:
+        Zt = torch.from_numpy(np.ascontiguousarray(Z)).cuda()
+        out = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
+        model.predict(Zt, out)
+        got = out.cpu().numpy()
+        Zo = Z if extra is None else np.vstack([Z, extra])
+        ref = oracle_fast(w, Z=Zo)[:Z.shape[0]]
+        assert rel(got, ref) <= tol
+        assert rel(got, oracle.direct(Z, w.X, w.windows, w.eta, w.ell, w.alpha)) <= 1e-5
+    Zin = cases[0][0]
+    Zt = torch.from_numpy(Zin).cuda()
+    out = torch.empty(Zin.shape[0], dtype=torch.float64, device="cuda")
+    model.predict(Zt, out)
+    serial = out.cpu().numpy()
+    outs = [torch.full_like(out, float("nan")) for _ in range(4)]
+    torch.cuda.synchronize()
+    errs = []
+
+    def work(k):
+        try:
+            s = torch.cuda.Stream()
+            for _ in range(5):
+                model.predict(Zt, outs[k], stream=s)
+        except Exception as e:   # reported below
+            errs.append(e)
+
+    ts = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs, errs
+    for o in outs:
+        assert rel(o.cpu().numpy(), serial) <= (1e-13 if precision == "FP64" else 1e-6)
+    model.close()
+
+
 def test_repeat_runs_agree(B, torch):
     w = W.random_problem(5000, 3, [(0, 1, 2)], 0.2, 32, 6, seed=61)
     plan = make_plan(B, torch, w, B.MIXED)

@@ -57,9 +57,13 @@ def serial_results(B, torch, probs):
         plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, precision=B.MIXED)
         alpha = torch.zeros_like(y)
         st, its, _ = B.krr_cg_solve(plan, LAM, y, alpha, TOL, 5000)
+        # the same 500-row batches as the served predictions: a batch that
+        # reaches outside the plan's ball is summed in a frame fitted to it,
+        # so the approximation depends on the batch
         Zt = torch.from_numpy(Z).cuda()
         pred = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
-        B.krr_predict(plan, alpha, Zt, pred)
+        for k in range(0, Z.shape[0], 500):
+            B.krr_predict(plan, alpha, Zt[k:k + 500], pred[k:k + 500])
         torch.cuda.synchronize()
         res.append((int(its[0]), pred.cpu().numpy()))
         plan.close()
