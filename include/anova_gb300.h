@@ -224,13 +224,18 @@ void krr_model_destroy(krr_model* model);
 
 /* ----------------------------------------------------------------------------
  * Request server: kernel ridge regression fits (anova_fastsum_plan with
- * ANOVA_MIXED + krr_cg_solve) and predictions (krr_predict) served by worker
- * threads, each on its own CUDA stream.  Requests are admitted in arrival order
- * as soon as a worker is free and their device memory fits the budget (a
- * request that alone exceeds the budget runs when nothing else does); work of
- * different requests overlaps on the GPU.  Fitted models stay on the device
- * until released.  The paper serves no requests; this is the serving form of
- * its fit (Sec. 2) and predict (Sec. 4.3) operations.
+ * ANOVA_MIXED, krr_cg_solve, krr_model_create) and predictions
+ * (krr_model_predict) served by worker threads, each on its own CUDA stream.
+ * Requests are admitted in arrival order as soon as a worker is free and
+ * their device memory fits the budget (a request that alone exceeds the
+ * budget runs when nothing else does).  Fits occupy at most
+ * n_workers - max(1, n_workers / 4) workers; the others stay free for
+ * predictions.  Work of different requests overlaps on the GPU, predictions
+ * on one model included.  Fitted models stay on the device until released.
+ * Plans made by the server do not capture CUDA graphs (anova_plan_set_graphs),
+ * so other threads of the process may synchronise the device at any time.
+ * The paper serves no requests; this is the serving form of its fit (Sec. 2)
+ * and predict (Sec. 4.3) operations.
  * ------------------------------------------------------------------------- */
 typedef struct anova_server anova_server;
 

@@ -5,7 +5,9 @@
 // Worker threads, each with its own CUDA stream, take requests from one
 // queue in arrival order as soon as a worker is idle and the request's device
 // memory fits under the budget (continuous admission: a request never waits
-// for a batch to fill).  Work of different requests overlaps on the GPU.
+// for a batch to fill).  Fits may hold all workers but a quarter (at least
+// one), so that predictions -- short by comparison -- never queue behind a
+// wall of fits.  Work of different requests overlaps on the GPU.
 // Fitted models -- plan and krr_model, whose convolved grids make a
 // prediction a binning and a gather -- stay resident on the device until
 // released; predictions on one model run concurrently.  Host code only; every computation is a call of the library's
@@ -82,6 +84,8 @@ struct anova_server {
     bool stop = false;
     int device = 0;
     int running = 0;
+    int running_fits = 0;
+    int max_fits = 1;             // workers a fit may occupy; the rest stay free for predictions
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -202,6 +206,8 @@ static void worker_main(anova_server* sv) {
                         } else if (!m->second.ready || m->second.releasing) {
                             continue;
                         }
+                    } else if (sv->running_fits >= sv->max_fits) {
+                        continue;   // predictions behind it may still use the reserved workers
                     }
                     if (sv->in_use + q->bytes <= sv->budget || sv->running == 0) {
                         pick = it;
@@ -214,6 +220,7 @@ static void worker_main(anova_server* sv) {
                     sv->queue.erase(pick);
                     sv->in_use += r->bytes;
                     sv->running++;
+                    if (r->kind == 0) sv->running_fits++;
                     if (r->kind == 1) {
                         auto m = sv->models.find(r->model);
                         if (m != sv->models.end()) m->second.inflight++;
@@ -236,6 +243,7 @@ static void worker_main(anova_server* sv) {
             r->latency_ms = std::chrono::duration<double, std::milli>(t1 - r->submitted).count();
             r->done = true;
             sv->running--;
+            if (r->kind == 0) sv->running_fits--;
             if (r->status == ANOVA_OK || r->status == ANOVA_ENOCONV) sv->latencies.push_back(r->latency_ms);
         }
         sv->cv_done.notify_all();
@@ -269,6 +277,7 @@ anova_status anova_server_create(int32_t n_workers, int64_t hbm_budget_bytes, an
     if (!sv) return ANOVA_ENOMEM;
     cudaGetDevice(&sv->device);
     sv->budget = hbm_budget_bytes;
+    sv->max_fits = std::max(1, n_workers - std::max(1, n_workers / 4));
     sv->t0 = std::chrono::steady_clock::now();
     for (int i = 0; i < n_workers; i++) sv->workers.emplace_back(worker_main, sv);
     *out = sv;

@@ -2,12 +2,12 @@
 threads give the results that the same calls give one at a time.
 
 Each model is fitted (mixed-precision CG of Sec. 2 to tol 1e-8) and evaluated
-at test points (Sec. 4.3) once through the plain entry points on one stream,
-then again through a server where all fits and many small prediction batches
-are in flight together.  The FP32 spread of the mixed operator sums with
+at test points (Sec. 4.3) once through the plain entry points (krr_cg_solve,
+krr_model_predict) on one stream, then again through a server where all fits
+and many small prediction batches are in flight together.  The FP32 spread of the mixed operator sums with
 atomics, so two runs agree to rounding, not bit for bit: predictions must match
 to 1e-6 relative (the CG tolerance times the conditioning margin of these
-problems), iteration counts within a few.
+problems), iteration counts within a refinement pass or so.
 """
 import numpy as np
 import pytest
@@ -34,12 +34,13 @@ def torch():
 def problems():
     out = []
     specs = [
-        (6000, 6, [(0, 1, 2), (3, 4, 5)], 0.2, 16, 4, 31),
-        (9000, 4, [(0, 1), (2, 3), (1, 2)], 0.15, 32, 5, 32),
-        (4000, 5, [(0, 1, 2), (2, 3), (4,)], 0.25, 16, 5, 33),
+        (6000, 6, [(0, 1, 2), (3, 4, 5)], 0.2, 32, 6, 31),
+        (9000, 4, [(0, 1), (2, 3), (1, 2)], 0.15, 32, 6, 32),
+        (4000, 5, [(0, 1, 2), (2, 3), (4,)], 0.25, 32, 6, 33),
     ]
     for N, d, wins, ell, n, m, seed in specs:
         w = W.random_problem(N, d, wins, ell, n, m, seed=seed)
+        w.epsB = 0.25
         rng = np.random.default_rng(seed + 100)
         Z = rng.uniform(w.X.min(0), w.X.max(0), size=(3000, d))
         out.append((w, Z))
@@ -61,11 +62,15 @@ def serial_results(B, torch, probs):
         # reaches outside the plan's ball is summed in a frame fitted to it,
         # so the approximation depends on the batch
         Zt = torch.from_numpy(Z).cuda()
+        model = B.Model(plan, alpha)
         pred = torch.empty(Z.shape[0], dtype=torch.float64, device="cuda")
+        plain = torch.empty_like(pred)
         for k in range(0, Z.shape[0], 500):
-            B.krr_predict(plan, alpha, Zt[k:k + 500], pred[k:k + 500])
+            model.predict(Zt[k:k + 500], pred[k:k + 500])
+            B.krr_predict(plan, alpha, Zt[k:k + 500], plain[k:k + 500])
         torch.cuda.synchronize()
-        res.append((int(its[0]), pred.cpu().numpy()))
+        res.append((int(its[0]), pred.cpu().numpy(), plain.cpu().numpy()))
+        model.close()
         plan.close()
     return res
 
@@ -96,11 +101,21 @@ def test_server_matches_serial_calls(B, torch):
             r = sv.wait(t)
             assert r["status"] == B.OK
             got[i][500 * k:500 * (k + 1)] = o.cpu().numpy()
-        for (its, pred), fi, g in zip(ref, fit_info, got):
-            assert fi["status"] == B.OK
-            assert abs(fi["iterations"] - its) <= max(3, its // 10)
+        report = []
+        for (its, pred, plain), fi, g in zip(ref, fit_info, got):
             err = np.max(np.abs(g - pred)) / np.max(np.abs(pred))
-            assert err < 1e-6, err
+            err_plain = np.max(np.abs(g - plain)) / np.max(np.abs(plain))
+            report.append((fi["status"], fi["iterations"], its, err, err_plain))
+        for st, it_served, it_alone, err, err_plain in report:
+            assert st == B.OK, report
+            # the FP32 inner passes of the refinement sum with atomics: a pass
+            # may end a check interval earlier or later
+            assert abs(it_served - it_alone) <= max(12, it_alone // 5), report
+            assert err < 1e-6, report
+            # krr_predict sums batches that leave the nodes' ball in a joint
+            # frame, the model in its wide frame: two approximations within
+            # the fast summation's error of each other
+            assert err_plain < 1e-5, report
         s = sv.stats()
         assert s["completed"] == len(fits) + len(tickets)
         assert 0 < s["p50_ms"] <= s["p99_ms"]
