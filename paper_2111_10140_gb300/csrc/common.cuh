@@ -79,8 +79,19 @@ struct WindowPlan {
     float* wtab = nullptr;     // dense 3-D windows, FP32 plans: N x 3 x 16 zero-padded window weights (sorted order)
     int box_lo[kMaxDim] = {0, 0, 0};   // grid cells touched by the training nodes: start (may be < 0)
     int box_ext[kMaxDim] = {0, 0, 0};  // and extent per axis (<= nos)
+    bool fft12 = false;        // 1-D / 2-D window on the batched box FFT (fft12.cu)
     PointSet X;
 };
+
+// Per-window arguments of the batched box-restricted 1-D / 2-D FFT (fft12.cu).
+struct Fft12Win {
+    void* grid;                // real grid, nos^dA
+    const void* tw;            // e^{-2 pi i r/nos}
+    const void* D;             // n^dA multiplier
+    int dA, n, nos;
+    int lo[2], B[2];           // box start and extent per axis
+};
+constexpr size_t kFft12MaxSmem = 227 * 1024;
 
 // Per-window arguments of the batched box-restricted 3-D FFT (fft3.cu).
 struct Fft3Win {
@@ -141,6 +152,9 @@ struct anova_plan {
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
     bool fft3_slab = false;             // every batched 3-D window fits the slab kernels
+    std::vector<int> fft12_windows;     // 1-D / 2-D windows on the batched box FFT
+    anova::Fft12Win* fft12_desc = nullptr;  // device, 2 x fft12_windows.size(): FP64 then FP32
+    size_t fft12_smem64 = 0, fft12_smem32 = 0;   // dynamic shared memory of the launch
     void* tmp = nullptr;                // P x N per-window results (8 bytes each)
     double* eta_dev = nullptr;          // P window weights on the device
     // CG state
@@ -252,6 +266,10 @@ anova_status fft_convolve_window(anova_plan* plan, const WindowPlan& w, T* grid,
 template <typename T>
 anova_status fft3_box_all(anova_plan* plan, cudaStream_t st);
 bool fft3_box_supported(const WindowPlan& w);
+template <typename T>
+anova_status fft12_box_all(anova_plan* plan, cudaStream_t st);
+bool fft12_box_supported(const WindowPlan& w);
+size_t fft12_window_smem(const WindowPlan& w, size_t real_bytes);
 bool fft3_slab_supported(const WindowPlan& w);
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st);

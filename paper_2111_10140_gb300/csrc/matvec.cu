@@ -107,9 +107,13 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
         ANOVA_TRY(fft3_box_all<T>(plan, st));
         nl += plan->fft3_slab ? 3 : 5;
     }
+    if (!plan->fft12_windows.empty()) {
+        ANOVA_TRY(fft12_box_all<T>(plan, st));
+        nl++;
+    }
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];
-        if (fft3_box_supported(w)) continue;
+        if (fft3_box_supported(w) || w.fft12) continue;
         ANOVA_TRY(fft_convolve_window<T>(plan, w, grid_of<T>(plan, w), st));
         nl += 2 * w.dA;
     }

@@ -835,6 +835,45 @@ static anova_status build_fft3_batch(anova_plan* plan, cudaStream_t st) {
     return ANOVA_OK;
 }
 
+// Descriptors of the batched 1-D / 2-D box FFT: every such window whose box
+// transform fits one thread block's shared memory in FP64.
+static anova_status build_fft12_batch(anova_plan* plan, cudaStream_t st) {
+    plan->fft12_windows.clear();
+    for (int l = 0; l < plan->P; l++) {
+        WindowPlan& w = plan->win[l];
+        w.fft12 = plan->N > 0 && fft12_box_supported(w);
+        if (w.fft12) plan->fft12_windows.push_back(l);
+    }
+    const int nw = (int)plan->fft12_windows.size();
+    if (nw == 0) return ANOVA_OK;
+    std::vector<Fft12Win> desc(2 * nw);
+    plan->fft12_smem64 = plan->fft12_smem32 = 0;
+    for (int k = 0; k < nw; k++) {
+        const WindowPlan& w = plan->win[plan->fft12_windows[k]];
+        plan->fft12_smem64 = std::max(plan->fft12_smem64, fft12_window_smem(w, sizeof(double)));
+        plan->fft12_smem32 = std::max(plan->fft12_smem32, fft12_window_smem(w, sizeof(float)));
+        for (int prec = 0; prec < 2; prec++) {
+            Fft12Win& d = desc[prec * nw + k];
+            d.grid = prec == 0 ? (void*)(static_cast<double*>(plan->grid) + w.grid_off)
+                               : (void*)(static_cast<float*>(plan->grid) + w.grid_off);
+            d.tw = prec == 0 ? (const void*)w.tw64 : (const void*)w.tw32;
+            d.D = prec == 0 ? (const void*)w.D64 : (const void*)w.D32;
+            d.dA = w.dA;
+            d.n = w.n;
+            d.nos = w.nos;
+            for (int t = 0; t < 2; t++) {
+                d.lo[t] = w.box_lo[t];
+                d.B[t] = w.box_ext[t];
+            }
+        }
+    }
+    ANOVA_CUDA_TRY(cudaMalloc(&plan->fft12_desc, 2 * nw * sizeof(Fft12Win)));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->fft12_desc, desc.data(), 2 * nw * sizeof(Fft12Win),
+                                   cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    return ANOVA_OK;
+}
+
 static anova_status validate(int64_t N, int32_t d, int64_t ld, const int32_t* windows, int32_t P,
                              const double* weights, double ell, const int32_t* n, int32_t m,
                              double sigma, double eps_B, int32_t p, int32_t precision) {
@@ -959,6 +998,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     }
     if (s == ANOVA_OK) s = build_dense_batch(plan, st);
     if (s == ANOVA_OK) s = build_fft3_batch(plan, st);
+    if (s == ANOVA_OK) s = build_fft12_batch(plan, st);
     if (s == ANOVA_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
@@ -1214,6 +1254,7 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->dense_desc);
     cudaFree(plan->dense_asort);
     cudaFree(plan->fft3_desc);
+    cudaFree(plan->fft12_desc);
     cudaFree(plan->psi_poly);
     cudaFree(plan->cg_vec);
     cudaFree(plan->cg_scal);

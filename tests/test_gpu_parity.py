@@ -385,11 +385,15 @@ def test_graph_replay_matches_direct_calls(B, torch):
         assert rel(out.cpu().numpy(), ref) <= 1e-5, call
 
 
-@pytest.mark.parametrize("n,m", [(4, 1), (8, 3), (32, 6), (64, 7)])
-def test_dense_small_windows(B, torch, n, m):
-    """1-D and 2-D windows on the dense FP32 kernels (and the generic FP64 ones)."""
+@pytest.mark.parametrize("n,m,epsB", [(4, 1, 0.25), (8, 3, 0.25), (16, 7, 0.25), (32, 6, 0.25), (64, 7, 0.25),
+                                      (64, 6, 1 / 16), (128, 6, 0.25)])
+def test_dense_small_windows(B, torch, n, m, epsB):
+    """1-D and 2-D windows on the dense FP32 kernels (and the generic FP64 ones);
+    their FFT on the batched box kernel where it fits one block's shared
+    memory (a box that covers the whole grid at n = 16, m = 7; n = 128 falls
+    back to the per-axis kernels in 2-D)."""
     w = W.random_problem(5000, 3, [(0,), (1, 2)], 0.25, n, m, seed=100 + n + m)
-    w.epsB = 0.25
+    w.epsB = epsB
     plan = make_plan(B, torch, w, B.MIXED)
     ref = oracle_fast(w)
     a64 = torch.from_numpy(w.alpha).cuda()
