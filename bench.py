@@ -510,6 +510,80 @@ def run_serve(args):
     }), flush=True)
 
 
+def run_batch(args):
+    """Batching form: 64 problems (N log-uniform in [2^10, 2^17], d 6..15, own
+    windows of 1-3 features, ell in [0.05, 0.5], lambda in [1e-4, 1e-1]) with
+    16 right-hand sides each, solved together by krr_batch_cg_solve (FP32
+    operator, FP64 CG, graph replay), against the same solves one system at a
+    time through krr_cg_solve on the same FP32 plans (timed on one right-hand
+    side per problem and scaled by the number of right-hand sides)."""
+    import time
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    from paper_2111_10140_gb300 import workloads as W
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    probs = W.batch_form(args.batch_problems, seed=3, nrhs=args.batch_rhs)
+    t0 = time.perf_counter()
+    plans = [B.anova_fastsum_plan(torch.from_numpy(w.X).to(dev), w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB,
+                                  precision=B.FP32) for w in probs]
+    batch = B.Batch(plans, args.batch_rhs)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    y = torch.empty(batch.size, dtype=torch.float64, device=dev)
+    for p, w in enumerate(probs):
+        batch.block(y, p).copy_(torch.from_numpy(w.meta["Y"]))
+    alpha = torch.empty_like(y)
+    lams = [w.lam for w in probs]
+    tol, maxit = args.batch_tol, args.batch_maxit
+    batch.cg_solve(lams, y, alpha, tol, maxit)          # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, its, rr = batch.cg_solve(lams, y, alpha, tol, maxit)
+    e1.record()
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    # one right-hand side per problem through the single-system solver
+    t_single = 0.0
+    its1 = []
+    for p, (w, plan) in enumerate(zip(probs, plans)):
+        y1 = torch.from_numpy(w.meta["Y"][0]).to(dev)
+        a1 = torch.zeros_like(y1)
+        B.krr_cg_solve(plan, w.lam, y1, a1, tol, maxit)   # warm
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        _, it1, _ = B.krr_cg_solve(plan, w.lam, y1, a1, tol, maxit)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - s0
+        its1.append(int(it1[0]))
+    ns = len(probs) * args.batch_rhs
+    work = sum(w.N * len(w.windows) for w in probs)
+    print(json.dumps({
+        "batch": True,
+        "workload": f"{len(probs)} problems, N log-uniform 2^10..2^17 (total {sum(w.N for w in probs)}), "
+                    f"{args.batch_rhs} right-hand sides each, d 6..15, 1-5 windows of 1-3 features",
+        "systems": ns, "status": int(st), "tol": tol, "setup_s": round(t_setup, 3),
+        "batch_solve_s": round(t_batch, 4), "systems_per_s": ns / t_batch,
+        "iters_median": float(np.median(its)), "iters_max": int(its.max()),
+        "relres_max": float(rr.max()), "relres_median": float(np.median(rr)),
+        "converged": int((rr <= 10 * tol).sum()),
+        "single_solves_one_rhs_s": round(t_single, 4),
+        "single_est_all_rhs_s": round(t_single * args.batch_rhs, 3),
+        "speedup_vs_single": t_single * args.batch_rhs / t_batch,
+        "node_window_iters_per_s": float(sum(w.N * len(w.windows) * int(its[p].sum())
+                                             for p, w in enumerate(probs)) / t_batch),
+        "work_node_windows": work,
+    }), flush=True)
+    batch.close()
+    for pl in plans:
+        pl.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,6 +605,12 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-models", type=int, default=4)
     ap.add_argument("--serve-fit-pool", type=int, default=6)
+    ap.add_argument("--batch", action="store_true",
+                    help="batching form: many problems x right-hand sides in one batched CG")
+    ap.add_argument("--batch-problems", type=int, default=64)
+    ap.add_argument("--batch-rhs", type=int, default=16)
+    ap.add_argument("--batch-tol", type=float, default=1e-6)
+    ap.add_argument("--batch-maxit", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -540,6 +620,8 @@ def main():
         run_crossover(args)
     elif args.serve:
         run_serve(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -223,6 +223,57 @@ anova_status krr_model_predict(krr_model* model, const double* Z, int64_t M, int
 void krr_model_destroy(krr_model* model);
 
 /* ----------------------------------------------------------------------------
+ * Batches: many problems and right-hand sides per launch.  The paper fits one
+ * problem at a time; a batch runs the fits of Sec. 2 for several problems
+ * (own nodes, windows, width, lambda) and several right-hand sides each in
+ * lockstep: one launch per (window dimension, region size) spreads every
+ * (problem, window, right-hand side), one launch sequence transforms all 3-D
+ * grids and one all 1-D / 2-D grids, and the CG vector updates of all systems
+ * are one launch each; the iteration is replayed as a CUDA graph.  FP32
+ * operator (the plans' FP32 kernels), FP64 CG vectors and scalars.
+ *
+ * Flat vector layout: problem p's right-hand side r, entry i (the problem's
+ * node order) at off[p] + r * N_p + i, off from anova_batch_layout.
+ * ------------------------------------------------------------------------- */
+typedef struct anova_batch anova_batch;
+
+/*
+ * plans: nprob plans holding FP32 (ANOVA_FP32 or ANOVA_MIXED), N >= 1, one
+ * cut-off m, every window on the dense kernels and box FFTs (EINVAL names the
+ * first that is not); the plans must outlive the batch.  nrhs >= 1,
+ * nprob * nrhs <= 65535, at most 65535 (problem, window, right-hand side)
+ * instances.  Device memory per instance: the window's grid (n_os^dA FP32),
+ * 3-D FFT work (2 n_os^2 n complex), sorted coefficients and results (2 N_p).
+ * Synchronous on `stream`.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t nrhs, void* stream,
+                                anova_batch** out);
+
+/* offsets (host, nprob + 1 entries) of the flat layout; offsets[nprob] is its length. */
+anova_status anova_batch_layout(const anova_batch* batch, int64_t* offsets);
+
+/* y = K x for every system (device, flat layout; y must not alias x).
+ * Asynchronous on `stream`; calls on one batch must not overlap. */
+anova_status anova_batch_matvec(anova_batch* batch, const double* x, double* y, void* stream);
+
+/*
+ * Solve (K_p + lambda_p I) alpha = y for every (problem p, right-hand side) by
+ * CG (Hestenes-Stiefel, alpha_0 = 0), each system stopping when its recursive
+ * residual reaches tol ||y|| or after maxit iterations.  lambda: host, nprob
+ * entries >= 0.  y, alpha: device, flat layout.  iters, relres: host, nprob *
+ * nrhs entries (system p * nrhs + r) or NULL; relres is recomputed with the
+ * batch's FP32 operator.  Returns ENOCONV if a system stopped at maxit,
+ * ERANGE on a non-finite residual.  Synchronous on `stream`; the iteration is
+ * captured as a CUDA graph on the second block of iterations (same caveat as
+ * anova_matvec on device-wide synchronisation from other threads).
+ */
+anova_status krr_batch_cg_solve(anova_batch* batch, const double* lambda, const double* y, double* alpha,
+                                double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
+
+/* Free the batch (not its plans).  NULL is ignored. */
+void anova_batch_destroy(anova_batch* batch);
+
+/* ----------------------------------------------------------------------------
  * Request server: kernel ridge regression fits (anova_fastsum_plan with
  * ANOVA_MIXED, krr_cg_solve, krr_model_create) and predictions
  * (krr_model_predict) served by worker threads, each on its own CUDA stream.

@@ -36,6 +36,11 @@ _SIGNATURES = {
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
+    "anova_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "anova_batch_layout": (_i32, [_vp, _pi64]),
+    "anova_batch_matvec": (_i32, [_vp, _vp, _vp, _vp]),
+    "krr_batch_cg_solve": (_i32, [_vp, _pf64, _vp, _vp, _f64, _i32, _pi32, _pf64, _vp]),
+    "anova_batch_destroy": (None, [_vp]),
     "krr_model_create": (_i32, [_vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "krr_model_predict": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
     "krr_model_destroy": (None, [_vp]),
@@ -261,6 +266,63 @@ def anova_stage_times(plan: Plan):
     la = (ctypes.c_int64 * 8)()
     k = lib().anova_stage_times(plan.handle, ms, la, 8)
     return list(ms[:k]), list(la[:k])
+
+
+class Batch:
+    """anova_batch over plans (kept alive here) with nrhs right-hand sides each."""
+
+    def __init__(self, plans, nrhs, stream=None):
+        arr = (_vp * len(plans))(*[p.handle.value for p in plans])
+        h = ctypes.c_void_p()
+        _check(lib().anova_batch_create(arr, len(plans), int(nrhs), _stream(stream), ctypes.byref(h)),
+               "anova_batch_create")
+        self.handle = h
+        self.plans = list(plans)
+        self.nrhs = int(nrhs)
+        off = np.zeros(len(plans) + 1, dtype=np.int64)
+        _check(lib().anova_batch_layout(h, off.ctypes.data_as(_pi64)), "anova_batch_layout")
+        self.offsets = off
+
+    @property
+    def size(self):
+        return int(self.offsets[-1])
+
+    def block(self, flat, p):
+        """View of problem p's nrhs x N_p block of a flat vector."""
+        return flat[self.offsets[p]:self.offsets[p + 1]].view(self.nrhs, -1)
+
+    def matvec(self, x, y, stream=None):
+        import torch
+        _require_cuda(x, "x", torch.float64)
+        _require_cuda(y, "y", torch.float64)
+        _check(lib().anova_batch_matvec(self.handle, _ptr(x), _ptr(y), _stream(stream)), "anova_batch_matvec")
+        return y
+
+    def cg_solve(self, lambdas, y, alpha, tol, maxit, stream=None):
+        """Returns (status, iterations, relres), both arrays of problems x nrhs."""
+        import torch
+        _require_cuda(y, "y", torch.float64)
+        _require_cuda(alpha, "alpha", torch.float64)
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lambdas, np.float64), (len(self.plans),)))
+        ns = len(self.plans) * self.nrhs
+        its = np.zeros(ns, dtype=np.int32)
+        rr = np.zeros(ns, dtype=np.float64)
+        st = lib().krr_batch_cg_solve(self.handle, lam.ctypes.data_as(_pf64), _ptr(y), _ptr(alpha), float(tol),
+                                      int(maxit), its.ctypes.data_as(_pi32), rr.ctypes.data_as(_pf64),
+                                      _stream(stream))
+        _check(st, "krr_batch_cg_solve", allow=(OK, ENOCONV))
+        return st, its.reshape(len(self.plans), self.nrhs), rr.reshape(len(self.plans), self.nrhs)
+
+    def close(self):
+        if self.handle:
+            lib().anova_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Model:

@@ -269,6 +269,21 @@ bool fft3_box_supported(const WindowPlan& w);
 template <typename T>
 anova_status fft12_box_all(anova_plan* plan, cudaStream_t st);
 bool fft12_box_supported(const WindowPlan& w);
+template <typename T>
+anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st);
+anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
+anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin* descs,
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
+// Shapes of a batched 3-D box FFT launch (maxima over its windows).
+struct Fft3Shape {
+    int nw = 0, nmax = 0, nosmax = 0, bx = 0, by = 0, bz = 0;
+    int64_t t1 = 0, t2 = 0, t3 = 0;
+    bool slab = true;
+    void add(const WindowPlan& w);
+};
+template <typename T>
+anova_status fft3_box_run(const Fft3Win* wins, const Fft3Shape& sh, int sm_count, cudaStream_t st);
 size_t fft12_window_smem(const WindowPlan& w, size_t real_bytes);
 bool fft3_slab_supported(const WindowPlan& w);
 template <typename T>

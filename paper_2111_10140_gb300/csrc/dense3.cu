@@ -986,6 +986,50 @@ static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int n
     return ANOVA_OK;
 }
 
+// FP32 dense kernels over any merged sub-problem list whose descriptors carry
+// sorted coefficients (plans and batches alike): one launch per (dims, R) group.
+anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st) {
+    for (const auto& g : groups) {
+        const int dA = g[0] / 100, R = g[0] % 100;
+        const int4* sub = sub_base + g[1];
+        const int nsub = g[2];
+        if (nsub == 0) continue;
+        switch (dA * 100 + R) {
+#define ANOVA_S(R_)                                                                           \
+    case 100 + R_: k_spread1_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, m); break;              \
+    case 200 + R_: k_spread2_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, m); break;              \
+    case 300 + R_: k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, m); break;
+            ANOVA_S(4) ANOVA_S(6) ANOVA_S(8) ANOVA_S(10) ANOVA_S(12) ANOVA_S(14) ANOVA_S(16)
+#undef ANOVA_S
+            default: set_error("dense FP32 spread: unsupported window dimension or region size"); return ANOVA_EINVAL;
+        }
+        ANOVA_CHECK_LAUNCH();
+    }
+    return ANOVA_OK;
+}
+
+anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin* descs,
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st) {
+    for (const auto& g : groups) {
+        const int dA = g[0] / 100, R = g[0] % 100;
+        const int4* sub = sub_base + g[1];
+        const int nsub = g[2];
+        if (nsub == 0) continue;
+        switch (dA * 100 + R) {
+#define ANOVA_G(R_)                                                                           \
+    case 100 + R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
+    case 200 + R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
+    case 300 + R_: k_gather3_tc<R_><<<nsub, kGatherTcThreads, 0, st>>>(sub, descs, m); break;
+            ANOVA_G(4) ANOVA_G(6) ANOVA_G(8) ANOVA_G(10) ANOVA_G(12) ANOVA_G(14) ANOVA_G(16)
+#undef ANOVA_G
+            default: set_error("dense FP32 gather: unsupported window dimension or region size"); return ANOVA_EINVAL;
+        }
+        ANOVA_CHECK_LAUNCH();
+    }
+    return ANOVA_OK;
+}
+
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st) {
     const int nd = (int)plan->dense_windows.size();

@@ -186,22 +186,28 @@ size_t fft12_window_smem(const WindowPlan& w, size_t real_bytes) {
 }
 
 template <typename T>
-anova_status fft12_box_all(anova_plan* plan, cudaStream_t st) {
-    const int nw = (int)plan->fft12_windows.size();
+anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st) {
     if (nw == 0) return ANOVA_OK;
-    const size_t sh = sizeof(T) == 8 ? plan->fft12_smem64 : plan->fft12_smem32;
     static bool attrs = [] {
         cudaFuncSetAttribute(k_fft12_box<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFft12MaxSmem);
         cudaFuncSetAttribute(k_fft12_box<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFft12MaxSmem);
         return true;
     }();
     (void)attrs;
-    const Fft12Win* desc = plan->fft12_desc + (sizeof(T) == 8 ? 0 : nw);
-    k_fft12_box<T><<<nw, kFft12Threads, sh, st>>>(desc);
+    k_fft12_box<T><<<nw, kFft12Threads, smem, st>>>(desc);
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
 }
 
+template <typename T>
+anova_status fft12_box_all(anova_plan* plan, cudaStream_t st) {
+    const int nw = (int)plan->fft12_windows.size();
+    const size_t sh = sizeof(T) == 8 ? plan->fft12_smem64 : plan->fft12_smem32;
+    return fft12_box_run<T>(plan->fft12_desc + (sizeof(T) == 8 ? 0 : nw), nw, sh, st);
+}
+
+template anova_status fft12_box_run<double>(const Fft12Win*, int, size_t, cudaStream_t);
+template anova_status fft12_box_run<float>(const Fft12Win*, int, size_t, cudaStream_t);
 template anova_status fft12_box_all<double>(anova_plan*, cudaStream_t);
 template anova_status fft12_box_all<float>(anova_plan*, cudaStream_t);
 

@@ -399,47 +399,43 @@ static size_t mid_bytes() {
     return ((size_t)(kMaxN3 + kMidStage) * kMidLanes + 4 * kMaxN3) * sizeof(C);
 }
 
-// every batched window: one launch per pass for all of them
+void Fft3Shape::add(const WindowPlan& w) {
+    nw++;
+    t1 = std::max<int64_t>(t1, (int64_t)w.box_ext[0] * w.box_ext[1] * w.n);
+    t2 = std::max<int64_t>(t2, (int64_t)w.box_ext[0] * w.n * w.n);
+    t3 = std::max<int64_t>(t3, (int64_t)w.box_ext[0] * w.box_ext[1] * w.box_ext[2]);
+    nmax = std::max(nmax, w.n);
+    nosmax = std::max(nosmax, w.nos);
+    bx = std::max(bx, w.box_ext[0]);
+    by = std::max(by, w.box_ext[1]);
+    bz = std::max(bz, w.box_ext[2]);
+    slab = slab && fft3_slab_supported(w);
+}
+
+// every window of a descriptor array: one launch per pass for all of them
 template <typename T>
-anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
+anova_status fft3_box_run(const Fft3Win* wins, const Fft3Shape& sh, int sm_count, cudaStream_t st) {
     static bool mid_attr = [] {
         cudaFuncSetAttribute(k_fft3_mid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_bytes<T>());
         return true;
     }();
     (void)mid_attr;
-    const int nw = (int)plan->fft3_windows.size();
+    const int nw = sh.nw;
     if (nw == 0) return ANOVA_OK;
-    const Fft3Win* wins = plan->fft3_desc + (sizeof(T) == 8 ? 0 : nw);
-    const int cap = 4 * plan->sm_count;
-    int64_t t1 = 0, t2 = 0, t3 = 0;
-    int nmax = 0;
-    for (int k = 0; k < nw; k++) {
-        const WindowPlan& w = plan->win[plan->fft3_windows[k]];
-        t1 = std::max<int64_t>(t1, (int64_t)w.box_ext[0] * w.box_ext[1] * w.n);
-        t2 = std::max<int64_t>(t2, (int64_t)w.box_ext[0] * w.n * w.n);
-        t3 = std::max<int64_t>(t3, (int64_t)w.box_ext[0] * w.box_ext[1] * w.box_ext[2]);
-        nmax = std::max(nmax, w.n);
-    }
-    const dim3 g1(grid_for(t1, kThreads, cap), nw), g2(grid_for(t2, kThreads, cap), nw);
-    const dim3 gm(nmax * ((nmax + kMidLanes - 1) / kMidLanes), nw), g3(grid_for(t3, kThreads, cap), nw);
-    if (plan->fft3_slab) {
-        int bxmax = 0, nosmax = 0, bymax = 0, bzmax = 0;
-        for (int k = 0; k < nw; k++) {
-            const WindowPlan& w = plan->win[plan->fft3_windows[k]];
-            bxmax = std::max(bxmax, w.box_ext[0]);
-            bymax = std::max(bymax, w.box_ext[1]);
-            bzmax = std::max(bzmax, w.box_ext[2]);
-            nosmax = std::max(nosmax, w.nos);
-        }
-        const size_t shf = slab_fwd_bytes<T>(nosmax, bymax, bzmax, nmax);
-        const size_t shi = slab_inv_bytes<T>(nosmax, bymax, nmax);
+    const int cap = 4 * sm_count;
+    const int nmax = sh.nmax;
+    const dim3 g1(grid_for(sh.t1, kThreads, cap), nw), g2(grid_for(sh.t2, kThreads, cap), nw);
+    const dim3 gm(nmax * ((nmax + kMidLanes - 1) / kMidLanes), nw), g3(grid_for(sh.t3, kThreads, cap), nw);
+    if (sh.slab) {
+        const size_t shf = slab_fwd_bytes<T>(sh.nosmax, sh.by, sh.bz, nmax);
+        const size_t shi = slab_inv_bytes<T>(sh.nosmax, sh.by, nmax);
         static bool attrs = [] {
             cudaFuncSetAttribute(k_fft3_slab_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             cudaFuncSetAttribute(k_fft3_slab_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             return true;
         }();
         (void)attrs;
-        const dim3 gs(bxmax, nw);
+        const dim3 gs(sh.bx, nw);
         k_fft3_slab_fwd<T><<<gs, kSlabThreads, shf, st>>>(wins);
         k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, mid_bytes<T>(), st>>>(wins);
         k_fft3_slab_inv<T><<<gs, kSlabThreads, shi, st>>>(wins);
@@ -453,6 +449,20 @@ anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
     k_fft3_i3<T><<<g3, kThreads, 0, st>>>(wins);
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
+}
+
+template anova_status fft3_box_run<float>(const Fft3Win*, const Fft3Shape&, int, cudaStream_t);
+template anova_status fft3_box_run<double>(const Fft3Win*, const Fft3Shape&, int, cudaStream_t);
+
+// the plan's batched 3-D windows
+template <typename T>
+anova_status fft3_box_all(anova_plan* plan, cudaStream_t st) {
+    const int nw = (int)plan->fft3_windows.size();
+    if (nw == 0) return ANOVA_OK;
+    Fft3Shape sh;
+    for (int k = 0; k < nw; k++) sh.add(plan->win[plan->fft3_windows[k]]);
+    sh.slab = plan->fft3_slab;
+    return fft3_box_run<T>(plan->fft3_desc + (sizeof(T) == 8 ? 0 : nw), sh, plan->sm_count, st);
 }
 
 template anova_status fft3_box_all<float>(anova_plan*, cudaStream_t);

@@ -161,3 +161,36 @@ def serving_problem(N, seed, M_test=0):
     return Workload(f"serving_N{N}_d{d}_P{P}", np.ascontiguousarray(Xall[:N]), windows, np.full(P, 1.0 / P), 0.25,
                     n, 6, 2.0, rng.standard_normal(N), y, 1e-2, 1e-6, epsB=0.25,
                     meta={"Z": np.ascontiguousarray(Xall[N:])})
+
+
+def batch_problem(N, seed, nrhs=16):
+    """One problem of the batching form: d uniform in 6..15 standard normal
+    features, windows of 1-3 distinct features covering at most all of them,
+    ell log-uniform in [0.05, 0.5], lambda log-uniform in [1e-4, 1e-1], nrhs
+    right-hand sides N(0, 1) (meta["Y"], nrhs x N); m = 6, eps_B = 0.25, n = 16
+    (3-D, ell >= 0.15) or 32 (3-D) and 32 / 64 for 1-D and 2-D (64 when
+    ell < 0.1)."""
+    rng = np.random.default_rng(seed)
+    d = int(rng.integers(6, 16))
+    feats = list(rng.permutation(d))
+    windows = []
+    while feats and len(windows) < 5:
+        k = min(int(rng.integers(1, 4)), len(feats))
+        windows.append(tuple(sorted(int(f) for f in feats[:k])))
+        feats = feats[k:]
+    ell = float(10 ** rng.uniform(np.log10(0.05), np.log10(0.5)))
+    lam = float(10 ** rng.uniform(-4, -1))
+    raw = rng.standard_normal((N, d))
+    X = _minmax_into_ball(raw, windows)
+    n = [(16 if ell >= 0.15 else 32) if len(w) == 3 else (64 if ell < 0.1 else 32) for w in windows]
+    P = len(windows)
+    Y = rng.standard_normal((nrhs, N))
+    return Workload(f"batch_N{N}_d{d}_P{P}", X, windows, np.full(P, 1.0 / P), ell, n, 6, 2.0,
+                    rng.standard_normal(N), Y[0].copy(), lam, 1e-6, epsB=0.25, meta={"Y": Y})
+
+
+def batch_form(count=64, seed=3, nrhs=16):
+    """The batching form: `count` problems with N log-uniform in [2^10, 2^17]."""
+    rng = np.random.default_rng(seed)
+    Ns = np.round(2.0 ** rng.uniform(10, 17, size=count)).astype(int)
+    return [batch_problem(int(N), seed=10_000 * seed + k, nrhs=nrhs) for k, N in enumerate(Ns)]

@@ -1,0 +1,133 @@
+"""Batches: several problems and right-hand sides per launch.
+
+The batch's operator must give, system by system, what the problem's own plan
+gives (same FP32 kernels; the atomics of the spread sum in another order, so
+1e-6) and the oracle's fast summation (1e-5, the FP32 bar).  The batched CG
+must stop each system at its own tolerance, agree with the single-problem
+solver on the same FP32 operator, and leave a residual under the oracle's FP64
+operator that exceeds the reported one by no more than the FP32 operator
+error on the solution itself.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_10140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_10140_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+SPECS = [
+    (700, 6, [(0, 1, 2), (3, 4)], 0.2, [16, 32], 1e-2),
+    (1500, 6, [(0,), (1, 2), (3, 4, 5)], 0.3, [32, 32, 16], 1e-1),
+    (2500, 3, [(0, 1), (2,)], 0.15, [32, 64], 3e-2),
+    (4000, 6, [(0, 1, 2), (3, 4, 5)], 0.25, [16, 16], 5e-2),
+    (1200, 3, [(1,), (0, 2)], 0.4, [32, 32], 1e-2),
+]
+NRHS = 3
+
+
+@pytest.fixture(scope="module")
+def setup(B, torch):
+    probs, plans = [], []
+    for k, (N, d, wins, ell, n, lam) in enumerate(SPECS):
+        w = W.random_problem(N, d, wins, ell, n, 6, seed=300 + k)
+        w.epsB = 0.25
+        w.lam = lam
+        w.meta["Y"] = np.random.default_rng(400 + k).standard_normal((NRHS, N))
+        probs.append(w)
+        plans.append(B.anova_fastsum_plan(torch.from_numpy(w.X).cuda(), w.windows, w.ell, n=w.n, m=w.m,
+                                          eps_B=w.epsB, precision=B.FP32))
+    batch = B.Batch(plans, NRHS)
+    return probs, plans, batch
+
+
+def flat(batch, torch, arrays):
+    v = torch.empty(batch.size, dtype=torch.float64, device="cuda")
+    for p, a in enumerate(arrays):
+        batch.block(v, p).copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    return v
+
+
+def test_batch_layout(setup):
+    probs, _, batch = setup
+    Ns = [w.N for w in probs]
+    assert list(np.diff(batch.offsets)) == [NRHS * N for N in Ns]
+    assert batch.offsets[0] == 0
+
+
+def test_batch_matvec_matches_plans_and_oracle(B, torch, setup):
+    probs, plans, batch = setup
+    rng = np.random.default_rng(5)
+    xs = [rng.standard_normal((NRHS, w.N)) for w in probs]
+    x = flat(batch, torch, xs)
+    y = torch.empty_like(x)
+    batch.matvec(x, y)
+    torch.cuda.synchronize()
+    for p, (w, plan) in enumerate(zip(probs, plans)):
+        yb = batch.block(y, p).cpu().numpy()
+        for r in range(NRHS):
+            a32 = torch.from_numpy(xs[p][r]).float().cuda()
+            o32 = torch.empty_like(a32)
+            B.anova_matvec(plan, a32, o32)
+            assert rel(yb[r], o32.double().cpu().numpy()) <= 1e-6, (p, r)
+            ref = oracle.fastsum(None, w.X, w.windows, w.eta, w.ell, w.n, w.m, xs[p][r], sigma=w.sigma,
+                                 epsB=w.epsB, p=w.p)
+            assert rel(yb[r], ref) <= 1e-5, (p, r)
+
+
+def test_batch_cg_matches_single_solves_and_oracle(B, torch, setup):
+    probs, plans, batch = setup
+    tol = 1e-6
+    y = flat(batch, torch, [w.meta["Y"] for w in probs])
+    alpha = torch.empty_like(y)
+    st, its, rr = batch.cg_solve([w.lam for w in probs], y, alpha, tol, 3000)
+    assert st == B.OK
+    torch.cuda.synchronize()
+    for p, (w, plan) in enumerate(zip(probs, plans)):
+        ab = batch.block(alpha, p).cpu().numpy()
+        for r in range(NRHS):
+            yr = w.meta["Y"][r]
+            # the single-problem solver on the same FP32 operator
+            a1 = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+            _, it1, _ = B.krr_cg_solve(plan, w.lam, torch.from_numpy(yr).cuda(), a1, tol, 3000)
+            assert abs(int(its[p, r]) - int(it1[0])) <= max(6, int(it1[0]) // 20), (p, r, its[p, r], it1)
+            assert rel(ab[r], a1.cpu().numpy()) <= 1e-3, (p, r)
+            # reported residual: recomputed with the FP32 operator
+            assert rr[p, r] <= 3 * tol, (p, r, rr[p, r])
+            # residual under the oracle's FP64 operator
+            Ka = oracle.fastsum(None, w.X, w.windows, w.eta, w.ell, w.n, w.m, ab[r], sigma=w.sigma,
+                                epsB=w.epsB, p=w.p)
+            res = np.linalg.norm(yr - Ka - w.lam * ab[r]) / np.linalg.norm(yr)
+            assert res <= rr[p, r] + 1e-5 * np.linalg.norm(Ka) / np.linalg.norm(yr) + 1e-12, (p, r, res)
+
+
+def test_batch_rejects_mismatched_plans(B, torch):
+    w1 = W.random_problem(500, 3, [(0, 1, 2)], 0.2, 16, 6, seed=1)
+    w2 = W.random_problem(500, 3, [(0, 1, 2)], 0.2, 16, 4, seed=2)
+    p1 = B.anova_fastsum_plan(torch.from_numpy(w1.X).cuda(), w1.windows, w1.ell, n=16, m=6, precision=B.FP32)
+    p2 = B.anova_fastsum_plan(torch.from_numpy(w2.X).cuda(), w2.windows, w2.ell, n=16, m=4, precision=B.FP32)
+    p3 = B.anova_fastsum_plan(torch.from_numpy(w1.X).cuda(), w1.windows, w1.ell, n=16, m=6, precision=B.FP64)
+    with pytest.raises(B.AnovaError):
+        B.Batch([p1, p2], 2)        # different cut-offs
+    with pytest.raises(B.AnovaError):
+        B.Batch([p1, p3], 2)        # no FP32 kernels in the second plan
