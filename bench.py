@@ -513,10 +513,13 @@ def run_serve(args):
 def run_batch(args):
     """Batching form: 64 problems (N log-uniform in [2^10, 2^17], d 6..15, own
     windows of 1-3 features, ell in [0.05, 0.5], lambda in [1e-4, 1e-1]) with
-    16 right-hand sides each, solved together by krr_batch_cg_solve (FP32
-    operator, FP64 CG, graph replay), against the same solves one system at a
-    time through krr_cg_solve on the same FP32 plans (timed on one right-hand
-    side per problem and scaled by the number of right-hand sides)."""
+    16 right-hand sides each.  Timed: (a) krr_batch_cg_solve (FP32 operator,
+    FP64 CG vectors, graph replay) to a recursive residual of tol; (b)
+    krr_batch_cg_solve_refined to an FP64 residual of tol; against the same
+    systems one at a time through krr_cg_solve: FP32 plans for (a), and the
+    plain FP64 path (FP64 plans) for (b), the single-system times taken on one
+    right-hand side of the first `--batch-sample` problems and scaled to all
+    systems by their share of the batch's node-window work."""
     import time
 
     import numpy as np
@@ -529,8 +532,9 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     probs = W.batch_form(args.batch_problems, seed=3, nrhs=args.batch_rhs)
     t0 = time.perf_counter()
-    plans = [B.anova_fastsum_plan(torch.from_numpy(w.X).to(dev), w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB,
-                                  precision=B.FP32) for w in probs]
+    Xs = [torch.from_numpy(w.X).to(dev) for w in probs]
+    plans = [B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, precision=B.MIXED)
+             for X, w in zip(Xs, probs)]
     batch = B.Batch(plans, args.batch_rhs)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
@@ -540,44 +544,58 @@ def run_batch(args):
     alpha = torch.empty_like(y)
     lams = [w.lam for w in probs]
     tol, maxit = args.batch_tol, args.batch_maxit
-    batch.cg_solve(lams, y, alpha, tol, maxit)          # warm-up (captures the graph)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    st, its, rr = batch.cg_solve(lams, y, alpha, tol, maxit)
-    e1.record()
-    e1.synchronize()
-    t_batch = e0.elapsed_time(e1) / 1e3
-    # one right-hand side per problem through the single-system solver
-    t_single = 0.0
-    its1 = []
-    for p, (w, plan) in enumerate(zip(probs, plans)):
-        y1 = torch.from_numpy(w.meta["Y"][0]).to(dev)
-        a1 = torch.zeros_like(y1)
-        B.krr_cg_solve(plan, w.lam, y1, a1, tol, maxit)   # warm
+
+    def timed(fn):
+        fn()                                           # warm-up (captures the graph)
         torch.cuda.synchronize()
-        s0 = time.perf_counter()
-        _, it1, _ = B.krr_cg_solve(plan, w.lam, y1, a1, tol, maxit)
-        torch.cuda.synchronize()
-        t_single += time.perf_counter() - s0
-        its1.append(int(it1[0]))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    (st32, its32, rr32), t32 = timed(lambda: batch.cg_solve(lams, y, alpha, tol, maxit))
+    (st64, its64, rr64), t64 = timed(lambda: batch.cg_solve(lams, y, alpha, tol, maxit, refined=True))
     ns = len(probs) * args.batch_rhs
-    work = sum(w.N * len(w.windows) for w in probs)
+    work = np.array([w.N * len(w.windows) for w in probs], dtype=float)
+    K = min(args.batch_sample, len(probs))
+    share = work[:K].sum() / work.sum()
+    single = {}
+    for name, prec in (("fp32", B.FP32), ("fp64", B.FP64)):
+        tt, it_s, rel_s = 0.0, [], []
+        for p in range(K):
+            w = probs[p]
+            pl = B.anova_fastsum_plan(Xs[p], w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, precision=prec)
+            y1 = torch.from_numpy(w.meta["Y"][0]).to(dev)
+            a1 = torch.zeros_like(y1)
+            B.krr_cg_solve(pl, w.lam, y1, a1, tol, maxit)    # warm
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            _, it1, r1 = B.krr_cg_solve(pl, w.lam, y1, a1, tol, maxit)
+            torch.cuda.synchronize()
+            tt += time.perf_counter() - s0
+            it_s.append(int(it1[0]))
+            rel_s.append(float(r1[0]))
+            pl.close()
+        single[name] = {"sample_s": round(tt, 4), "est_all_systems_s": round(tt * args.batch_rhs / share, 3),
+                        "iters": it_s, "relres_max": max(rel_s)}
     print(json.dumps({
         "batch": True,
         "workload": f"{len(probs)} problems, N log-uniform 2^10..2^17 (total {sum(w.N for w in probs)}), "
-                    f"{args.batch_rhs} right-hand sides each, d 6..15, 1-5 windows of 1-3 features",
-        "systems": ns, "status": int(st), "tol": tol, "setup_s": round(t_setup, 3),
-        "batch_solve_s": round(t_batch, 4), "systems_per_s": ns / t_batch,
-        "iters_median": float(np.median(its)), "iters_max": int(its.max()),
-        "relres_max": float(rr.max()), "relres_median": float(np.median(rr)),
-        "converged": int((rr <= 10 * tol).sum()),
-        "single_solves_one_rhs_s": round(t_single, 4),
-        "single_est_all_rhs_s": round(t_single * args.batch_rhs, 3),
-        "speedup_vs_single": t_single * args.batch_rhs / t_batch,
-        "node_window_iters_per_s": float(sum(w.N * len(w.windows) * int(its[p].sum())
-                                             for p, w in enumerate(probs)) / t_batch),
-        "work_node_windows": work,
+                    f"{args.batch_rhs} right-hand sides each, d 6..15, 1-5 windows of 1-3 features, "
+                    f"lambda 1e-4..1e-1",
+        "systems": ns, "tol": tol, "setup_s": round(t_setup, 3),
+        "fp32_operator": {"status": int(st32), "solve_s": round(t32, 4), "systems_per_s": ns / t32,
+                          "iters_median": float(np.median(its32)), "iters_max": int(its32.max()),
+                          "relres_fp32_median": float(np.median(rr32)), "relres_fp32_max": float(rr32.max()),
+                          "speedup_vs_single_fp32": single["fp32"]["est_all_systems_s"] / t32},
+        "fp64_refined": {"status": int(st64), "solve_s": round(t64, 4), "systems_per_s": ns / t64,
+                         "iters_median": float(np.median(its64)), "relres_fp64_max": float(rr64.max()),
+                         "converged": int((rr64 <= tol).sum()),
+                         "speedup_vs_single_fp64": single["fp64"]["est_all_systems_s"] / t64},
+        "single_sample_problems": K, "single_sample_work_share": round(float(share), 4),
+        "single": single,
     }), flush=True)
     batch.close()
     for pl in plans:
@@ -611,6 +629,7 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=16)
     ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--batch-maxit", type=int, default=3000)
+    ap.add_argument("--batch-sample", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

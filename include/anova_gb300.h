@@ -270,6 +270,18 @@ anova_status anova_batch_matvec(anova_batch* batch, const double* x, double* y, 
 anova_status krr_batch_cg_solve(anova_batch* batch, const double* lambda, const double* y, double* alpha,
                                 double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
 
+/*
+ * As krr_batch_cg_solve, to an FP64 residual: every plan must hold FP64 too
+ * (ANOVA_MIXED).  Passes: r = y - (K64 + lambda I) alpha with each problem's
+ * FP64 operator (anova_matvec), systems with ||r|| <= tol ||y|| drop out, the
+ * batched FP32 CG solves the rest to 1e-4 relative (less when less is left),
+ * alpha += correction.  relres is the FP64 residual; iters sums the inner
+ * iterations; maxit bounds them per system.  Synchronous on `stream`;
+ * allocates its work vectors stream-ordered.  Errors as krr_batch_cg_solve.
+ */
+anova_status krr_batch_cg_solve_refined(anova_batch* batch, const double* lambda, const double* y, double* alpha,
+                                        double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
+
 /* Free the batch (not its plans).  NULL is ignored. */
 void anova_batch_destroy(anova_batch* batch);
 

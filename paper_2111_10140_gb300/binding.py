@@ -40,6 +40,7 @@ _SIGNATURES = {
     "anova_batch_layout": (_i32, [_vp, _pi64]),
     "anova_batch_matvec": (_i32, [_vp, _vp, _vp, _vp]),
     "krr_batch_cg_solve": (_i32, [_vp, _pf64, _vp, _vp, _f64, _i32, _pi32, _pf64, _vp]),
+    "krr_batch_cg_solve_refined": (_i32, [_vp, _pf64, _vp, _vp, _f64, _i32, _pi32, _pf64, _vp]),
     "anova_batch_destroy": (None, [_vp]),
     "krr_model_create": (_i32, [_vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "krr_model_predict": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
@@ -298,8 +299,9 @@ class Batch:
         _check(lib().anova_batch_matvec(self.handle, _ptr(x), _ptr(y), _stream(stream)), "anova_batch_matvec")
         return y
 
-    def cg_solve(self, lambdas, y, alpha, tol, maxit, stream=None):
-        """Returns (status, iterations, relres), both arrays of problems x nrhs."""
+    def cg_solve(self, lambdas, y, alpha, tol, maxit, stream=None, refined=False):
+        """Returns (status, iterations, relres), both arrays of problems x nrhs.
+        refined=True: krr_batch_cg_solve_refined (FP64 residual)."""
         import torch
         _require_cuda(y, "y", torch.float64)
         _require_cuda(alpha, "alpha", torch.float64)
@@ -307,9 +309,9 @@ class Batch:
         ns = len(self.plans) * self.nrhs
         its = np.zeros(ns, dtype=np.int32)
         rr = np.zeros(ns, dtype=np.float64)
-        st = lib().krr_batch_cg_solve(self.handle, lam.ctypes.data_as(_pf64), _ptr(y), _ptr(alpha), float(tol),
-                                      int(maxit), its.ctypes.data_as(_pi32), rr.ctypes.data_as(_pf64),
-                                      _stream(stream))
+        fn = lib().krr_batch_cg_solve_refined if refined else lib().krr_batch_cg_solve
+        st = fn(self.handle, lam.ctypes.data_as(_pf64), _ptr(y), _ptr(alpha), float(tol), int(maxit),
+                its.ctypes.data_as(_pi32), rr.ctypes.data_as(_pf64), _stream(stream))
         _check(st, "krr_batch_cg_solve", allow=(OK, ENOCONV))
         return st, its.reshape(len(self.plans), self.nrhs), rr.reshape(len(self.plans), self.nrhs)
 

@@ -273,6 +273,57 @@ __global__ void k_b_totals(const BSysInfo* __restrict__ sys, const double* __res
     if (s < NS) out[s] = chunk_total(part, s, nchunk, sys[s].len);
 }
 
+// r = y - q - lambda x; partial r.r (q = K x in FP64, from the problems' plans)
+__global__ void __launch_bounds__(kBThreads)
+k_b_refine(const BSysInfo* __restrict__ sys, const double* __restrict__ lam, const double* __restrict__ y,
+           const double* __restrict__ q, const double* __restrict__ x, double* __restrict__ r,
+           double* __restrict__ part, int nchunk) {
+    __shared__ double sh[32];
+    const BSysInfo s = sys[blockIdx.y];
+    const double lambda = lam[blockIdx.y];
+    const int64_t lo = (int64_t)blockIdx.x * kBChunk;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) {
+        const int64_t e = s.off + i;
+        const double v = y[e] - q[e] - lambda * x[e];
+        r[e] = v;
+        acc += v * v;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.y * nchunk + blockIdx.x] = acc;
+}
+
+// partial v.v per system
+__global__ void __launch_bounds__(kBThreads)
+k_b_norm(const BSysInfo* __restrict__ sys, const double* __restrict__ v, double* __restrict__ part, int nchunk) {
+    __shared__ double sh[32];
+    const BSysInfo s = sys[blockIdx.y];
+    const int64_t lo = (int64_t)blockIdx.x * kBChunk;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) {
+        const double t = v[s.off + i];
+        acc += t * t;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.y * nchunk + blockIdx.x] = acc;
+}
+
+// zero the right-hand side of systems already converged; x += dx for the others
+__global__ void __launch_bounds__(kBThreads)
+k_b_mask(const BSysInfo* __restrict__ sys, const int* __restrict__ done, double* __restrict__ r) {
+    if (!done[blockIdx.y]) return;
+    const BSysInfo s = sys[blockIdx.y];
+    const int64_t lo = (int64_t)blockIdx.x * kBChunk;
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) r[s.off + i] = 0.0;
+}
+
+__global__ void __launch_bounds__(kBThreads)
+k_b_axpy(const BSysInfo* __restrict__ sys, const double* __restrict__ dx, double* __restrict__ x) {
+    const BSysInfo s = sys[blockIdx.y];
+    const int64_t lo = (int64_t)blockIdx.x * kBChunk;
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) x[s.off + i] += dx[s.off + i];
+}
+
 // tmp <- K_l x for every instance (FP32 operator on the FP64 flat vector x)
 static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t st) {
     if (b->ninst == 0) return ANOVA_OK;
@@ -673,6 +724,116 @@ anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const doub
             return ANOVA_ERANGE;
         }
     }
+    return all ? ANOVA_OK : ANOVA_ENOCONV;
+}
+
+anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, const double* y, double* alpha,
+                                        double tol, int32_t maxit, int32_t* iters, double* relres, void* stream) {
+    if (!b || !lambda || !y || !alpha || y == alpha || !(tol > 0.0) || maxit < 1) {
+        set_error("krr_batch_cg_solve_refined: bad batch, lambda, vectors, tol or maxit");
+        return ANOVA_EINVAL;
+    }
+    for (const anova_plan* pl : b->plans)
+        if (!(pl->precision & ANOVA_FP64)) {
+            set_error("krr_batch_cg_solve_refined: every plan must hold FP64 as well (ANOVA_MIXED)");
+            return ANOVA_EINVAL;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    const dim3 gv(b->nchunk, b->NS);
+    const int gs = (b->NS + kBThreads - 1) / kBThreads;
+    double *q = nullptr, *r = nullptr, *dx = nullptr, *tot = nullptr;
+    int* done = nullptr;
+    ANOVA_CUDA_TRY(cudaMallocAsync(&q, b->S * sizeof(double), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&r, b->S * sizeof(double), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&dx, b->S * sizeof(double), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&tot, b->NS * sizeof(double), st));
+    ANOVA_CUDA_TRY(cudaMallocAsync(&done, b->NS * sizeof(int), st));
+    std::vector<double> lam(b->NS), yy(b->NS), rr(b->NS);
+    std::vector<int> conv(b->NS, 0), total_it(b->NS, 0), it(b->NS);
+    for (int s = 0; s < b->NS; s++) lam[s] = lambda[s / b->nrhs];
+    anova_status s = ANOVA_OK;
+    auto totals = [&](std::vector<double>& out) -> anova_status {
+        k_b_totals<<<gs, kBThreads, 0, st>>>(b->sys, b->part, b->nchunk, b->NS, tot);
+        ANOVA_CHECK_LAUNCH();
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(out.data(), tot, b->NS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        return ANOVA_OK;
+    };
+    if (cudaMemcpyAsync(b->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(alpha, 0, b->S * sizeof(double), st) != cudaSuccess) {
+        set_error("krr_batch_cg_solve_refined: setup copy failed");
+        s = ANOVA_ECUDA;
+    }
+    if (s == ANOVA_OK) {
+        k_b_norm<<<gv, kBThreads, 0, st>>>(b->sys, y, b->part, b->nchunk);
+        s = totals(yy);
+    }
+    // outer passes: FP64 residual of the problems' own plans, FP32 batched CG
+    // on it to 1e-4 relative (tighter as the target nears), alpha += correction
+    const int kMaxPass = 40;
+    bool all = false;
+    for (int pass = 0; s == ANOVA_OK && pass < kMaxPass; pass++) {
+        if (pass == 0) {
+            if (cudaMemcpyAsync(r, y, b->S * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                s = ANOVA_ECUDA;
+                break;
+            }
+            rr = yy;
+        } else {
+            for (int p = 0; p < b->nprob && s == ANOVA_OK; p++)
+                s = anova_matvec(b->plans[p], ANOVA_FP64, alpha + b->off[p], q + b->off[p], b->nrhs, b->plans[p]->N,
+                                 stream);
+            if (s != ANOVA_OK) break;
+            k_b_refine<<<gv, kBThreads, 0, st>>>(b->sys, b->lam, y, q, alpha, r, b->part, b->nchunk);
+            s = totals(rr);
+            if (s != ANOVA_OK) break;
+        }
+        all = true;
+        double worst = 0.0;
+        for (int k = 0; k < b->NS; k++) {
+            const double rel = yy[k] > 0.0 ? std::sqrt(rr[k] / yy[k]) : 0.0;
+            if (!std::isfinite(rel)) {
+                set_error("krr_batch_cg_solve_refined: non-finite residual in system " + std::to_string(k));
+                s = ANOVA_ERANGE;
+                break;
+            }
+            conv[k] = rel <= tol || total_it[k] >= maxit;
+            if (relres) relres[k] = rel;
+            if (rel > tol) {
+                all = false;
+                worst = std::max(worst, rel);
+            }
+        }
+        if (s != ANOVA_OK) break;
+        bool any_open = false;
+        for (int k = 0; k < b->NS; k++) any_open = any_open || !conv[k];
+        if (!any_open) break;
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(done, conv.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_b_mask<<<gv, kBThreads, 0, st>>>(b->sys, done, r);
+        ANOVA_CHECK_LAUNCH();
+        // relative to this pass's residual: 1e-4 (about what the FP32 operator
+        // resolves), or only what is left to the target when that is less
+        const double inner = std::min(0.5, std::max(1e-4, 0.5 * tol / std::max(worst, 1e-300)));
+        s = krr_batch_cg_solve(b, lambda, r, dx, inner, maxit, it.data(), nullptr, stream);
+        if (s == ANOVA_ENOCONV) s = ANOVA_OK;
+        if (s != ANOVA_OK) break;
+        for (int k = 0; k < b->NS; k++) total_it[k] += it[k];
+        k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, dx, alpha);
+        ANOVA_CHECK_LAUNCH();
+    }
+    if (iters)
+        for (int k = 0; k < b->NS; k++) iters[k] = total_it[k];
+    cudaFreeAsync(q, st);
+    cudaFreeAsync(r, st);
+    cudaFreeAsync(dx, st);
+    cudaFreeAsync(tot, st);
+    cudaFreeAsync(done, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == ANOVA_OK && e != cudaSuccess) {
+        set_error(std::string("krr_batch_cg_solve_refined: ") + cudaGetErrorString(e));
+        s = ANOVA_ECUDA;
+    }
+    if (s != ANOVA_OK) return s;
     return all ? ANOVA_OK : ANOVA_ENOCONV;
 }
 
