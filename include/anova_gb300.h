@@ -262,8 +262,10 @@ anova_status anova_batch_matvec(anova_batch* batch, const double* x, double* y, 
  * residual reaches tol ||y|| or after maxit iterations.  lambda: host, nprob
  * entries >= 0.  y, alpha: device, flat layout.  iters, relres: host, nprob *
  * nrhs entries (system p * nrhs + r) or NULL; relres is recomputed with the
- * batch's FP32 operator.  Returns ENOCONV if a system stopped at maxit,
- * ERANGE on a non-finite residual.  Synchronous on `stream`; the iteration is
+ * batch's FP32 operator (NaN for a system whose CG broke down: with the FP32
+ * operator K + lambda I may lose definiteness when lambda is below its
+ * rounding).  Systems that stop iterate no more (their kernels exit at once).
+ * Returns ENOCONV if a system stopped short of tol.  Synchronous on `stream`; the iteration is
  * captured as a CUDA graph on the second block of iterations (same caveat as
  * anova_matvec on device-wide synchronisation from other threads).
  */
@@ -276,7 +278,8 @@ anova_status krr_batch_cg_solve(anova_batch* batch, const double* lambda, const 
  * FP64 operator (anova_matvec), systems with ||r|| <= tol ||y|| drop out, the
  * batched FP32 CG solves the rest to 1e-4 relative (less when less is left),
  * alpha += correction.  relres is the FP64 residual; iters sums the inner
- * iterations; maxit bounds them per system.  Synchronous on `stream`;
+ * iterations; maxit bounds them per system; a system whose correction breaks
+ * down keeps its last iterate.  Synchronous on `stream`;
  * allocates its work vectors stream-ordered.  Errors as krr_batch_cg_solve.
  */
 anova_status krr_batch_cg_solve_refined(anova_batch* batch, const double* lambda, const double* y, double* alpha,

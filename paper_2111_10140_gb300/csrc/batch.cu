@@ -43,6 +43,7 @@ struct SortInst {
     const int32_t* perm;
     float* asort;
     int64_t N, src;                    // nodes; flat offset of the system's coefficients
+    const int* live;                   // the system still iterates
 };
 
 }  // namespace anova
@@ -95,6 +96,7 @@ __global__ void k_b_tag(const int4* __restrict__ src, int n, int slot, int4* __r
 // asort of every instance: the system's coefficients in the window's sorted order, FP32
 __global__ void k_b_sort(const SortInst* __restrict__ inst, const double* __restrict__ x) {
     const SortInst s = inst[blockIdx.y];
+    if (!*s.live) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.N; i += (int64_t)gridDim.x * blockDim.x)
         s.asort[i] = (float)x[s.src + s.perm[i]];
 }
@@ -240,6 +242,11 @@ k_b_p(const BSysInfo* __restrict__ sys, const BSys* __restrict__ sc, const doubl
     }
 }
 
+__global__ void k_b_live_all(BSys* __restrict__ sc, int NS) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < NS) sc[s].active = 1;
+}
+
 __global__ void k_b_count(const BSys* __restrict__ sc, int NS, int* __restrict__ count) {
     __shared__ int c;
     if (threadIdx.x == 0) c = 0;
@@ -318,7 +325,9 @@ k_b_mask(const BSysInfo* __restrict__ sys, const int* __restrict__ done, double*
 }
 
 __global__ void __launch_bounds__(kBThreads)
-k_b_axpy(const BSysInfo* __restrict__ sys, const double* __restrict__ dx, double* __restrict__ x) {
+k_b_axpy(const BSysInfo* __restrict__ sys, const int* __restrict__ apply, const double* __restrict__ dx,
+         double* __restrict__ x) {
+    if (!apply[blockIdx.y]) return;
     const BSysInfo s = sys[blockIdx.y];
     const int64_t lo = (int64_t)blockIdx.x * kBChunk;
     for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) x[s.off + i] += dx[s.off + i];
@@ -502,7 +511,9 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
         d.Tb = w.T;
         d.nb = w.nb;
         d.pad = 0;
-        sorts[k] = {w.X.perm, b->asort + I.as, pl->N, b->off[I.p] + (int64_t)I.r * pl->N};
+        const int* live = &b->scal[I.p * nrhs + I.r].active;
+        d.live = live;
+        sorts[k] = {w.X.perm, b->asort + I.as, pl->N, b->off[I.p] + (int64_t)I.r * pl->N, live};
         b->max_inst_N = std::max(b->max_inst_N, pl->N);
         if (w.dA == 3) {
             Fft3Win f;
@@ -517,6 +528,7 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
             }
             f.n = w.n;
             f.nos = w.nos;
+            f.live = live;
             f3.push_back(f);
             b->fft3_shape.add(w);
         } else {
@@ -531,6 +543,7 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
                 f.lo[t] = w.box_lo[t];
                 f.B[t] = w.box_ext[t];
             }
+            f.live = live;
             f12.push_back(f);
             b->smem12 = std::max(b->smem12, fft12_window_smem(w, sizeof(float)));
         }
@@ -626,6 +639,7 @@ anova_status anova_batch_matvec(anova_batch* b, const double* x, double* y, void
         return ANOVA_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    k_b_live_all<<<(b->NS + kBThreads - 1) / kBThreads, kBThreads, 0, st>>>(b->scal, b->NS);
     ANOVA_TRY(batch_operator(b, x, st));
     k_b_q<<<dim3(b->nchunk, b->NS), kBThreads, 0, st>>>(b->sys, b->scal, b->eta, b->zero, b->tmp, x, y, b->part,
                                                         b->nchunk, 1);
@@ -703,27 +717,25 @@ anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const doub
     }
     ANOVA_CUDA_TRY(cudaMemcpyAsync(alpha, x, b->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // recomputed residual ||y - (K + lambda I) alpha|| / ||y|| with the batch's operator
+    std::vector<BSys> sc(b->NS);
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(sc.data(), b->scal, b->NS * sizeof(BSys), cudaMemcpyDeviceToHost, st));
+    k_b_live_all<<<gs, kBThreads, 0, st>>>(b->scal, b->NS);
     ANOVA_TRY(batch_operator(b, alpha, st));
     k_b_q<<<gv, kBThreads, 0, st>>>(b->sys, b->scal, b->eta, b->lam, b->tmp, alpha, q, b->part, b->nchunk, 1);
     k_b_resid<<<gv, kBThreads, 0, st>>>(b->sys, y, q, b->part, b->nchunk);
     k_b_totals<<<gs, kBThreads, 0, st>>>(b->sys, b->part, b->nchunk, b->NS, r);
     ANOVA_CHECK_LAUNCH();
     std::vector<double> rr(b->NS);
-    std::vector<BSys> sc(b->NS);
     ANOVA_CUDA_TRY(cudaMemcpyAsync(rr.data(), r, b->NS * sizeof(double), cudaMemcpyDeviceToHost, st));
-    ANOVA_CUDA_TRY(cudaMemcpyAsync(sc.data(), b->scal, b->NS * sizeof(BSys), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     bool all = true;
     for (int s = 0; s < b->NS; s++) {
         const double rel = sc[s].yy > 0.0 ? std::sqrt(rr[s] / sc[s].yy) : 0.0;
         if (iters) iters[s] = sc[s].iters;
-        if (relres) relres[s] = rel;
-        if (!(sc[s].rr <= tol2 * sc[s].yy)) all = false;
-        if (!std::isfinite(rel)) {
-            set_error("krr_batch_cg_solve: non-finite residual in system " + std::to_string(s));
-            return ANOVA_ERANGE;
-        }
+        if (relres) relres[s] = rel;     // NaN / inf for a system that broke down
+        if (!(sc[s].rr <= tol2 * sc[s].yy) || !std::isfinite(rel)) all = false;
     }
+    if (!all) set_error("krr_batch_cg_solve: some systems stopped before reaching tol (see relres)");
     return all ? ANOVA_OK : ANOVA_ENOCONV;
 }
 
@@ -749,7 +761,8 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
     ANOVA_CUDA_TRY(cudaMallocAsync(&tot, b->NS * sizeof(double), st));
     ANOVA_CUDA_TRY(cudaMallocAsync(&done, b->NS * sizeof(int), st));
     std::vector<double> lam(b->NS), yy(b->NS), rr(b->NS);
-    std::vector<int> conv(b->NS, 0), total_it(b->NS, 0), it(b->NS);
+    std::vector<int> conv(b->NS, 0), total_it(b->NS, 0), it(b->NS), apply(b->NS), failed(b->NS, 0);
+    std::vector<double> inner_rel(b->NS);
     for (int s = 0; s < b->NS; s++) lam[s] = lambda[s / b->nrhs];
     anova_status s = ANOVA_OK;
     auto totals = [&](std::vector<double>& out) -> anova_status {
@@ -797,7 +810,7 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
                 s = ANOVA_ERANGE;
                 break;
             }
-            conv[k] = rel <= tol || total_it[k] >= maxit;
+            conv[k] = rel <= tol || total_it[k] >= maxit || failed[k];
             if (relres) relres[k] = rel;
             if (rel > tol) {
                 all = false;
@@ -814,11 +827,18 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
         // relative to this pass's residual: 1e-4 (about what the FP32 operator
         // resolves), or only what is left to the target when that is less
         const double inner = std::min(0.5, std::max(1e-4, 0.5 * tol / std::max(worst, 1e-300)));
-        s = krr_batch_cg_solve(b, lambda, r, dx, inner, maxit, it.data(), nullptr, stream);
+        s = krr_batch_cg_solve(b, lambda, r, dx, inner, maxit, it.data(), inner_rel.data(), stream);
         if (s == ANOVA_ENOCONV) s = ANOVA_OK;
         if (s != ANOVA_OK) break;
-        for (int k = 0; k < b->NS; k++) total_it[k] += it[k];
-        k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, dx, alpha);
+        // a correction that broke down (non-finite) is dropped and its system
+        // stops refining: its FP32 operator is not definite at this lambda
+        for (int k = 0; k < b->NS; k++) {
+            total_it[k] += it[k];
+            apply[k] = !conv[k] && std::isfinite(inner_rel[k]);
+            if (!conv[k] && !apply[k]) failed[k] = 1;
+        }
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(done, apply.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, done, dx, alpha);
         ANOVA_CHECK_LAUNCH();
     }
     if (iters)

@@ -90,6 +90,7 @@ struct Fft12Win {
     const void* D;             // n^dA multiplier
     int dA, n, nos;
     int lo[2], B[2];           // box start and extent per axis
+    const int* live = nullptr;   // batches: the instance's system still iterates (null: always)
 };
 constexpr size_t kFft12MaxSmem = 227 * 1024;
 
@@ -102,6 +103,7 @@ struct Fft3Win {
     const void* D;             // n^3 multiplier
     int lo[3], B[3];           // box start and extent per axis
     int n, nos;
+    const int* live = nullptr;   // batches: the instance's system still iterates (null: always)
 };
 
 // Per-window arguments of the batched dense 3-D kernels (one launch, all windows).
@@ -115,6 +117,7 @@ struct DenseWin {
     void* out;                 // gather output (this window's slice of plan->tmp)
     int64_t N;
     int nos, Tb, nb, pad;
+    const int* live = nullptr;   // batches: the instance's system still iterates (null: always)
 };
 
 struct StageClock {

@@ -69,6 +69,7 @@ k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
         for (int i = threadIdx.x; i < 2 * m * kPsiStride; i += blockDim.x) sP[i] = poly[i];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs ? descs[sp.w] : one;
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const int32_t* __restrict__ perm = W.perm;
     const int32_t* __restrict__ cell = W.cell;
     const T* __restrict__ frac = static_cast<const T*>(W.frac);
@@ -146,6 +147,7 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
     __shared__ __align__(16) T wzs[kSpreadChunk][kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs ? descs[sp.w] : one;
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const int32_t* __restrict__ perm = W.perm;
     const int32_t* __restrict__ cell = W.cell;
     const T* __restrict__ frac = static_cast<const T*>(W.frac);
@@ -242,6 +244,7 @@ k_gather3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     __shared__ __align__(16) float reg[R * R * kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const float* __restrict__ h = static_cast<const float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
@@ -352,6 +355,7 @@ k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
     __shared__ __align__(16) float wzs[kSpreadChunk][kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     float* __restrict__ grid = static_cast<float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
@@ -477,6 +481,7 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
     __shared__ __align__(16) float sz[kSpreadChunk][kTcPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     float* __restrict__ grid = static_cast<float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
@@ -583,6 +588,7 @@ k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
     __shared__ __align__(16) uint32_t rl[R * R * kTcRowPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const float* __restrict__ h = static_cast<const float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
@@ -692,6 +698,7 @@ __global__ void __launch_bounds__(32) k_spread2_f32(const int4* __restrict__ sub
     __shared__ __align__(16) float sy[kSpreadChunk][kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     float* __restrict__ grid = static_cast<float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int by = sp.x % nb, bx = sp.x / nb;
@@ -744,6 +751,7 @@ __global__ void __launch_bounds__(128) k_gather2_f32(const int4* __restrict__ su
     __shared__ __align__(16) float reg[R * kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const float* __restrict__ h = static_cast<const float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb, nb = W.nb;
     const int by = sp.x % nb, bx = sp.x / nb;
@@ -789,6 +797,7 @@ __global__ void __launch_bounds__(32) k_spread1_f32(const int4* __restrict__ sub
     __shared__ __align__(16) float sx[kSpreadChunk][kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     float* __restrict__ grid = static_cast<float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb;
     const int bx = sp.x;
@@ -820,6 +829,7 @@ __global__ void __launch_bounds__(128) k_gather1_f32(const int4* __restrict__ su
     __shared__ __align__(16) float reg[kPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const float* __restrict__ h = static_cast<const float*>(W.grid);
     const int nos = W.nos, Tb = W.Tb;
     const int bx = sp.x;

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kFft12Threads)
 k_fft12_box(const Fft12Win* __restrict__ descs) {
     using C = typename Cplx12<T>::type;
     const Fft12Win d = descs[blockIdx.x];
+    if (d.live && !*d.live) return;   // a batch system that has stopped
     const int n = d.n, nos = d.nos, half = nos / 2;
     const bool two = d.dA == 2;
     const int B0 = two ? d.B[0] : 1, B1 = two ? d.B[1] : d.B[0];

@@ -52,6 +52,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fft3_f1(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const T* __restrict__ g = static_cast<const T*>(W.grid);
     C* __restrict__ A = static_cast<C*>(W.buf1);
     const C* __restrict__ tw = static_cast<const C*>(W.tw);
@@ -87,6 +88,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const C* __restrict__ A = static_cast<const C*>(W.buf1);
     C* __restrict__ Bo = static_cast<C*>(W.buf2);
     const C* __restrict__ tw = static_cast<const C*>(W.tw);
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Wi
     extern __shared__ __align__(16) unsigned char mid_raw[];
     C (*sH)[kMidLanes] = reinterpret_cast<C (*)[kMidLanes]>(mid_raw);
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const int n = W.n, nos = W.nos, Bx = W.B[0];
     const int lines_per_ky = (n + kMidLanes - 1) / kMidLanes;
     if ((int)blockIdx.x >= n * lines_per_ky) return;
@@ -197,6 +200,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fft3_i2(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const C* __restrict__ Ci = static_cast<const C*>(W.buf1);
     C* __restrict__ E = static_cast<C*>(W.buf2);
     const C* __restrict__ tw = static_cast<const C*>(W.tw);
@@ -227,6 +231,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fft3_i3(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const C* __restrict__ E = static_cast<const C*>(W.buf2);
     T* __restrict__ g = static_cast<T*>(W.grid);
     const C* __restrict__ tw = static_cast<const C*>(W.tw);
@@ -267,6 +272,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
     using C = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char slab_raw[];
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
     const int x = blockIdx.x;
     if (x >= W.B[0]) return;
@@ -325,6 +331,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* _
     using C = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char slab_raw[];
     const Fft3Win W = wins[blockIdx.y];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
     const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
     const int x = blockIdx.x;
     if (x >= W.B[0]) return;
