@@ -326,11 +326,12 @@ k_b_mask(const BSysInfo* __restrict__ sys, const int* __restrict__ done, double*
 
 __global__ void __launch_bounds__(kBThreads)
 k_b_axpy(const BSysInfo* __restrict__ sys, const int* __restrict__ apply, const double* __restrict__ dx,
-         double* __restrict__ x) {
+         double* __restrict__ x, double sign) {
     if (!apply[blockIdx.y]) return;
     const BSysInfo s = sys[blockIdx.y];
     const int64_t lo = (int64_t)blockIdx.x * kBChunk;
-    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) x[s.off + i] += dx[s.off + i];
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x)
+        x[s.off + i] += sign * dx[s.off + i];
 }
 
 // tmp <- K_l x for every instance (FP32 operator on the FP64 flat vector x)
@@ -761,7 +762,9 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
     ANOVA_CUDA_TRY(cudaMallocAsync(&tot, b->NS * sizeof(double), st));
     ANOVA_CUDA_TRY(cudaMallocAsync(&done, b->NS * sizeof(int), st));
     std::vector<double> lam(b->NS), yy(b->NS), rr(b->NS);
-    std::vector<int> conv(b->NS, 0), total_it(b->NS, 0), it(b->NS), apply(b->NS), failed(b->NS, 0);
+    std::vector<int> conv(b->NS, 0), total_it(b->NS, 0), it(b->NS), apply(b->NS, 0), failed(b->NS, 0),
+        revert(b->NS, 0);
+    std::vector<double> rr_prev(b->NS);
     std::vector<double> inner_rel(b->NS);
     for (int s = 0; s < b->NS; s++) lam[s] = lambda[s / b->nrhs];
     anova_status s = ANOVA_OK;
@@ -800,7 +803,24 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
             k_b_refine<<<gv, kBThreads, 0, st>>>(b->sys, b->lam, y, q, alpha, r, b->part, b->nchunk);
             s = totals(rr);
             if (s != ANOVA_OK) break;
+            // a correction that left the FP64 residual larger is taken back and
+            // its system stops refining (the FP32 operator does not resolve it)
+            bool any = false;
+            for (int k = 0; k < b->NS; k++) {
+                revert[k] = apply[k] && !(rr[k] <= rr_prev[k]);
+                if (revert[k]) {
+                    rr[k] = rr_prev[k];
+                    failed[k] = 1;
+                    any = true;
+                }
+            }
+            if (any) {
+                ANOVA_CUDA_TRY(cudaMemcpyAsync(done, revert.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
+                k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, done, dx, alpha, -1.0);
+                ANOVA_CHECK_LAUNCH();
+            }
         }
+        rr_prev = rr;
         all = true;
         double worst = 0.0;
         for (int k = 0; k < b->NS; k++) {
@@ -838,7 +858,7 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
             if (!conv[k] && !apply[k]) failed[k] = 1;
         }
         ANOVA_CUDA_TRY(cudaMemcpyAsync(done, apply.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, done, dx, alpha);
+        k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, done, dx, alpha, 1.0);
         ANOVA_CHECK_LAUNCH();
     }
     if (iters)

@@ -163,7 +163,7 @@ def serving_problem(N, seed, M_test=0):
                     meta={"Z": np.ascontiguousarray(Xall[N:])})
 
 
-def batch_problem(N, seed, nrhs=16):
+def batch_problem(N, seed, nrhs=16, lam_range=(1e-4, 1e-1)):
     """One problem of the batching form: d uniform in 6..15 standard normal
     features, windows of 1-3 distinct features covering at most all of them,
     ell log-uniform in [0.05, 0.5], lambda log-uniform in [1e-4, 1e-1], nrhs
@@ -179,7 +179,7 @@ def batch_problem(N, seed, nrhs=16):
         windows.append(tuple(sorted(int(f) for f in feats[:k])))
         feats = feats[k:]
     ell = float(10 ** rng.uniform(np.log10(0.05), np.log10(0.5)))
-    lam = float(10 ** rng.uniform(-4, -1))
+    lam = float(10 ** rng.uniform(np.log10(lam_range[0]), np.log10(lam_range[1])))
     raw = rng.standard_normal((N, d))
     X = _minmax_into_ball(raw, windows)
     n = [(16 if ell >= 0.15 else 32) if len(w) == 3 else (64 if ell < 0.1 else 32) for w in windows]
@@ -189,8 +189,9 @@ def batch_problem(N, seed, nrhs=16):
                     rng.standard_normal(N), Y[0].copy(), lam, 1e-6, epsB=0.25, meta={"Y": Y})
 
 
-def batch_form(count=64, seed=3, nrhs=16):
+def batch_form(count=64, seed=3, nrhs=16, lam_range=(1e-4, 1e-1)):
     """The batching form: `count` problems with N log-uniform in [2^10, 2^17]."""
     rng = np.random.default_rng(seed)
     Ns = np.round(2.0 ** rng.uniform(10, 17, size=count)).astype(int)
-    return [batch_problem(int(N), seed=10_000 * seed + k, nrhs=nrhs) for k, N in enumerate(Ns)]
+    return [batch_problem(int(N), seed=10_000 * seed + k, nrhs=nrhs, lam_range=lam_range)
+            for k, N in enumerate(Ns)]
