@@ -60,8 +60,18 @@ struct anova_batch {
     float* asort = nullptr;
     float* tmp = nullptr;
     anova::DenseWin* desc = nullptr;
-    int4* sub = nullptr;
-    std::vector<std::array<int, 3>> groups;
+    int4* sub = nullptr;                           // launch list: sub-problems of the live systems
+    int4* sub_full = nullptr;                      // every instance's sub-problems, grouped by (dims, R)
+    std::vector<std::array<int, 3>> groups;        // of the launch list
+    // host copies for rebuilding the launch lists over the systems still iterating
+    struct InstHost { int key, sys, inst, f3, f12; int64_t first, count; };
+    std::vector<InstHost> ih;                      // per instance, in sub_full order within a group
+    std::vector<int> keys;                         // group keys in launch order
+    std::vector<anova::Fft3Win> f3_all;
+    std::vector<anova::Fft12Win> f12_all;
+    std::vector<anova::SortInst> sort_all;
+    int4* copy_tab = nullptr;                      // (src, dst, count) per live instance
+    int nsort = 0, live_systems = -1;
     anova::SortInst* sorts = nullptr;
     int64_t max_inst_N = 0;
     anova::Fft3Win* fft3 = nullptr;
@@ -334,11 +344,75 @@ k_b_axpy(const BSysInfo* __restrict__ sys, const int* __restrict__ apply, const 
         x[s.off + i] += sign * dx[s.off + i];
 }
 
+__global__ void k_b_copy_subs(const int4* __restrict__ src, const int4* __restrict__ tab, int4* __restrict__ dst) {
+    const int4 t = tab[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < t.z; i += gridDim.x * blockDim.x) dst[t.y + i] = src[t.x + i];
+}
+
+// Launch lists (sub-problems, FFT descriptors, sort table) over the systems
+// with live[s] != 0 only: a stopped system's blocks are not even scheduled.
+// The kernels' own live checks cover systems that stop between rebuilds.
+static anova_status batch_compact(anova_batch* b, const std::vector<int>& live, cudaStream_t st) {
+    std::vector<int4> tab;
+    b->groups.clear();
+    int at = 0, maxc = 0;
+    size_t k = 0;
+    for (int key : b->keys) {
+        const int first = at;
+        for (; k < b->ih.size() && b->ih[k].key == key; k++) {
+            const auto& I = b->ih[k];
+            if (!live[I.sys] || I.count == 0) continue;
+            tab.push_back(make_int4((int)I.first, at, (int)I.count, 0));
+            at += (int)I.count;
+            maxc = std::max(maxc, (int)I.count);
+        }
+        if (at > first) b->groups.push_back({key, first, at - first});
+    }
+    std::vector<Fft3Win> f3;
+    std::vector<Fft12Win> f12;
+    std::vector<SortInst> so;
+    for (const auto& I : b->ih) {
+        if (!live[I.sys]) continue;
+        if (I.f3 >= 0) f3.push_back(b->f3_all[I.f3]);
+        if (I.f12 >= 0) f12.push_back(b->f12_all[I.f12]);
+        so.push_back(b->sort_all[I.inst]);
+    }
+    if (!tab.empty()) {
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(b->copy_tab, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        const int gx = std::max(1, std::min((maxc + kThreads - 1) / kThreads, 64));
+        k_b_copy_subs<<<dim3(gx, (unsigned)tab.size()), kThreads, 0, st>>>(b->sub_full, b->copy_tab, b->sub);
+        ANOVA_CHECK_LAUNCH();
+    }
+    if (!f3.empty())
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(b->fft3, f3.data(), f3.size() * sizeof(Fft3Win), cudaMemcpyHostToDevice, st));
+    if (!f12.empty())
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(b->fft12, f12.data(), f12.size() * sizeof(Fft12Win), cudaMemcpyHostToDevice, st));
+    if (!so.empty())
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(b->sorts, so.data(), so.size() * sizeof(SortInst), cudaMemcpyHostToDevice, st));
+    // the host vectors are pageable: the copies complete before they return
+    b->fft3_shape.nw = (int)f3.size();
+    b->n12 = (int)f12.size();
+    b->nsort = (int)so.size();
+    int nl = 0;
+    for (int v : live) nl += v != 0;
+    b->live_systems = nl;
+    if (b->graph) {                  // launch sizes changed: capture again
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return ANOVA_OK;
+}
+
+static anova_status batch_compact_all(anova_batch* b, cudaStream_t st) {
+    if (b->live_systems == b->NS) return ANOVA_OK;
+    return batch_compact(b, std::vector<int>(b->NS, 1), st);
+}
+
 // tmp <- K_l x for every instance (FP32 operator on the FP64 flat vector x)
 static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t st) {
-    if (b->ninst == 0) return ANOVA_OK;
+    if (b->nsort == 0) return ANOVA_OK;
     const int gx = (int)std::min<int64_t>((b->max_inst_N + kThreads - 1) / kThreads, 64);
-    k_b_sort<<<dim3(gx, b->ninst), kThreads, 0, st>>>(b->sorts, x);
+    k_b_sort<<<dim3(gx, b->nsort), kThreads, 0, st>>>(b->sorts, x);
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaMemsetAsync(b->grids, 0, b->grid_elems * sizeof(float), st));
     ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st));
@@ -381,6 +455,8 @@ void anova_batch_destroy(anova_batch* b) {
     cudaFree(b->tmp);
     cudaFree(b->desc);
     cudaFree(b->sub);
+    cudaFree(b->sub_full);
+    cudaFree(b->copy_tab);
     cudaFree(b->sorts);
     cudaFree(b->fft3);
     cudaFree(b->fft12);
@@ -564,6 +640,8 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
         return ANOVA_EINVAL;
     }
     alloc((void**)&b->sub, total_sub * sizeof(int4));
+    alloc((void**)&b->sub_full, total_sub * sizeof(int4));
+    alloc((void**)&b->copy_tab, inst.size() * sizeof(int4));
     alloc((void**)&b->desc, desc.size() * sizeof(DenseWin));
     alloc((void**)&b->sorts, sorts.size() * sizeof(SortInst));
     alloc((void**)&b->fft3, f3.size() * sizeof(Fft3Win));
@@ -573,16 +651,28 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
         return s;
     }
     int at = 0;
-    for (const auto& kv : by_key) {
-        const int first = at;
-        for (int k : kv.second) {
-            const WindowPlan& w = plans[inst[k].p]->win[inst[k].l];
-            if (w.X.nsub == 0) continue;
-            k_b_tag<<<grid_for(w.X.nsub, kThreads, 256), kThreads, 0, st>>>(w.X.sub, w.X.nsub, k, b->sub + at);
-            at += w.X.nsub;
+    {
+        std::vector<int> f3_of(inst.size(), -1), f12_of(inst.size(), -1);
+        int c3 = 0, c12 = 0;
+        for (size_t k = 0; k < inst.size(); k++) {
+            if (plans[inst[k].p]->win[inst[k].l].dA == 3) f3_of[k] = c3++;
+            else f12_of[k] = c12++;
         }
-        if (at > first) b->groups.push_back({kv.first, first, at - first});
+        for (const auto& kv : by_key) {
+            b->keys.push_back(kv.first);
+            for (int k : kv.second) {
+                const WindowPlan& w = plans[inst[k].p]->win[inst[k].l];
+                b->ih.push_back({kv.first, inst[k].p * nrhs + inst[k].r, k, f3_of[k], f12_of[k], at, w.X.nsub});
+                if (w.X.nsub == 0) continue;
+                k_b_tag<<<grid_for(w.X.nsub, kThreads, 256), kThreads, 0, st>>>(w.X.sub, w.X.nsub, k,
+                                                                               b->sub_full + at);
+                at += w.X.nsub;
+            }
+        }
     }
+    b->f3_all = f3;
+    b->f12_all = f12;
+    b->sort_all = sorts;
     // per-system data and weights
     std::vector<BSysInfo> sys(b->NS);
     std::vector<double> eta;
@@ -617,6 +707,7 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->eta, eta.data(), eta.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->zero, 0, (size_t)b->NS * sizeof(double), st);
+    if (e == cudaSuccess && batch_compact_all(b, st) != ANOVA_OK) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -641,6 +732,7 @@ anova_status anova_batch_matvec(anova_batch* b, const double* x, double* y, void
     }
     cudaStream_t st = (cudaStream_t)stream;
     k_b_live_all<<<(b->NS + kBThreads - 1) / kBThreads, kBThreads, 0, st>>>(b->scal, b->NS);
+    ANOVA_TRY(batch_compact_all(b, st));
     ANOVA_TRY(batch_operator(b, x, st));
     k_b_q<<<dim3(b->nchunk, b->NS), kBThreads, 0, st>>>(b->sys, b->scal, b->eta, b->zero, b->tmp, x, y, b->part,
                                                         b->nchunk, 1);
@@ -680,9 +772,19 @@ anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const doub
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
+    std::vector<BSys> hs(b->NS);
+    std::vector<int> live(b->NS);
+    auto recompact = [&]() -> anova_status {
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(hs.data(), b->scal, b->NS * sizeof(BSys), cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int k = 0; k < b->NS; k++) live[k] = hs[k].active;
+        return batch_compact(b, live, st);
+    };
+    ANOVA_TRY(recompact());
     int done = 0, blocks = 0;
-    int active = b->NS;
+    int active = b->live_systems;
     while (done < maxit && active > 0) {
+        if (active <= (3 * b->live_systems) / 4) ANOVA_TRY(recompact());   // drop stopped systems' launches
         if (b->graph) {
             ANOVA_CUDA_TRY(cudaGraphLaunch(b->graph, st));
         } else if (blocks == 0) {
@@ -721,6 +823,7 @@ anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const doub
     std::vector<BSys> sc(b->NS);
     ANOVA_CUDA_TRY(cudaMemcpyAsync(sc.data(), b->scal, b->NS * sizeof(BSys), cudaMemcpyDeviceToHost, st));
     k_b_live_all<<<gs, kBThreads, 0, st>>>(b->scal, b->NS);
+    ANOVA_TRY(batch_compact_all(b, st));
     ANOVA_TRY(batch_operator(b, alpha, st));
     k_b_q<<<gv, kBThreads, 0, st>>>(b->sys, b->scal, b->eta, b->lam, b->tmp, alpha, q, b->part, b->nchunk, 1);
     k_b_resid<<<gv, kBThreads, 0, st>>>(b->sys, y, q, b->part, b->nchunk);
