@@ -191,6 +191,48 @@ anova_status anova_direct_matvec(const double* Z, int64_t M, int64_t ldz, const 
                                  double* out, void* stream);
 
 /* ----------------------------------------------------------------------------
+ * Window construction upstream of the fast summation.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * anova_zscore_fit -- per-column mean and standard deviation (divisor N) of the
+ * training matrix X (device, N x d row-major, row stride ld >= d, d <= 2048)
+ * into mean, sd (device, d each); a constant column gets sd = 1 (Sec. 6.1:
+ * columns standardised with training statistics only).  Asynchronous on
+ * `stream`.  Errors: EINVAL, ECUDA.
+ */
+anova_status anova_zscore_fit(const double* X, int64_t N, int32_t d, int64_t ld, double* mean, double* sd,
+                              void* stream);
+
+/* X <- (X - mean) / sd column by column, in place (device; training or test rows). */
+anova_status anova_zscore_apply(double* X, int64_t N, int32_t d, int64_t ld, const double* mean, const double* sd,
+                                void* stream);
+
+/*
+ * anova_mis -- mutual information score (nats) of every column of X (device,
+ * N x d, ld) with the class labels (device, N int32 in [0, nclass)), Sec. 5.
+ * The paper leaves the estimator open; this is the plug-in estimate
+ * sum_{q,y} (n_qy / N) ln(N n_qy / (n_q n_y)) over `bins` quantile bins q of the
+ * column: a value's fine bin is floor((v - lo) 4096 / (hi - lo)) on the
+ * column's [lo, hi] (last bin closed), fine bin j maps to quantile bin
+ * floor(bins (2 C_j + c_j) / (2 N)), C_j the count below j, c_j its own.
+ * mis: host, d doubles.  nclass <= 64, bins <= 64, d * bins * nclass <= 51200.
+ * Synchronous.  Errors: EINVAL (also for labels out of range), ECUDA.
+ */
+anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const int32_t* labels, int32_t nclass,
+                       int32_t bins, double* mis, void* stream);
+
+/*
+ * anova_windows_from_mis -- Sec. 5's grouping: features ranked by score
+ * (descending, equal scores by index), scores below `threshold` dropped, the
+ * rest in consecutive groups of three; the last group holds the one to three
+ * left.  windows: host, 3 * d int32 (-1 padded rows, the layout
+ * anova_fastsum_plan takes); P: number of windows (0 if none survive).
+ * Host only.
+ */
+anova_status anova_windows_from_mis(const double* mis, int32_t d, double threshold, int32_t* windows, int32_t* P);
+
+/* ----------------------------------------------------------------------------
  * Fitted models (Sec. 4.3).  For fixed coefficients alpha the factor
  * D_l Phi_{X,l}^* alpha of the test-point summation -- alpha spread onto window
  * l's grid and convolved with the kernel's Fourier multiplier -- does not

@@ -36,6 +36,10 @@ _SIGNATURES = {
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
+    "anova_zscore_fit": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
+    "anova_zscore_apply": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
+    "anova_mis": (_i32, [_vp, _i64, _i32, _i64, _vp, _i32, _i32, _pf64, _vp]),
+    "anova_windows_from_mis": (_i32, [_pf64, _i32, _f64, _pi32, _pi32]),
     "anova_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "anova_batch_layout": (_i32, [_vp, _pi64]),
     "anova_batch_matvec": (_i32, [_vp, _vp, _vp, _vp]),
@@ -267,6 +271,44 @@ def anova_stage_times(plan: Plan):
     la = (ctypes.c_int64 * 8)()
     k = lib().anova_stage_times(plan.handle, ms, la, 8)
     return list(ms[:k]), list(la[:k])
+
+
+def anova_zscore_fit(X, stream=None):
+    """(mean, sd) device tensors of the columns of X (device, N x d float64)."""
+    import torch
+    _require_cuda(X, "X", torch.float64)
+    mean = torch.empty(X.shape[1], dtype=torch.float64, device=X.device)
+    sd = torch.empty_like(mean)
+    _check(lib().anova_zscore_fit(_ptr(X), X.shape[0], X.shape[1], X.stride(0), _ptr(mean), _ptr(sd),
+                                  _stream(stream)), "anova_zscore_fit")
+    return mean, sd
+
+
+def anova_zscore_apply(X, mean, sd, stream=None):
+    import torch
+    _require_cuda(X, "X", torch.float64)
+    _check(lib().anova_zscore_apply(_ptr(X), X.shape[0], X.shape[1], X.stride(0), _ptr(mean), _ptr(sd),
+                                    _stream(stream)), "anova_zscore_apply")
+    return X
+
+
+def anova_mis(X, labels, nclass, bins=16, stream=None):
+    import torch
+    _require_cuda(X, "X", torch.float64)
+    _require_cuda(labels, "labels", torch.int32)
+    out = np.zeros(X.shape[1], dtype=np.float64)
+    _check(lib().anova_mis(_ptr(X), X.shape[0], X.shape[1], X.stride(0), _ptr(labels), int(nclass), int(bins),
+                           out.ctypes.data_as(_pf64), _stream(stream)), "anova_mis")
+    return out
+
+
+def anova_windows_from_mis(scores, threshold=0.0):
+    s = np.ascontiguousarray(scores, dtype=np.float64)
+    w = np.full(3 * len(s), -1, dtype=np.int32)
+    P = ctypes.c_int32()
+    _check(lib().anova_windows_from_mis(s.ctypes.data_as(_pf64), len(s), float(threshold), w.ctypes.data_as(_pi32),
+                                        ctypes.byref(P)), "anova_windows_from_mis")
+    return [tuple(int(f) for f in w[3 * p:3 * p + 3] if f >= 0) for p in range(P.value)]
 
 
 class Batch:

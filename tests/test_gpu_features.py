@@ -1,0 +1,69 @@
+"""Window construction on the GPU (z-score, mutual information score, grouping)
+against the plain reference in oracle/features.py (Sec. 5, Sec. 6.1)."""
+import numpy as np
+import pytest
+
+from oracle import features as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_10140_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def data(N=20000, d=12, seed=7):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, d)) * rng.uniform(0.1, 10, d) + rng.uniform(-5, 5, d)
+    X[:, 3] = rng.standard_t(3.0, N)                  # heavy tails
+    X[:, 5] = np.round(X[:, 5])                       # repeated values (ties)
+    X[:, 7] = 2.5                                     # constant column
+    z = 1.5 * X[:, 0] / X[:, 0].std() - X[:, 2] / X[:, 2].std() + 0.5 * np.sin(X[:, 4])
+    y = (z + 0.7 * rng.standard_normal(N) > 0).astype(np.int32)
+    return X, y
+
+
+def test_zscore_matches_oracle(B, torch):
+    X, _ = data()
+    Xd = torch.from_numpy(X).cuda()
+    mean, sd = B.anova_zscore_fit(Xd)
+    m_ref, s_ref = F.zscore_fit(X)
+    assert np.allclose(mean.cpu().numpy(), m_ref, rtol=1e-13, atol=1e-13)
+    assert np.allclose(sd.cpu().numpy(), s_ref, rtol=1e-13, atol=0)
+    T = np.random.default_rng(8).standard_normal((500, X.shape[1]))
+    Td = torch.from_numpy(T).cuda()
+    B.anova_zscore_apply(Td, mean, sd)
+    assert np.allclose(Td.cpu().numpy(), F.zscore_apply(T, m_ref, s_ref), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("bins,nclass", [(16, 2), (8, 3)])
+def test_mis_and_windows_match_oracle(B, torch, bins, nclass):
+    X, y = data()
+    if nclass == 3:
+        y = (y + (X[:, 1] > 0)).astype(np.int32)
+    Xd = torch.from_numpy(X).cuda()
+    yd = torch.from_numpy(y).cuda()
+    got = B.anova_mis(Xd, yd, nclass, bins)
+    ref = F.mis(X, y, nclass, B=bins)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-15)
+    assert got[7] == 0.0                               # constant column: one bin, no information
+    for thr in (0.0, 1e-3, 0.01):
+        assert B.anova_windows_from_mis(got, thr) == F.windows_from_mis(ref, thr)
+
+
+def test_mis_rejects_bad_labels(B, torch):
+    X, y = data(N=1000)
+    y = y.copy()
+    y[17] = 5
+    with pytest.raises(B.AnovaError):
+        B.anova_mis(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), 2, 16)
