@@ -46,7 +46,7 @@ def tf32_peak_tflops():
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture of the
 # current kernels on this workload (profiles/); None for a kernel not captured since it changed
-TRAFFIC = {"k_spread3_tc<14>": 59278080 + 36864, "k_gather3_tc<14>": 59397888 + 5120}
+TRAFFIC = {"k_spread3_tc<14>": 59292160 + 4096, "k_gather3_tc<14>": 59388672 + 768}
 
 
 def traffic_per_launch(name):
