@@ -390,6 +390,12 @@ void anova_plan_destroy(anova_plan* plan);
 /* Static description of a status code. */
 const char* anova_status_string(anova_status status);
 
+/* Number of bounded waits inside the library's kernels that gave up (an
+ * mbarrier that never completed) since the library was loaded; 0 in normal
+ * operation, -1 if it cannot be read.  Such a kernel skips its remaining work,
+ * frees its tensor memory and returns. */
+int64_t anova_wait_timeouts(void);
+
 /* Thread-local detail of the last error on the calling thread ("" if none). */
 const char* anova_last_error(void);
 

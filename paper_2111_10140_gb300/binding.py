@@ -36,6 +36,7 @@ _SIGNATURES = {
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
+    "anova_wait_timeouts": (_i64, []),
     "anova_zscore_fit": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_zscore_apply": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_mis": (_i32, [_vp, _i64, _i32, _i64, _vp, _i32, _i32, _pf64, _vp]),
@@ -309,6 +310,10 @@ def anova_windows_from_mis(scores, threshold=0.0):
     _check(lib().anova_windows_from_mis(s.ctypes.data_as(_pf64), len(s), float(threshold), w.ctypes.data_as(_pi32),
                                         ctypes.byref(P)), "anova_windows_from_mis")
     return [tuple(int(f) for f in w[3 * p:3 * p + 3] if f >= 0) for p in range(P.value)]
+
+
+def anova_wait_timeouts():
+    return int(lib().anova_wait_timeouts())
 
 
 class Batch:

@@ -152,6 +152,7 @@ struct anova_plan {
     float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
+    bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
     bool fft3_slab = false;             // every batched 3-D window fits the slab kernels
@@ -274,6 +275,7 @@ anova_status fft12_box_all(anova_plan* plan, cudaStream_t st);
 bool fft12_box_supported(const WindowPlan& w);
 template <typename T>
 anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st);
+anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
 anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin* descs,

@@ -974,6 +974,7 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
 static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
+    if (plan->gather_tc && plan->gather_umma) return gather3_umma(R, sub, nsub, descs, plan->m, st);
     if (plan->gather_tc) {
         switch (R) {
 #define ANOVA_GATHER_TC(R_) \
@@ -1030,7 +1031,7 @@ anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin
 #define ANOVA_G(R_)                                                                           \
     case 100 + R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
     case 200 + R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
-    case 300 + R_: k_gather3_tc<R_><<<nsub, kGatherTcThreads, 0, st>>>(sub, descs, m); break;
+    case 300 + R_: ANOVA_TRY(gather3_umma(R_, sub, nsub, descs, m, st)); break;
             ANOVA_G(4) ANOVA_G(6) ANOVA_G(8) ANOVA_G(10) ANOVA_G(12) ANOVA_G(14) ANOVA_G(16)
 #undef ANOVA_G
             default: set_error("dense FP32 gather: unsupported window dimension or region size"); return ANOVA_EINVAL;

@@ -1,0 +1,244 @@
+// umma.cu -- the FP32 3-D gather (the NFFT step of the fast summation,
+// arXiv 2111.10140 Sec. 4.1 Eq. nfft, applied to the convolved grid as in
+// Sec. 4.2 Eq. fastsum) on the fifth-generation tensor cores: tcgen05.mma
+// with operands in shared memory and the accumulator in tensor memory.
+//
+// Per sub-problem (one bin, at most 256 nodes, in tiles of 128):
+//
+//   U[j][(a,b)] = sum_c wz_j[c] h[a][b][c]        (tcgen05.mma, M = 128 nodes,
+//                                                   N = R^2 pairs padded to 16,
+//                                                   K = 16 z cells)
+//   s_j         = sum_(a,b) wx_j[a] wy_j[b] U[j][(a,b)]   (epilogue, CUDA cores)
+//
+// A (the nodes' z weights) and B (the staged region, row (a,b) holding the R
+// cells along z) are split into TF32 heads and tails; head x head, head x
+// tail and tail x head accumulate in FP32 in tensor memory, which keeps the
+// product at FP32 accuracy.  Operands use the K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes, 128 bytes apart along K and 512 bytes
+// apart along M / N.  One thread issues the six MMAs of a tile and commits
+// them to an mbarrier; every wait on it is bounded and a wait that gives up
+// is counted (anova_wait_timeouts).  Thread (warp w, lane l) reads row
+// 32 (w mod 4) + l of the accumulator; warps 0-3 and 4-7 take half of the
+// columns each.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace anova {
+
+__device__ unsigned long long g_wait_timeouts = 0;
+
+constexpr int kUmmaThreads = 256;
+constexpr int kUmmaTile = 128;              // nodes per MMA tile (M)
+constexpr int kUmmaSpin = 1 << 22;          // mbarrier polls before giving up
+constexpr uint32_t kUmmaCols = 256;         // tensor-memory columns per block (N <= 256)
+constexpr size_t kUmmaSmem = 80 * 1024;     // shared memory requested: two blocks per SM (tensor memory 2 x 256)
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+    constexpr uint32_t kLbo = 128, kSbo = 512;
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(kLbo >> 4) << 16;
+    d |= (uint64_t)(kSbo >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// float offset of element (row, k) of a rows x 16 K-major operand
+__device__ __forceinline__ int core_off(int row, int k) {
+    return ((row >> 3) * 4 + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < kUmmaSpin && !done; it++)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+#define ANOVA_TMEM_LD16(taddr, r)                                                                             \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}," \
+                 " [%16];"                                                                                    \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),         \
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
+                   "=r"(r[14]), "=r"(r[15])                                                                   \
+                 : "r"(taddr))
+
+template <int R>
+__global__ void __launch_bounds__(kUmmaThreads, 2)
+k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
+    static_assert(R >= 4 && R <= 16 && R % 2 == 0, "even region up to 16");
+    constexpr int NP = ((R * R + 15) / 16) * 16;     // MMA N: (a,b) pairs padded to a multiple of 16
+    constexpr int NCH = NP / 16;                     // 16-column chunks of the accumulator
+    constexpr int HALF = (NCH + 1) / 2;              // chunks of warps 0-3 (the rest: warps 4-7)
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float* sAh = reinterpret_cast<float*>(sm);       // 128 x 16 z weights: heads
+    float* sAl = sAh + kUmmaTile * 16;               //                     tails
+    float* sBh = sAl + kUmmaTile * 16;               // NP x 16 region rows: heads
+    float* sBl = sBh + NP * 16;                      //                      tails
+    float* part = sBl + NP * 16;                     // 128 partial sums of warps 4-7
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(part + kUmmaTile);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
+    const float* __restrict__ h = static_cast<const float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // B: row n = (a, b), column c: the region cell (a, b, c), zero beyond R
+    for (int i = tid; i < NP * 16; i += kUmmaThreads) {
+        const int n = i >> 4, c = i & 15;
+        float v = 0.f;
+        if (n < R * R && c < R) {
+            const int a = n / R, b = n - (n / R) * R;
+            int ga = ox + a, gb = oy + b, gc = oz + c;
+            ga += ga < 0 ? nos : (ga >= nos ? -nos : 0);
+            gb += gb < 0 ? nos : (gb >= nos ? -nos : 0);
+            gc += gc < 0 ? nos : (gc >= nos ? -nos : 0);
+            v = h[((size_t)ga * nos + gb) * nos + gc];
+        }
+        const uint32_t hi = tf32_rna(v);
+        sBh[core_off(n, c)] = __uint_as_float(hi);
+        sBl[core_off(n, c)] = __uint_as_float(tf32_rna(v - __uint_as_float(hi)));
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(kUmmaCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(mbar)), "r"(1));
+
+    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) |
+                               ((uint32_t)(kUmmaTile >> 4) << 24);
+    float* __restrict__ out = static_cast<float*>(W.out);
+    uint32_t phase = 0;
+    bool ok = true;
+    uint32_t taddr = 0;
+    for (int t0 = 0; t0 < sp.z && ok; t0 += kUmmaTile) {
+        const int rows = min(kUmmaTile, sp.z - t0);
+        // A: the tile's z weights (zero rows past the bin's nodes)
+        for (int i = tid; i < kUmmaTile * 16; i += kUmmaThreads) {
+            const int j = i >> 4, c = i & 15;
+            const float v = j < rows ? __ldg(W.wtab + ((int64_t)sp.y + t0 + j) * 48 + 32 + c) : 0.f;
+            const uint32_t hi = tf32_rna(v);
+            sAh[core_off(j, c)] = __uint_as_float(hi);
+            sAl[core_off(j, c)] = __uint_as_float(tf32_rna(v - __uint_as_float(hi)));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        taddr = *tslot;
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++) {
+                const uint64_t ah = umma_desc(su32(sAh) + ks * 256), al = umma_desc(su32(sAl) + ks * 256);
+                const uint64_t bh = umma_desc(su32(sBh) + ks * 256), bl = umma_desc(su32(sBl) + ks * 256);
+                umma_tf32(taddr, ah, bh, idesc, ks > 0);
+                umma_tf32(taddr, ah, bl, idesc, 1);
+                umma_tf32(taddr, al, bh, idesc, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(mbar)) : "memory");
+        }
+        ok = __syncthreads_and(mbar_wait(su32(mbar), phase)) != 0;   // one verdict for the whole block
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) {
+            if (tid == 0) atomicAdd(&g_wait_timeouts, 1ull);
+            break;
+        }
+        // epilogue: row j of the accumulator is node t0 + j
+        const int j = 32 * (warp & 3) + lane;
+        const bool valid = j < rows;
+        const float* wr = W.wtab + ((int64_t)sp.y + t0 + (valid ? j : 0)) * 48;
+        float wx[16], wy[16];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float4 x4 = __ldg(reinterpret_cast<const float4*>(wr) + q);
+            const float4 y4 = __ldg(reinterpret_cast<const float4*>(wr + 16) + q);
+            wx[4 * q] = x4.x; wx[4 * q + 1] = x4.y; wx[4 * q + 2] = x4.z; wx[4 * q + 3] = x4.w;
+            wy[4 * q] = y4.x; wy[4 * q + 1] = y4.y; wy[4 * q + 2] = y4.z; wy[4 * q + 3] = y4.w;
+        }
+        const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+        float s = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ch++) {
+            if ((ch < HALF) != (warp < 4)) continue;     // warp-uniform
+            uint32_t r[16];
+            ANOVA_TMEM_LD16(trow + (uint32_t)(16 * ch), r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const int n = 16 * ch + e;
+                if (n < R * R) s = fmaf(wx[n / R] * wy[n % R], __uint_as_float(r[e]), s);
+            }
+        }
+        if (warp >= 4) part[j] = s;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp < 4 && valid) out[W.perm[(int64_t)sp.y + t0 + j]] = s + part[j];
+    }
+    if (!ok) mbar_wait(su32(mbar), phase ^ 1);    // let the tile's MMAs finish before freeing their memory
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        taddr = *tslot;
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kUmmaCols));
+    }
+}
+
+template <int R>
+static void launch_gather_umma(const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
+    static bool attr = [] {
+        cudaFuncSetAttribute(k_gather3_umma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+        return true;
+    }();
+    (void)attr;
+    k_gather3_umma<R><<<nsub, kUmmaThreads, kUmmaSmem, st>>>(sub, descs, m);
+}
+
+anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
+    if (nsub == 0) return ANOVA_OK;
+    switch (R) {
+        case 4: launch_gather_umma<4>(sub, nsub, descs, m, st); break;
+        case 6: launch_gather_umma<6>(sub, nsub, descs, m, st); break;
+        case 8: launch_gather_umma<8>(sub, nsub, descs, m, st); break;
+        case 10: launch_gather_umma<10>(sub, nsub, descs, m, st); break;
+        case 12: launch_gather_umma<12>(sub, nsub, descs, m, st); break;
+        case 14: launch_gather_umma<14>(sub, nsub, descs, m, st); break;
+        case 16: launch_gather_umma<16>(sub, nsub, descs, m, st); break;
+        default: set_error("tcgen05 gather: unsupported region size"); return ANOVA_EINVAL;
+    }
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+}  // namespace anova
+
+extern "C" int64_t anova_wait_timeouts(void) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, anova::g_wait_timeouts, sizeof(v)) != cudaSuccess) return -1;
+    return (int64_t)v;
+}

@@ -62,3 +62,12 @@ def test_noalloc_predict_limits(env):
     with pytest.raises(B.AnovaError) as e:
         B.krr_predict_noalloc(plan, alpha, Z, out)
     assert e.value.status == B.ERANGE
+
+
+def test_no_kernel_wait_gave_up():
+    """Runs last: no bounded wait inside the library's kernels (the tcgen05
+    gather's mbarrier) gave up during any earlier test of this process."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_10140_gb300 import binding
+    assert binding.anova_wait_timeouts() == 0
