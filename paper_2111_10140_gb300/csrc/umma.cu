@@ -15,11 +15,12 @@
 // tail and tail x head accumulate in FP32 in tensor memory, which keeps the
 // product at FP32 accuracy.  Operands use the K-major layout without swizzle:
 // core matrices of 8 rows x 16 bytes, 128 bytes apart along K and 512 bytes
-// apart along M / N.  One thread issues the six MMAs of a tile and commits
-// them to an mbarrier; every wait on it is bounded and a wait that gives up
-// is counted (anova_wait_timeouts).  Thread (warp w, lane l) reads row
-// 32 (w mod 4) + l of the accumulator; warps 0-3 and 4-7 take half of the
-// columns each.
+// apart along M / N; float4 unit u of an operand holds row 8 (u / 32) + u mod 8,
+// columns 4 ((u / 8) mod 4) .. +3.  One thread issues the six MMAs of a tile
+// and commits them to an mbarrier; every wait on it is bounded and a wait that
+// gives up is counted (anova_wait_timeouts).  Thread (warp w, lane l) reads row
+// 32 (w mod 4) + l of the accumulator; with 256 threads warps 0-3 and 4-7 take
+// half of the columns each.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -28,11 +29,13 @@ namespace anova {
 
 __device__ unsigned long long g_wait_timeouts = 0;
 
-constexpr int kUmmaThreads = 256;
+constexpr int kUmmaThreads = 256;           // 128 (one column group) or 256 (two)
+constexpr int kUmmaMinBlocks = 2;           // resident blocks per SM asked of the compiler
 constexpr int kUmmaTile = 128;              // nodes per MMA tile (M)
 constexpr int kUmmaSpin = 1 << 22;          // mbarrier polls before giving up
 constexpr uint32_t kUmmaCols = 256;         // tensor-memory columns per block (N <= 256)
-constexpr size_t kUmmaSmem = 80 * 1024;     // shared memory requested: two blocks per SM (tensor memory 2 x 256)
+constexpr size_t kUmmaSmem = 80 * 1024;     // shared memory requested per block (sets blocks per SM)
+constexpr int kUmmaGroups = kUmmaThreads / 128;   // column groups of the epilogue
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -52,9 +55,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
     return d;
 }
 
-// float offset of element (row, k) of a rows x 16 K-major operand
-__device__ __forceinline__ int core_off(int row, int k) {
-    return ((row >> 3) * 4 + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+// TF32 head and tail of four values
+__device__ __forceinline__ void split4(const float* v, float4& hv, float4& lv) {
+    float hh[4], ll[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const uint32_t hi = tf32_rna(v[e]);
+        hh[e] = __uint_as_float(hi);
+        ll[e] = __uint_as_float(tf32_rna(v[e] - hh[e]));
+    }
+    hv = make_float4(hh[0], hh[1], hh[2], hh[3]);
+    lv = make_float4(ll[0], ll[1], ll[2], ll[3]);
 }
 
 __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -81,12 +92,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
                  : "r"(taddr))
 
 template <int R>
-__global__ void __launch_bounds__(kUmmaThreads, 2)
+__global__ void __launch_bounds__(kUmmaThreads, kUmmaMinBlocks)
 k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
     static_assert(R >= 4 && R <= 16 && R % 2 == 0, "even region up to 16");
     constexpr int NP = ((R * R + 15) / 16) * 16;     // MMA N: (a,b) pairs padded to a multiple of 16
     constexpr int NCH = NP / 16;                     // 16-column chunks of the accumulator
-    constexpr int HALF = (NCH + 1) / 2;              // chunks of warps 0-3 (the rest: warps 4-7)
+    constexpr int PER = (NCH + kUmmaGroups - 1) / kUmmaGroups;   // chunks per column group
     extern __shared__ __align__(1024) unsigned char sm[];
     float* sAh = reinterpret_cast<float*>(sm);       // 128 x 16 z weights: heads
     float* sAl = sAh + kUmmaTile * 16;               //                     tails
@@ -105,21 +116,29 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // B: row n = (a, b), column c: the region cell (a, b, c), zero beyond R
-    for (int i = tid; i < NP * 16; i += kUmmaThreads) {
-        const int n = i >> 4, c = i & 15;
-        float v = 0.f;
-        if (n < R * R && c < R) {
+    // B: row n = (a, b), column c: the region cell (a, b, c), zero beyond R.
+    // Unit u (4 consecutive c of one row) goes to float4 u of the operand, so
+    // a warp's stores are contiguous: u = (row group, k group, row in group).
+    for (int u = tid; u < NP * 4; u += kUmmaThreads) {
+        const int n = (u >> 5) * 8 + (u & 7), c0 = 4 * ((u >> 3) & 3);
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (n < R * R) {
             const int a = n / R, b = n - (n / R) * R;
-            int ga = ox + a, gb = oy + b, gc = oz + c;
+            int ga = ox + a, gb = oy + b;
             ga += ga < 0 ? nos : (ga >= nos ? -nos : 0);
             gb += gb < 0 ? nos : (gb >= nos ? -nos : 0);
-            gc += gc < 0 ? nos : (gc >= nos ? -nos : 0);
-            v = h[((size_t)ga * nos + gb) * nos + gc];
+            const float* row = h + ((size_t)ga * nos + gb) * nos;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                int gc = oz + c0 + e;
+                gc += gc < 0 ? nos : (gc >= nos ? -nos : 0);
+                if (c0 + e < R) v[e] = row[gc];
+            }
         }
-        const uint32_t hi = tf32_rna(v);
-        sBh[core_off(n, c)] = __uint_as_float(hi);
-        sBl[core_off(n, c)] = __uint_as_float(tf32_rna(v - __uint_as_float(hi)));
+        float4 hv, lv;
+        split4(v, hv, lv);
+        reinterpret_cast<float4*>(sBh)[u] = hv;
+        reinterpret_cast<float4*>(sBl)[u] = lv;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
@@ -136,13 +155,18 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     uint32_t taddr = 0;
     for (int t0 = 0; t0 < sp.z && ok; t0 += kUmmaTile) {
         const int rows = min(kUmmaTile, sp.z - t0);
-        // A: the tile's z weights (zero rows past the bin's nodes)
-        for (int i = tid; i < kUmmaTile * 16; i += kUmmaThreads) {
-            const int j = i >> 4, c = i & 15;
-            const float v = j < rows ? __ldg(W.wtab + ((int64_t)sp.y + t0 + j) * 48 + 32 + c) : 0.f;
-            const uint32_t hi = tf32_rna(v);
-            sAh[core_off(j, c)] = __uint_as_float(hi);
-            sAl[core_off(j, c)] = __uint_as_float(tf32_rna(v - __uint_as_float(hi)));
+        // A: the tile's z weights (zero rows past the bin's nodes), one float4 per unit
+        for (int u = tid; u < kUmmaTile * 4; u += kUmmaThreads) {
+            const int j = (u >> 5) * 8 + (u & 7), kg = (u >> 3) & 3;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (j < rows) {
+                const float4 w4 = __ldg(reinterpret_cast<const float4*>(W.wtab + ((int64_t)sp.y + t0 + j) * 48 + 32) + kg);
+                v[0] = w4.x; v[1] = w4.y; v[2] = w4.z; v[3] = w4.w;
+            }
+            float4 hv, lv;
+            split4(v, hv, lv);
+            reinterpret_cast<float4*>(sAh)[u] = hv;
+            reinterpret_cast<float4*>(sAl)[u] = lv;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -184,7 +208,7 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
         float s = 0.f;
 #pragma unroll
         for (int ch = 0; ch < NCH; ch++) {
-            if ((ch < HALF) != (warp < 4)) continue;     // warp-uniform
+            if (ch / PER != (warp >> 2)) continue;       // this warp's column group (warp-uniform)
             uint32_t r[16];
             ANOVA_TMEM_LD16(trow + (uint32_t)(16 * ch), r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -194,10 +218,10 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
                 if (n < R * R) s = fmaf(wx[n / R] * wy[n % R], __uint_as_float(r[e]), s);
             }
         }
-        if (warp >= 4) part[j] = s;
+        if (kUmmaGroups > 1 && warp >= 4) part[j] = s;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (warp < 4 && valid) out[W.perm[(int64_t)sp.y + t0 + j]] = s + part[j];
+        if (warp < 4 && valid) out[W.perm[(int64_t)sp.y + t0 + j]] = kUmmaGroups > 1 ? s + part[j] : s;
     }
     if (!ok) mbar_wait(su32(mbar), phase ^ 1);    // let the tile's MMAs finish before freeing their memory
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
