@@ -34,7 +34,7 @@ constexpr int kUmmaMinBlocks = 2;           // resident blocks per SM asked of t
 constexpr int kUmmaTile = 128;              // nodes per MMA tile (M)
 constexpr int kUmmaSpin = 1 << 22;          // mbarrier polls before giving up
 constexpr uint32_t kUmmaCols = 256;         // tensor-memory columns per block (N <= 256)
-constexpr size_t kUmmaSmem = 80 * 1024;     // shared memory requested per block (sets blocks per SM)
+constexpr size_t kUmmaSmem = 80 * 1024;     // shared memory requested per block at least (sets blocks per SM)
 constexpr int kUmmaGroups = kUmmaThreads / 128;   // column groups of the epilogue
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -233,14 +233,22 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     }
 }
 
+// shared memory the kernel uses for region size R: A and B heads and tails,
+// the partial sums, the mbarrier and the tensor-memory address
+constexpr size_t umma_need(int R) {
+    return (size_t)(kUmmaTile * 16 * 2 + ((R * R + 15) / 16) * 16 * 16 * 2 + kUmmaTile) * 4 + 16;
+}
+
 template <int R>
 static void launch_gather_umma(const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
+    constexpr size_t sh = umma_need(R) > kUmmaSmem ? umma_need(R) : kUmmaSmem;   // the floor sets blocks per SM
+    static_assert(sh <= 227 * 1024, "shared memory per block");
     static bool attr = [] {
-        cudaFuncSetAttribute(k_gather3_umma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+        cudaFuncSetAttribute(k_gather3_umma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
         return true;
     }();
     (void)attr;
-    k_gather3_umma<R><<<nsub, kUmmaThreads, kUmmaSmem, st>>>(sub, descs, m);
+    k_gather3_umma<R><<<nsub, kUmmaThreads, sh, st>>>(sub, descs, m);
 }
 
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
