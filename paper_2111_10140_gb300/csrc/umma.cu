@@ -30,11 +30,12 @@ namespace anova {
 __device__ unsigned long long g_wait_timeouts = 0;
 
 constexpr int kUmmaThreads = 256;           // 128 (one column group) or 256 (two)
-constexpr int kUmmaMinBlocks = 2;           // resident blocks per SM asked of the compiler
+constexpr int kUmmaMinBlocks = 3;           // resident blocks per SM asked of the compiler
 constexpr int kUmmaTile = 128;              // nodes per MMA tile (M)
 constexpr int kUmmaSpin = 1 << 22;          // mbarrier polls before giving up
 constexpr uint32_t kUmmaCols = 256;         // tensor-memory columns per block (N <= 256)
-constexpr size_t kUmmaSmem = 80 * 1024;     // shared memory requested per block at least (sets blocks per SM)
+constexpr size_t kUmmaSmem = 64 * 1024;     // shared memory requested per block at least (three blocks per SM:
+                                            // two hold tensor memory, the third stages its operands)
 constexpr int kUmmaGroups = kUmmaThreads / 128;   // column groups of the epilogue
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
