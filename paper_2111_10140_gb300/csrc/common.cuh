@@ -179,13 +179,12 @@ struct anova_plan {
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
-    // window pipeline of the FP32 matrix-vector product (a window's FFT on a
-    // side stream overlaps the next window's spread): streams and events
+    // per-window pipelines of the FP32 matrix-vector product (spread, FFT and
+    // gather of different windows overlap): side streams and fork/join events
     static constexpr int kSideStreams = 4;
     cudaStream_t side[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t ev_spread[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
     bool window_streams = true;
     bool use_graphs = true;
 };

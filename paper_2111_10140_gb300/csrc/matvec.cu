@@ -80,14 +80,14 @@ k_window_sum(const Tin* __restrict__ tmp, const double* __restrict__ eta, int P,
 // -------------------------------------------------------------- matvec core
 // tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum).
 // `tmp` must be plan->tmp: the batched dense kernels write their slices of it.
-// FP32, every window dense with a batched box FFT (at most four windows): a
-// pipeline over the windows in which each window's FFT overlaps the next
-// window's spread.  The merged sub-problem list holds each window's
+// FP32, every window dense with a batched box FFT: one pipeline per window
+// (sort, spread, FFT, gather) on side streams forked from `st` and joined
+// back, so that the small FFT launches of one window overlap the spread and
+// gather of the others.  The merged sub-problem list holds each window's
 // sub-problems contiguously, in dense-window order within its (dims, R) group.
 static bool window_streams_ok(const anova_plan* plan) {
     if (!plan->window_streams || plan->clock.enabled || !plan->dense_asort) return false;
-    if ((int)plan->dense_windows.size() != plan->P || plan->P < 2 || plan->P > anova_plan::kSideStreams)
-        return false;
+    if ((int)plan->dense_windows.size() != plan->P || plan->P < 2) return false;
     for (int l = 0; l < plan->P; l++) {
         const WindowPlan& w = plan->win[l];
         if (!w.dense || !(w.dA == 3 ? fft3_box_supported(w) : w.fft12)) return false;
@@ -97,55 +97,45 @@ static bool window_streams_ok(const anova_plan* plan) {
 
 static anova_status windows_apply_streams(anova_plan* plan, const void* alpha, int alpha_is_double,
                                           cudaStream_t st) {
-    // Software pipeline over the windows: spreads and gathers in order on `st`,
-    // the FFTs on a side stream, each waiting for its window's spread; window
-    // k's FFT runs while window k+1 is spread (and the last one while the
-    // first is gathered).
     const int nd = (int)plan->dense_windows.size();
-    if (nd > anova_plan::kSideStreams) return ANOVA_EINVAL;
+    const int ns = std::min(nd, (int)anova_plan::kSideStreams);
     if (!plan->ev_fork) {
         ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming));
         for (int k = 0; k < anova_plan::kSideStreams; k++) {
             ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&plan->side[k], cudaStreamNonBlocking));
             ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_join[k], cudaEventDisableTiming));
         }
-        for (int k = 0; k < anova_plan::kSideStreams; k++)
-            ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_spread[k], cudaEventDisableTiming));
     }
-    cudaStream_t fs = plan->side[0];
     ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(float), st));
+    ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_fork, st));
+    for (int k = 0; k < ns; k++) ANOVA_CUDA_TRY(cudaStreamWaitEvent(plan->side[k], plan->ev_fork, 0));
     const DenseWin* descs = plan->dense_desc + nd;
     const int n3 = (int)plan->fft3_windows.size(), n12 = (int)plan->fft12_windows.size();
-    std::vector<std::array<int, 3>> grp(nd);
     int first = 0;
-    for (int k = 0; k < nd; k++) {
-        const WindowPlan& w = plan->win[plan->dense_windows[k]];
-        grp[k] = {w.dA * 100 + w.R, first, w.X.nsub};
-        first += w.X.nsub;
-    }
     for (int k = 0; k < nd; k++) {
         const int l = plan->dense_windows[k];
         const WindowPlan& w = plan->win[l];
-        ANOVA_TRY(sort_alpha_window(plan, k, alpha, alpha_is_double, st));
-        ANOVA_TRY(dense_f32_spread_groups(plan->m, plan->dense_sub, descs, {grp[k]}, st));
-        ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_spread[k], st));
-        ANOVA_CUDA_TRY(cudaStreamWaitEvent(fs, plan->ev_spread[k], 0));
+        cudaStream_t s = plan->side[k % ns];
+        const std::vector<std::array<int, 3>> grp = {{w.dA * 100 + w.R, first, w.X.nsub}};
+        first += w.X.nsub;
+        ANOVA_TRY(sort_alpha_window(plan, k, alpha, alpha_is_double, s));
+        if (w.X.nsub > 0) ANOVA_TRY(dense_f32_spread_groups(plan->m, plan->dense_sub, descs, grp, s));
         if (w.dA == 3) {
             const int i3 = (int)(std::find(plan->fft3_windows.begin(), plan->fft3_windows.end(), l) -
                                  plan->fft3_windows.begin());
             Fft3Shape sh;
             sh.add(w);
-            ANOVA_TRY(fft3_box_run<float>(plan->fft3_desc + n3 + i3, sh, plan->sm_count, fs));
+            ANOVA_TRY(fft3_box_run<float>(plan->fft3_desc + n3 + i3, sh, plan->sm_count, s));
         } else {
             const int i12 = (int)(std::find(plan->fft12_windows.begin(), plan->fft12_windows.end(), l) -
                                   plan->fft12_windows.begin());
-            ANOVA_TRY(fft12_box_run<float>(plan->fft12_desc + n12 + i12, 1, fft12_window_smem(w, sizeof(float)), fs));
+            ANOVA_TRY(fft12_box_run<float>(plan->fft12_desc + n12 + i12, 1, fft12_window_smem(w, sizeof(float)), s));
         }
-        ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_join[k], fs));
+        if (w.X.nsub > 0) ANOVA_TRY(dense_f32_gather_groups(plan->m, plan->dense_sub, descs, grp, s));
     }
-    for (int k = 0; k < nd; k++) {
+    for (int k = 0; k < ns; k++) {
+        ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_join[k], plan->side[k]));
         ANOVA_CUDA_TRY(cudaStreamWaitEvent(st, plan->ev_join[k], 0));
-        ANOVA_TRY(dense_f32_gather_groups(plan->m, plan->dense_sub, descs, {grp[k]}, st));
     }
     return ANOVA_OK;
 }

@@ -1266,7 +1266,6 @@ void anova_plan_destroy(anova_plan* plan) {
     for (int k = 0; k < anova_plan::kSideStreams; k++) {
         if (plan->side[k]) cudaStreamDestroy(plan->side[k]);
         if (plan->ev_join[k]) cudaEventDestroy(plan->ev_join[k]);
-        if (plan->ev_spread[k]) cudaEventDestroy(plan->ev_spread[k]);
     }
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     delete plan;
