@@ -179,13 +179,6 @@ struct anova_plan {
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
-    // per-window pipelines of the FP32 matrix-vector product (spread, FFT and
-    // gather of different windows overlap): side streams and fork/join events
-    static constexpr int kSideStreams = 4;
-    cudaStream_t side[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_join[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
-    bool window_streams = true;
     bool use_graphs = true;
 };
 
@@ -283,7 +276,6 @@ bool fft12_box_supported(const WindowPlan& w);
 template <typename T>
 anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st);
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
-anova_status sort_alpha_window(anova_plan* plan, int k, const void* alpha, int alpha_double, cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
 anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin* descs,

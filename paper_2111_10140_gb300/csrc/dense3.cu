@@ -997,15 +997,6 @@ static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int n
     return ANOVA_OK;
 }
 
-// sorted FP32 coefficients of dense window k alone (its own launch)
-anova_status sort_alpha_window(anova_plan* plan, int k, const void* alpha, int alpha_double, cudaStream_t st) {
-    const int nd = (int)plan->dense_windows.size();
-    k_sort_alpha<<<grid_for(plan->N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
-        plan->dense_desc + nd + k, 1, plan->N, alpha, alpha_double);
-    ANOVA_CHECK_LAUNCH();
-    return ANOVA_OK;
-}
-
 // FP32 dense kernels over any merged sub-problem list whose descriptors carry
 // sorted coefficients (plans and batches alike): one launch per (dims, R) group.
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,

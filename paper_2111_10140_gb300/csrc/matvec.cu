@@ -80,70 +80,9 @@ k_window_sum(const Tin* __restrict__ tmp, const double* __restrict__ eta, int P,
 // -------------------------------------------------------------- matvec core
 // tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum).
 // `tmp` must be plan->tmp: the batched dense kernels write their slices of it.
-// FP32, every window dense with a batched box FFT: one pipeline per window
-// (sort, spread, FFT, gather) on side streams forked from `st` and joined
-// back, so that the small FFT launches of one window overlap the spread and
-// gather of the others.  The merged sub-problem list holds each window's
-// sub-problems contiguously, in dense-window order within its (dims, R) group.
-static bool window_streams_ok(const anova_plan* plan) {
-    if (!plan->window_streams || plan->clock.enabled || !plan->dense_asort) return false;
-    if ((int)plan->dense_windows.size() != plan->P || plan->P < 2) return false;
-    for (int l = 0; l < plan->P; l++) {
-        const WindowPlan& w = plan->win[l];
-        if (!w.dense || !(w.dA == 3 ? fft3_box_supported(w) : w.fft12)) return false;
-    }
-    return true;
-}
-
-static anova_status windows_apply_streams(anova_plan* plan, const void* alpha, int alpha_is_double,
-                                          cudaStream_t st) {
-    const int nd = (int)plan->dense_windows.size();
-    const int ns = std::min(nd, (int)anova_plan::kSideStreams);
-    if (!plan->ev_fork) {
-        ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming));
-        for (int k = 0; k < anova_plan::kSideStreams; k++) {
-            ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&plan->side[k], cudaStreamNonBlocking));
-            ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_join[k], cudaEventDisableTiming));
-        }
-    }
-    ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(float), st));
-    ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_fork, st));
-    for (int k = 0; k < ns; k++) ANOVA_CUDA_TRY(cudaStreamWaitEvent(plan->side[k], plan->ev_fork, 0));
-    const DenseWin* descs = plan->dense_desc + nd;
-    const int n3 = (int)plan->fft3_windows.size(), n12 = (int)plan->fft12_windows.size();
-    int first = 0;
-    for (int k = 0; k < nd; k++) {
-        const int l = plan->dense_windows[k];
-        const WindowPlan& w = plan->win[l];
-        cudaStream_t s = plan->side[k % ns];
-        const std::vector<std::array<int, 3>> grp = {{w.dA * 100 + w.R, first, w.X.nsub}};
-        first += w.X.nsub;
-        ANOVA_TRY(sort_alpha_window(plan, k, alpha, alpha_is_double, s));
-        if (w.X.nsub > 0) ANOVA_TRY(dense_f32_spread_groups(plan->m, plan->dense_sub, descs, grp, s));
-        if (w.dA == 3) {
-            const int i3 = (int)(std::find(plan->fft3_windows.begin(), plan->fft3_windows.end(), l) -
-                                 plan->fft3_windows.begin());
-            Fft3Shape sh;
-            sh.add(w);
-            ANOVA_TRY(fft3_box_run<float>(plan->fft3_desc + n3 + i3, sh, plan->sm_count, s));
-        } else {
-            const int i12 = (int)(std::find(plan->fft12_windows.begin(), plan->fft12_windows.end(), l) -
-                                  plan->fft12_windows.begin());
-            ANOVA_TRY(fft12_box_run<float>(plan->fft12_desc + n12 + i12, 1, fft12_window_smem(w, sizeof(float)), s));
-        }
-        if (w.X.nsub > 0) ANOVA_TRY(dense_f32_gather_groups(plan->m, plan->dense_sub, descs, grp, s));
-    }
-    for (int k = 0; k < ns; k++) {
-        ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_join[k], plan->side[k]));
-        ANOVA_CUDA_TRY(cudaStreamWaitEvent(st, plan->ev_join[k], 0));
-    }
-    return ANOVA_OK;
-}
-
 template <typename T>
 static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha_is_double, T* tmp,
                                   cudaStream_t st) {
-    if (sizeof(T) == 4 && window_streams_ok(plan)) return windows_apply_streams(plan, alpha, alpha_is_double, st);
     const int64_t N = plan->N;
     ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(T), st));
     int nl = 0;

@@ -1263,11 +1263,6 @@ void anova_plan_destroy(anova_plan* plan) {
     for (auto& g : plan->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
-    for (int k = 0; k < anova_plan::kSideStreams; k++) {
-        if (plan->side[k]) cudaStreamDestroy(plan->side[k]);
-        if (plan->ev_join[k]) cudaEventDestroy(plan->ev_join[k]);
-    }
-    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     delete plan;
 }
 
