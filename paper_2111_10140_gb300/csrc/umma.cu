@@ -120,6 +120,7 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     // B: row n = (a, b), column c: the region cell (a, b, c), zero beyond R.
     // Unit u (4 consecutive c of one row) goes to float4 u of the operand, so
     // a warp's stores are contiguous: u = (row group, k group, row in group).
+#pragma unroll 4
     for (int u = tid; u < NP * 4; u += kUmmaThreads) {
         const int n = (u >> 5) * 8 + (u & 7), c0 = 4 * ((u >> 3) & 3);
         float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -156,18 +157,34 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     uint32_t taddr = 0;
     for (int t0 = 0; t0 < sp.z && ok; t0 += kUmmaTile) {
         const int rows = min(kUmmaTile, sp.z - t0);
-        // A: the tile's z weights (zero rows past the bin's nodes), one float4 per unit
-        for (int u = tid; u < kUmmaTile * 4; u += kUmmaThreads) {
-            const int j = (u >> 5) * 8 + (u & 7), kg = (u >> 3) & 3;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (j < rows) {
-                const float4 w4 = __ldg(reinterpret_cast<const float4*>(W.wtab + ((int64_t)sp.y + t0 + j) * 48 + 32) + kg);
-                v[0] = w4.x; v[1] = w4.y; v[2] = w4.z; v[3] = w4.w;
+        // Thread (warp w, lane l) owns node row j = 32 (w mod 4) + l of the tile:
+        // it loads the node's x and y weights for the epilogue now, and warps
+        // 0-3 also its z weights, written as row j of A (zero rows past the
+        // bin's nodes) -- one round trip to the weight table per tile.
+        const int j = 32 * (warp & 3) + lane;
+        const bool valid = j < rows;
+        const float4* wr4 = reinterpret_cast<const float4*>(W.wtab + ((int64_t)sp.y + t0 + (valid ? j : 0)) * 48);
+        float wx[16], wy[16];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float4 x4 = __ldg(wr4 + q);
+            const float4 y4 = __ldg(wr4 + 4 + q);
+            wx[4 * q] = x4.x; wx[4 * q + 1] = x4.y; wx[4 * q + 2] = x4.z; wx[4 * q + 3] = x4.w;
+            wy[4 * q] = y4.x; wy[4 * q + 1] = y4.y; wy[4 * q + 2] = y4.z; wy[4 * q + 3] = y4.w;
+        }
+        if (warp < 4) {
+            float4 z4[4];
+#pragma unroll
+            for (int kg = 0; kg < 4; kg++) z4[kg] = valid ? __ldg(wr4 + 8 + kg) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int kg = 0; kg < 4; kg++) {
+                const float v[4] = {z4[kg].x, z4[kg].y, z4[kg].z, z4[kg].w};
+                float4 hv, lv;
+                split4(v, hv, lv);
+                const int u = (j >> 3) * 32 + kg * 8 + (j & 7);     // float4 unit of (row j, columns 4 kg ..)
+                reinterpret_cast<float4*>(sAh)[u] = hv;
+                reinterpret_cast<float4*>(sAl)[u] = lv;
             }
-            float4 hv, lv;
-            split4(v, hv, lv);
-            reinterpret_cast<float4*>(sAh)[u] = hv;
-            reinterpret_cast<float4*>(sAl)[u] = lv;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -194,17 +211,6 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
             break;
         }
         // epilogue: row j of the accumulator is node t0 + j
-        const int j = 32 * (warp & 3) + lane;
-        const bool valid = j < rows;
-        const float* wr = W.wtab + ((int64_t)sp.y + t0 + (valid ? j : 0)) * 48;
-        float wx[16], wy[16];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const float4 x4 = __ldg(reinterpret_cast<const float4*>(wr) + q);
-            const float4 y4 = __ldg(reinterpret_cast<const float4*>(wr + 16) + q);
-            wx[4 * q] = x4.x; wx[4 * q + 1] = x4.y; wx[4 * q + 2] = x4.z; wx[4 * q + 3] = x4.w;
-            wy[4 * q] = y4.x; wy[4 * q + 1] = y4.y; wy[4 * q + 2] = y4.z; wy[4 * q + 3] = y4.w;
-        }
         const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
         float s = 0.f;
 #pragma unroll
