@@ -86,6 +86,36 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
                                 void* stream, anova_plan** out);
 
 /*
+ * anova_fastsum_plan_bins -- anova_fastsum_plan with the bin side of the dense
+ * spread / gather kernels chosen per window dimension: bin_side (host, 3
+ * int32) for the 1-D, 2-D and 3-D windows, 0 = the default rule.  A side is
+ * taken when it is even, the region side + 2m <= 16, the bins fit the binning
+ * (at most 32768) and, in 1-D, side + m - 2 < n_os; otherwise the default rule
+ * applies (anova_plan_window_bins reports what was taken).  bin_side NULL is
+ * anova_fastsum_plan.  The paper fixes no binning: a tuning parameter of the
+ * GPU design.
+ */
+anova_status anova_fastsum_plan_bins(const double* points, int64_t N, int32_t d, int64_t ld,
+                                     const int32_t* windows, int32_t P, const double* weights, double ell,
+                                     const int32_t* n, int32_t m, double sigma, double eps_B, int32_t p,
+                                     int32_t precision, const int32_t* bin_side, void* stream, anova_plan** out);
+
+/*
+ * anova_autotune_bins -- the bin sides (per window dimension) that make the
+ * matrix-vector product fastest on this GPU, by measurement: the default rule
+ * first, then every admissible side for the 1-D, 2-D and 3-D windows in turn,
+ * each timed over `reps` products (FP32 if the precision holds it) after three
+ * warm-up products.  Arguments as anova_fastsum_plan; bin_side (host, 3 int32)
+ * receives the choice for anova_fastsum_plan_bins (0 = default rule), ms (host
+ * or NULL) its time per product.  Builds and frees one plan per candidate;
+ * synchronous.  Errors: those of the plan build, EINVAL.
+ */
+anova_status anova_autotune_bins(const double* points, int64_t N, int32_t d, int64_t ld, const int32_t* windows,
+                                 int32_t P, const double* weights, double ell, const int32_t* n, int32_t m,
+                                 double sigma, double eps_B, int32_t p, int32_t precision, int32_t reps,
+                                 int32_t* bin_side, double* ms, void* stream);
+
+/*
  * anova_matvec -- out = K alpha with the fast operator (Sec. 4.3, K alpha ~=
  * sum_l eta_l Phi_l D_l Phi_l^* alpha).
  *
@@ -422,6 +452,9 @@ anova_status anova_plan_window(const anova_plan* plan, int32_t l, double* centre
 anova_status anova_debug_spread(anova_plan* plan, int32_t l, int32_t dtype, const void* alpha,
                                 void* grid, void* stream);
 
+/* Bin side, region side and whether window l runs on the dense kernels. */
+anova_status anova_plan_window_bins(const anova_plan* plan, int32_t l, int32_t* bin_side, int32_t* region,
+                                    int32_t* dense);
 /*
  * anova_debug_diag -- copy window l's FP64 multiplier D_k (host, n^dims
  * doubles, centred index) = b_k / prod_t psihat(k_t)^2 with the normalised

@@ -36,6 +36,11 @@ _SIGNATURES = {
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
+    "anova_fastsum_plan_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
+                                       _i32, _i32, _pi32, _vp, ctypes.POINTER(_vp)]),
+    "anova_autotune_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
+                                   _i32, _i32, _i32, _pi32, _pf64, _vp]),
+    "anova_plan_window_bins": (_i32, [_vp, _i32, _pi32, _pi32, _pi32]),
     "anova_wait_timeouts": (_i64, []),
     "anova_zscore_fit": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_zscore_apply": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
@@ -167,6 +172,54 @@ def anova_fastsum_plan(points, windows, ell, n=None, m=6, sigma=2.0, eps_B=1.0 /
         int(precision), _stream(stream), ctypes.byref(h))
     _check(st, "anova_fastsum_plan")
     return Plan(h, N, d, P, precision)
+
+
+def _plan_args(points, windows, n):
+    W = windows_array(windows) if not isinstance(windows, np.ndarray) else np.ascontiguousarray(windows, np.int32)
+    P = W.shape[0]
+    nv = None if n is None else np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int32), (P,)), dtype=np.int32)
+    return W, P, nv
+
+
+def anova_fastsum_plan_bins(points, windows, ell, bin_side, n=None, m=6, sigma=2.0, eps_B=1.0 / 16, p=8,
+                            precision=FP64, weights=None, stream=None) -> Plan:
+    import torch
+    _require_cuda(points, "points", torch.float64)
+    N, d = points.shape
+    W, P, nv = _plan_args(points, windows, n)
+    wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    bs = np.ascontiguousarray(bin_side, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = lib().anova_fastsum_plan_bins(
+        _ptr(points), N, d, d, W.ctypes.data_as(_pi32), P, wts.ctypes.data_as(_pf64) if wts is not None else None,
+        float(ell), nv.ctypes.data_as(_pi32) if nv is not None else None, int(m), float(sigma), float(eps_B), int(p),
+        int(precision), bs.ctypes.data_as(_pi32), _stream(stream), ctypes.byref(h))
+    _check(st, "anova_fastsum_plan_bins")
+    return Plan(h, N, d, P, precision)
+
+
+def anova_autotune_bins(points, windows, ell, n=None, m=6, sigma=2.0, eps_B=1.0 / 16, p=8, precision=FP32,
+                        reps=10, stream=None):
+    """Returns (bin_side [3], ms per product)."""
+    import torch
+    _require_cuda(points, "points", torch.float64)
+    N, d = points.shape
+    W, P, nv = _plan_args(points, windows, n)
+    bs = np.zeros(3, dtype=np.int32)
+    ms = ctypes.c_double()
+    st = lib().anova_autotune_bins(_ptr(points), N, d, d, W.ctypes.data_as(_pi32), P, None, float(ell),
+                                   nv.ctypes.data_as(_pi32) if nv is not None else None, int(m), float(sigma),
+                                   float(eps_B), int(p), int(precision), int(reps), bs.ctypes.data_as(_pi32),
+                                   ctypes.byref(ms), _stream(stream))
+    _check(st, "anova_autotune_bins")
+    return [int(v) for v in bs], ms.value
+
+
+def anova_plan_window_bins(plan: Plan, l: int) -> dict:
+    t, r, dn = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().anova_plan_window_bins(plan.handle, l, ctypes.byref(t), ctypes.byref(r), ctypes.byref(dn)),
+           "anova_plan_window_bins")
+    return {"bin_side": t.value, "region": r.value, "dense": bool(dn.value)}
 
 
 def anova_matvec(plan: Plan, alpha, out, stream=None):

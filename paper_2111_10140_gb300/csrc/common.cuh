@@ -153,6 +153,7 @@ struct anova_plan {
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
+    int bin_side[3] = {0, 0, 0};        // bin side of the dense 1-D / 2-D / 3-D windows (0: the default rule)
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
     bool fft3_slab = false;             // every batched 3-D window fits the slab kernels

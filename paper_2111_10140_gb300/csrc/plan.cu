@@ -545,7 +545,30 @@ __global__ void k_twiddles(int nos, double2* __restrict__ tw64, float2* __restri
 }
 
 // ================================================================ set-up
-static void choose_bins(WindowPlan& w, int m) {
+// a requested bin side for the dense kernels: even, region Tb + 2m <= 16, the
+// bins within kMaxBins, and the region cells bin Tb - m + r inside [-nos, 2 nos)
+// (the kernels wrap an index with one conditional): Tb + m - 2 < nos
+static bool dense_side_ok(const WindowPlan& w, int m, int Tb) {
+    if (Tb < 2 || Tb % 2 || Tb + 2 * m > 16 || Tb > w.nos) return false;
+    if (!(Tb + m - 2 < w.nos)) return false;
+    const int64_t nb = (w.nos + Tb - 1) / Tb;
+    int64_t nbins = 1;
+    for (int t = 0; t < w.dA; t++) nbins *= nb;
+    return nbins <= kMaxBins;
+}
+
+static void choose_bins(WindowPlan& w, int m, const int* side) {
+    if (side && side[w.dA - 1] > 0 && dense_side_ok(w, m, side[w.dA - 1])) {
+        const int Tb = side[w.dA - 1];
+        const int nb = (w.nos + Tb - 1) / Tb;
+        w.dense = true;
+        w.T = Tb;
+        w.nb = nb;
+        w.nbins = nb;
+        for (int t = 1; t < w.dA; t++) w.nbins *= nb;
+        w.R = Tb + 2 * m;
+        return;
+    }
     if (w.dA <= 2 && 2 * m + 2 <= 16) {
         // dense small-region kernels: 2-D bins of 2x2 cells (R = 2m + 2); 1-D bins of 16 - 2m cells
         // (R = 16) when the region cells bin*Tb - m + r stay inside [-nos, 2 nos), else 2 cells
@@ -948,7 +971,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
         w.n = n ? n[l] : 32;
         w.nos = (int)std::lround(sigma * w.n);
         w.eta = weights ? weights[l] : 1.0 / P;
-        choose_bins(w, m);
+        choose_bins(w, m, plan->bin_side);
         if (w.nbins > kMaxBins) {
             set_error("window " + std::to_string(l) + ": grid too fine for the binning (reduce n or m)");
             return ANOVA_EINVAL;
@@ -1210,6 +1233,14 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
                                 double ell, const int32_t* n, int32_t m, double sigma,
                                 double eps_B, int32_t p, int32_t precision, void* stream,
                                 anova_plan** out) {
+    return anova_fastsum_plan_bins(points, N, d, ld, windows, P, weights, ell, n, m, sigma, eps_B, p, precision,
+                                   nullptr, stream, out);
+}
+
+anova_status anova_fastsum_plan_bins(const double* points, int64_t N, int32_t d, int64_t ld,
+                                     const int32_t* windows, int32_t P, const double* weights, double ell,
+                                     const int32_t* n, int32_t m, double sigma, double eps_B, int32_t p,
+                                     int32_t precision, const int32_t* bin_side, void* stream, anova_plan** out) {
     set_error("");
     if (!out) {
         set_error("out is NULL");
@@ -1223,6 +1254,8 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
     ANOVA_TRY(validate(N, d, ld, windows, P, weights, ell, n, m, sigma, eps_B, p, precision));
     anova_plan* plan = new (std::nothrow) anova_plan();
     if (!plan) return ANOVA_ENOMEM;
+    if (bin_side)
+        for (int t = 0; t < 3; t++) plan->bin_side[t] = bin_side[t] > 0 ? bin_side[t] : 0;
     anova_status s = plan_build(points, N, d, ld, windows, P, weights, ell, n, m, sigma, eps_B, p,
                                 precision, (cudaStream_t)stream, plan);
     if (s != ANOVA_OK) {
@@ -1294,6 +1327,19 @@ anova_status anova_plan_window(const anova_plan* plan, int32_t l, double* centre
     if (dims) *dims = w.dA;
     if (n) *n = w.n;
     if (nos) *nos = w.nos;
+    return ANOVA_OK;
+}
+
+anova_status anova_plan_window_bins(const anova_plan* plan, int32_t l, int32_t* bin_side, int32_t* region,
+                                    int32_t* dense) {
+    if (!plan || l < 0 || l >= plan->P) {
+        set_error("bad plan or window index");
+        return ANOVA_EINVAL;
+    }
+    const WindowPlan& w = plan->win[l];
+    if (bin_side) *bin_side = w.T;
+    if (region) *region = w.R;
+    if (dense) *dense = w.dense ? 1 : 0;
     return ANOVA_OK;
 }
 
