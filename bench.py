@@ -605,6 +605,30 @@ def run_batch(args):
         pl.close()
 
 
+def run_autotune(args):
+    """Bin sides chosen by anova_autotune_bins for the mid workload and the
+    precision form, against the default rule."""
+    import torch
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    from paper_2111_10140_gb300 import workloads as W
+    __graft_entry__.build()
+    for w in (W.plain_mid(), W.precision_form()):
+        X = torch.from_numpy(w.X).cuda()
+        sides, ms = B.anova_autotune_bins(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                          precision=B.FP32, reps=20)
+        d_sides, d_ms = None, None
+        plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                    precision=B.FP32)
+        d_sides = sorted({(len(win), B.anova_plan_window_bins(plan, l)["bin_side"]) for l, win in enumerate(w.windows)})
+        plan.close()
+        print(json.dumps({"autotune": True, "workload": w.name, "chosen_bin_side_1d_2d_3d": sides,
+                          "ms_per_fp32_matvec": ms, "default_rule_sides": d_sides}), flush=True)
+        del X
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -626,6 +650,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-models", type=int, default=4)
     ap.add_argument("--serve-fit-pool", type=int, default=6)
+    ap.add_argument("--autotune", action="store_true", help="bin sides chosen by the autotuner (mid, precision form)")
     ap.add_argument("--batch", action="store_true",
                     help="batching form: many problems x right-hand sides in one batched CG")
     ap.add_argument("--batch-problems", type=int, default=64)
@@ -645,6 +670,8 @@ def main():
         run_serve(args)
     elif args.batch:
         run_batch(args)
+    elif args.autotune:
+        run_autotune(args)
     else:
         run_ours(args)
 
