@@ -46,7 +46,8 @@ def tf32_peak_tflops():
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture of the
 # current kernels on this workload (profiles/); None for a kernel not captured since it changed
-TRAFFIC = {"k_spread3_tc<14>": 59292160 + 4096, "k_gather3_tc<14>": 59388672 + 768}
+TRAFFIC = {"k_spread3_tc<14>": 59281920 + 11520, "k_gather3_umma<14>": 59399424 + 14592,
+           "k_spread3_tc<16>": 59310336 + 10880, "k_gather3_umma<16>": 59434880 + 10240}
 
 
 def traffic_per_launch(name):
@@ -190,7 +191,9 @@ def run_ours(args):
     X = torch.from_numpy(w.X).to(dev)
     # bin sides per window dimension from the library's autotuner (outside any timed region)
     sides = [0, 0, 0]
-    if not args.no_autotune:
+    if args.bin_side:
+        sides = [int(v) for v in args.bin_side.split(",")]
+    elif not args.no_autotune:
         sides, _ = B.anova_autotune_bins(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
                                          precision=B.FP32, reps=10)
     plan = B.anova_fastsum_plan_bins(X, w.windows, w.ell, sides, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
@@ -355,7 +358,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "N": N, "d": 9, "windows": "3x3D", "n": 32, "m": 6,
                            "sigma": 2.0, "eps_B": w.epsB, "ell": w.ell, "precision": "fp32 operator",
-                           "bin_side_1d_2d_3d": sides, "bin_sides": "autotuned" if not args.no_autotune else "rule",
+                           "bin_side_1d_2d_3d": sides, "bin_sides": "given" if args.bin_side else ("autotuned" if not args.no_autotune else "rule"),
                            "l2": "flushed before every step (256 MB write outside the step events)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu,
@@ -648,6 +651,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--check-rows", type=int, default=2048)
     ap.add_argument("--no-autotune", action="store_true", help="bin sides from the default rule")
+    ap.add_argument("--bin-side", default="", help="bin sides for 1-D,2-D,3-D windows (e.g. 0,0,4), no autotuning")
     ap.add_argument("--crossover", action="store_true",
                     help="direct vs fast matvec time over N (the paper's Fig. 1 on synthetic data); prints one line per N")
     ap.add_argument("--serve", action="store_true",
