@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict_
         const int step = modp(ky, nos);
         T ar = T(0), ai = T(0);
         const C* a = A + (int64_t)x * By * n + kz;
+#pragma unroll 4
         for (int y = 0; y < By; y++) {
             cmac(a[(int64_t)y * n], tw[r], 0, ar, ai);
             r += step;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict_
 
 // Fused middle pass along x for up to 32 consecutive kz of one ky per block:
 // H[kx] = D[kx] sum_x B[x] e^{-2 pi i kx x/nos}, then C[x] = sum_kx H[kx] e^{+...}.
-constexpr int kMidLanes = 32, kMidWarps = 8, kMaxN3 = 64, kMaxBox3 = 256;
+constexpr int kMidLanes = 32, kMidWarps = 32, kMaxN3 = 64, kMaxBox3 = 256;
 // Dynamic shared memory: H (n x 32), the staged lines (Bx x 32) when Bx <= kMidStage, twiddles (nos).
 constexpr int kMidStage = 64;
 template <typename T>
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Wi
         int r = modp(kxv * x0v, nos);
         const int step = modp(kxv, nos);
         T ar = T(0), ai = T(0);
+#pragma unroll 4
         for (int x = 0; x < Bx; x++) {
             C v;
             if (staged) {
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Wi
         int r = modp((-n / 2) * xv, nos);
         const int step = modp(xv, nos);
         T ar = T(0), ai = T(0);
+#pragma unroll 4
         for (int kx = 0; kx < n; kx++) {
             cmac(sH[kx][lane], stw[r], 1, ar, ai);
             r += step;
@@ -215,6 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_fft3_i2(const Fft3Win* __restrict_
         const int step = modp(yv, nos);
         T ar = T(0), ai = T(0);
         const C* c = Ci + (int64_t)x * n * n + kz;
+#pragma unroll 4
         for (int ky = 0; ky < n; ky++) {
             cmac(c[(int64_t)ky * n], tw[r], 1, ar, ai);
             r += step;
@@ -247,6 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_fft3_i3(const Fft3Win* __restrict_
         const int step = modp(zv, nos);
         const C* e = E + ((int64_t)x * By + y) * n;
         T ar = T(0);
+#pragma unroll 4
         for (int kz = 0; kz < n; kz++) {
             const C v = e[kz];
             const C w = tw[r];
@@ -295,6 +300,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
         const int step = modp(kz, nos);
         T ar = T(0), ai = T(0);
         const T* prow = P + y * Bz;
+#pragma unroll 4
         for (int z = 0; z < Bz; z++) {
             const C w = stw[r];
             ar = fma(prow[z], w.x, ar);
@@ -314,6 +320,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
         int r = modp(ky * y0v, nos);
         const int step = modp(ky, nos);
         T ar = T(0), ai = T(0);
+#pragma unroll 4
         for (int y = 0; y < By; y++) {
             cmac(Q[y * n + kz], stw[r], 0, ar, ai);
             r += step;
@@ -349,6 +356,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* _
         int r = modp((-n / 2) * yv, nos);
         const int step = modp(yv, nos);
         T ar = T(0), ai = T(0);
+#pragma unroll 4
         for (int ky = 0; ky < n; ky++) {
             cmac(Cs[ky * n + kz], stw[r], 1, ar, ai);
             r += step;
@@ -370,6 +378,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* _
         const int step = modp(zv, nos);
         T ar = T(0);
         const C* e = E + y * n;
+#pragma unroll 4
         for (int kz = 0; kz < n; kz++) {
             const C v = e[kz];
             const C w = stw[r];
