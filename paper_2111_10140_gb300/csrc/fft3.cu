@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict_
 // Fused middle pass along x for up to 32 consecutive kz of one ky per block:
 // H[kx] = D[kx] sum_x B[x] e^{-2 pi i kx x/nos}, then C[x] = sum_kx H[kx] e^{+...}.
 constexpr int kMidLanes = 32, kMidWarps = 32, kMaxN3 = 64, kMaxBox3 = 256;
+constexpr int kSlabParts = 2;   // blocks per slab in the slab kernels (kz columns forward, y rows inverse)
 // Dynamic shared memory: H (n x 32), the staged lines (Bx x 32) when Bx <= kMidStage, twiddles (nos).
 constexpr int kMidStage = 64;
 template <typename T>
@@ -294,8 +295,11 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
     }
     __syncthreads();
     const int z0v = box_value0(W.lo[2], nos), y0v = box_value0(W.lo[1], nos);
-    for (int i = threadIdx.x; i < By * n; i += blockDim.x) {      // F1: z -> kz
-        const int y = i / n, kz = i % n - n / 2;
+    // this block's share of the kz columns (blockIdx.z of gridDim.z parts)
+    const int ns = (n + gridDim.z - 1) / gridDim.z, kzb = blockIdx.z * ns, kze = min(n, kzb + ns);
+    const int nc = kze - kzb;
+    for (int i = threadIdx.x; i < By * nc; i += blockDim.x) {     // F1: z -> kz
+        const int y = i / nc, kz = kzb + i % nc - n / 2;
         int r = modp(kz * z0v, nos);
         const int step = modp(kz, nos);
         T ar = T(0), ai = T(0);
@@ -311,12 +315,12 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
         C o;
         o.x = ar;
         o.y = ai;
-        Q[i] = o;
+        Q[y * n + kz + n / 2] = o;
     }
     __syncthreads();
     C* __restrict__ Bo = static_cast<C*>(W.buf2);
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {       // F2: y -> ky
-        const int ky = i / n - n / 2, kz = i % n;
+    for (int i = threadIdx.x; i < n * nc; i += blockDim.x) {      // F2: y -> ky
+        const int ky = i / nc - n / 2, kz = kzb + i % nc;
         int r = modp(ky * y0v, nos);
         const int step = modp(ky, nos);
         T ar = T(0), ai = T(0);
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
         C o;
         o.x = ar;
         o.y = ai;
-        Bo[(int64_t)x * n * n + i] = o;
+        Bo[(int64_t)x * n * n + (ky + n / 2) * n + kz] = o;
     }
 }
 
@@ -350,8 +354,10 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* _
     const C* __restrict__ Ci = static_cast<const C*>(W.buf1) + (int64_t)x * n * n;
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) Cs[i] = Ci[i];
     __syncthreads();
-    for (int i = threadIdx.x; i < By * n; i += blockDim.x) {      // I2: ky -> y
-        const int y = i / n, kz = i % n;
+    // this block's share of the y rows (blockIdx.z of gridDim.z parts)
+    const int ys = (By + gridDim.z - 1) / gridDim.z, yb = blockIdx.z * ys, ye = min(By, yb + ys);
+    for (int i = threadIdx.x; i < (ye - yb) * n; i += blockDim.x) {   // I2: ky -> y
+        const int y = yb + i / n, kz = i % n;
         const int yv = modp(W.lo[1] + y, nos) - nos / 2;
         int r = modp((-n / 2) * yv, nos);
         const int step = modp(yv, nos);
@@ -365,13 +371,13 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* _
         C o;
         o.x = ar;
         o.y = ai;
-        E[i] = o;
+        E[y * n + kz] = o;
     }
     __syncthreads();
     T* __restrict__ g = static_cast<T*>(W.grid);
     const int gx = modp(W.lo[0] + x, nos);
-    for (int i = threadIdx.x; i < By * Bz; i += blockDim.x) {     // I3: kz -> z, real part
-        const int y = i / Bz, z = i % Bz;
+    for (int i = threadIdx.x; i < (ye - yb) * Bz; i += blockDim.x) {  // I3: kz -> z, real part
+        const int y = yb + i / Bz, z = i % Bz;
         const int gz = modp(W.lo[2] + z, nos);
         const int zv = gz - nos / 2;
         int r = modp((-n / 2) * zv, nos);
@@ -451,7 +457,7 @@ anova_status fft3_box_run(const Fft3Win* wins, const Fft3Shape& sh, int sm_count
             return true;
         }();
         (void)attrs;
-        const dim3 gs(sh.bx, nw);
+        const dim3 gs(sh.bx, nw, kSlabParts);
         k_fft3_slab_fwd<T><<<gs, kSlabThreads, shf, st>>>(wins);
         k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, mid_bytes<T>(), st>>>(wins);
         k_fft3_slab_inv<T><<<gs, kSlabThreads, shi, st>>>(wins);
