@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kThreads) k_fft3_f2(const Fft3Win* __restrict_
 // Fused middle pass along x for up to 32 consecutive kz of one ky per block:
 // H[kx] = D[kx] sum_x B[x] e^{-2 pi i kx x/nos}, then C[x] = sum_kx H[kx] e^{+...}.
 constexpr int kMidLanes = 32, kMidWarps = 32, kMaxN3 = 64, kMaxBox3 = 256;
-constexpr int kSlabParts = 2;   // blocks per slab in the slab kernels (kz columns forward, y rows inverse)
+constexpr int kSlabParts = 1;   // blocks per slab in the slab kernels (kz columns forward, y rows inverse);
+                                // 2 and 4 measured slower on the mid workload (duplicated staging)
 // Dynamic shared memory: H (n x 32), the staged lines (Bx x 32) when Bx <= kMidStage, twiddles (nos).
 constexpr int kMidStage = 64;
 template <typename T>
