@@ -153,6 +153,7 @@ struct anova_plan {
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
+    bool spread_umma = false;           // FP32 dense 3-D spread on tcgen05 instead of mma.sync
     int bin_side[3] = {0, 0, 0};        // bin side of the dense 1-D / 2-D / 3-D windows (0: the default rule)
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
@@ -277,6 +278,7 @@ bool fft12_box_supported(const WindowPlan& w);
 template <typename T>
 anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st);
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
+anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
 anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin* descs,

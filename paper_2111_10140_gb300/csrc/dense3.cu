@@ -949,6 +949,7 @@ static bool table_kernels(const anova_plan* plan, int R) {
 static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  const void* alpha, int alpha_double, cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
+    if (plan->spread_tc && plan->spread_umma) return spread3_umma(R, sub, nsub, descs, plan->m, st);
     if (plan->spread_tc) {
         switch (R) {
 #define ANOVA_SPREAD_TC(R_) \
