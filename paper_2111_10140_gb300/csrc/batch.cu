@@ -418,7 +418,7 @@ static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t
     ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st));
     ANOVA_TRY(fft3_box_run<float>(b->fft3, b->fft3_shape, b->sm_count, st));
     ANOVA_TRY(fft12_box_run<float>(b->fft12, b->n12, b->smem12, st));
-    return dense_f32_gather_groups(b->m, b->sub, b->desc, b->groups, st);
+    return dense_f32_gather_groups(b->m, b->plans[0]->psi_poly, b->sub, b->desc, b->groups, st);
 }
 
 static anova_status batch_iteration(anova_batch* b, double tol2, int maxit, cudaStream_t st) {
@@ -480,8 +480,9 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
     *out = nullptr;
     for (int p = 0; p < nprob; p++) {
         const anova_plan* pl = plans[p];
-        if (!pl || !(pl->precision & ANOVA_FP32) || pl->N < 1 || pl->m != plans[0]->m) {
-            set_error("anova_batch_create: every plan must hold FP32, have nodes and share the cut-off m");
+        if (!pl || !(pl->precision & ANOVA_FP32) || pl->N < 1 || pl->m != plans[0]->m ||
+            pl->sigma != plans[0]->sigma) {
+            set_error("anova_batch_create: every plan must hold FP32, have nodes and share the cut-off m and sigma");
             return ANOVA_EINVAL;
         }
         for (int l = 0; l < pl->P; l++) {

@@ -975,7 +975,7 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
 static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
-    if (plan->gather_tc && plan->gather_umma) return gather3_umma(R, sub, nsub, descs, plan->m, st);
+    if (plan->gather_tc && plan->gather_umma) return gather3_umma(R, sub, nsub, descs, plan->m, plan->psi_poly, st);
     if (plan->gather_tc) {
         switch (R) {
 #define ANOVA_GATHER_TC(R_) \
@@ -1021,7 +1021,7 @@ anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin
     return ANOVA_OK;
 }
 
-anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin* descs,
+anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st) {
     for (const auto& g : groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
@@ -1032,7 +1032,7 @@ anova_status dense_f32_gather_groups(int m, const int4* sub_base, const DenseWin
 #define ANOVA_G(R_)                                                                           \
     case 100 + R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
     case 200 + R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
-    case 300 + R_: ANOVA_TRY(gather3_umma(R_, sub, nsub, descs, m, st)); break;
+    case 300 + R_: ANOVA_TRY(gather3_umma(R_, sub, nsub, descs, m, poly, st)); break;
             ANOVA_G(4) ANOVA_G(6) ANOVA_G(8) ANOVA_G(10) ANOVA_G(12) ANOVA_G(14) ANOVA_G(16)
 #undef ANOVA_G
             default: set_error("dense FP32 gather: unsupported window dimension or region size"); return ANOVA_EINVAL;

@@ -37,6 +37,10 @@ constexpr uint32_t kUmmaCols = 256;         // tensor-memory columns per block (
 constexpr size_t kUmmaSmem = 64 * 1024;     // shared memory requested per block at least (three blocks per SM:
                                             // two hold tensor memory, the third stages its operands)
 constexpr int kUmmaGroups = kUmmaThreads / 128;   // column groups of the epilogue
+// node weights of the gather: evaluated from each node's cell and offset with the plan's
+// per-interval FP32 window polynomials (true), or read from the plan's weight table
+constexpr bool kGatherPolyW = true;
+constexpr int kPolyFloats = 2 * 8 * kPsiStride;   // coefficients for m <= 8
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -94,7 +98,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 
 template <int R>
 __global__ void __launch_bounds__(kUmmaThreads, kUmmaMinBlocks)
-k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
+k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m,
+               const float* __restrict__ poly) {
     static_assert(R >= 4 && R <= 16 && R % 2 == 0, "even region up to 16");
     constexpr int NP = ((R * R + 15) / 16) * 16;     // MMA N: (a,b) pairs padded to a multiple of 16
     constexpr int NCH = NP / 16;                     // 16-column chunks of the accumulator
@@ -105,7 +110,8 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     float* sBh = sAl + kUmmaTile * 16;               // NP x 16 region rows: heads
     float* sBl = sBh + NP * 16;                      //                      tails
     float* part = sBl + NP * 16;                     // 128 partial sums of warps 4-7
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(part + kUmmaTile);
+    float* sP = part + kUmmaTile;                    // window polynomial coefficients
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sP + kPolyFloats);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
     const int4 sp = sub[blockIdx.x];
@@ -116,6 +122,8 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
     const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (kGatherPolyW)
+        for (int i = tid; i < 2 * m * kPsiStride; i += kUmmaThreads) sP[i] = poly[i];
 
     // B: row n = (a, b), column c: the region cell (a, b, c), zero beyond R.
     // Unit u (4 consecutive c of one row) goes to float4 u of the operand, so
@@ -163,19 +171,43 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
         // bin's nodes) -- one round trip to the weight table per tile.
         const int j = 32 * (warp & 3) + lane;
         const bool valid = j < rows;
-        const float4* wr4 = reinterpret_cast<const float4*>(W.wtab + ((int64_t)sp.y + t0 + (valid ? j : 0)) * 48);
+        const int64_t pos = (int64_t)sp.y + t0 + (valid ? j : 0);
         float wx[16], wy[16];
+        float4 z4[4];
+        if (kGatherPolyW) {
+            // tap r of axis t: psi(cell - Tb bin + m - r + offset), from the node's cell and offset
+            const float* __restrict__ fr = static_cast<const float*>(W.frac);
+            const int64_t Nn = W.N;
+            const int jx = W.cell[pos] - Tb * bx + m, jy = W.cell[Nn + pos] - Tb * by + m;
+            const float fx = fr[pos], fy = fr[Nn + pos];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const float4 x4 = __ldg(wr4 + q);
-            const float4 y4 = __ldg(wr4 + 4 + q);
-            wx[4 * q] = x4.x; wx[4 * q + 1] = x4.y; wx[4 * q + 2] = x4.z; wx[4 * q + 3] = x4.w;
-            wy[4 * q] = y4.x; wy[4 * q + 1] = y4.y; wy[4 * q + 2] = y4.z; wy[4 * q + 3] = y4.w;
+            for (int q = 0; q < 16; q++) {
+                wx[q] = q < R ? psi_poly_eval(sP, jx - q, fx, m) : 0.f;
+                wy[q] = q < R ? psi_poly_eval(sP, jy - q, fy, m) : 0.f;
+            }
+            if (warp < 4) {
+                const int jz = W.cell[2 * Nn + pos] - Tb * bz + m;
+                const float fz = fr[2 * Nn + pos];
+                float wz[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) wz[q] = (valid && q < R) ? psi_poly_eval(sP, jz - q, fz, m) : 0.f;
+#pragma unroll
+                for (int kg = 0; kg < 4; kg++) z4[kg] = make_float4(wz[4 * kg], wz[4 * kg + 1], wz[4 * kg + 2], wz[4 * kg + 3]);
+            }
+        } else {
+            const float4* wr4 = reinterpret_cast<const float4*>(W.wtab + pos * 48);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float4 x4 = __ldg(wr4 + q);
+                const float4 y4 = __ldg(wr4 + 4 + q);
+                wx[4 * q] = x4.x; wx[4 * q + 1] = x4.y; wx[4 * q + 2] = x4.z; wx[4 * q + 3] = x4.w;
+                wy[4 * q] = y4.x; wy[4 * q + 1] = y4.y; wy[4 * q + 2] = y4.z; wy[4 * q + 3] = y4.w;
+            }
+            if (warp < 4)
+#pragma unroll
+                for (int kg = 0; kg < 4; kg++) z4[kg] = valid ? __ldg(wr4 + 8 + kg) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (warp < 4) {
-            float4 z4[4];
-#pragma unroll
-            for (int kg = 0; kg < 4; kg++) z4[kg] = valid ? __ldg(wr4 + 8 + kg) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int kg = 0; kg < 4; kg++) {
                 const float v[4] = {z4[kg].x, z4[kg].y, z4[kg].z, z4[kg].w};
@@ -243,11 +275,12 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
 // shared memory the kernel uses for region size R: A and B heads and tails,
 // the partial sums, the mbarrier and the tensor-memory address
 constexpr size_t umma_need(int R) {
-    return (size_t)(kUmmaTile * 16 * 2 + ((R * R + 15) / 16) * 16 * 16 * 2 + kUmmaTile) * 4 + 16;
+    return (size_t)(kUmmaTile * 16 * 2 + ((R * R + 15) / 16) * 16 * 16 * 2 + kUmmaTile + kPolyFloats) * 4 + 16;
 }
 
 template <int R>
-static void launch_gather_umma(const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
+static void launch_gather_umma(const int4* sub, int nsub, const DenseWin* descs, int m, const float* poly,
+                               cudaStream_t st) {
     constexpr size_t sh = umma_need(R) > kUmmaSmem ? umma_need(R) : kUmmaSmem;   // the floor sets blocks per SM
     static_assert(sh <= 227 * 1024, "shared memory per block");
     static bool attr = [] {
@@ -255,19 +288,24 @@ static void launch_gather_umma(const int4* sub, int nsub, const DenseWin* descs,
         return true;
     }();
     (void)attr;
-    k_gather3_umma<R><<<nsub, kUmmaThreads, sh, st>>>(sub, descs, m);
+    k_gather3_umma<R><<<nsub, kUmmaThreads, sh, st>>>(sub, descs, m, poly);
 }
 
-anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
+anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, const float* poly,
+                          cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
+    if (kGatherPolyW && (m > 8 || !poly)) {
+        set_error("tcgen05 gather: window polynomials missing or m > 8");
+        return ANOVA_EINVAL;
+    }
     switch (R) {
-        case 4: launch_gather_umma<4>(sub, nsub, descs, m, st); break;
-        case 6: launch_gather_umma<6>(sub, nsub, descs, m, st); break;
-        case 8: launch_gather_umma<8>(sub, nsub, descs, m, st); break;
-        case 10: launch_gather_umma<10>(sub, nsub, descs, m, st); break;
-        case 12: launch_gather_umma<12>(sub, nsub, descs, m, st); break;
-        case 14: launch_gather_umma<14>(sub, nsub, descs, m, st); break;
-        case 16: launch_gather_umma<16>(sub, nsub, descs, m, st); break;
+        case 4: launch_gather_umma<4>(sub, nsub, descs, m, poly, st); break;
+        case 6: launch_gather_umma<6>(sub, nsub, descs, m, poly, st); break;
+        case 8: launch_gather_umma<8>(sub, nsub, descs, m, poly, st); break;
+        case 10: launch_gather_umma<10>(sub, nsub, descs, m, poly, st); break;
+        case 12: launch_gather_umma<12>(sub, nsub, descs, m, poly, st); break;
+        case 14: launch_gather_umma<14>(sub, nsub, descs, m, poly, st); break;
+        case 16: launch_gather_umma<16>(sub, nsub, descs, m, poly, st); break;
         default: set_error("tcgen05 gather: unsupported region size"); return ANOVA_EINVAL;
     }
     ANOVA_CHECK_LAUNCH();
