@@ -39,7 +39,7 @@ constexpr size_t kUmmaSmem = 64 * 1024;     // shared memory requested per block
 constexpr int kUmmaGroups = kUmmaThreads / 128;   // column groups of the epilogue
 // node weights of the gather: evaluated from each node's cell and offset with the plan's
 // per-interval FP32 window polynomials (true), or read from the plan's weight table
-constexpr bool kGatherPolyW = true;
+constexpr bool kGatherPolyW = false;   // measured: 71 us against 45 us with the table (mid workload)
 constexpr int kPolyFloats = 2 * 8 * kPsiStride;   // coefficients for m <= 8
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
