@@ -152,7 +152,9 @@ anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, vo
  * FP32 operator (FP64 vectors and scalars); ANOVA_MIXED runs FP32 inner CG
  * inside FP64 iterative refinement until the FP64 residual meets tol.
  * Synchronises `stream`.  Errors: EINVAL (lambda <= 0, tol <= 0 ...),
- * ENOCONV (maxit reached; alpha and relres hold the last iterate).
+ * ENOCONV (maxit reached; alpha and relres hold the last iterate), ETIMEOUT
+ * (a bounded wait inside a kernel gave up during the call, as counted by
+ * anova_wait_timeouts; the result is not to be trusted).
  */
 anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, double* alpha,
                           int32_t nrhs, int64_t ld, double tol, int32_t maxit,

@@ -280,6 +280,7 @@ anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, const float* poly,
                           cudaStream_t st);
 anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
+uint64_t wait_timeouts_on(cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
 anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_base, const DenseWin* descs,

@@ -608,6 +608,7 @@ anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, doub
     }
     CgBuffers B;
     ANOVA_TRY(cg_buffers(plan, maxit, B));
+    const uint64_t waits0 = wait_timeouts_on(st);
     for (int c = 0; c < nrhs; c++) {
         const double* b = y + c * ld;
         double* x = alpha + c * ld;
@@ -629,6 +630,10 @@ anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, doub
         if (relres) relres[c] = rel;
         if (s != ANOVA_OK && s != ANOVA_ENOCONV) return s;
         if (s == ANOVA_ENOCONV) worst = s;
+    }
+    if (wait_timeouts_on(st) != waits0) {
+        set_error("krr_cg_solve: a bounded wait inside a kernel gave up during the solve");
+        return ANOVA_ETIMEOUT;
     }
     return worst;
 }

@@ -518,6 +518,16 @@ anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* desc
     return ANOVA_OK;
 }
 
+// The device counter of abandoned waits, read on `st` (stream-ordered, then
+// synchronised): a synchronous entry point compares it before and after.
+uint64_t wait_timeouts_on(cudaStream_t st) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, g_wait_timeouts, sizeof(v), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return 0;
+    return v;
+}
+
 }  // namespace anova
 
 extern "C" int64_t anova_wait_timeouts(void) {
