@@ -416,3 +416,28 @@ def test_direct_matvec_matches_oracle_direct(B, torch, dtype, tol):
                           torch.from_numpy(w.alpha).cuda(), out, weights=eta, dtype=getattr(B, dtype))
     ref = oracle.direct(Z, w.X, w.windows, eta, w.ell, w.alpha)
     assert rel(out.cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.slow
+def test_precision_form_full_size_sampled(B, torch):
+    """The precision form at its full size (N = 1e6, d = 28, nine windows of 1-3
+    features): on 256 sampled rows the FP64 product is within the fast
+    summation's error of the oracle's direct sum (1e-6 at these parameters) and
+    the FP32 product within 1e-5; over all rows FP32 agrees with FP64 to 1e-5."""
+    w = W.precision_form()
+    X = torch.from_numpy(w.X).cuda()
+    plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                precision=B.MIXED)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    o64 = torch.empty_like(a64)
+    B.anova_matvec(plan, a64, o64)
+    a32 = a64.float()
+    o32 = torch.empty_like(a32)
+    B.anova_matvec(plan, a32, o32)
+    g64, g32 = o64.cpu().numpy(), o32.double().cpu().numpy()
+    assert rel(g32, g64) <= 1e-5
+    idx = np.sort(np.random.default_rng(11).choice(w.N, 256, replace=False))
+    direct = oracle.direct(w.X[idx], w.X, w.windows, w.eta, w.ell, w.alpha)
+    assert rel(g64[idx], direct) <= 1e-6
+    assert rel(g32[idx], direct) <= 1e-5
+    plan.close()
