@@ -40,7 +40,8 @@ constexpr int kUmmaGroups = kUmmaThreads / 128;   // column groups of the epilog
 // node weights of the gather: evaluated from each node's cell and offset with the plan's
 // per-interval FP32 window polynomials (true), or read from the plan's weight table
 constexpr bool kGatherPolyW = false;   // measured: 71 us against 45 us with the table (mid workload)
-constexpr int kPolyFloats = 2 * 8 * kPsiStride;   // coefficients for m <= 8
+constexpr int kPolyFloats = kGatherPolyW ? 2 * 8 * kPsiStride : 0;   // coefficients for m <= 8
+constexpr int kWPitch = 52;                       // staged weight-table rows (floats; conflict-free float4 reads)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -111,7 +112,8 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     float* sBl = sBh + NP * 16;                      //                      tails
     float* part = sBl + NP * 16;                     // 128 partial sums of warps 4-7
     float* sP = part + kUmmaTile;                    // window polynomial coefficients
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sP + kPolyFloats);
+    float* sW = sP + kPolyFloats;                    // 128 x kWPitch: the tile's weight-table rows
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sW + kUmmaTile * kWPitch);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
     const int4 sp = sub[blockIdx.x];
@@ -124,6 +126,20 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (kGatherPolyW)
         for (int i = tid; i < 2 * m * kPsiStride; i += kUmmaThreads) sP[i] = poly[i];
+    // weight-table rows of the tile starting at node t: asynchronous copies into sW,
+    // waited for where they are used (they overlap the region staging and the MMAs)
+    auto prefetch = [&](int t) {
+        if (kGatherPolyW) return;
+        const int rows = min(kUmmaTile, sp.z - t);
+        for (int u = tid; u < rows * 12; u += kUmmaThreads) {
+            const int node = u / 12, k = u - (u / 12) * 12;
+            const float* src = W.wtab + ((int64_t)sp.y + t + node) * 48 + 4 * k;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(sW + node * kWPitch + 4 * k)),
+                         "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    prefetch(0);
 
     // B: row n = (a, b), column c: the region cell (a, b, c), zero beyond R.
     // Unit u (4 consecutive c of one row) goes to float4 u of the operand, so
@@ -195,17 +211,19 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
                 for (int kg = 0; kg < 4; kg++) z4[kg] = make_float4(wz[4 * kg], wz[4 * kg + 1], wz[4 * kg + 2], wz[4 * kg + 3]);
             }
         } else {
-            const float4* wr4 = reinterpret_cast<const float4*>(W.wtab + pos * 48);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            const float4* wr4 = reinterpret_cast<const float4*>(sW + j * kWPitch);
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const float4 x4 = __ldg(wr4 + q);
-                const float4 y4 = __ldg(wr4 + 4 + q);
+                const float4 x4 = wr4[q];
+                const float4 y4 = wr4[4 + q];
                 wx[4 * q] = x4.x; wx[4 * q + 1] = x4.y; wx[4 * q + 2] = x4.z; wx[4 * q + 3] = x4.w;
                 wy[4 * q] = y4.x; wy[4 * q + 1] = y4.y; wy[4 * q + 2] = y4.z; wy[4 * q + 3] = y4.w;
             }
             if (warp < 4)
 #pragma unroll
-                for (int kg = 0; kg < 4; kg++) z4[kg] = valid ? __ldg(wr4 + 8 + kg) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int kg = 0; kg < 4; kg++) z4[kg] = valid ? wr4[8 + kg] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (warp < 4) {
 #pragma unroll
@@ -222,6 +240,7 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (t0 + kUmmaTile < sp.z) prefetch(t0 + kUmmaTile);   // sW is free: every thread holds its weights
         taddr = *tslot;
         if (tid == 0) {
 #pragma unroll
@@ -275,7 +294,8 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
 // shared memory the kernel uses for region size R: A and B heads and tails,
 // the partial sums, the mbarrier and the tensor-memory address
 constexpr size_t umma_need(int R) {
-    return (size_t)(kUmmaTile * 16 * 2 + ((R * R + 15) / 16) * 16 * 16 * 2 + kUmmaTile + kPolyFloats) * 4 + 16;
+    return (size_t)(kUmmaTile * 16 * 2 + ((R * R + 15) / 16) * 16 * 16 * 2 + kUmmaTile + kPolyFloats +
+                    kUmmaTile * kWPitch) * 4 + 16;
 }
 
 template <int R>
