@@ -469,36 +469,16 @@ __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b
 }
 
 constexpr int kTcPitch = 24;   // shared row pitch: rows p and p+1..3 land in distinct bank groups
-
-// cp.async of `cnt` weight-table rows (48 floats each, 16-byte pieces) starting at
-// sorted position `pos0`, and of their sorted coefficients, into raw / ral
-template <int NT, int PITCH>
-__device__ __forceinline__ void spread_prefetch(const float* __restrict__ wtab, const float* __restrict__ asort,
-                                                int64_t pos0, int cnt, float* raw, float* ral, int tid) {
-    for (int u = tid; u < cnt * 12; u += NT) {
-        const int p = u / 12, k = u - (u / 12) * 12;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(raw + p * PITCH + 4 * k)),
-                     "l"(wtab + (pos0 + p) * 48 + 4 * k) : "memory");
-    }
-    for (int p = tid; p < cnt; p += NT)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(ral + p)),
-                     "l"(asort + pos0 + p) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
 template <int R>
 __global__ void __launch_bounds__(32 * ((R + 1) / 2))
 k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
     static_assert(R <= kPitch && R % 2 == 0, "even region up to 16");
     constexpr int NW = R / 2;                  // warps, two b rows each
     constexpr int NT = 32 * NW;
-    constexpr int kRawPitch = 52;              // staged weight-table rows (floats)
     __shared__ __align__(16) uint32_t sxh[kSpreadChunk][kTcPitch];   // alpha wx, TF32 head
     __shared__ __align__(16) uint32_t sxl[kSpreadChunk][kTcPitch];   // and tail
     __shared__ __align__(16) float sy[kSpreadChunk][kTcPitch];
     __shared__ __align__(16) float sz[kSpreadChunk][kTcPitch];
-    __shared__ __align__(16) float raw[kSpreadChunk][kRawPitch];     // next chunk's table rows (cp.async)
-    __shared__ float ral[kSpreadChunk];                              // and sorted coefficients
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
     if (W.live && !*W.live) return;   // a batch system that has stopped
@@ -514,20 +494,18 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
         for (int j = 0; j < 2; j++)
 #pragma unroll
             for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
-    // table rows and coefficients of a chunk, copied asynchronously (spread_prefetch)
-    spread_prefetch<NT, kRawPitch>(W.wtab, W.asort, (int64_t)sp.y, min(kSpreadChunk, sp.z), &raw[0][0], ral, tid);
     for (int first = 0; first < sp.z; first += kSpreadChunk) {
         const int cnt = min(kSpreadChunk, sp.z - first);
         const int cnt8 = (cnt + 7) & ~7;
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         for (int i = tid; i < cnt8 * 12; i += NT) {
             const int p = i / 12, k = i % 12;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             float al = 0.f;
             if (p < cnt) {
-                v = *reinterpret_cast<const float4*>(&raw[p][4 * k]);
-                if (k < 4) al = ral[p];
+                const int64_t pos = (int64_t)sp.y + first + p;
+                v = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
+                if (k < 4) al = W.asort[pos];
             }
             if (k < 4) {
                 const float xs[4] = {al * v.x, al * v.y, al * v.z, al * v.w};
@@ -545,9 +523,6 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
             }
         }
         __syncthreads();
-        if (first + kSpreadChunk < sp.z)   // raw is free again
-            spread_prefetch<NT, kRawPitch>(W.wtab, W.asort, (int64_t)sp.y + first + kSpreadChunk,
-                                           min(kSpreadChunk, sp.z - first - kSpreadChunk), &raw[0][0], ral, tid);
         for (int p0 = 0; p0 < cnt8; p0 += 8) {
             const int pa = p0 + t, pb = p0 + t + 4;
             const float z0 = sz[pa][g], z1 = sz[pa][g + 8], z2 = sz[pb][g], z3 = sz[pb][g + 8];
