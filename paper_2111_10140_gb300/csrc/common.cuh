@@ -288,6 +288,7 @@ anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_b
 // Shapes of a batched 3-D box FFT launch (maxima over its windows).
 struct Fft3Shape {
     int nw = 0, nmax = 0, nosmax = 0, bx = 0, by = 0, bz = 0;
+    int uniform_n = 0;         // n of every window when all share it with n_os = 2 n, else 0
     int64_t t1 = 0, t2 = 0, t3 = 0;
     bool slab = true;
     void add(const WindowPlan& w);

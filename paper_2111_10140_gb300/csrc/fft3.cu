@@ -123,14 +123,15 @@ constexpr int kSlabParts = 1;   // blocks per slab in the slab kernels (kz colum
                                 // 2 and 4 measured slower on the mid workload (duplicated staging)
 // Dynamic shared memory: H (n x 32), the staged lines (Bx x 32) when Bx <= kMidStage, twiddles (nos).
 constexpr int kMidStage = 64;
-template <typename T>
+// NC > 0: every window of the launch has n = NC and n_os = 2 NC (index arithmetic on constants)
+template <typename T, int NC = 0>
 __global__ void __launch_bounds__(kMidLanes * kMidWarps) k_fft3_mid(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char mid_raw[];
     C (*sH)[kMidLanes] = reinterpret_cast<C (*)[kMidLanes]>(mid_raw);
     const Fft3Win W = wins[blockIdx.y];
     if (W.live && !*W.live) return;   // a batch system that has stopped
-    const int n = W.n, nos = W.nos, Bx = W.B[0];
+    const int n = NC ? NC : W.n, nos = NC ? 2 * NC : W.nos, Bx = W.B[0];
     const int lines_per_ky = (n + kMidLanes - 1) / kMidLanes;
     if ((int)blockIdx.x >= n * lines_per_ky) return;
     const int lane = threadIdx.x % kMidLanes, warp = threadIdx.x / kMidLanes;
@@ -274,13 +275,13 @@ __global__ void __launch_bounds__(kThreads) k_fft3_i3(const Fft3Win* __restrict_
 constexpr int kSlab = 64;
 constexpr int kSlabThreads = 1024;
 
-template <typename T>
+template <typename T, int NC = 0>
 __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char slab_raw[];
     const Fft3Win W = wins[blockIdx.y];
     if (W.live && !*W.live) return;   // a batch system that has stopped
-    const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
+    const int n = NC ? NC : W.n, nos = NC ? 2 * NC : W.nos, By = W.B[1], Bz = W.B[2];
     const int x = blockIdx.x;
     if (x >= W.B[0]) return;
     C* stw = reinterpret_cast<C*>(slab_raw);                  // nos twiddles
@@ -338,13 +339,13 @@ __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_fwd(const Fft3Win* _
     }
 }
 
-template <typename T>
+template <typename T, int NC = 0>
 __global__ void __launch_bounds__(kSlabThreads) k_fft3_slab_inv(const Fft3Win* __restrict__ wins) {
     using C = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char slab_raw[];
     const Fft3Win W = wins[blockIdx.y];
     if (W.live && !*W.live) return;   // a batch system that has stopped
-    const int n = W.n, nos = W.nos, By = W.B[1], Bz = W.B[2];
+    const int n = NC ? NC : W.n, nos = NC ? 2 * NC : W.nos, By = W.B[1], Bz = W.B[2];
     const int x = blockIdx.x;
     if (x >= W.B[0]) return;
     C* stw = reinterpret_cast<C*>(slab_raw);       // nos twiddles
@@ -433,6 +434,22 @@ void Fft3Shape::add(const WindowPlan& w) {
     by = std::max(by, w.box_ext[1]);
     bz = std::max(bz, w.box_ext[2]);
     slab = slab && fft3_slab_supported(w);
+    const int un = w.nos == 2 * w.n ? w.n : 0;
+    uniform_n = (nw == 1) ? un : (uniform_n == un ? un : 0);
+}
+
+template <typename T, int NC>
+static void launch_slab(const Fft3Win* wins, dim3 gs, dim3 gm, size_t shf, size_t shi, cudaStream_t st) {
+    static bool attrs = [] {
+        cudaFuncSetAttribute(k_fft3_slab_fwd<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_fft3_slab_inv<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_fft3_mid<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_bytes<T>());
+        return true;
+    }();
+    (void)attrs;
+    k_fft3_slab_fwd<T, NC><<<gs, kSlabThreads, shf, st>>>(wins);
+    k_fft3_mid<T, NC><<<gm, kMidLanes * kMidWarps, mid_bytes<T>(), st>>>(wins);
+    k_fft3_slab_inv<T, NC><<<gs, kSlabThreads, shi, st>>>(wins);
 }
 
 // every window of a descriptor array: one launch per pass for all of them
@@ -452,16 +469,13 @@ anova_status fft3_box_run(const Fft3Win* wins, const Fft3Shape& sh, int sm_count
     if (sh.slab) {
         const size_t shf = slab_fwd_bytes<T>(sh.nosmax, sh.by, sh.bz, nmax);
         const size_t shi = slab_inv_bytes<T>(sh.nosmax, sh.by, nmax);
-        static bool attrs = [] {
-            cudaFuncSetAttribute(k_fft3_slab_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            cudaFuncSetAttribute(k_fft3_slab_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            return true;
-        }();
-        (void)attrs;
         const dim3 gs(sh.bx, nw, kSlabParts);
-        k_fft3_slab_fwd<T><<<gs, kSlabThreads, shf, st>>>(wins);
-        k_fft3_mid<T><<<gm, kMidLanes * kMidWarps, mid_bytes<T>(), st>>>(wins);
-        k_fft3_slab_inv<T><<<gs, kSlabThreads, shi, st>>>(wins);
+        switch (sh.uniform_n) {
+            case 16: launch_slab<T, 16>(wins, gs, gm, shf, shi, st); break;
+            case 32: launch_slab<T, 32>(wins, gs, gm, shf, shi, st); break;
+            case 64: launch_slab<T, 64>(wins, gs, gm, shf, shi, st); break;
+            default: launch_slab<T, 0>(wins, gs, gm, shf, shi, st); break;
+        }
         ANOVA_CHECK_LAUNCH();
         return ANOVA_OK;
     }
