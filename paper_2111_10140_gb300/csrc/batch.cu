@@ -78,6 +78,7 @@ struct anova_batch {
     anova::Fft3Shape fft3_shape;
     anova::Fft12Win* fft12 = nullptr;
     int n12 = 0;
+    int n12_uniform = -1;                          // shared n of the 1-D / 2-D instances (n_os = 2n), else 0
     size_t smem12 = 0;
     double* eta = nullptr;                         // concatenated window weights
     double* lam = nullptr;                         // per system: lambda of its problem (solve)
@@ -417,7 +418,7 @@ static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t
     ANOVA_CUDA_TRY(cudaMemsetAsync(b->grids, 0, b->grid_elems * sizeof(float), st));
     ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st));
     ANOVA_TRY(fft3_box_run<float>(b->fft3, b->fft3_shape, b->sm_count, st));
-    ANOVA_TRY(fft12_box_run<float>(b->fft12, b->n12, b->smem12, st));
+    ANOVA_TRY(fft12_box_run<float>(b->fft12, b->n12, b->smem12, st, b->n12_uniform));
     return dense_f32_gather_groups(b->m, b->plans[0]->psi_poly, b->sub, b->desc, b->groups, st);
 }
 
@@ -623,6 +624,8 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
             }
             f.live = live;
             f12.push_back(f);
+            const int un = w.nos == 2 * w.n ? w.n : 0;
+            b->n12_uniform = (b->n12_uniform < 0) ? un : (b->n12_uniform == un ? un : 0);
             b->smem12 = std::max(b->smem12, fft12_window_smem(w, sizeof(float)));
         }
     }

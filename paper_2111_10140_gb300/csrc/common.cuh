@@ -161,6 +161,7 @@ struct anova_plan {
     std::vector<int> fft12_windows;     // 1-D / 2-D windows on the batched box FFT
     anova::Fft12Win* fft12_desc = nullptr;  // device, 2 x fft12_windows.size(): FP64 then FP32
     size_t fft12_smem64 = 0, fft12_smem32 = 0;   // dynamic shared memory of the launch
+    int fft12_uniform_n = 0;            // n of every such window when all share it with n_os = 2 n, else 0
     void* tmp = nullptr;                // P x N per-window results (8 bytes each)
     double* eta_dev = nullptr;          // P window weights on the device
     // CG state
@@ -276,7 +277,7 @@ template <typename T>
 anova_status fft12_box_all(anova_plan* plan, cudaStream_t st);
 bool fft12_box_supported(const WindowPlan& w);
 template <typename T>
-anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st);
+anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st, int uniform_n);
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, const float* poly,
                           cudaStream_t st);
 anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);

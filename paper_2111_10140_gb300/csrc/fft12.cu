@@ -44,13 +44,14 @@ __device__ __forceinline__ int mod_pos(int64_t a, int m) {
     return r < 0 ? r + m : r;
 }
 
-template <typename T>
+// NC > 0: every window of the launch has n = NC and n_os = 2 NC
+template <typename T, int NC = 0>
 __global__ void __launch_bounds__(kFft12Threads)
 k_fft12_box(const Fft12Win* __restrict__ descs) {
     using C = typename Cplx12<T>::type;
     const Fft12Win d = descs[blockIdx.x];
     if (d.live && !*d.live) return;   // a batch system that has stopped
-    const int n = d.n, nos = d.nos, half = nos / 2;
+    const int n = NC ? NC : d.n, nos = NC ? 2 * NC : d.nos, half = nos / 2;
     const bool two = d.dA == 2;
     const int B0 = two ? d.B[0] : 1, B1 = two ? d.B[1] : d.B[0];
     const int lo0 = two ? d.lo[0] : 0, lo1 = two ? d.lo[1] : d.lo[0];
@@ -186,16 +187,25 @@ size_t fft12_window_smem(const WindowPlan& w, size_t real_bytes) {
     return fft12_smem(w.dA, w.n, w.nos, B0, B1, real_bytes);
 }
 
-template <typename T>
-anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st) {
-    if (nw == 0) return ANOVA_OK;
+template <typename T, int NC>
+static void launch_fft12(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st) {
     static bool attrs = [] {
-        cudaFuncSetAttribute(k_fft12_box<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFft12MaxSmem);
-        cudaFuncSetAttribute(k_fft12_box<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFft12MaxSmem);
+        cudaFuncSetAttribute(k_fft12_box<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFft12MaxSmem);
         return true;
     }();
     (void)attrs;
-    k_fft12_box<T><<<nw, kFft12Threads, smem, st>>>(desc);
+    k_fft12_box<T, NC><<<nw, kFft12Threads, smem, st>>>(desc);
+}
+
+template <typename T>
+anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st, int uniform_n) {
+    if (nw == 0) return ANOVA_OK;
+    switch (uniform_n) {
+        case 16: launch_fft12<T, 16>(desc, nw, smem, st); break;
+        case 32: launch_fft12<T, 32>(desc, nw, smem, st); break;
+        case 64: launch_fft12<T, 64>(desc, nw, smem, st); break;
+        default: launch_fft12<T, 0>(desc, nw, smem, st); break;
+    }
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
 }
@@ -204,11 +214,11 @@ template <typename T>
 anova_status fft12_box_all(anova_plan* plan, cudaStream_t st) {
     const int nw = (int)plan->fft12_windows.size();
     const size_t sh = sizeof(T) == 8 ? plan->fft12_smem64 : plan->fft12_smem32;
-    return fft12_box_run<T>(plan->fft12_desc + (sizeof(T) == 8 ? 0 : nw), nw, sh, st);
+    return fft12_box_run<T>(plan->fft12_desc + (sizeof(T) == 8 ? 0 : nw), nw, sh, st, plan->fft12_uniform_n);
 }
 
-template anova_status fft12_box_run<double>(const Fft12Win*, int, size_t, cudaStream_t);
-template anova_status fft12_box_run<float>(const Fft12Win*, int, size_t, cudaStream_t);
+template anova_status fft12_box_run<double>(const Fft12Win*, int, size_t, cudaStream_t, int);
+template anova_status fft12_box_run<float>(const Fft12Win*, int, size_t, cudaStream_t, int);
 template anova_status fft12_box_all<double>(anova_plan*, cudaStream_t);
 template anova_status fft12_box_all<float>(anova_plan*, cudaStream_t);
 

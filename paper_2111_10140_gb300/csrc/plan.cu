@@ -873,6 +873,8 @@ static anova_status build_fft12_batch(anova_plan* plan, cudaStream_t st) {
     plan->fft12_smem64 = plan->fft12_smem32 = 0;
     for (int k = 0; k < nw; k++) {
         const WindowPlan& w = plan->win[plan->fft12_windows[k]];
+        const int un = w.nos == 2 * w.n ? w.n : 0;
+        plan->fft12_uniform_n = (k == 0) ? un : (plan->fft12_uniform_n == un ? un : 0);
         plan->fft12_smem64 = std::max(plan->fft12_smem64, fft12_window_smem(w, sizeof(double)));
         plan->fft12_smem32 = std::max(plan->fft12_smem32, fft12_window_smem(w, sizeof(float)));
         for (int prec = 0; prec < 2; prec++) {
