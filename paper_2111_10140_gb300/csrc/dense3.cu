@@ -689,56 +689,86 @@ k_gather3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
 // (R^2 or R multiply-adds), so one warp accumulates a sub-problem's region in
 // registers and adds it to the grid once, and the gather is one thread per node.
 
-// 2-D spread: lane (a = lane/2, half h) keeps cells (a, 8h .. 8h+7).
+// 2-D spread: a block of kGroupWarps warps takes as many consecutive
+// sub-problems, one per warp; lane (a = lane/2, half h) keeps cells
+// (a, 8h .. 8h+7) of its warp's region.  Warps whose sub-problems share a bin
+// (consecutive in the list) add their regions in shared memory and the first
+// of them adds the sum to the grid: with many nodes per cell the grid atomics,
+// contended by every sub-problem of the neighbouring bins, are the cost.
+constexpr int kGroupWarps = 8;
+constexpr int kGroupChunk = 32;            // nodes staged per warp at a time
+
 template <int R>
-__global__ void __launch_bounds__(32) k_spread2_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
-                                                    int m) {
+__global__ void __launch_bounds__(32 * kGroupWarps) k_spread2_f32(const int4* __restrict__ sub,
+                                                                  const DenseWin* __restrict__ descs, int m,
+                                                                  int nsub) {
     static_assert(R <= kPitch, "region up to 16");
-    __shared__ __align__(16) float sx[kSpreadChunk][kPitch];
-    __shared__ __align__(16) float sy[kSpreadChunk][kPitch];
-    const int4 sp = sub[blockIdx.x];
-    const DenseWin W = descs[sp.w];
-    if (W.live && !*W.live) return;   // a batch system that has stopped
-    float* __restrict__ grid = static_cast<float*>(W.grid);
-    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
-    const int by = sp.x % nb, bx = sp.x / nb;
-    const int lane = threadIdx.x, a = lane >> 1, h = lane & 1;
+    __shared__ __align__(16) float sx[kGroupWarps][kGroupChunk][kPitch];
+    __shared__ __align__(16) float sy[kGroupWarps][kGroupChunk][kPitch];
+    __shared__ __align__(16) float red[kGroupWarps][16][16];
+    __shared__ int key[kGroupWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = lane >> 1, h = lane & 1;
+    const int si = blockIdx.x * kGroupWarps + warp;
+    int4 sp = make_int4(0, 0, 0, 0);
+    bool active = si < nsub;
+    if (active) sp = sub[si];
+    const DenseWin W = descs[active ? sp.w : sub[blockIdx.x * kGroupWarps].w];
+    if (active && W.live && !*W.live) active = false;   // a batch system that has stopped
     float acc[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) acc[k] = 0.f;
-    for (int first = 0; first < sp.z; first += kSpreadChunk) {
-        const int cnt = min(kSpreadChunk, sp.z - first);
-        __syncwarp();
-        for (int i = lane; i < cnt * 8; i += 32) {
-            const int p = i >> 3, k = i & 7;
-            const int64_t pos = (int64_t)sp.y + first + p;
-            float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 32)[k];
-            if (k < 4) {
-                const float al = W.asort[pos];
-                v.x *= al; v.y *= al; v.z *= al; v.w *= al;
-                reinterpret_cast<float4*>(sx[p])[k] = v;
-            } else {
-                reinterpret_cast<float4*>(sy[p])[k - 4] = v;
+    if (active) {
+        for (int first = 0; first < sp.z; first += kGroupChunk) {
+            const int cnt = min(kGroupChunk, sp.z - first);
+            __syncwarp();
+            for (int i = lane; i < cnt * 8; i += 32) {
+                const int p = i >> 3, k = i & 7;
+                const int64_t pos = (int64_t)sp.y + first + p;
+                float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 32)[k];
+                if (k < 4) {
+                    const float al = W.asort[pos];
+                    v.x *= al; v.y *= al; v.z *= al; v.w *= al;
+                    reinterpret_cast<float4*>(sx[warp][p])[k] = v;
+                } else {
+                    reinterpret_cast<float4*>(sy[warp][p])[k - 4] = v;
+                }
             }
+            __syncwarp();
+            if (a < R)
+                for (int p = 0; p < cnt; p++) {
+                    const float wa = sx[warp][p][a];
+                    const float4 y0 = *reinterpret_cast<const float4*>(&sy[warp][p][8 * h]);
+                    const float4 y1 = *reinterpret_cast<const float4*>(&sy[warp][p][8 * h + 4]);
+                    acc[0] = fmaf(wa, y0.x, acc[0]); acc[1] = fmaf(wa, y0.y, acc[1]);
+                    acc[2] = fmaf(wa, y0.z, acc[2]); acc[3] = fmaf(wa, y0.w, acc[3]);
+                    acc[4] = fmaf(wa, y1.x, acc[4]); acc[5] = fmaf(wa, y1.y, acc[5]);
+                    acc[6] = fmaf(wa, y1.z, acc[6]); acc[7] = fmaf(wa, y1.w, acc[7]);
+                }
         }
-        __syncwarp();
-        if (a < R)
-            for (int p = 0; p < cnt; p++) {
-                const float wa = sx[p][a];
-                const float4 y0 = *reinterpret_cast<const float4*>(&sy[p][8 * h]);
-                const float4 y1 = *reinterpret_cast<const float4*>(&sy[p][8 * h + 4]);
-                acc[0] = fmaf(wa, y0.x, acc[0]); acc[1] = fmaf(wa, y0.y, acc[1]);
-                acc[2] = fmaf(wa, y0.z, acc[2]); acc[3] = fmaf(wa, y0.w, acc[3]);
-                acc[4] = fmaf(wa, y1.x, acc[4]); acc[5] = fmaf(wa, y1.y, acc[5]);
-                acc[6] = fmaf(wa, y1.z, acc[6]); acc[7] = fmaf(wa, y1.w, acc[7]);
-            }
     }
+    if (a < 16)
+#pragma unroll
+        for (int k = 0; k < 8; k++) red[warp][a][8 * h + k] = acc[k];
+    if (lane == 0) {
+        key[warp][0] = active ? sp.x : -1;
+        key[warp][1] = active ? sp.w : -1;
+    }
+    __syncthreads();
+    const bool leader = active && (warp == 0 || key[warp - 1][0] != sp.x || key[warp - 1][1] != sp.w);
+    if (!leader) return;
+    int last = warp;
+    while (last + 1 < kGroupWarps && key[last + 1][0] == sp.x && key[last + 1][1] == sp.w) last++;
+    float* __restrict__ grid = static_cast<float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int by = sp.x % nb, bx = sp.x / nb;
     if (a < R) {
         const int ga = wrap_idx(Tb * bx - m + a, nos);
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             const int c = 8 * h + k;
-            if (c < R) atomicAdd(&grid[ga * nos + wrap_idx(Tb * by - m + c, nos)], acc[k]);
+            float v = 0.f;
+            for (int w2 = warp; w2 <= last; w2++) v += red[w2][a][c];
+            if (c < R) atomicAdd(&grid[ga * nos + wrap_idx(Tb * by - m + c, nos)], v);
         }
     }
 }
@@ -789,36 +819,57 @@ __global__ void __launch_bounds__(128) k_gather2_f32(const int4* __restrict__ su
     }
 }
 
-// 1-D spread: lane a < R keeps cell a.
+// 1-D spread: as the 2-D one, lane a < R of each warp keeps cell a of its
+// sub-problem's region; warps sharing a bin add up before the grid atomics.
 template <int R>
-__global__ void __launch_bounds__(32) k_spread1_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
-                                                    int m) {
+__global__ void __launch_bounds__(32 * kGroupWarps) k_spread1_f32(const int4* __restrict__ sub,
+                                                                  const DenseWin* __restrict__ descs, int m,
+                                                                  int nsub) {
     static_assert(R <= kPitch, "region up to 16");
-    __shared__ __align__(16) float sx[kSpreadChunk][kPitch];
-    const int4 sp = sub[blockIdx.x];
-    const DenseWin W = descs[sp.w];
-    if (W.live && !*W.live) return;   // a batch system that has stopped
-    float* __restrict__ grid = static_cast<float*>(W.grid);
-    const int nos = W.nos, Tb = W.Tb;
-    const int bx = sp.x;
-    const int lane = threadIdx.x;
+    __shared__ __align__(16) float sx[kGroupWarps][kGroupChunk][kPitch];
+    __shared__ float red[kGroupWarps][32];
+    __shared__ int key[kGroupWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int si = blockIdx.x * kGroupWarps + warp;
+    int4 sp = make_int4(0, 0, 0, 0);
+    bool active = si < nsub;
+    if (active) sp = sub[si];
+    const DenseWin W = descs[active ? sp.w : sub[blockIdx.x * kGroupWarps].w];
+    if (active && W.live && !*W.live) active = false;   // a batch system that has stopped
     float acc = 0.f;
-    for (int first = 0; first < sp.z; first += kSpreadChunk) {
-        const int cnt = min(kSpreadChunk, sp.z - first);
-        __syncwarp();
-        for (int i = lane; i < cnt * 4; i += 32) {
-            const int p = i >> 2, k = i & 3;
-            const int64_t pos = (int64_t)sp.y + first + p;
-            float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 16)[k];
-            const float al = W.asort[pos];
-            v.x *= al; v.y *= al; v.z *= al; v.w *= al;
-            reinterpret_cast<float4*>(sx[p])[k] = v;
+    if (active) {
+        for (int first = 0; first < sp.z; first += kGroupChunk) {
+            const int cnt = min(kGroupChunk, sp.z - first);
+            __syncwarp();
+            for (int i = lane; i < cnt * 4; i += 32) {
+                const int p = i >> 2, k = i & 3;
+                const int64_t pos = (int64_t)sp.y + first + p;
+                float4 v = reinterpret_cast<const float4*>(W.wtab + pos * 16)[k];
+                const float al = W.asort[pos];
+                v.x *= al; v.y *= al; v.z *= al; v.w *= al;
+                reinterpret_cast<float4*>(sx[warp][p])[k] = v;
+            }
+            __syncwarp();
+            if (lane < R)
+                for (int p = 0; p < cnt; p++) acc += sx[warp][p][lane];
         }
-        __syncwarp();
-        if (lane < R)
-            for (int p = 0; p < cnt; p++) acc += sx[p][lane];
     }
-    if (lane < R) atomicAdd(&grid[wrap_idx(Tb * bx - m + lane, nos)], acc);
+    red[warp][lane] = acc;
+    if (lane == 0) {
+        key[warp][0] = active ? sp.x : -1;
+        key[warp][1] = active ? sp.w : -1;
+    }
+    __syncthreads();
+    const bool leader = active && (warp == 0 || key[warp - 1][0] != sp.x || key[warp - 1][1] != sp.w);
+    if (!leader) return;
+    int last = warp;
+    while (last + 1 < kGroupWarps && key[last + 1][0] == sp.x && key[last + 1][1] == sp.w) last++;
+    if (lane < R) {
+        float v = 0.f;
+        for (int w2 = warp; w2 <= last; w2++) v += red[w2][lane];
+        float* __restrict__ grid = static_cast<float*>(W.grid);
+        atomicAdd(&grid[wrap_idx(W.Tb * sp.x - m + lane, W.nos)], v);
+    }
 }
 
 // 1-D gather: one thread per node.
@@ -1009,8 +1060,8 @@ anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin
         if (nsub == 0) continue;
         switch (dA * 100 + R) {
 #define ANOVA_S(R_)                                                                           \
-    case 100 + R_: k_spread1_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, m); break;              \
-    case 200 + R_: k_spread2_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, m); break;              \
+    case 100 + R_: k_spread1_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, m, nsub); break;              \
+    case 200 + R_: k_spread2_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, m, nsub); break;              \
     case 300 + R_: k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, m); break;
             ANOVA_S(4) ANOVA_S(6) ANOVA_S(8) ANOVA_S(10) ANOVA_S(12) ANOVA_S(14) ANOVA_S(16)
 #undef ANOVA_S
@@ -1059,14 +1110,14 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
             if (sizeof(T) != 4 || !plan->dense_asort) continue;   // FP64: generic kernels per window
             if (dA == 2) {
                 switch (R) {
-#define ANOVA_S2(R_) case R_: k_spread2_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, plan->m); break;
+#define ANOVA_S2(R_) case R_: k_spread2_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, plan->m, nsub); break;
                     ANOVA_S2(4) ANOVA_S2(6) ANOVA_S2(8) ANOVA_S2(10) ANOVA_S2(12) ANOVA_S2(14) ANOVA_S2(16)
 #undef ANOVA_S2
                     default: set_error("dense 2-D spread: unsupported region size"); return ANOVA_EINVAL;
                 }
             } else {
                 switch (R) {
-#define ANOVA_S1(R_) case R_: k_spread1_f32<R_><<<nsub, 32, 0, st>>>(sub, descs, plan->m); break;
+#define ANOVA_S1(R_) case R_: k_spread1_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, plan->m, nsub); break;
                     ANOVA_S1(4) ANOVA_S1(6) ANOVA_S1(8) ANOVA_S1(10) ANOVA_S1(12) ANOVA_S1(14) ANOVA_S1(16)
 #undef ANOVA_S1
                     default: set_error("dense 1-D spread: unsupported region size"); return ANOVA_EINVAL;
