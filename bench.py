@@ -614,6 +614,75 @@ def run_batch(args):
         pl.close()
 
 
+def run_precision(args):
+    """Precision form (N = 1e6, d = 28, nine windows of 1-3 features): FP32 and
+    FP64 products, the mixed-precision KRR solve to 1e-8 against the FP64
+    operator, and the FP32 product's error against the FP64 direct sum on a
+    10 000-row subsample."""
+    import time
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    from paper_2111_10140_gb300 import workloads as W
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    w = W.precision_form()
+    X = torch.from_numpy(w.X).to(dev)
+    sides, _ = B.anova_autotune_bins(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                     precision=B.FP32, reps=10)
+    plan = B.anova_fastsum_plan_bins(X, w.windows, w.ell, sides, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
+                                     precision=B.MIXED)
+    a64 = torch.from_numpy(w.alpha).to(dev)
+    a32 = a64.float()
+    o64, o32 = torch.empty_like(a64), torch.empty_like(a32)
+
+    def timeit(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t32 = timeit(lambda: B.anova_matvec(plan, a32, o32), 20)
+    t64 = timeit(lambda: B.anova_matvec(plan, a64, o64), 3)
+    B.anova_set_profiling(plan, True)
+    B.anova_matvec(plan, a32, o32)
+    torch.cuda.synchronize()
+    stages = B.anova_stage_times(plan)[0]
+    B.anova_set_profiling(plan, False)
+    rows = torch.from_numpy(np.sort(np.random.default_rng(3).choice(w.N, 10_000, replace=False))).to(dev)
+    dref = torch.empty(rows.numel(), dtype=torch.float64, device=dev)
+    B.anova_direct_matvec(X[rows].contiguous(), X, w.windows, w.ell, a64, dref)
+    B.anova_matvec(plan, a32, o32)
+    B.anova_matvec(plan, a64, o64)
+    torch.cuda.synchronize()
+    err32 = (torch.linalg.norm(o32.double()[rows] - dref) / torch.linalg.norm(dref)).item()
+    err64 = (torch.linalg.norm(o64[rows] - dref) / torch.linalg.norm(dref)).item()
+    y = torch.from_numpy(w.y).to(dev)
+    alpha = torch.zeros_like(y)
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    st, its, rr = B.krr_cg_solve(plan, w.lam, y, alpha, w.tol, 20000)
+    torch.cuda.synchronize()
+    t_krr = time.perf_counter() - s0
+    print(json.dumps({
+        "precision_form": True, "workload": w.name, "N": w.N, "windows": [len(x) for x in w.windows],
+        "bin_side_1d_2d_3d": sides, "fp32_matvec_ms": t32, "fp64_matvec_ms": t64,
+        "fp32_stage_ms": dict(zip(["spread", "fft", "gather", "window_sum"], [round(x, 4) for x in stages])),
+        "rel_err_vs_direct_10k": {"fp32": err32, "fp64": err64},
+        "krr_mixed": {"status": int(st), "seconds": round(t_krr, 3), "iterations": int(its[0]),
+                      "relres_fp64": float(rr[0]), "tol": w.tol, "lambda": w.lam}}), flush=True)
+    plan.close()
+
+
 def run_autotune(args):
     """Bin sides chosen by anova_autotune_bins for the mid workload and the
     precision form, against the default rule."""
@@ -661,6 +730,8 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-models", type=int, default=4)
     ap.add_argument("--serve-fit-pool", type=int, default=6)
+    ap.add_argument("--precision-form", action="store_true",
+                    help="precision form (N = 1e6, nine windows): products, mixed KRR to 1e-8, error vs direct")
     ap.add_argument("--autotune", action="store_true", help="bin sides chosen by the autotuner (mid, precision form)")
     ap.add_argument("--batch", action="store_true",
                     help="batching form: many problems x right-hand sides in one batched CG")
@@ -683,6 +754,8 @@ def main():
         run_batch(args)
     elif args.autotune:
         run_autotune(args)
+    elif args.precision_form:
+        run_precision(args)
     else:
         run_ours(args)
 
