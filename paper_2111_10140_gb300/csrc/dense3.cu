@@ -471,7 +471,8 @@ __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b
 constexpr int kTcPitch = 24;   // shared row pitch: rows p and p+1..3 land in distinct bank groups
 template <int R>
 __global__ void __launch_bounds__(32 * ((R + 1) / 2))
-k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
+k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m,
+             const void* __restrict__ alpha = nullptr, int alpha_double = 0) {
     static_assert(R <= kPitch && R % 2 == 0, "even region up to 16");
     constexpr int NW = R / 2;                  // warps, two b rows each
     constexpr int NT = 32 * NW;
@@ -505,7 +506,12 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
             if (p < cnt) {
                 const int64_t pos = (int64_t)sp.y + first + p;
                 v = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
-                if (k < 4) al = W.asort[pos];
+                // the coefficient of the node: gathered through the permutation from the
+                // caller's vector (L2-resident), or the sorted copy of a batch instance
+                if (k < 4)
+                    al = !alpha ? W.asort[pos]
+                                : alpha_double ? (float)static_cast<const double*>(alpha)[W.perm[pos]]
+                                               : static_cast<const float*>(alpha)[W.perm[pos]];
             }
             if (k < 4) {
                 const float xs[4] = {al * v.x, al * v.y, al * v.z, al * v.w};
@@ -1004,7 +1010,7 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
     if (plan->spread_tc) {
         switch (R) {
 #define ANOVA_SPREAD_TC(R_) \
-    case R_: k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, plan->m); ANOVA_CHECK_LAUNCH(); return ANOVA_OK;
+    case R_: k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, plan->m, alpha, alpha_double); ANOVA_CHECK_LAUNCH(); return ANOVA_OK;
             ANOVA_SPREAD_TC(4) ANOVA_SPREAD_TC(6) ANOVA_SPREAD_TC(8) ANOVA_SPREAD_TC(10) ANOVA_SPREAD_TC(12)
             ANOVA_SPREAD_TC(14) ANOVA_SPREAD_TC(16)
 #undef ANOVA_SPREAD_TC
@@ -1097,7 +1103,12 @@ template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
-    if (sizeof(T) == 4 && plan->dense_asort) {
+    // the sorted coefficient copies serve the 1-D / 2-D kernels and the packed
+    // FP32 3-D ones; the tensor-core 3-D spread gathers through the permutation
+    bool need_sort = false;
+    for (const auto& g : plan->dense_groups)
+        if (g[0] / 100 < 3 || !plan->spread_tc || plan->spread_umma) need_sort = true;
+    if (sizeof(T) == 4 && plan->dense_asort && need_sort) {
         k_sort_alpha<<<grid_for(plan->N * nd, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
             descs, nd, plan->N, alpha, alpha_double);
         ANOVA_CHECK_LAUNCH();
