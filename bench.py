@@ -54,6 +54,22 @@ def traffic_per_launch(name):
     return TRAFFIC.get(name)
 
 
+def max_over_ranks(ms, ws, device=None):
+    """The largest per-rank time (all_reduce MAX over the process group); ms itself at ws == 1."""
+    if ws == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gpts(n_per_rank, ws, steps, total_ms):
+    """Whole-job throughput of ws replicas, each processing n_per_rank points per step."""
+    return ws * n_per_rank * steps / (total_ms * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,13 +262,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     stage_ms, stage_launch = B.anova_stage_times(plan)
     B.anova_set_profiling(plan, False)
-    total_ms = sum(step_ms)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * N * args.steps / (total_ms * 1e-3) / 1e9
+    value = aggregate_gpts(N, ws, args.steps, total_ms)
     launches = int(sum(stage_launch))
 
     # dominant kernel: spread (stage 0) or gather (stage 2); the dense 3-D kernels
@@ -307,10 +319,7 @@ def run_ours(args):
         e_ev.synchronize()
         if i >= args.warmup:
             e2e_ms.append(s_ev.elapsed_time(e_ev))
-    e2e_t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * N * args.steps / (float(e2e_t.item()) * 1e-3) / 1e9
+    e2e_value = aggregate_gpts(N, ws, args.steps, max_over_ranks(sum(e2e_ms), ws, dev))
 
     # KRR solves/s (mixed precision: FP32 inner CG, FP64 refinement) to the workload's tolerance
     krr = None
