@@ -46,8 +46,7 @@ def tf32_peak_tflops():
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture of the
 # current kernels on this workload (profiles/); None for a kernel not captured since it changed
-TRAFFIC = {"k_spread3_tc<14>": 59281920 + 11520, "k_spread3_tc<16>": 59310336 + 10880,
-           "k_gather3_umma<16>": 59438000 + 4250}
+TRAFFIC = {"k_gather3_umma<16>": 59438000 + 4250}
 
 
 def traffic_per_launch(name):
