@@ -38,53 +38,62 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
+def compile_library(src: str, out: str) -> str:
+    """Compile one C source of the oracle into a shared library with gcc (FP64, OpenMP)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile anova_oracle.c into a shared library with gcc (FP64, OpenMP)."""
+    """Compile anova_oracle.c into the package's shared library."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_library(_SRC, _LIB_PATH)
+
+
+def bind(lib):
+    """Declare the C signatures on a loaded oracle library and return it."""
+    d, i, L, p_d, p_i = (ctypes.c_double, ctypes.c_int, ctypes.c_long, _dp, _ip)
+    sig = {
+        "orc_direct": (None, [p_d, L, L, p_d, L, L, p_i, i, p_d, d, p_d, p_d]),
+        "orc_window_frame": (None, [p_d, L, L, p_d, L, L, p_i, d, p_d, p_d]),
+        "orc_bessel_i0": (d, [d]),
+        "orc_kb_phi": (d, [d, i, d]),
+        "orc_kb_phihat": (d, [L, L, i, d]),
+        "orc_gauss_deriv": (d, [i, d, d]),
+        "orc_two_point_taylor": (d, [d, d, d, i, d, d]),
+        "orc_kreg": (d, [d, d, d, i]),
+        "orc_kernel_coeffs": (None, [i, i, d, d, i, p_d, p_d]),
+        "orc_diag": (None, [i, i, i, i, d, p_d, p_d]),
+        "orc_spread": (None, [p_d, L, i, i, i, d, p_d, p_d]),
+        "orc_gather": (None, [p_d, L, i, i, i, d, p_d, p_d]),
+        "orc_grid_dft": (None, [p_d, i, i, i, p_d, p_d]),
+        "orc_grid_idft": (None, [p_d, p_d, i, i, i, p_d, p_d]),
+        "orc_adjoint_ndft": (None, [p_d, L, i, i, p_d, p_d, p_d]),
+        "orc_adjoint_nfft": (None, [p_d, L, i, i, i, i, d, p_d, p_d, p_d]),
+        "orc_nfft_real": (None, [p_d, L, i, i, i, i, d, p_d, p_d, p_d]),
+        "orc_fastsum_window": (None, [p_d, L, p_d, L, i, i, i, i, d, p_d, p_d, p_d, p_d, p_d]),
+        "orc_fastsum": (i, [p_d, L, L, p_d, L, L, p_i, i, p_d, d, p_i, i, d, d, i, p_d, p_d]),
+        "orc_cg": (i, [p_d, L, L, p_i, i, p_d, d, p_i, i, d, d, i, i, d, p_d, d, i, p_d, p_d]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            d, i, L, p_d, p_i = (ctypes.c_double, ctypes.c_int, ctypes.c_long, _dp, _ip)
-            sig = {
-                "orc_direct": (None, [p_d, L, L, p_d, L, L, p_i, i, p_d, d, p_d, p_d]),
-                "orc_window_frame": (None, [p_d, L, L, p_d, L, L, p_i, d, p_d, p_d]),
-                "orc_bessel_i0": (d, [d]),
-                "orc_kb_phi": (d, [d, i, d]),
-                "orc_kb_phihat": (d, [L, L, i, d]),
-                "orc_gauss_deriv": (d, [i, d, d]),
-                "orc_two_point_taylor": (d, [d, d, d, i, d, d]),
-                "orc_kreg": (d, [d, d, d, i]),
-                "orc_kernel_coeffs": (None, [i, i, d, d, i, p_d, p_d]),
-                "orc_diag": (None, [i, i, i, i, d, p_d, p_d]),
-                "orc_spread": (None, [p_d, L, i, i, i, d, p_d, p_d]),
-                "orc_gather": (None, [p_d, L, i, i, i, d, p_d, p_d]),
-                "orc_grid_dft": (None, [p_d, i, i, i, p_d, p_d]),
-                "orc_grid_idft": (None, [p_d, p_d, i, i, i, p_d, p_d]),
-                "orc_adjoint_ndft": (None, [p_d, L, i, i, p_d, p_d, p_d]),
-                "orc_adjoint_nfft": (None, [p_d, L, i, i, i, i, d, p_d, p_d, p_d]),
-                "orc_nfft_real": (None, [p_d, L, i, i, i, i, d, p_d, p_d, p_d]),
-                "orc_fastsum_window": (None, [p_d, L, p_d, L, i, i, i, i, d, p_d, p_d, p_d, p_d, p_d]),
-                "orc_fastsum": (i, [p_d, L, L, p_d, L, L, p_i, i, p_d, d, p_i, i, d, d, i, p_d, p_d]),
-                "orc_cg": (i, [p_d, L, L, p_i, i, p_d, d, p_i, i, d, d, i, i, d, p_d, d, i, p_d, p_d]),
-            }
-            for name, (res, args) in sig.items():
-                fn = getattr(lib, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = lib
+            _lib = bind(ctypes.CDLL(build()))
     return _lib
 
 

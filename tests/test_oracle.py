@@ -330,10 +330,15 @@ def test_fastsum_linear_over_windows_and_translation_invariant():
 def test_fastsum_predict_frame_rule():
     """Test points outside the ball of the training frame switch to the joint
     frame; the result is still the kernel sum of Eq. (kernelsum)."""
-    w = W.random_problem(300, 2, [(0, 1)], 0.1, 32, 4, seed=12)
-    Zin = w.X[:40] * 0.5
-    Zout = w.X[:40] * 1.6
-    for Z in (Zin, Zout):
+    RB = 0.25 - 1 / 32
+    # Zout reaches radius 0.45 of the training frame: pairs further apart than
+    # 1/2 - epsB there would meet the periodisation (about 7e-4 error with
+    # ell = 0.15), so only the joint frame meets the tolerance.
+    for scale, ell in ((0.5, 0.1), (2.5, 0.15)):
+        w = W.random_problem(300, 2, [(0, 1)], ell, 32, 4, seed=12)
+        Z = w.X[:40] * scale
+        c, s = oracle.window_frame(w.X, (0, 1), RB)
+        assert (s * np.linalg.norm(Z - c, axis=1).max() > RB) == (scale > 1)
         d = oracle.direct(Z, w.X, w.windows, w.eta, w.ell, w.alpha)
         f = oracle.fastsum(Z, w.X, w.windows, w.eta, w.ell, [32], 4, w.alpha, epsB=1 / 16)
         assert rel(f, d) <= 1e-6
