@@ -6,15 +6,20 @@ copy on the CPU, points the oracle's wrapper at it and runs the pins of
 ``test_oracle.py`` that guard that part.  At least one of them must fail.  The
 unmodified source, compiled the same way, must pass the same pins (the
 control), so a failure is due to the planted mistake and not to the harness.
+The window-construction reference ``oracle/features.py`` gets the same
+treatment against the pins of ``test_oracle_features.py``.
 """
 import ctypes
 import os
+import types
 
 import numpy as np
 import pytest
 
 import oracle
 import test_oracle as T
+import test_oracle_features as TF
+from oracle import features as FEAT
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "anova_oracle.c")
 
@@ -196,3 +201,61 @@ def test_pins_catch_planted_mistake(tmp_path, monkeypatch, source, mid, old, new
     with np.errstate(all="ignore"):
         with pytest.raises((AssertionError, ValueError, np.linalg.LinAlgError, FloatingPointError)):
             PIN_GROUPS[group]()
+
+
+# ------------------------------------------------- window construction (numpy)
+FEAT_SRC = FEAT.__file__
+
+
+def pins_features():
+    for name in dir(TF):
+        if name.startswith("test_"):
+            getattr(TF, name)()
+
+
+FEAT_MUTANTS = [
+    ("zscore_sample_divisor", "std = np.sqrt(((X - mean) ** 2).sum(axis=0) / N)",
+     "std = np.sqrt(((X - mean) ** 2).sum(axis=0) / (N - 1))"),
+    ("zscore_constant_column", "std = np.where(std > 0.0, std, 1.0)", "std = std + 0.0"),
+    ("zscore_apply_variance", "return (np.asarray(X, dtype=np.float64) - mean) / std",
+     "return (np.asarray(X, dtype=np.float64) - mean) / std ** 2"),
+    ("fine_last_bin_open", "return min(max(j, 0), F - 1)", "return max(j, 0)"),
+    ("fine_rounds", "j = int(math.floor((v - lo) * F / (hi - lo)))", "j = int(round((v - lo) * F / (hi - lo)))"),
+    ("quantile_counts_shifted", "C = np.concatenate([[0], np.cumsum(c)[:-1]])", "C = np.cumsum(c)"),
+    ("mis_missing_N", "math.log(N * n[a, y] / (nq[a] * ny[y]))", "math.log(n[a, y] / (nq[a] * ny[y]))"),
+    ("mis_conditional_weight", "s += (n[a, y] / N) * math.log", "s += (n[a, y] / nq[a]) * math.log"),
+    ("mis_class_marginal", "ny = n.sum(axis=0)", "ny = n.sum(axis=0) * 0 + n.sum(axis=0).max()"),
+    ("windows_ascending", "key=lambda f: (-scores[f], f)", "key=lambda f: (scores[f], f)"),
+    ("windows_tie_order", "key=lambda f: (-scores[f], f)", "key=lambda f: (-scores[f], -f)"),
+    ("windows_strict_threshold", "if scores[f] >= threshold", "if scores[f] > threshold"),
+    ("windows_pairs", "tuple(keep[i:i + 3])", "tuple(keep[i:i + 2])"),
+]
+
+
+def _load_feature_mutant(text):
+    mod = types.ModuleType("oracle.features_mutant")
+    exec(compile(text, FEAT_SRC, "exec"), mod.__dict__)
+    return mod
+
+
+def _patch_features(monkeypatch, mod):
+    for name in ("zscore_fit", "zscore_apply", "fine_index", "quantile_bins", "mis", "windows_from_mis"):
+        monkeypatch.setattr(FEAT, name, getattr(mod, name))
+
+
+def test_features_control_passes(monkeypatch):
+    with open(FEAT_SRC) as f:
+        _patch_features(monkeypatch, _load_feature_mutant(f.read()))
+    pins_features()
+
+
+@pytest.mark.parametrize("mid,old,new", FEAT_MUTANTS, ids=[m[0] for m in FEAT_MUTANTS])
+def test_feature_pins_catch_planted_mistake(monkeypatch, mid, old, new):
+    with open(FEAT_SRC) as f:
+        text = f.read()
+    mutated = _replace_nth(text, old, new, 0)
+    assert mutated != text
+    _patch_features(monkeypatch, _load_feature_mutant(mutated))
+    with np.errstate(all="ignore"):
+        with pytest.raises((AssertionError, ValueError, IndexError, ZeroDivisionError)):
+            pins_features()
