@@ -46,7 +46,7 @@ def tf32_peak_tflops():
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture of the
 # current kernels on this workload (profiles/); None for a kernel not captured since it changed
-TRAFFIC = {"k_spread3_tc<16>": 59704000 + 29000, "k_gather3_umma<16>": 59454000 + 6000}
+TRAFFIC = {"k_spread3_tc<16>": 59711000 + 14000, "k_gather3_umma<16>": 59438500 + 3700}
 
 
 def traffic_per_launch(name):

@@ -446,13 +446,16 @@ k_spread3_f32(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
 }
 
 // ------------------------------------------------- tensor-core spread (TF32)
-// The spread of one sub-problem is the product C[(b,c), a] = sum_p A[(b,c), p]
-// B[p, a] with A = wy (x) wz and B = alpha wx: a dense contraction over the
+// The spread of one sub-problem is the product C[(a,b), c] = sum_p A[(a,b), p]
+// B[p, c] with A = wx (x) wy and B = alpha wz: a dense contraction over the
 // nodes of the bin, run on mma.sync m16n8k8 TF32.  FP32 accuracy comes from
-// splitting every operand into a TF32 head and a TF32 tail and accumulating
+// splitting every operand into a TF32 head and a tail and accumulating
 // head*head + head*tail + tail*head in FP32 (the dropped tail*tail term is
-// 2^-22 relative).  Warp w owns the M-tiles b = 2w, 2w+1 (16 c-rows each) and
-// both N-tiles (a = 0..7, 8..15).
+// 2^-22 relative).  The tail is passed as the FP32 residual x - head: the
+// tensor core reads only its TF32 bits (rounding toward zero, 2^-21 relative
+// to x).  Warp w owns the M-tiles a = 2w, 2w+1 (16 b-rows each) and both
+// N-tiles (c = 0..7, 8..15), so every accumulator pair of a thread is two
+// neighbouring cells along the grid's last axis: one 8-byte atomic each.
 __device__ __forceinline__ uint32_t tf32_of(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -461,6 +464,10 @@ __device__ __forceinline__ uint32_t tf32_of(float x) {
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
     hi = tf32_of(x);
     lo = tf32_of(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void tf32_split_fast(float x, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_of(x);
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
     asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
@@ -474,12 +481,12 @@ __global__ void __launch_bounds__(32 * ((R + 1) / 2))
 k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m,
              const void* __restrict__ alpha = nullptr, int alpha_double = 0) {
     static_assert(R <= kPitch && R % 2 == 0, "even region up to 16");
-    constexpr int NW = R / 2;                  // warps, two b rows each
+    constexpr int NW = R / 2;                  // warps, two a-tiles each
     constexpr int NT = 32 * NW;
-    __shared__ __align__(16) uint32_t sxh[kSpreadChunk][kTcPitch];   // alpha wx, TF32 head
-    __shared__ __align__(16) uint32_t sxl[kSpreadChunk][kTcPitch];   // and tail
+    __shared__ __align__(16) uint32_t szh[kSpreadChunk][kTcPitch];   // alpha wz, TF32 head
+    __shared__ __align__(16) uint32_t szl[kSpreadChunk][kTcPitch];   // and tail
+    __shared__ __align__(16) float sx[kSpreadChunk][kTcPitch];
     __shared__ __align__(16) float sy[kSpreadChunk][kTcPitch];
-    __shared__ __align__(16) float sz[kSpreadChunk][kTcPitch];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs[sp.w];
     if (W.live && !*W.live) return;   // a batch system that has stopped
@@ -508,47 +515,47 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
                 v = reinterpret_cast<const float4*>(W.wtab + pos * 48)[k];
                 // the coefficient of the node: gathered through the permutation from the
                 // caller's vector (L2-resident), or the sorted copy of a batch instance
-                if (k < 4)
+                if (k >= 8)
                     al = !alpha ? W.asort[pos]
                                 : alpha_double ? (float)static_cast<const double*>(alpha)[W.perm[pos]]
                                                : static_cast<const float*>(alpha)[W.perm[pos]];
             }
             if (k < 4) {
-                const float xs[4] = {al * v.x, al * v.y, al * v.z, al * v.w};
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    uint32_t hi, lo;
-                    tf32_split(xs[e], hi, lo);
-                    sxh[p][4 * k + e] = hi;
-                    sxl[p][4 * k + e] = lo;
-                }
+                *reinterpret_cast<float4*>(&sx[p][4 * k]) = v;
             } else if (k < 8) {
                 *reinterpret_cast<float4*>(&sy[p][4 * (k - 4)]) = v;
             } else {
-                *reinterpret_cast<float4*>(&sz[p][4 * (k - 8)]) = v;
+                const float zs[4] = {al * v.x, al * v.y, al * v.z, al * v.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    uint32_t hi, lo;
+                    tf32_split_fast(zs[e], hi, lo);
+                    szh[p][4 * (k - 8) + e] = hi;
+                    szl[p][4 * (k - 8) + e] = lo;
+                }
             }
         }
         __syncthreads();
         for (int p0 = 0; p0 < cnt8; p0 += 8) {
             const int pa = p0 + t, pb = p0 + t + 4;
-            const float z0 = sz[pa][g], z1 = sz[pa][g + 8], z2 = sz[pb][g], z3 = sz[pb][g + 8];
+            const float y0 = sy[pa][g], y1 = sy[pa][g + 8], y2 = sy[pb][g], y3 = sy[pb][g + 8];
             uint32_t bh[2][2], bl[2][2];
 #pragma unroll
             for (int nt = 0; nt < 2; nt++) {
-                bh[nt][0] = sxh[pa][8 * nt + g];
-                bl[nt][0] = sxl[pa][8 * nt + g];
-                bh[nt][1] = sxh[pb][8 * nt + g];
-                bl[nt][1] = sxl[pb][8 * nt + g];
+                bh[nt][0] = szh[pa][8 * nt + g];
+                bl[nt][0] = szl[pa][8 * nt + g];
+                bh[nt][1] = szh[pb][8 * nt + g];
+                bl[nt][1] = szl[pb][8 * nt + g];
             }
 #pragma unroll
             for (int i = 0; i < 2; i++) {
-                const int b = 2 * warp + i;
-                const float y0 = sy[pa][b], y1 = sy[pb][b];
+                const int a = 2 * warp + i;
+                const float x0 = sx[pa][a], x1 = sx[pb][a];
                 uint32_t ah[4], alo[4];
-                tf32_split(y0 * z0, ah[0], alo[0]);
-                tf32_split(y0 * z1, ah[1], alo[1]);
-                tf32_split(y1 * z2, ah[2], alo[2]);
-                tf32_split(y1 * z3, ah[3], alo[3]);
+                tf32_split_fast(x0 * y0, ah[0], alo[0]);
+                tf32_split_fast(x0 * y1, ah[1], alo[1]);
+                tf32_split_fast(x1 * y2, ah[2], alo[2]);
+                tf32_split_fast(x1 * y3, ah[3], alo[3]);
 #pragma unroll
                 for (int nt = 0; nt < 2; nt++) {
                     mma_tf32(acc[i][nt], ah, bh[nt][0], bh[nt][1]);
@@ -558,20 +565,31 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
             }
         }
     }
-    // acc[i][nt] holds C rows c = g, g+8 and columns a = 8 nt + 2t, 8 nt + 2t + 1
+    // acc[i][nt] holds C rows b = g (e = 0, 1) and b = g + 8 (e = 2, 3), columns
+    // c = 8 nt + 2t (e even) and c + 1 (e odd) of the M-tile a = 2 warp + i.
+    // A pair goes out as one float2 atomic when its first cell is 8-byte aligned
+    // (an aligned grid and an even index; nos is even, so c + 1 does not wrap).
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(grid) & 7) == 0;
 #pragma unroll
     for (int i = 0; i < 2; i++) {
-        const int b = 2 * warp + i;
-        const int gb = wrap_idx(Tb * by - m + b, nos);
+        const int a = 2 * warp + i;
+        const int ga = wrap_idx(Tb * bx - m + a, nos);
 #pragma unroll
         for (int nt = 0; nt < 2; nt++)
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int c = g + 8 * (e >> 1);
-                const int a = 8 * nt + 2 * t + (e & 1);
-                if (a < R && c < R) {
-                    const int ga = wrap_idx(Tb * bx - m + a, nos);
-                    atomicAdd(&grid[(ga * nos + gb) * nos + wrap_idx(Tb * bz - m + c, nos)], acc[i][nt][e]);
+            for (int h = 0; h < 2; h++) {
+                const int b = g + 8 * h;
+                const int c = 8 * nt + 2 * t;
+                if (b < R && c < R) {
+                    const int row = (ga * nos + wrap_idx(Tb * by - m + b, nos)) * nos;
+                    const int gc = wrap_idx(Tb * bz - m + c, nos);
+                    const float v0 = acc[i][nt][2 * h], v1 = acc[i][nt][2 * h + 1];
+                    if (vec_ok && (gc & 1) == 0 && gc + 1 < nos) {
+                        atomicAdd(reinterpret_cast<float2*>(&grid[row + gc]), make_float2(v0, v1));
+                    } else {
+                        atomicAdd(&grid[row + gc], v0);
+                        atomicAdd(&grid[row + wrap_idx(Tb * bz - m + c + 1, nos)], v1);
+                    }
                 }
             }
     }
