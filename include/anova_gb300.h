@@ -151,11 +151,13 @@ anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, vo
  * Plans with ANOVA_FP64 run CG with the FP64 operator; ANOVA_FP32 with the
  * FP32 operator (FP64 vectors and scalars); ANOVA_MIXED runs FP32 inner CG
  * inside FP64 iterative refinement until the FP64 residual meets tol.
- * Synchronises `stream`.  Errors: EINVAL (lambda <= 0, tol <= 0 ...),
- * ENOCONV (maxit reached; alpha and relres hold the last iterate), ETIMEOUT
+ * maxit: 0 .. ANOVA_MAX_CG_ITERS (the residual history lives on the device).
+ * Synchronises `stream`.  Errors: EINVAL (lambda <= 0, tol <= 0, maxit out of
+ * range ...), ENOCONV (maxit reached; alpha and relres hold the last iterate), ETIMEOUT
  * (a bounded wait inside a kernel gave up during the call, as counted by
  * anova_wait_timeouts; the result is not to be trusted).
  */
+#define ANOVA_MAX_CG_ITERS (1 << 24)
 anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, double* alpha,
                           int32_t nrhs, int64_t ld, double tol, int32_t maxit,
                           int32_t* iters, double* relres, void* stream);

@@ -592,7 +592,8 @@ anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, vo
 anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, double* alpha, int32_t nrhs,
                           int64_t ld, double tol, int32_t maxit, int32_t* iters, double* relres,
                           void* stream) {
-    if (!plan || !(lambda > 0.0) || !std::isfinite(lambda) || !(tol > 0.0) || maxit < 0 || nrhs < 1 ||
+    if (!plan || !(lambda > 0.0) || !std::isfinite(lambda) || !(tol > 0.0) || maxit < 0 ||
+        maxit > ANOVA_MAX_CG_ITERS || nrhs < 1 ||
         ld < plan->N || (plan->N > 0 && (!y || !alpha))) {
         set_error("krr_cg_solve: bad plan, lambda, tol, maxit, nrhs, ld or pointers");
         return ANOVA_EINVAL;

@@ -52,7 +52,7 @@ k_model_sum(const T* __restrict__ tmp, const double* __restrict__ eta, int P, in
 }
 
 // rho of the wide frame for window l (1 when no widening is possible)
-static double wide_rho(const anova_plan* plan, const WindowPlan& w) {
+static double wide_rho(const WindowPlan& w) {
     const double pi = 3.14159265358979323846;
     const double rho = pi * w.ell_l * w.n / (2.0 * std::sqrt(std::log(1e12)));
     return std::min(2.0, rho);
@@ -77,7 +77,7 @@ static anova_status model_grids(krr_model* md, cudaStream_t st) {
         ANOVA_TRY(convolved_grid<T>(plan, plan->win[l], md->alpha, g + md->off[l], st));
         if (md->wide[l].dA == 0) continue;
         WindowPlan wide;
-        anova_status s = window_widened(plan, l, wide_rho(plan, plan->win[l]), wide, st);
+        anova_status s = window_widened(plan, l, wide_rho(plan->win[l]), wide, st);
         if (s == ANOVA_OK) s = convolved_grid<T>(plan, wide, md->alpha, g + md->off_wide[l], st);
         if (s == ANOVA_OK && cudaStreamSynchronize(st) != cudaSuccess) s = ANOVA_ECUDA;
         WindowPlan keep = wide;       // frame and binning parameters only
@@ -187,7 +187,7 @@ anova_status krr_model_create(anova_plan* plan, const double* alpha, void* strea
         ge = (ge + 63) & ~(size_t)63;           // 256-byte aligned window grids
         md->off[l] = md->elems;
         md->elems += ge;
-        if (plan->N > 0 && wide_rho(plan, plan->win[l]) > 1.05) {
+        if (plan->N > 0 && wide_rho(plan->win[l]) > 1.05) {
             md->wide[l].dA = plan->win[l].dA;   // marks a wide grid, filled by model_grids
             md->off_wide[l] = md->elems;
             md->elems += ge;

@@ -288,7 +288,8 @@ anova_status anova_server_submit_fit(anova_server* sv, const double* points, int
                                      const int32_t* windows, int32_t P, double ell, const int32_t* n, int32_t m,
                                      double eps_B, double lambda, const double* y, double tol, int32_t maxit,
                                      int64_t* ticket) {
-    if (!sv || !ticket || !windows || P < 1 || P > kMaxWindows || N < 0) {
+    if (!sv || !ticket || !windows || P < 1 || P > kMaxWindows || N < 0 || maxit < 0 ||
+        maxit > ANOVA_MAX_CG_ITERS) {
         set_error("anova_server_submit_fit: bad arguments");
         return ANOVA_EINVAL;
     }
