@@ -26,6 +26,10 @@
  *   - Errors are returned as anova_status; no exception crosses the ABI.
  *     anova_last_error() returns a thread-local detail string for the last
  *     failure on the calling thread.
+ *   - A plan serves one call at a time: its grids and work buffers are shared
+ *     by every call on it, so calls on one plan from several threads (or on
+ *     several streams at once) must be serialised by the caller.  Fitted
+ *     models and the server state their own rules below.
  *   - Arrays of points are row-major: point i, feature f at [i*ld + f].
  *   - Multiple right-hand sides are column-major: column r at [r*ld + i].
  */
@@ -406,7 +410,10 @@ anova_status anova_server_submit_predict(anova_server* server, int64_t model, co
 anova_status anova_server_wait(anova_server* server, int64_t ticket, anova_status* result, double* latency_ms,
                                int32_t* iterations, double* relres);
 
-/* Drop a fitted model and return its memory to the budget. */
+/* Drop a fitted model and return its memory to the budget.  `model` is the
+ * ticket of a fit whose anova_server_wait has returned (EINVAL for an unknown
+ * ticket, a fit still queued or running, or a model already released);
+ * predictions still running on it finish first, the last one frees it. */
 anova_status anova_server_release(anova_server* server, int64_t model);
 
 /* Latency percentiles of the completed requests, their number, and the budgeted
