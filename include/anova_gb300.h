@@ -437,6 +437,19 @@ const char* anova_status_string(anova_status status);
  * frees its tensor memory and returns. */
 int64_t anova_wait_timeouts(void);
 
+/*
+ * anova_debug_wait_probe -- checks the bounded-wait path of the library's
+ * kernels without a fault: one warp waits on a shared-memory mbarrier that
+ * nothing arrives on, polling at most `polls` times (1 .. 2^22, the limit of
+ * the kernels' own waits), and reports that it gave up.  The paper has no
+ * counterpart; this exists so that the ETIMEOUT path can be tested.  Touches
+ * neither anova_wait_timeouts nor any plan.  Synchronises `stream`.
+ * Returns ETIMEOUT when the wait gave up (the expected outcome), OK if the
+ * barrier completed, EINVAL for polls out of range (checked before any CUDA
+ * call), ECUDA if the probe could not run.
+ */
+anova_status anova_debug_wait_probe(int32_t polls, void* stream);
+
 /* Thread-local detail of the last error on the calling thread ("" if none). */
 const char* anova_last_error(void);
 

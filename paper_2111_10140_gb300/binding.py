@@ -42,6 +42,7 @@ _SIGNATURES = {
                                    _i32, _i32, _i32, _pi32, _pf64, _vp]),
     "anova_plan_window_bins": (_i32, [_vp, _i32, _pi32, _pi32, _pi32]),
     "anova_wait_timeouts": (_i64, []),
+    "anova_debug_wait_probe": (_i32, [_i32, _vp]),
     "anova_zscore_fit": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_zscore_apply": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_mis": (_i32, [_vp, _i64, _i32, _i64, _vp, _i32, _i32, _pf64, _vp]),
@@ -367,6 +368,11 @@ def anova_windows_from_mis(scores, threshold=0.0):
 
 def anova_wait_timeouts():
     return int(lib().anova_wait_timeouts())
+
+
+def anova_debug_wait_probe(polls, stream=None):
+    """Status of the bounded-wait probe (ETIMEOUT when its wait gave up)."""
+    return int(lib().anova_debug_wait_probe(int(polls), _stream(stream)))
 
 
 class Batch:

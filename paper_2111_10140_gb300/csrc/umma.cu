@@ -80,9 +80,9 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t 
                  "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int polls = kUmmaSpin) {
     uint32_t done = 0;
-    for (int it = 0; it < kUmmaSpin && !done; it++)
+    for (int it = 0; it < polls && !done; it++)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
@@ -538,6 +538,19 @@ anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* desc
     return ANOVA_OK;
 }
 
+// ------------------------------------------------------------- wait probe
+// One warp waits on an mbarrier that nothing arrives on, with the bounded poll
+// loop of the kernels above cut to `polls` polls, so the wait gives up; the
+// block's verdict goes to *gave_up (1 gave up, 0 completed).  No tensor memory,
+// no asynchronous copies, no other counter touched.
+__global__ void k_wait_probe(int polls, int* gave_up) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar)), "r"(1));
+    __syncthreads();
+    const bool done = __syncthreads_and(mbar_wait(su32(&mbar), 0, polls)) != 0;
+    if (threadIdx.x == 0) *gave_up = done ? 0 : 1;
+}
+
 // The device counter of abandoned waits, read on `st` (stream-ordered, then
 // synchronised): a synchronous entry point compares it before and after.
 uint64_t wait_timeouts_on(cudaStream_t st) {
@@ -549,6 +562,30 @@ uint64_t wait_timeouts_on(cudaStream_t st) {
 }
 
 }  // namespace anova
+
+extern "C" anova_status anova_debug_wait_probe(int32_t polls, void* stream) {
+    if (polls < 1 || polls > anova::kUmmaSpin) {
+        anova::set_error("anova_debug_wait_probe: polls must be in 1 .. 2^22");
+        return ANOVA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int* flag = nullptr;
+    ANOVA_CUDA_TRY(cudaMallocAsync(&flag, sizeof(int), st));
+    ANOVA_CUDA_TRY(cudaMemsetAsync(flag, 0xff, sizeof(int), st));   // -1: the probe did not run
+    anova::k_wait_probe<<<1, 32, 0, st>>>(polls, flag);
+    ANOVA_CHECK_LAUNCH();
+    int h = -1;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaFreeAsync(flag, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h == 1) {
+        anova::set_error("anova_debug_wait_probe: the bounded wait gave up");
+        return ANOVA_ETIMEOUT;
+    }
+    if (h == 0) return ANOVA_OK;
+    anova::set_error("anova_debug_wait_probe: the probe did not report");
+    return ANOVA_ECUDA;
+}
 
 extern "C" int64_t anova_wait_timeouts(void) {
     unsigned long long v = 0;

@@ -82,6 +82,14 @@ def test_plan_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert "ell" in L.anova_last_error().decode() or L.anova_last_error().decode() != ""
 
 
+def test_wait_probe_rejects_bad_poll_counts_without_touching_the_gpu(lib):
+    from paper_2111_10140_gb300 import binding as B
+    L = B.lib()
+    assert L.anova_debug_wait_probe(0, None) == B.EINVAL
+    assert L.anova_debug_wait_probe((1 << 22) + 1, None) == B.EINVAL
+    assert "polls" in L.anova_last_error().decode()
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2111_10140_gb300 import binding as B
     monkeypatch.setattr(B, "_lib", None)
