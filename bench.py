@@ -164,10 +164,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(ns):
-    """One timed oracle fast summation on a bounded sample (about 10-30 s of CPU work)."""
+def cpu_baseline(ns, what="fastsum", data=None):
+    """One timed oracle run on a bounded sample: the fast summation of the mid
+    workload (about 10-30 s of CPU work), or with what="features" the window
+    construction (z-score fit on all rows of `data` = (X, labels), MIS on the
+    first ns rows)."""
     import oracle
     from paper_2111_10140_gb300 import workloads as W
+    if what == "features":
+        from oracle import features as F
+        X, labels = data
+        t0 = time.perf_counter()
+        F.zscore_fit(X)
+        t_fit = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        F.mis(X[:ns], labels[:ns], int(labels.max()) + 1)
+        t_mis = time.perf_counter() - t0
+        return {"zscore_fit_s": t_fit, "mis_s": t_mis, "mis_rows": ns, "cores": 1, "kind": "oracle",
+                "sample": f"numpy z-score fit on {X.shape[0]} x {X.shape[1]}; Python-loop MIS on the first {ns} rows"}
     oracle.build()
     w = W.plain_mid()
     t0 = time.perf_counter()
@@ -691,6 +705,73 @@ def run_precision(args):
     plan.close()
 
 
+def run_features(args):
+    """Window construction on the GPU at the precision form's shape (N rows,
+    d = 28, six Student-t columns, columns on their own scales, two classes):
+    z-score fit, z-score apply (in place) and the MIS scores, each call timed
+    with CUDA events after an L2 flush; the kernels are HBM-bound, so the
+    figure is algorithmic bytes (one read of X, plus one write for apply, plus
+    the labels for MIS) / time against the measured copy bandwidth."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2111_10140_gb300 import binding as B
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    N, d = args.features_n, 28
+    rng = np.random.default_rng(2)
+    Xh = rng.standard_normal((N, d))
+    for c in (0, 4, 8, 10, 13, 17):
+        Xh[:, c] = rng.standard_t(3.0, N)
+    Xh = Xh * rng.uniform(0.5, 3.0, d) + rng.uniform(-2.0, 2.0, d)
+    lab = ((Xh[:, 0] + 0.5 * Xh[:, 3] - Xh[:, 7]) > 0).astype(np.int32)
+    cpu = None if args.skip_cpu else cpu_baseline(args.features_cpu_rows, "features", (Xh, lab))
+    X = torch.from_numpy(Xh).to(dev)
+    labels = torch.from_numpy(lab).to(dev)
+    Xw = torch.empty_like(X)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    mean, sd = B.anova_zscore_fit(X)
+
+    def timed(fn, before=None):
+        ts = []
+        for i in range(args.warmup + args.steps):
+            if before is not None:
+                before()
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    t_fit = timed(lambda: B.anova_zscore_fit(X))
+    t_apply = timed(lambda: B.anova_zscore_apply(Xw, mean, sd), before=lambda: Xw.copy_(X))
+    scores = []
+    t_mis = timed(lambda: scores.append(B.anova_mis(X, labels, 2)))
+    windows = B.anova_windows_from_mis(scores[-1], 0.0)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm, src = float(json.load(f)["hbm_gbs"]), "measured copy (MEASURED_PEAKS.json)"
+    except Exception:
+        hbm, src = 6800.0, "fallback figure"
+    xb = N * d * 8
+
+    def row(ms, nbytes):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"ms": ms, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac_of_hbm": gbs / hbm}
+
+    print(json.dumps({"features": True, "N": N, "d": d, "hbm_peak_gbs": hbm, "peak_source": src,
+                      "zscore_fit": row(t_fit, xb), "zscore_apply": row(t_apply, 2 * xb),
+                      "mis": dict(row(t_mis, xb + 4 * N), note="synchronous call: includes the host's score formation"),
+                      "top_windows": windows[:3], "cpu_baseline": cpu, "steps": args.steps, "warmup": args.warmup,
+                      "l2": "flushed before every call (256 MB write outside the events)"}), flush=True)
+
+
 def run_autotune(args):
     """Bin sides chosen by anova_autotune_bins for the mid workload and the
     precision form, against the default rule."""
@@ -749,6 +830,10 @@ def main():
     ap.add_argument("--batch-maxit", type=int, default=3000)
     ap.add_argument("--batch-sample", type=int, default=8)
     ap.add_argument("--batch-lambda-min", type=float, default=1e-4)
+    ap.add_argument("--features", action="store_true",
+                    help="window construction (z-score fit / apply, MIS) at the precision form's shape")
+    ap.add_argument("--features-n", type=int, default=1_000_000)
+    ap.add_argument("--features-cpu-rows", type=int, default=20_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -764,6 +849,8 @@ def main():
         run_autotune(args)
     elif args.precision_form:
         run_precision(args)
+    elif args.features:
+        run_features(args)
     else:
         run_ours(args)
 
