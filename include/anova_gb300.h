@@ -479,6 +479,27 @@ anova_status anova_debug_spread(anova_plan* plan, int32_t l, int32_t dtype, cons
 /* Bin side, region side and whether window l runs on the dense kernels. */
 anova_status anova_plan_window_bins(const anova_plan* plan, int32_t l, int32_t* bin_side, int32_t* region,
                                     int32_t* dense);
+
+/*
+ * anova_plan_bin_rule -- the binning a plan would give one window of `dims`
+ * features with bandwidth n, cut-off m and oversampling sigma, without a plan
+ * and without touching the GPU.  bin_side (host, 3 entries for 1-D / 2-D /
+ * 3-D windows, 0 = the default rule, may be NULL) is the request that
+ * anova_fastsum_plan_bins takes.  Outputs (host, may be NULL): side = bin side
+ * in grid cells, region = side + 2m (the cells a bin's nodes reach along one
+ * axis), dense = 1 when the window runs on the dense region kernels (region at
+ * most 16 cells, at most 32768 bins), nbins = bins of the window.
+ * The default rule: 3-D windows take bins of 2 cells (4 when 2 gives too many
+ * bins) while the region stays within 16 cells; 2-D windows bins of 2 cells;
+ * 1-D windows bins of 16 - 2m cells (2 on grids too small for that); other
+ * windows the generic kernels.  A
+ * requested side is taken when it is even, its region stays within 16 cells,
+ * the bins number at most 32768 and side + m - 2 < sigma n.
+ * Errors: EINVAL for arguments anova_fastsum_plan would reject, or a grid
+ * too fine for the binning.
+ */
+anova_status anova_plan_bin_rule(int32_t dims, int32_t n, int32_t m, double sigma, const int32_t* bin_side,
+                                 int32_t* side, int32_t* region, int32_t* dense, int32_t* nbins);
 /*
  * anova_debug_diag -- copy window l's FP64 multiplier D_k (host, n^dims
  * doubles, centred index) = b_k / prod_t psihat(k_t)^2 with the normalised

@@ -41,6 +41,7 @@ _SIGNATURES = {
     "anova_autotune_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
                                    _i32, _i32, _i32, _pi32, _pf64, _vp]),
     "anova_plan_window_bins": (_i32, [_vp, _i32, _pi32, _pi32, _pi32]),
+    "anova_plan_bin_rule": (_i32, [_i32, _i32, _i32, _f64, _pi32, _pi32, _pi32, _pi32, _pi32]),
     "anova_wait_timeouts": (_i64, []),
     "anova_debug_wait_probe": (_i32, [_i32, _vp]),
     "anova_zscore_fit": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
@@ -364,6 +365,19 @@ def anova_windows_from_mis(scores, threshold=0.0):
     _check(lib().anova_windows_from_mis(s.ctypes.data_as(_pf64), len(s), float(threshold), w.ctypes.data_as(_pi32),
                                         ctypes.byref(P)), "anova_windows_from_mis")
     return [tuple(int(f) for f in w[3 * p:3 * p + 3] if f >= 0) for p in range(P.value)]
+
+
+def anova_plan_bin_rule(dims, n, m, sigma=2.0, bin_side=None):
+    """Binning a plan would give one window (no GPU): side, region, dense, nbins."""
+    req = None
+    if bin_side is not None:
+        req = np.ascontiguousarray(bin_side, dtype=np.int32)
+        assert req.shape == (3,)
+    out = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().anova_plan_bin_rule(int(dims), int(n), int(m), float(sigma),
+                                     req.ctypes.data_as(_pi32) if req is not None else None,
+                                     *[ctypes.byref(o) for o in out]), "anova_plan_bin_rule")
+    return {"bin_side": out[0].value, "region": out[1].value, "dense": bool(out[2].value), "nbins": out[3].value}
 
 
 def anova_wait_timeouts():

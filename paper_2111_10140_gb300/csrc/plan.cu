@@ -1345,6 +1345,33 @@ anova_status anova_plan_window_bins(const anova_plan* plan, int32_t l, int32_t* 
     return ANOVA_OK;
 }
 
+anova_status anova_plan_bin_rule(int32_t dims, int32_t n, int32_t m, double sigma, const int32_t* bin_side,
+                                 int32_t* side, int32_t* region, int32_t* dense, int32_t* nbins) {
+    if (dims < 1 || dims > 3) {
+        set_error("anova_plan_bin_rule: dims must be 1, 2 or 3");
+        return ANOVA_EINVAL;
+    }
+    const int32_t win[3] = {0, dims > 1 ? 1 : -1, dims > 2 ? 2 : -1};
+    ANOVA_TRY(validate(0, dims, dims, win, 1, nullptr, 1.0, &n, m, sigma, 1.0 / 16, 8, ANOVA_FP64));
+    WindowPlan w;
+    w.dA = dims;
+    w.n = n;
+    w.nos = (int)std::lround(sigma * n);
+    int32_t req[3] = {0, 0, 0};
+    if (bin_side)
+        for (int t = 0; t < 3; t++) req[t] = bin_side[t] > 0 ? bin_side[t] : 0;
+    choose_bins(w, m, req);
+    if (side) *side = w.T;
+    if (region) *region = w.R;
+    if (dense) *dense = w.dense ? 1 : 0;
+    if (nbins) *nbins = w.nbins;
+    if (w.nbins > kMaxBins) {
+        set_error("anova_plan_bin_rule: grid too fine for the binning (reduce n or m)");
+        return ANOVA_EINVAL;
+    }
+    return ANOVA_OK;
+}
+
 anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host) {
     if (!plan || l < 0 || l >= plan->P || !D_host) {
         set_error("bad plan, window index or output");

@@ -90,6 +90,32 @@ def test_wait_probe_rejects_bad_poll_counts_without_touching_the_gpu(lib):
     assert "polls" in L.anova_last_error().decode()
 
 
+def test_bin_rule_is_host_logic(lib):
+    """The plan's binning rule for one window, computed without a GPU."""
+    from paper_2111_10140_gb300 import binding as B
+    rule = B.anova_plan_bin_rule
+    assert rule(3, 32, 6) == {"bin_side": 2, "region": 14, "dense": True, "nbins": 32 ** 3}
+    assert rule(3, 32, 6, bin_side=[0, 0, 4]) == {"bin_side": 4, "region": 16, "dense": True, "nbins": 16 ** 3}
+    assert rule(3, 32, 6, bin_side=[0, 0, 6])["bin_side"] == 2      # region 18 > 16: the request is ignored
+    assert rule(3, 32, 6, bin_side=[0, 0, 3])["bin_side"] == 2      # odd side: ignored
+    assert rule(3, 32, 6, bin_side=[4, 4, 0])["bin_side"] == 2      # requests for other dimensions
+    assert rule(3, 64, 6) == {"bin_side": 4, "region": 16, "dense": True, "nbins": 32 ** 3}   # 2 gives 64^3 bins
+    assert rule(3, 32, 7) == {"bin_side": 2, "region": 16, "dense": True, "nbins": 32 ** 3}
+    r = rule(3, 32, 8)                                               # region 2 + 16 > 16: generic kernels
+    assert not r["dense"] and r["nbins"] <= 32768
+    r = rule(3, 128, 6)                                              # too many bins for the dense kernels
+    assert not r["dense"] and r["nbins"] <= 32768
+    assert rule(2, 64, 6) == {"bin_side": 2, "region": 14, "dense": True, "nbins": 64 ** 2}
+    assert rule(1, 64, 6) == {"bin_side": 4, "region": 16, "dense": True, "nbins": 32}
+    assert rule(1, 64, 6, bin_side=[6, 0, 0])["bin_side"] == 4      # region 18 > 16: default
+    assert rule(1, 64, 4, bin_side=[8, 0, 0]) == {"bin_side": 8, "region": 16, "dense": True, "nbins": 16}
+    for bad in [dict(dims=4, n=32, m=6), dict(dims=3, n=31, m=6), dict(dims=3, n=4, m=6),
+                dict(dims=3, n=32, m=0), dict(dims=3, n=32, m=6, sigma=1.7)]:
+        with pytest.raises(B.AnovaError) as e:
+            rule(**bad)
+        assert e.value.status == B.EINVAL
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2111_10140_gb300 import binding as B
     monkeypatch.setattr(B, "_lib", None)
