@@ -97,7 +97,7 @@ anova_status anova_fastsum_plan(const double* points, int64_t N, int32_t d, int6
  * (at most 32768) and, in 1-D, side + m - 2 < n_os; otherwise the default rule
  * applies (anova_plan_window_bins reports what was taken).  bin_side NULL is
  * anova_fastsum_plan.  The paper fixes no binning: a tuning parameter of the
- * GPU design.
+ * GPU design.  Errors as anova_fastsum_plan.
  */
 anova_status anova_fastsum_plan_bins(const double* points, int64_t N, int32_t d, int64_t ld,
                                      const int32_t* windows, int32_t P, const double* weights, double ell,
@@ -109,7 +109,8 @@ anova_status anova_fastsum_plan_bins(const double* points, int64_t N, int32_t d,
  * matrix-vector product fastest on this GPU, by measurement: the default rule
  * first, then every admissible side for the 1-D, 2-D and 3-D windows in turn,
  * each timed over `reps` products (FP32 if the precision holds it) after three
- * warm-up products.  Arguments as anova_fastsum_plan; bin_side (host, 3 int32)
+ * warm-up products (a GPU tuning step; the paper has no counterpart).
+ * Arguments as anova_fastsum_plan; bin_side (host, 3 int32)
  * receives the choice for anova_fastsum_plan_bins (0 = default rule), ms (host
  * or NULL) its time per product.  Builds and frees one plan per candidate;
  * synchronous.  Errors: those of the plan build, EINVAL.
@@ -176,7 +177,9 @@ anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, doub
  * Uses the plan's highest precision (FP64 when held).  When a test point maps
  * outside the plan's ball the library builds a temporary frame over X and Z
  * together (the kernel is shift- and scale-invariant in user units), so the
- * call still returns ANOVA_OK.  Synchronises `stream`.
+ * call still returns ANOVA_OK.  Synchronises `stream`; allocates its scratch
+ * stream-ordered.  Errors: EINVAL (M < 0 or M >= 2^31, ldz < d, missing
+ * pointers), ECUDA (a failed allocation included).
  */
 anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
                          int64_t ldz, double* out, void* stream);
@@ -242,7 +245,10 @@ anova_status anova_direct_matvec(const double* Z, int64_t M, int64_t ldz, const 
 anova_status anova_zscore_fit(const double* X, int64_t N, int32_t d, int64_t ld, double* mean, double* sd,
                               void* stream);
 
-/* X <- (X - mean) / sd column by column, in place (device; training or test rows). */
+/* X <- (X - mean) / sd column by column, in place (device; training or test
+ * rows; Sec. 6.1: test rows take the training statistics).  mean, sd: device,
+ * d entries (from anova_zscore_fit).  Asynchronous on `stream`.  Errors:
+ * EINVAL (shapes as anova_zscore_fit, missing pointers), ECUDA. */
 anova_status anova_zscore_apply(double* X, int64_t N, int32_t d, int64_t ld, const double* mean, const double* sd,
                                 void* stream);
 
@@ -266,7 +272,7 @@ anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const 
  * rest in consecutive groups of three; the last group holds the one to three
  * left.  windows: host, 3 * d int32 (-1 padded rows, the layout
  * anova_fastsum_plan takes); P: number of windows (0 if none survive).
- * Host only.
+ * Host only.  Errors: EINVAL (d < 1, missing pointers, a non-finite score).
  */
 anova_status anova_windows_from_mis(const double* mis, int32_t d, double threshold, int32_t* windows, int32_t* P);
 
@@ -329,23 +335,27 @@ typedef struct anova_batch anova_batch;
 anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t nrhs, void* stream,
                                 anova_batch** out);
 
-/* offsets (host, nprob + 1 entries) of the flat layout; offsets[nprob] is its length. */
+/* offsets (host, nprob + 1 entries) of the flat layout; offsets[nprob] is its
+ * length.  Errors: EINVAL (NULL batch or offsets). */
 anova_status anova_batch_layout(const anova_batch* batch, int64_t* offsets);
 
-/* y = K x for every system (device, flat layout; y must not alias x).
- * Asynchronous on `stream`; calls on one batch must not overlap. */
+/* y = K x for every system (device, flat layout; y must not alias x), each
+ * problem's fast operator of Sec. 4.3.  Asynchronous on `stream`; calls on one
+ * batch must not overlap.  Errors: EINVAL (NULL or aliasing vectors), ECUDA. */
 anova_status anova_batch_matvec(anova_batch* batch, const double* x, double* y, void* stream);
 
 /*
  * Solve (K_p + lambda_p I) alpha = y for every (problem p, right-hand side) by
- * CG (Hestenes-Stiefel, alpha_0 = 0), each system stopping when its recursive
+ * CG (Sec. 2; Hestenes-Stiefel, alpha_0 = 0), each system stopping when its recursive
  * residual reaches tol ||y|| or after maxit iterations.  lambda: host, nprob
  * entries >= 0.  y, alpha: device, flat layout.  iters, relres: host, nprob *
  * nrhs entries (system p * nrhs + r) or NULL; relres is recomputed with the
  * batch's FP32 operator (NaN for a system whose CG broke down: with the FP32
  * operator K + lambda I may lose definiteness when lambda is below its
  * rounding).  Systems that stop iterate no more (their kernels exit at once).
- * Returns ENOCONV if a system stopped short of tol.  Synchronous on `stream`; the iteration is
+ * Returns ENOCONV if a system stopped short of tol, EINVAL for a NULL batch,
+ * lambda, y or alpha, y aliasing alpha, tol <= 0 or maxit < 1, ECUDA if a CUDA
+ * call fails.  Synchronous on `stream`; the iteration is
  * captured as a CUDA graph on the second block of iterations (same caveat as
  * anova_matvec on device-wide synchronisation from other threads).
  */
@@ -385,7 +395,9 @@ void anova_batch_destroy(anova_batch* batch);
  * ------------------------------------------------------------------------- */
 typedef struct anova_server anova_server;
 
-/* n_workers in 1..64; hbm_budget_bytes > 0. */
+/* n_workers in 1..64; hbm_budget_bytes > 0 (device bytes the admitted
+ * requests and resident models may hold by the server's estimate).  Starts the
+ * worker threads on the current device.  Errors: EINVAL, ENOMEM. */
 anova_status anova_server_create(int32_t n_workers, int64_t hbm_budget_bytes, anova_server** out);
 
 /*
@@ -393,6 +405,9 @@ anova_status anova_server_create(int32_t n_workers, int64_t hbm_budget_bytes, an
  * stay valid until anova_server_wait on the returned ticket has returned.
  * windows / n (host, copied), ell, m, eps_B as in anova_fastsum_plan (sigma 2,
  * p 8); lambda, tol, maxit as in krr_cg_solve.  The ticket also names the model.
+ * Returns at once; the fit's own errors arrive through anova_server_wait.
+ * Errors: EINVAL (NULL server or ticket, P outside 1..256, N < 0, maxit out of
+ * range).
  */
 anova_status anova_server_submit_fit(anova_server* server, const double* points, int64_t N, int32_t d,
                                      const int32_t* windows, int32_t P, double ell, const int32_t* n,
@@ -400,13 +415,19 @@ anova_status anova_server_submit_fit(anova_server* server, const double* points,
                                      int32_t maxit, int64_t* ticket);
 
 /* Queue a prediction at M test points Z (device, M x d) into out (device, M)
- * with the model of fit ticket `model` (waits for that fit if needed). */
+ * with the model of fit ticket `model` (waits for that fit if needed); Z and
+ * out must stay valid until anova_server_wait on the returned ticket has
+ * returned.  Errors: EINVAL (NULL server or ticket, M < 0, `model` not a fit
+ * ticket); a prediction whose fit failed or whose model was released
+ * completes with EINVAL through anova_server_wait. */
 anova_status anova_server_submit_predict(anova_server* server, int64_t model, const double* Z, int64_t M,
                                          double* out, int64_t* ticket);
 
-/* Block until the request is done; result receives its status, latency_ms the
- * time from submission to completion; iterations / relres the CG figures of a
- * fit.  Output pointers may be NULL. */
+/* Block until the request is done; result receives its status (its detail in
+ * anova_last_error), latency_ms the time from submission to completion;
+ * iterations / relres the CG figures of a fit.  Output pointers may be NULL.
+ * A prediction's ticket is forgotten after its wait; a fit's stays (it names
+ * the model).  Errors: EINVAL (NULL server, unknown ticket). */
 anova_status anova_server_wait(anova_server* server, int64_t ticket, anova_status* result, double* latency_ms,
                                int32_t* iterations, double* relres);
 
@@ -417,7 +438,8 @@ anova_status anova_server_wait(anova_server* server, int64_t ticket, anova_statu
 anova_status anova_server_release(anova_server* server, int64_t model);
 
 /* Latency percentiles of the completed requests, their number, and the budgeted
- * bytes currently held (resident models and running requests). */
+ * bytes currently held (resident models and running requests).  Output
+ * pointers may be NULL.  Errors: EINVAL (NULL server). */
 anova_status anova_server_stats(anova_server* server, double* p50_ms, double* p99_ms, int64_t* completed,
                                 int64_t* bytes_in_use);
 
@@ -460,7 +482,8 @@ const char* anova_last_error(void);
 /*
  * anova_plan_window -- frame and grid of window l (Sec. 4.2 scaled nodes):
  * torus coordinate = scale * (x - centre).  centre (host, 3 doubles, unused
- * entries 0), scale, ell_l = scale * ell, dims (1..3), n, nos = sigma*n.
+ * entries 0), scale, ell_l = scale * ell, dims (1..3), n, nos = sigma*n; output
+ * pointers may be NULL.  Host only.  Errors: EINVAL (NULL plan, l out of range).
  */
 anova_status anova_plan_window(const anova_plan* plan, int32_t l, double* centre, double* scale,
                                double* ell_l, int32_t* dims, int32_t* n, int32_t* nos);
@@ -472,11 +495,16 @@ anova_status anova_plan_window(const anova_plan* plan, int32_t l, double* centre
  *   g_u = sum_j alpha_j prod_t psi(nos x_{j,t} - u_t),
  * where psi is the Kaiser-Bessel window normalised to psi(0) = 1, i.e. the
  * window phi(t) = sinh(b sqrt(m^2-t^2)) / (pi sqrt(m^2-t^2)) divided by phi(0).
+ * alpha: device, N entries of dtype in the user's node order.  Asynchronous on
+ * `stream`.  Errors: EINVAL (bad plan, l, dtype the plan does not hold, NULL
+ * pointers).
  */
 anova_status anova_debug_spread(anova_plan* plan, int32_t l, int32_t dtype, const void* alpha,
                                 void* grid, void* stream);
 
-/* Bin side, region side and whether window l runs on the dense kernels. */
+/* Bin side, region side and whether window l runs on the dense kernels (the
+ * binning is a GPU design choice; the paper fixes none).  Output pointers may
+ * be NULL.  Host only.  Errors: EINVAL (NULL plan, l out of range). */
 anova_status anova_plan_window_bins(const anova_plan* plan, int32_t l, int32_t* bin_side, int32_t* region,
                                     int32_t* dense);
 
@@ -492,9 +520,10 @@ anova_status anova_plan_window_bins(const anova_plan* plan, int32_t l, int32_t* 
  * The default rule: 3-D windows take bins of 2 cells (4 when 2 gives too many
  * bins) while the region stays within 16 cells; 2-D windows bins of 2 cells;
  * 1-D windows bins of 16 - 2m cells (2 on grids too small for that); other
- * windows the generic kernels.  A
- * requested side is taken when it is even, its region stays within 16 cells,
- * the bins number at most 32768 and side + m - 2 < sigma n.
+ * windows the generic kernels.  A requested side is taken when it is even, its
+ * region stays within 16 cells, the bins number at most 32768 and
+ * side + m - 2 < sigma n.
+ * The paper fixes no binning; this is the GPU design's rule.
  * Errors: EINVAL for arguments anova_fastsum_plan would reject, or a grid
  * too fine for the binning.
  */
@@ -504,6 +533,7 @@ anova_status anova_plan_bin_rule(int32_t dims, int32_t n, int32_t m, double sigm
  * anova_debug_diag -- copy window l's FP64 multiplier D_k (host, n^dims
  * doubles, centred index) = b_k / prod_t psihat(k_t)^2 with the normalised
  * window (Sec. 4.3 D = diag(c_k) with the window deconvolution folded in).
+ * Synchronous.  Errors: EINVAL (NULL plan or output, l out of range), ECUDA.
  */
 anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host);
 
@@ -514,16 +544,20 @@ anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host)
  * last call (which resets them):
  *   0 spreading, 1 forward FFT, multiply by D, inverse FFT, 2 gathering,
  *   3 window sum and CG vector kernels (grid clearing is a memset, not timed).
- * `ms` and `launches` are host arrays of `cap` entries; returns the number of
- * stages written.  Reading synchronises the recorded events.
+ * `ms` and `launches` are host arrays of `cap` entries (either may be NULL);
+ * returns the number of stages written (0 for a NULL plan).  Reading
+ * synchronises the recorded events.  While timing is on, captured graphs are
+ * not replayed.  The paper has no counterpart: a measurement aid.
+ * anova_set_profiling errors: EINVAL (NULL plan).
  */
 anova_status anova_set_profiling(anova_plan* plan, int32_t enable);
+int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap);
 
 /* Graph capture and replay of anova_matvec / krr_cg_solve on (enable != 0,
  * the default) or off; switching off drops the captured graphs.  The paper has
- * no counterpart: this is a launch-overhead setting. */
+ * no counterpart: this is a launch-overhead setting.  Errors: EINVAL (NULL
+ * plan). */
 anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable);
-int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap);
 
 #ifdef __cplusplus
 }

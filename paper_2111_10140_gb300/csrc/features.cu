@@ -336,6 +336,11 @@ anova_status anova_windows_from_mis(const double* mis, int32_t d, double thresho
         set_error("anova_windows_from_mis: bad arguments");
         return ANOVA_EINVAL;
     }
+    for (int f = 0; f < d; f++)
+        if (!std::isfinite(mis[f])) {   // the ranking needs a total order of the scores
+            set_error("anova_windows_from_mis: score " + std::to_string(f) + " is not finite");
+            return ANOVA_EINVAL;
+        }
     std::vector<int> order(d);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mis[a] > mis[b]; });

@@ -116,6 +116,24 @@ def test_bin_rule_is_host_logic(lib):
         assert e.value.status == B.EINVAL
 
 
+def test_windows_from_mis_is_host_logic_matching_the_reference(lib):
+    """anova_windows_from_mis runs on the host: the same windows as the
+    reference grouping of Sec. 5 for random scores with ties and thresholds."""
+    import numpy as np
+    from oracle import features as F
+    from paper_2111_10140_gb300 import binding as B
+    rng = np.random.default_rng(3)
+    for trial in range(200):
+        d = int(rng.integers(1, 40))
+        s = np.round(rng.uniform(0, 1, d), int(rng.integers(1, 3)))    # rounding makes ties
+        thr = float(rng.choice([0.0, 0.2, 0.5, 1.1]))
+        assert B.anova_windows_from_mis(s, thr) == F.windows_from_mis(list(s), thr)
+    for bad in (np.array([0.1, np.nan, 0.3]), np.array([np.inf, 0.2])):
+        with pytest.raises(B.AnovaError) as e:
+            B.anova_windows_from_mis(bad)
+        assert e.value.status == B.EINVAL
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2111_10140_gb300 import binding as B
     monkeypatch.setattr(B, "_lib", None)
