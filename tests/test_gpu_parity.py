@@ -349,6 +349,15 @@ def test_full_mid_workload_parity(B, torch):
     idx = np.random.default_rng(7).choice(w.N, 500, replace=False)
     direct = oracle.direct(w.X[idx], w.X, w.windows, w.eta, w.ell, w.alpha)
     assert rel(out32.cpu().numpy()[idx], direct) <= 1e-5
+    # the launch configuration the benchmark times: 3-D bins of 4 cells (region 16)
+    X = torch.from_numpy(w.X).cuda()
+    plan16 = B.anova_fastsum_plan_bins(X, w.windows, w.ell, [0, 0, 4], n=w.n, m=w.m, sigma=w.sigma,
+                                       eps_B=w.epsB, p=w.p, precision=B.MIXED)
+    assert B.anova_plan_window_bins(plan16, 0)["region"] == 16
+    B.anova_matvec(plan16, a64, out)
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+    B.anova_matvec(plan16, a32, out32)
+    assert rel(out32.cpu().numpy(), ref) <= 1e-5
 
 
 @pytest.mark.parametrize("n,m", [(64, 6), (16, 7), (16, 5), (16, 3), (8, 1)])
