@@ -207,7 +207,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
-    if rank == 0 or not os.path.exists(B.lib_path()):
+    if rank == 0:   # one builder; the other ranks load its library after the barrier
         __graft_entry__.build()
     if ws > 1:
         dist.barrier()
