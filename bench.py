@@ -1,6 +1,8 @@
-"""Benchmark: ANOVA fast-summation matvec throughput (Gpts/s) on the mid
-workload (N = 1e5, d = 9, three 3-D windows, n = 32, m = 6, sigma = 2), plus
-KRR CG solves/s and p50/p99 step latency.
+"""Benchmark: ANOVA fast-summation matvec throughput (Gpts/s) on the
+precision form (N = 1e6, d = 28, nine windows: 3 x 3-D at n = 32, 4 x 2-D and
+2 x 1-D at n = 64, m = 6, sigma = 2), plus KRR solves/s, p50/p99 step latency
+and, as a secondary key, the same figures on the mid workload (N = 1e5, three
+3-D windows) where the plain FP64 solve is timed beside the mixed one.
 
 A step is one full ANOVA matvec K alpha (all windows: spread, FFT, multiply,
 inverse FFT, gather, weighted window sum) in FP32 through the C ABI, inputs
@@ -10,11 +12,14 @@ replica (the path has no exchange step); value = points of all ranks / max
 time over ranks.
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the
-method used for parity) on the same workload on the host cores, rank 0 only.
+method used for parity) on the same workload on the host cores, rank 0 only:
+every step is the oracle's fast summation of a bounded slice of the
+workload's points.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -29,28 +34,59 @@ if ROOT not in sys.path:
 
 METRIC = "ANOVA fastsum matvec Gpts/s & KRR solves/s at rel err 1e-5; p50/p99 latency"
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+CSRC = os.path.join(ROOT, "paper_2111_10140_gb300", "csrc")
 
 
 def fp32_peak_tflops():
     return 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def tf32_peak_tflops():
+def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16 = float(json.load(f)["bf16_tflops"])
+            return json.load(f), "measured"
     except Exception:
-        bf16 = 1900.0   # fallback figure for a GB300
-    return bf16 * (1.1 / 2.25)
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture of the
-# current kernels on this workload (profiles/); None for a kernel not captured since it changed
-TRAFFIC = {"k_spread3_tc<16>": 59711000 + 14000, "k_gather3_umma<16>": 59438500 + 3700}
+def tf32_peak_tflops():
+    pk, _ = measured_peaks()
+    return float(pk["bf16_tflops"]) * (1.1 / 2.25)
 
 
-def traffic_per_launch(name):
-    return TRAFFIC.get(name)
+def source_sha(files):
+    """sha256 (first 16 hex digits) of the concatenated sources a kernel is built from."""
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel, workload, path=None):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu summary, or None when there is none or when the kernel's
+    sources have changed since the counters were taken.  Rows of the table in
+    profiles/dram_traffic.md: | kernel | workload | bytes per launch | sources | sha |"""
+    try:
+        with open(path or TRAFFIC_FILE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
+        if len(cells) < 5 or cells[0] != kernel or cells[1] != workload:
+            continue
+        try:
+            nbytes = int(cells[2].replace(",", ""))
+            files = [x.strip() for x in cells[3].split("+")]
+            if source_sha(files) != cells[4]:
+                return None
+        except (ValueError, OSError):
+            return None
+        return nbytes
+    return None
 
 
 def max_over_ranks(ms, ws, device=None):
@@ -131,21 +167,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def workload_config(w):
+    """The `config` object of both arms: the workload by its sizes (no plan choices)."""
+    dims = [len(x) for x in w.windows]
+    desc = "+".join(f"{dims.count(k)}x{k}D" for k in (3, 2, 1) if dims.count(k))
+    return {"workload": w.name, "N": w.N, "d": w.d, "windows": desc,
+            "n": sorted(set(w.n), reverse=True), "m": w.m, "sigma": w.sigma, "eps_B": w.epsB, "ell": w.ell,
+            "lambda": w.lam, "tol": w.tol}
+
+
 def run_reference(args):
-    """Time the FP64 CPU oracle's fast summation on a bounded sample of the workload."""
+    """Time the FP64 CPU oracle's fast summation: every step is the oracle's
+    fast summation of a slice of `--ref-sample` consecutive points of the
+    benchmark workload (slices rotate through the N points)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
     import oracle
     from paper_2111_10140_gb300 import workloads as W
     oracle.build()
-    w = W.plain_mid()
-    ns = args.ref_sample
-    Xs, alpha = w.X[:ns], w.alpha[:ns]
+    w = W.precision_form()
+    ns = min(args.ref_sample, w.N)
     cores = len(os.sched_getaffinity(0))
     times = []
     for it in range(args.warmup + args.steps):
+        lo = (it * ns) % (w.N - ns + 1)
+        Xs, alpha = w.X[lo:lo + ns], w.alpha[lo:lo + ns]
         t0 = time.perf_counter()
         oracle.fastsum(None, Xs, w.windows, w.eta, w.ell, w.n, w.m, alpha, sigma=w.sigma, epsB=w.epsB, p=w.p)
         dt = time.perf_counter() - t0
@@ -153,22 +200,22 @@ def run_reference(args):
             times.append(dt)
     t = sum(times) / len(times)
     value = ns / t / 1e9
-    sample = f"oracle fast summation on the first {ns} of {w.N} points (same windows, n, m, sigma, eps_B)"
+    sample = (f"each step: the oracle's FP64 fast summation (OpenMP) of {ns} consecutive points of the "
+              f"{w.N}-point workload (slices rotate), same windows, n, m, sigma, eps_B")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "N": w.N, "windows": "3x3D", "n": 32, "m": 6, "sigma": 2.0,
-                       "eps_B": w.epsB, "ell": w.ell},
+            "config": workload_config(w),
             "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(ns, what="fastsum", data=None):
-    """One timed oracle run on a bounded sample: the fast summation of the mid
-    workload (about 10-30 s of CPU work), or with what="features" the window
-    construction (z-score fit on all rows of `data` = (X, labels), MIS on the
-    first ns rows)."""
+def cpu_baseline(ns, what="fastsum", data=None, workload=None):
+    """One timed oracle run on a bounded sample: the fast summation of the
+    first ns points of `workload` (default the precision form; about 10-30 s
+    of CPU work), or with what="features" the window construction (z-score
+    fit on all rows of `data` = (X, labels), MIS on the first ns rows)."""
     import oracle
     from paper_2111_10140_gb300 import workloads as W
     if what == "features":
@@ -183,14 +230,114 @@ def cpu_baseline(ns, what="fastsum", data=None):
         return {"zscore_fit_s": t_fit, "mis_s": t_mis, "mis_rows": ns, "cores": 1, "kind": "oracle",
                 "sample": f"numpy z-score fit on {X.shape[0]} x {X.shape[1]}; Python-loop MIS on the first {ns} rows"}
     oracle.build()
-    w = W.plain_mid()
+    w = workload if workload is not None else W.precision_form()
+    ns = min(ns, w.N)
     t0 = time.perf_counter()
     oracle.fastsum(None, w.X[:ns], w.windows, w.eta, w.ell, w.n, w.m, w.alpha[:ns], sigma=w.sigma,
                    epsB=w.epsB, p=w.p)
     t = time.perf_counter() - t0
     return {"value": ns / t / 1e9, "unit": "Gpts/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"one oracle fast summation (FP64, OpenMP) on the first {ns} of {w.N} points, "
-                      f"same windows/n/m/sigma/eps_B; {t:.2f} s"}
+            "sample": f"one oracle fast summation (FP64, OpenMP) of the first {ns} of the {w.N} points of "
+                      f"{w.name}, same windows/n/m/sigma/eps_B; {t:.2f} s"}
+
+
+STAGES = ["spread", "fft", "gather", "window_sum", "spread_3d_kernel", "gather_3d_kernel"]
+
+
+def time_matvec(B, plan, alpha, out, flush, steps, warmup, stream, lead_in_s=0.0):
+    """Per-step CUDA-event times of anova_matvec with an L2 flush before every step."""
+    import torch
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        B.anova_matvec(plan, alpha, out)
+    torch.cuda.synchronize()
+    # keep the GPU busy before the timed region so that the 200 ms clock samples straddle it
+    t_end = time.perf_counter() + lead_in_s
+    while time.perf_counter() < t_end:
+        for _ in range(20):
+            B.anova_matvec(plan, alpha, out)
+        torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        B.anova_matvec(plan, alpha, out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def stage_profile(B, plan, alpha, out, flush, steps):
+    """Milliseconds and launches per stage over `steps` profiled matvecs (library events)."""
+    import torch
+    B.anova_set_profiling(plan, True)
+    B.anova_stage_times(plan)   # reset
+    for i in range(steps):
+        flush.fill_(float(i))
+        B.anova_matvec(plan, alpha, out)
+    torch.cuda.synchronize()
+    ms, la = B.anova_stage_times(plan)
+    B.anova_set_profiling(plan, False)
+    return dict(zip(STAGES, ms)), dict(zip(STAGES, la))
+
+
+def dominant_roofline(B, plan, w, stage_ms, stage_la, steps):
+    """Roofline of the slower of the 3-D spread and 3-D gather kernels (one launch
+    each per matvec, covering every 3-D window), timed live by library events on
+    the launch stream.  Algorithmic work: one FP32 multiply-add (2 flop) per tap
+    (2m+1)^3, node and 3-D window."""
+    P3 = sum(1 for x in w.windows if len(x) == 3)
+    l3 = next(l for l, x in enumerate(w.windows) if len(x) == 3)
+    R = B.anova_plan_window_bins(plan, l3)["region"]
+    names = B.anova_dense3_kernels(plan)
+    key = "spread_3d_kernel" if stage_ms["spread_3d_kernel"] >= stage_ms["gather_3d_kernel"] else "gather_3d_kernel"
+    kernel = (names["spread"] if key == "spread_3d_kernel" else names["gather"]).replace("<R>", f"<{R}>")
+    launches = max(1, stage_la[key])
+    per_launch_ms = stage_ms[key] / launches
+    units = w.N * P3 * steps / launches                      # node-windows per launch
+    taps = (2 * w.m + 1) ** 3
+    flops = 2.0 * taps * units
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    tc_flops = 3.0 * flops                                    # 3xTF32: three TF32 products per FP32 multiply-add
+    tf32 = tf32_peak_tflops()
+    _, src = measured_peaks()
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_per_launch(kernel, w.name),
+            "units_per_launch": units, "flop_per_unit": 2 * taps,
+            "peak_source": f"derived FP32 FMA peak ({FP32_PEAK_NOTE}); algorithmic FP32 multiply-adds "
+                           f"(executed on tcgen05 / mma.sync tensor cores as 3xTF32)",
+            "tensor_view": {"achieved": tc_flops / (per_launch_ms * 1e-3) / 1e12, "peak": tf32,
+                            "frac": tc_flops / (per_launch_ms * 1e-3) / 1e12 / tf32,
+                            "what": "the FP32-accurate contraction as 3 TF32 products per multiply-add, unpadded",
+                            "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25"},
+            "per_launch_ms": per_launch_ms,
+            "stage_ms_per_step": {k: v / steps for k, v in stage_ms.items()}}
+
+
+def accuracy_vs_direct(B, torch, np, X, w, out, rows_n, seed, dev):
+    """Relative 2-norm error of the FP32 product against the FP64 direct sum on sampled rows."""
+    rows = torch.from_numpy(np.sort(np.random.default_rng(seed).choice(w.N, rows_n, replace=False))).to(dev)
+    dref = torch.empty(rows_n, dtype=torch.float64, device=dev)
+    B.anova_direct_matvec(X[rows].contiguous(), X, w.windows, w.ell, torch.from_numpy(w.alpha).to(dev), dref,
+                          dtype=B.FP64)
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(out.double()[rows] - dref) / torch.linalg.norm(dref)).item()
+    return {"rel_err_vs_direct": err, "sample_rows": rows_n, "direct": "anova_direct_matvec FP64",
+            "target": 1e-5, "meets_target": bool(err <= 1e-5)}
+
+
+def krr_solve(B, torch, plan, w, dev, maxit, what):
+    y = torch.from_numpy(w.y).to(dev)
+    sol = torch.zeros_like(y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, its, rel = B.krr_cg_solve(plan, w.lam, y, sol, w.tol, maxit)
+    t = time.perf_counter() - t0
+    return {"solves_per_s": 1.0 / t, "seconds": t, "iterations": int(its[0]), "relres": float(rel[0]),
+            "status": int(st), "converged": bool(st == B.OK and rel[0] <= w.tol), "precision": what,
+            "tol": w.tol, "lambda": w.lam}
 
 
 def run_ours(args):
@@ -215,107 +362,43 @@ def run_ours(args):
     # the CPU baseline runs before any kernel work (rank 0, N = 1 only)
     cpu = cpu_baseline(args.cpu_sample) if (rank == 0 and ws == 1 and not args.skip_cpu) else None
 
-    w = W.plain_mid(seed=1 + rank)
+    w = W.precision_form(seed=2 + rank)
     N = w.N
     X = torch.from_numpy(w.X).to(dev)
     # bin sides per window dimension from the library's autotuner (outside any timed region)
-    sides = [0, 0, 0]
     if args.bin_side:
         sides = [int(v) for v in args.bin_side.split(",")]
     elif not args.no_autotune:
         sides, _ = B.anova_autotune_bins(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
-                                         precision=B.FP32, reps=10)
+                                         precision=B.FP32, reps=5)
+    else:
+        sides = [0, 0, 0]
     plan = B.anova_fastsum_plan_bins(X, w.windows, w.ell, sides, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
                                      precision=B.MIXED)
-    R = B.anova_plan_window_bins(plan, 0)["region"]
     alpha = torch.from_numpy(w.alpha).to(dev).float()
     out = torch.empty_like(alpha)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        B.anova_matvec(plan, alpha, out)
-
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        step()
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.__enter__()
-    # keep the GPU busy for ~0.6 s before the timed region so that the 200 ms
-    # nvidia-smi samples straddle it (the region itself is only milliseconds long)
-    t_end = time.perf_counter() + 0.6
-    while time.perf_counter() < t_end:
-        for _ in range(20):
-            step()
-        torch.cuda.synchronize()
+    step_ms = time_matvec(B, plan, alpha, out, flush, args.steps, args.warmup, stream, lead_in_s=0.6)
     if ws > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    # stage breakdown from a second, profiled pass (events between the stages)
-    B.anova_set_profiling(plan, True)
-    B.anova_stage_times(plan)   # reset
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        step()
-    torch.cuda.synchronize()
-    stage_ms, stage_launch = B.anova_stage_times(plan)
-    B.anova_set_profiling(plan, False)
     total_ms = max_over_ranks(sum(step_ms), ws, dev)
     ms_per_step = total_ms / args.steps
     value = aggregate_gpts(N, ws, args.steps, total_ms)
-    launches = int(sum(stage_launch))
 
-    # dominant kernel: spread (stage 0) or gather (stage 2); the dense 3-D kernels
-    # cover all windows of the step in one launch
-    taps = (2 * w.m + 1) ** 3
-    P = len(w.windows)
-    dom = 0 if stage_ms[0] >= stage_ms[2] else 2
-    dom_name = f"k_spread3_tc<{R}>" if dom == 0 else f"k_gather3_umma<{R}>"
-    per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
-    launches_per_step = max(1, stage_launch[dom] // args.steps)
-    # algorithmic work: one FP32 multiply-add (2 flop) per tap, node and window
-    flops_per_launch = 2.0 * taps * N * P / launches_per_step
-    achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops()
-    # the same launch seen from the tensor pipe: 3 TF32 products per padded region cell
-    tc_flops = 2.0 * 3 * (R * R * 16) * N * P / launches_per_step
-    tf32_peak = tf32_peak_tflops()
-    roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(dom_name),
-                "peak_source": f"derived FP32 FMA peak ({FP32_PEAK_NOTE}); algorithmic FP32 multiply-adds, "
-                               + ("executed as 3xTF32 mma.sync" if dom == 0 else "executed as 3xTF32 tcgen05.mma"),
-                "tensor_view": {"executed_tflops": tc_flops / (per_launch_ms * 1e-3) / 1e12, "peak": tf32_peak,
-                                "frac": tc_flops / (per_launch_ms * 1e-3) / 1e12 / tf32_peak,
-                                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 0.49"},
-                "per_launch_ms": per_launch_ms,
-                "stage_ms_per_step": {k: v / args.steps for k, v in
-                                      zip(["spread", "fft", "gather", "window_sum"], stage_ms)}}
+    # stage breakdown and the dominant kernel from a second, profiled pass (events between the stages)
+    stage_ms, stage_la = stage_profile(B, plan, alpha, out, flush, args.steps)
+    launches = int(sum(stage_la[k] for k in STAGES[:4]))
+    roofline = dominant_roofline(B, plan, w, stage_ms, stage_la, args.steps)
 
-    # accuracy of the timed operator: FP32 fast matvec vs the direct sum on sampled rows (GPU, exact FP64 kernel)
-    rows = torch.from_numpy(np.sort(np.random.default_rng(7).choice(N, args.check_rows, replace=False))).to(dev)
-    dref = torch.empty(args.check_rows, dtype=torch.float64, device=dev)
-    B.anova_direct_matvec(X[rows].contiguous(), X, w.windows, w.ell, torch.from_numpy(w.alpha).to(dev), dref,
-                          dtype=B.FP64)
-    step()
-    torch.cuda.synchronize()
-    err = (torch.linalg.norm(out.double()[rows] - dref) / torch.linalg.norm(dref)).item()
-    accuracy = {"rel_err_vs_direct": err, "sample_rows": args.check_rows, "direct": "anova_direct_matvec FP64",
-                "target": 1e-5, "meets_target": bool(err <= 1e-5)}
+    B.anova_matvec(plan, alpha, out)
+    accuracy = accuracy_vs_direct(B, torch, np, X, w, out, args.check_rows, 7, dev)
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     a_host = torch.from_numpy(w.alpha.astype(np.float32)).pin_memory()
@@ -326,7 +409,7 @@ def run_ours(args):
         s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s_ev.record(stream)
         alpha.copy_(a_host, non_blocking=True)
-        step()
+        B.anova_matvec(plan, alpha, out)
         o_host.copy_(out, non_blocking=True)
         e_ev.record(stream)
         e_ev.synchronize()
@@ -335,61 +418,75 @@ def run_ours(args):
     e2e_value = aggregate_gpts(N, ws, args.steps, max_over_ranks(sum(e2e_ms), ws, dev))
 
     # KRR solves/s (mixed precision: FP32 inner CG, FP64 refinement) to the workload's tolerance
-    krr = None
-    if not args.skip_krr:
-        y = torch.from_numpy(w.y).to(dev)
-        sol = torch.zeros_like(y)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, its, rel = B.krr_cg_solve(plan, w.lam, y, sol, w.tol, 5000)
-        t = time.perf_counter() - t0
-        krr = {"solves_per_s": 1.0 / t, "seconds": t, "iterations": int(its[0]), "relres": float(rel[0]),
-               "status": int(st), "precision": "mixed (FP32 inner CG, FP64 refinement)", "tol": w.tol,
-               "lambda": w.lam}
-
+    krr = None if args.skip_krr else krr_solve(B, torch, plan, w, dev, 20000,
+                                               "mixed (FP32 inner CG, FP64 refinement)")
     clk.__exit__(None, None, None)
-    krr64 = None
-    if not args.skip_krr and not args.skip_fp64:
-        plan64 = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
-                                      precision=B.FP64)
-        y = torch.from_numpy(w.y).to(dev)
-        sol = torch.zeros_like(y)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, its, rel = B.krr_cg_solve(plan64, w.lam, y, sol, w.tol, 5000)
-        t = time.perf_counter() - t0
-        a64 = torch.from_numpy(w.alpha).to(dev)
-        o64 = torch.empty_like(a64)
-        B.anova_matvec(plan64, a64, o64)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(5):
-            B.anova_matvec(plan64, a64, o64)
-        e1.record(stream)
-        e1.synchronize()
-        krr64 = {"solves_per_s": 1.0 / t, "seconds": t, "iterations": int(its[0]), "relres": float(rel[0]),
-                 "status": int(st), "precision": "plain FP64 CG on the FP64 operator", "tol": w.tol,
-                 "fp64_matvec_ms": e0.elapsed_time(e1) / 5}
-        plan64.close()
+    plan.close()
+    del X
+
+    # secondary key: the mid workload, where the plain FP64 solve is timed beside the mixed one
+    mid = None
+    if not args.skip_mid:
+        wm = W.plain_mid(seed=1 + rank)
+        Xm = torch.from_numpy(wm.X).to(dev)
+        sm, _ = B.anova_autotune_bins(Xm, wm.windows, wm.ell, n=wm.n, m=wm.m, sigma=wm.sigma, eps_B=wm.epsB,
+                                      p=wm.p, precision=B.FP32, reps=5)
+        pm = B.anova_fastsum_plan_bins(Xm, wm.windows, wm.ell, sm, n=wm.n, m=wm.m, sigma=wm.sigma, eps_B=wm.epsB,
+                                       p=wm.p, precision=B.MIXED)
+        am = torch.from_numpy(wm.alpha).to(dev).float()
+        om = torch.empty_like(am)
+        mid_ms = time_matvec(B, pm, am, om, flush, args.steps, args.warmup, stream)
+        mst, mla = stage_profile(B, pm, am, om, flush, args.steps)
+        mroof = dominant_roofline(B, pm, wm, mst, mla, args.steps)
+        B.anova_matvec(pm, am, om)
+        macc = accuracy_vs_direct(B, torch, np, Xm, wm, om, 2048, 7, dev)
+        mkrr = None if args.skip_krr else krr_solve(B, torch, pm, wm, dev, 5000,
+                                                    "mixed (FP32 inner CG, FP64 refinement)")
+        pm.close()
+        mkrr64 = None
+        if not args.skip_krr and not args.skip_fp64:
+            p64 = B.anova_fastsum_plan(Xm, wm.windows, wm.ell, n=wm.n, m=wm.m, sigma=wm.sigma, eps_B=wm.epsB,
+                                       p=wm.p, precision=B.FP64)
+            mkrr64 = krr_solve(B, torch, p64, wm, dev, 5000, "plain FP64 CG on the FP64 operator")
+            a64 = torch.from_numpy(wm.alpha).to(dev)
+            o64 = torch.empty_like(a64)
+            B.anova_matvec(p64, a64, o64)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                B.anova_matvec(p64, a64, o64)
+            e1.record(stream)
+            e1.synchronize()
+            mkrr64["fp64_matvec_ms"] = e0.elapsed_time(e1) / 5
+            p64.close()
+        mid = {"config": workload_config(wm), "bin_side_1d_2d_3d": sm,
+               "value": wm.N * len(mid_ms) / (sum(mid_ms) * 1e-3) / 1e9, "unit": "Gpts/s",
+               "ms_per_step": sum(mid_ms) / len(mid_ms), "roofline": mroof, "accuracy": macc,
+               "krr": mkrr, "krr_plain_fp64": mkrr64}
+        del Xm
+
     q = sorted(step_ms)
     lat = {"p50": q[len(q) // 2], "p99": q[min(len(q) - 1, int(0.99 * len(q)))], "unit": "ms"}
     if rank == 0:
+        cfg = workload_config(w)
+        cfg.update({"precision": "fp32 operator (spread, FFT, gather); FP64 CG scalars and refinement",
+                    "l2": "flushed before every step (256 MB write outside the step events)",
+                    "parallelism": f"replicas x{ws}"})
         line = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name, "N": N, "d": 9, "windows": "3x3D", "n": 32, "m": 6,
-                           "sigma": 2.0, "eps_B": w.epsB, "ell": w.ell, "precision": "fp32 operator",
-                           "bin_side_1d_2d_3d": sides, "bin_sides": "given" if args.bin_side else ("autotuned" if not args.no_autotune else "rule"),
-                           "l2": "flushed before every step (256 MB write outside the step events)",
-                           "parallelism": f"replicas x{ws}"},
+                "config": cfg,
+                "plan": {"bin_side_1d_2d_3d": sides,
+                         "bin_sides": "given" if args.bin_side else ("autotuned" if not args.no_autotune else "rule")},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": 4 * N,
                         "d2h_bytes_per_step": 4 * N},
-                "gpu_launches": launches, "latency_ms": lat, "accuracy": accuracy, "krr": krr, "krr_plain_fp64": krr64,
-                "clocks": dict(clk.summary(), window="0.6 s busy lead-in, timed steps, e2e steps and the KRR solve")}
+                "gpu_launches": launches, "latency_ms": lat, "accuracy": accuracy, "krr": krr,
+                "plain_mid": mid,
+                "clocks": dict(clk.summary(), window="0.6 s busy lead-in, timed steps, profiled steps, e2e steps "
+                                                     "and the KRR solve of the headline workload")}
         print(json.dumps(line), flush=True)
-    plan.close()
     if ws > 1:
         dist.destroy_process_group()
 
@@ -803,11 +900,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
-    ap.add_argument("--ref-sample", type=int, default=10_000)
+    ap.add_argument("--ref-sample", type=int, default=40_000)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-krr", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
-    ap.add_argument("--check-rows", type=int, default=2048)
+    ap.add_argument("--check-rows", type=int, default=10_000)
+    ap.add_argument("--skip-mid", action="store_true", help="no secondary mid-workload figures")
     ap.add_argument("--no-autotune", action="store_true", help="bin sides from the default rule")
     ap.add_argument("--bin-side", default="", help="bin sides for 1-D,2-D,3-D windows (e.g. 0,0,4), no autotuning")
     ap.add_argument("--crossover", action="store_true",

@@ -543,7 +543,9 @@ anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host)
  * the accumulated milliseconds and kernel launch counts per stage since the
  * last call (which resets them):
  *   0 spreading, 1 forward FFT, multiply by D, inverse FFT, 2 gathering,
- *   3 window sum and CG vector kernels (grid clearing is a memset, not timed).
+ *   3 window sum and CG vector kernels (grid clearing is a memset, not timed),
+ *   4 the 3-D spread kernel launches alone (part of 0), 5 the 3-D gather
+ *   kernel launches alone (part of 2).
  * `ms` and `launches` are host arrays of `cap` entries (either may be NULL);
  * returns the number of stages written (0 for a NULL plan).  Reading
  * synchronises the recorded events.  While timing is on, captured graphs are
@@ -552,6 +554,12 @@ anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host)
  */
 anova_status anova_set_profiling(anova_plan* plan, int32_t enable);
 int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap);
+
+/* Names of the FP32 3-D spread and gather kernels the plan launches (static
+ * strings such as "k_spread3_tc<R>", R standing for the region size), so that
+ * a measurement can name the kernel stages 4 and 5 time.  The paper has no
+ * counterpart: a measurement aid.  Errors: EINVAL (a NULL argument). */
+anova_status anova_plan_dense3_kernels(const anova_plan* plan, const char** spread, const char** gather);
 
 /* Graph capture and replay of anova_matvec / krr_cg_solve on (enable != 0,
  * the default) or off; switching off drops the captured graphs.  The paper has

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "anova_debug_diag": (_i32, [_vp, _i32, _pf64]),
     "anova_set_profiling": (_i32, [_vp, _i32]),
     "anova_stage_times": (_i32, [_vp, _pf64, _pi64, _i32]),
+    "anova_plan_dense3_kernels": (_i32, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_char_p)]),
 }
 
 
@@ -327,6 +328,14 @@ def anova_stage_times(plan: Plan):
     la = (ctypes.c_int64 * 8)()
     k = lib().anova_stage_times(plan.handle, ms, la, 8)
     return list(ms[:k]), list(la[:k])
+
+
+def anova_dense3_kernels(plan: Plan) -> dict:
+    """Kernel names of the plan's FP32 3-D spread and gather ("<R>": the region size)."""
+    sp, ga = ctypes.c_char_p(), ctypes.c_char_p()
+    _check(lib().anova_plan_dense3_kernels(plan.handle, ctypes.byref(sp), ctypes.byref(ga)),
+           "anova_plan_dense3_kernels")
+    return {"spread": sp.value.decode(), "gather": ga.value.decode()}
 
 
 def anova_zscore_fit(X, stream=None):

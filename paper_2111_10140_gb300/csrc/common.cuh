@@ -122,11 +122,14 @@ struct DenseWin {
 
 struct StageClock {
     bool enabled = false;
-    static constexpr int kStages = 4;
+    // 0 spread, 1 FFT / multiply / inverse FFT, 2 gather, 3 window sum and CG vectors;
+    // 4 and 5 time the 3-D spread and 3-D gather launches alone (inside stages 0 and 2)
+    static constexpr int kStages = 6;
     std::vector<cudaEvent_t> ev;       // pairs (start, stop)
     std::vector<int> stage_of_pair;
-    double ms[kStages] = {0, 0, 0, 0};
-    int64_t launches[kStages] = {0, 0, 0, 0};
+    double ms[kStages] = {0, 0, 0, 0, 0, 0};
+    int64_t launches[kStages] = {0, 0, 0, 0, 0, 0};
+    int open[kStages] = {-1, -1, -1, -1, -1, -1};   // index in ev of the stage's open start event
 };
 
 }  // namespace anova
@@ -299,7 +302,8 @@ anova_status fft3_box_run(const Fft3Win* wins, const Fft3Shape& sh, int sm_count
 size_t fft12_window_smem(const WindowPlan& w, size_t real_bytes);
 bool fft3_slab_supported(const WindowPlan& w);
 template <typename T>
-anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st);
+anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st,
+                              int* launches = nullptr);
 template <typename T>
 anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st);
 

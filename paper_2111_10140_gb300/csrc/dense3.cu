@@ -1118,7 +1118,8 @@ anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_b
 }
 
 template <typename T>
-anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st) {
+anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st,
+                              int* launches) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
     // the sorted coefficient copies serve the 1-D / 2-D kernels and the packed
@@ -1130,7 +1131,9 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
         k_sort_alpha<<<grid_for(plan->N * nd, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
             descs, nd, plan->N, alpha, alpha_double);
         ANOVA_CHECK_LAUNCH();
+        if (launches) ++*launches;
     }
+    if (launches) *launches += (int)plan->dense_groups.size();
     for (const auto& g : plan->dense_groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
         const int4* sub = plan->dense_sub + g[1];
@@ -1155,10 +1158,12 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
             ANOVA_CHECK_LAUNCH();
             continue;
         }
+        clock_begin(plan, 4, st);
         if (sizeof(T) == 4 && table_kernels(plan, R))
             ANOVA_TRY(spread_table(plan, R, sub, nsub, descs, alpha, alpha_double, st));
         else
             ANOVA_TRY(spread_dispatch<T>(plan, R, sub, nsub, descs, DenseWin(), alpha, alpha_double, st));
+        clock_end(plan, 4, 1, st);
     }
     return ANOVA_OK;
 }
@@ -1191,16 +1196,28 @@ anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
             ANOVA_CHECK_LAUNCH();
             continue;
         }
+        clock_begin(plan, 5, st);
         if (sizeof(T) == 4 && table_kernels(plan, R))
             ANOVA_TRY(gather_table(plan, R, sub, nsub, descs, st));
         else
             ANOVA_TRY(gather_dispatch<T>(plan, R, sub, nsub, descs, DenseWin(), st));
+        clock_end(plan, 5, 1, st);
     }
     return ANOVA_OK;
 }
 
-template anova_status dense3_spread_all<float>(anova_plan*, const void*, int, cudaStream_t);
-template anova_status dense3_spread_all<double>(anova_plan*, const void*, int, cudaStream_t);
+// kernel names of the FP32 3-D spread and gather the plan launches ("<R>" = region size)
+static const char* spread3_name(const anova_plan* plan) {
+    if (plan->spread_tc && plan->spread_umma) return "k_spread3_umma<R>";
+    return plan->spread_tc ? "k_spread3_tc<R>" : "k_spread3_f32<R>";
+}
+static const char* gather3_name(const anova_plan* plan) {
+    if (plan->gather_tc && plan->gather_umma) return "k_gather3_umma<R>";
+    return plan->gather_tc ? "k_gather3_tc<R>" : "k_gather3_f32<R>";
+}
+
+template anova_status dense3_spread_all<float>(anova_plan*, const void*, int, cudaStream_t, int*);
+template anova_status dense3_spread_all<double>(anova_plan*, const void*, int, cudaStream_t, int*);
 template anova_status dense3_gather_all<float>(anova_plan*, cudaStream_t);
 template anova_status dense3_gather_all<double>(anova_plan*, cudaStream_t);
 template anova_status spread3_dense<float>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,
@@ -1213,3 +1230,13 @@ template anova_status gather3_dense<double>(anova_plan*, const WindowPlan&, cons
                                             double*, cudaStream_t);
 
 }  // namespace anova
+
+extern "C" anova_status anova_plan_dense3_kernels(const anova_plan* plan, const char** spread, const char** gather) {
+    if (!plan || !spread || !gather) {
+        anova::set_error("anova_plan_dense3_kernels: NULL argument");
+        return ANOVA_EINVAL;
+    }
+    *spread = anova::spread3_name(plan);
+    *gather = anova::gather3_name(plan);
+    return ANOVA_OK;
+}

@@ -23,15 +23,18 @@ void clock_begin(anova_plan* plan, int stage, cudaStream_t st) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaEventRecord(a, st);
+    c.open[stage] = (int)c.ev.size();
     c.ev.push_back(a);
     c.ev.push_back(b);
     c.stage_of_pair.push_back(stage);
 }
 
+// closes the stage's most recent open pair (stages may nest: 4 inside 0, 5 inside 2)
 void clock_end(anova_plan* plan, int stage, int launches, cudaStream_t st) {
     StageClock& c = plan->clock;
-    if (!c.enabled || c.ev.empty()) return;
-    cudaEventRecord(c.ev.back(), st);
+    if (!c.enabled || c.open[stage] < 0) return;
+    cudaEventRecord(c.ev[c.open[stage] + 1], st);
+    c.open[stage] = -1;
     c.launches[stage] += launches;
 }
 
@@ -88,8 +91,7 @@ static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha
     int nl = 0;
     clock_begin(plan, 0, st);
     if (!plan->dense_windows.empty()) {
-        ANOVA_TRY(dense3_spread_all<T>(plan, alpha, alpha_is_double, st));
-        nl += (int)plan->dense_groups.size();
+        ANOVA_TRY(dense3_spread_all<T>(plan, alpha, alpha_is_double, st, &nl));
     }
     // windows not on the batched dense kernels: generic kernels, one window at a time
     // (FP64 runs the dense 1-D / 2-D windows here too)
@@ -693,6 +695,7 @@ int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32
     }
     c.ev.clear();
     c.stage_of_pair.clear();
+    for (int& o : c.open) o = -1;
     int k = std::min<int>(cap, StageClock::kStages);
     for (int i = 0; i < k; i++) {
         if (ms) ms[i] = c.ms[i];
