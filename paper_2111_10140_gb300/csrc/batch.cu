@@ -419,7 +419,9 @@ static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t
     ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st));
     ANOVA_TRY(fft3_box_run<float>(b->fft3, b->fft3_shape, b->sm_count, st));
     ANOVA_TRY(fft12_box_run<float>(b->fft12, b->n12, b->smem12, st, b->n12_uniform));
-    return dense_f32_gather_groups(b->m, b->plans[0]->psi_poly, b->sub, b->desc, b->groups, st);
+    return dense_f32_gather_groups(b->m, b->plans[0]->psi_poly, b->sub, b->desc, b->groups, st,
+                                   b->plans[0]->gather_tc5 ? b->plans[0]->psi_host.data() : nullptr,
+                                   b->plans[0]->sm_count);
 }
 
 static anova_status batch_iteration(anova_batch* b, double tol2, int maxit, cudaStream_t st) {

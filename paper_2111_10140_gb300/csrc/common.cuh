@@ -157,6 +157,8 @@ struct anova_plan {
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
     bool spread_umma = false;           // FP32 dense 3-D spread on tcgen05 instead of mma.sync
+    bool gather_tc5 = true;             // FP32 dense 3-D gather: persistent tcgen05 kernel, weights on the fly
+    std::vector<float> psi_host;        // host copy of psi_poly (kernel parameters of the persistent kernels)
     int bin_side[3] = {0, 0, 0};        // bin side of the dense 1-D / 2-D / 3-D windows (0: the default rule)
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
     anova::Fft3Win* fft3_desc = nullptr;    // device, 2 x fft3_windows.size(): FP64 then FP32
@@ -284,11 +286,16 @@ anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, const float* poly,
                           cudaStream_t st);
 anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
+// persistent tcgen05 3-D kernels (tc3.cu): (R, m) pairs built, and the launches
+bool tc5_supported(int R, int m);
+anova_status gather3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const float* psi_host,
+                         int sms, cudaStream_t st);
 uint64_t wait_timeouts_on(cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
 anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_base, const DenseWin* descs,
-                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
+                                     const float* psi_host = nullptr, int sms = 0);
 // Shapes of a batched 3-D box FFT launch (maxima over its windows).
 struct Fft3Shape {
     int nw = 0, nmax = 0, nosmax = 0, bx = 0, by = 0, bz = 0;

@@ -1050,6 +1050,8 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
 static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
+    if (plan->gather_tc5 && tc5_supported(R, plan->m))
+        return gather3_tc5(R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count, st);
     if (plan->gather_tc && plan->gather_umma) return gather3_umma(R, sub, nsub, descs, plan->m, plan->psi_poly, st);
     if (plan->gather_tc) {
         switch (R) {
@@ -1097,7 +1099,8 @@ anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin
 }
 
 anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_base, const DenseWin* descs,
-                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st) {
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
+                                     const float* psi_host, int sms) {
     for (const auto& g : groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
         const int4* sub = sub_base + g[1];
@@ -1107,7 +1110,10 @@ anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_b
 #define ANOVA_G(R_)                                                                           \
     case 100 + R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
     case 200 + R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
-    case 300 + R_: ANOVA_TRY(gather3_umma(R_, sub, nsub, descs, m, poly, st)); break;
+    case 300 + R_:                                                                            \
+        if (psi_host && tc5_supported(R_, m)) ANOVA_TRY(gather3_tc5(R_, m, sub, nsub, descs, psi_host, sms, st)); \
+        else ANOVA_TRY(gather3_umma(R_, sub, nsub, descs, m, poly, st));                      \
+        break;
             ANOVA_G(4) ANOVA_G(6) ANOVA_G(8) ANOVA_G(10) ANOVA_G(12) ANOVA_G(14) ANOVA_G(16)
 #undef ANOVA_G
             default: set_error("dense FP32 gather: unsupported window dimension or region size"); return ANOVA_EINVAL;
@@ -1212,6 +1218,8 @@ static const char* spread3_name(const anova_plan* plan) {
     return plan->spread_tc ? "k_spread3_tc<R>" : "k_spread3_f32<R>";
 }
 static const char* gather3_name(const anova_plan* plan) {
+    if (plan->gather_tc5 && tc5_supported(plan->dense_groups.empty() ? 0 : plan->dense_groups[0][0] % 100, plan->m))
+        return "k_gather3_tc5<R>";
     if (plan->gather_tc && plan->gather_umma) return "k_gather3_umma<R>";
     return plan->gather_tc ? "k_gather3_tc<R>" : "k_gather3_f32<R>";
 }

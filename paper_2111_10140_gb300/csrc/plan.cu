@@ -962,6 +962,10 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     ANOVA_CUDA_TRY(cudaMalloc(&plan->psi_poly, 2 * m * kPsiStride * sizeof(float)));
     k_psi_poly_fit<<<1, 64, 0, st>>>(m, plan->b, plan->psi_norm, plan->psi_poly);
     ANOVA_CHECK_LAUNCH();
+    plan->psi_host.assign(2 * m * kPsiStride, 0.f);
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->psi_host.data(), plan->psi_poly, plan->psi_host.size() * sizeof(float),
+                                   cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     size_t max_tk = 1;
     for (int l = 0; l < P; l++) {
         WindowPlan& w = plan->win[l];

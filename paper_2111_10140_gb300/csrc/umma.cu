@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "umma.cuh"
 
 namespace anova {
 
@@ -32,7 +33,6 @@ __device__ unsigned long long g_wait_timeouts = 0;
 constexpr int kUmmaThreads = 256;           // 128 (one column group) or 256 (two)
 constexpr int kUmmaMinBlocks = 3;           // resident blocks per SM asked of the compiler
 constexpr int kUmmaTile = 128;              // nodes per MMA tile (M)
-constexpr int kUmmaSpin = 1 << 22;          // mbarrier polls before giving up
 constexpr uint32_t kUmmaCols = 256;         // tensor-memory columns per block (N <= 256)
 constexpr size_t kUmmaSmem = 64 * 1024;     // shared memory requested per block at least (three blocks per SM:
                                             // two hold tensor memory, the third stages its operands)
@@ -43,25 +43,7 @@ constexpr bool kGatherPolyW = false;   // measured: 71 us against 45 us with the
 constexpr int kPolyFloats = kGatherPolyW ? 2 * 8 * kPsiStride : 0;   // coefficients for m <= 8
 constexpr int kWPitch = 52;                       // staged weight-table rows (floats; conflict-free float4 reads)
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-    constexpr uint32_t kLbo = 128, kSbo = 512;
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(kLbo >> 4) << 16;
-    d |= (uint64_t)(kSbo >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// TF32 head and tail of four values
+// TF32 head and tail of four values (both rounded to nearest)
 __device__ __forceinline__ void split4(const float* v, float4& hv, float4& lv) {
     float hh[4], ll[4];
 #pragma unroll
@@ -73,29 +55,6 @@ __device__ __forceinline__ void split4(const float* v, float4& hv, float4& lv) {
     hv = make_float4(hh[0], hh[1], hh[2], hh[3]);
     lv = make_float4(ll[0], ll[1], ll[2], ll[3]);
 }
-
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int polls = kUmmaSpin) {
-    uint32_t done = 0;
-    for (int it = 0; it < polls && !done; it++)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-    return done != 0;
-}
-
-#define ANOVA_TMEM_LD16(taddr, r)                                                                             \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}," \
-                 " [%16];"                                                                                    \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),         \
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
-                   "=r"(r[14]), "=r"(r[15])                                                                   \
-                 : "r"(taddr))
 
 template <int R>
 __global__ void __launch_bounds__(kUmmaThreads, kUmmaMinBlocks)
@@ -345,14 +304,6 @@ constexpr int kSpKC = 32;                   // nodes per chunk (MMA K, 4 steps o
 constexpr int kSpPitch = 36;                // row pitch of the staged y / z weights (floats)
 constexpr uint32_t kSpCols = 32;            // tensor memory: two tiles x 16 columns
 
-__device__ __forceinline__ uint64_t umma_desc_sbo(uint32_t addr, uint32_t sbo) {
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(sbo >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
 template <int R>
 constexpr size_t spread_umma_need() {
     constexpr int MT = (R * R + 127) / 128;
@@ -549,6 +500,15 @@ __global__ void k_wait_probe(int polls, int* gave_up) {
     __syncthreads();
     const bool done = __syncthreads_and(mbar_wait(su32(&mbar), 0, polls)) != 0;
     if (threadIdx.x == 0) *gave_up = done ? 0 : 1;
+}
+
+unsigned long long* wait_counter() {
+    static unsigned long long* addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev] && cudaGetSymbolAddress(reinterpret_cast<void**>(&addr[dev]), g_wait_timeouts) != cudaSuccess)
+        return nullptr;
+    return addr[dev];
 }
 
 // The device counter of abandoned waits, read on `st` (stream-ordered, then
