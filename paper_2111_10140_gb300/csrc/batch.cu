@@ -416,7 +416,9 @@ static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t
     k_b_sort<<<dim3(gx, b->nsort), kThreads, 0, st>>>(b->sorts, x);
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaMemsetAsync(b->grids, 0, b->grid_elems * sizeof(float), st));
-    ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st));
+    ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st,
+                                      b->plans[0]->pw12 ? b->plans[0]->psi_host.data() : nullptr,
+                                      b->plans[0]->sm_count));
     ANOVA_TRY(fft3_box_run<float>(b->fft3, b->fft3_shape, b->sm_count, st));
     ANOVA_TRY(fft12_box_run<float>(b->fft12, b->n12, b->smem12, st, b->n12_uniform));
     return dense_f32_gather_groups(b->m, b->plans[0]->psi_poly, b->sub, b->desc, b->groups, st,

@@ -158,6 +158,7 @@ struct anova_plan {
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
     bool spread_umma = false;           // FP32 dense 3-D spread on tcgen05 instead of mma.sync
     bool gather_tc5 = true;             // FP32 dense 3-D gather: persistent tcgen05 kernel, weights on the fly
+    bool pw12 = true;                   // FP32 dense 1-D / 2-D kernels: persistent, weights on the fly
     std::vector<float> psi_host;        // host copy of psi_poly (kernel parameters of the persistent kernels)
     int bin_side[3] = {0, 0, 0};        // bin side of the dense 1-D / 2-D / 3-D windows (0: the default rule)
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
@@ -290,9 +291,13 @@ anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* desc
 bool tc5_supported(int R, int m);
 anova_status gather3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const float* psi_host,
                          int sms, cudaStream_t st);
+// persistent FP32 1-D / 2-D kernels with on-the-fly weights (dense12.cu)
+anova_status dense12_pw(int dA, bool spread, int R, int m, const int4* sub, int nsub, const DenseWin* descs,
+                        const float* psi_host, int sms, const void* alpha, int alpha_double, cudaStream_t st);
 uint64_t wait_timeouts_on(cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
-                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st);
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
+                                     const float* psi_host = nullptr, int sms = 0);
 anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
                                      const float* psi_host = nullptr, int sms = 0);

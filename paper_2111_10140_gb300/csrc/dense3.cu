@@ -1078,12 +1078,17 @@ static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int n
 // FP32 dense kernels over any merged sub-problem list whose descriptors carry
 // sorted coefficients (plans and batches alike): one launch per (dims, R) group.
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
-                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st) {
+                                     const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
+                                     const float* psi_host, int sms) {
     for (const auto& g : groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
         const int4* sub = sub_base + g[1];
         const int nsub = g[2];
         if (nsub == 0) continue;
+        if (dA < 3 && psi_host && tc5_supported(R, m)) {
+            ANOVA_TRY(dense12_pw(dA, true, R, m, sub, nsub, descs, psi_host, sms, nullptr, 0, st));
+            continue;
+        }
         switch (dA * 100 + R) {
 #define ANOVA_S(R_)                                                                           \
     case 100 + R_: k_spread1_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, m, nsub); break;              \
@@ -1106,6 +1111,10 @@ anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_b
         const int4* sub = sub_base + g[1];
         const int nsub = g[2];
         if (nsub == 0) continue;
+        if (dA < 3 && psi_host && tc5_supported(R, m)) {
+            ANOVA_TRY(dense12_pw(dA, false, R, m, sub, nsub, descs, psi_host, sms, nullptr, 0, st));
+            continue;
+        }
         switch (dA * 100 + R) {
 #define ANOVA_G(R_)                                                                           \
     case 100 + R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
@@ -1131,8 +1140,11 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
     // the sorted coefficient copies serve the 1-D / 2-D kernels and the packed
     // FP32 3-D ones; the tensor-core 3-D spread gathers through the permutation
     bool need_sort = false;
-    for (const auto& g : plan->dense_groups)
-        if (g[0] / 100 < 3 || !plan->spread_tc || plan->spread_umma) need_sort = true;
+    for (const auto& g : plan->dense_groups) {
+        const int dA = g[0] / 100, R = g[0] % 100;
+        if (dA < 3 ? !(plan->pw12 && tc5_supported(R, plan->m)) : (!plan->spread_tc || plan->spread_umma))
+            need_sort = true;
+    }
     if (sizeof(T) == 4 && plan->dense_asort && need_sort) {
         k_sort_alpha<<<grid_for(plan->N * nd, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
             descs, nd, plan->N, alpha, alpha_double);
@@ -1146,6 +1158,11 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
         const int nsub = g[2];
         if (dA < 3) {
             if (sizeof(T) != 4 || !plan->dense_asort) continue;   // FP64: generic kernels per window
+            if (plan->pw12 && tc5_supported(R, plan->m)) {
+                ANOVA_TRY(dense12_pw(dA, true, R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count,
+                                     alpha, alpha_double, st));
+                continue;
+            }
             if (dA == 2) {
                 switch (R) {
 #define ANOVA_S2(R_) case R_: k_spread2_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, plan->m, nsub); break;
@@ -1184,6 +1201,11 @@ anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
         const int nsub = g[2];
         if (dA < 3) {
             if (sizeof(T) != 4 || !plan->dense_asort) continue;
+            if (plan->pw12 && tc5_supported(R, plan->m)) {
+                ANOVA_TRY(dense12_pw(dA, false, R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count,
+                                     nullptr, 0, st));
+                continue;
+            }
             if (dA == 2) {
                 switch (R) {
 #define ANOVA_G2(R_) case R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, plan->m); break;

@@ -24,48 +24,12 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "psi.cuh"
 #include "umma.cuh"
 
 namespace anova {
 
 constexpr int kT5Tile = 128;        // nodes per gather tile (MMA M)
-
-template <int M>
-struct PsiCoef {
-    float c[2 * M][kPsiStride];     // interval q: psi(q - M + f) ~ sum_k c[q][k] (f - 1/2)^k
-};
-
-// psi(q - M + f) for q in [0, 2M); the coefficients are compile-time offsets into the parameter bank
-template <int M>
-__device__ __forceinline__ void psi_taps(const PsiCoef<M>& P, float f, float (&t)[2 * M]) {
-    const float u = f - 0.5f;
-#pragma unroll
-    for (int q = 0; q < 2 * M; q++) {
-        float acc = P.c[q][kPsiDeg];
-#pragma unroll
-        for (int k = kPsiDeg - 1; k >= 0; k--) acc = fmaf(acc, u, P.c[q][k]);
-        t[q] = acc;
-    }
-}
-
-// region row r of a node in cell c of its bin: psi(c + M - r + f) = t[c + 2M - r]
-// where that tap exists, 0 elsewhere (and for r >= R)
-template <int R, int M>
-__device__ __forceinline__ void place_taps(const float (&t)[2 * M], int c, float (&w)[16]) {
-    constexpr int TB = R - 2 * M;
-#pragma unroll
-    for (int r = 0; r < 16; r++) {
-        float v = 0.f;
-#pragma unroll
-        for (int cc = 0; cc < TB; cc++) {
-            const int q = cc + 2 * M - r;
-            if (q >= 0 && q < 2 * M) v = (c == cc) ? t[q] : v;
-        }
-        w[r] = v;
-    }
-}
-
-__device__ __forceinline__ int wrap_cell(int g, int nos) { return g < 0 ? g + nos : (g >= nos ? g - nos : g); }
 
 // ------------------------------------------------------------------ gather
 // Per tile of 128 nodes of a run:
