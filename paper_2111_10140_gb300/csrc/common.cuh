@@ -34,6 +34,43 @@ void set_error(const std::string& msg);
     } while (0)
 #define ANOVA_CHECK_LAUNCH() ANOVA_CUDA_TRY(cudaGetLastError())
 
+// ------------------------------------------------------ device allocation
+// Every device allocation of the library goes through these two calls.  A
+// host-side hook (anova_debug_fail_alloc) can make the k-th one fail, to test
+// the error paths without a device fault.
+cudaError_t dev_malloc(void** ptr, size_t bytes);
+cudaError_t dev_malloc_async(void** ptr, size_t bytes, cudaStream_t st);
+
+// The device scratch of one call: freed (stream-ordered when `async`) when the
+// guard leaves scope, on every exit path, unless handed to an owner first.
+struct Scratch {
+    cudaStream_t st = nullptr;
+    bool async = true;
+    std::vector<void*> ptrs;
+    Scratch(cudaStream_t s, bool a = true) : st(s), async(a) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    template <typename T>
+    cudaError_t alloc(T** p, size_t bytes) {
+        void* v = nullptr;
+        const cudaError_t e = async ? dev_malloc_async(&v, bytes, st) : dev_malloc(&v, bytes);
+        *p = static_cast<T*>(v);
+        if (e == cudaSuccess && v) ptrs.push_back(v);
+        return e;
+    }
+    void keep(const void* p) {   // ownership passes to the caller's structure
+        for (auto& q : ptrs)
+            if (q == p) q = nullptr;
+    }
+    ~Scratch() {
+        for (void* p : ptrs)
+            if (p) {
+                if (async) cudaFreeAsync(p, st);
+                else cudaFree(p);
+            }
+    }
+};
+
 // ------------------------------------------------------------- constants
 constexpr int kMaxDim = 3;
 constexpr int kMaxWindows = 256;
@@ -156,9 +193,9 @@ struct anova_plan {
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
-    bool spread_umma = false;           // FP32 dense 3-D spread on tcgen05 instead of mma.sync
     bool gather_tc5 = true;             // FP32 dense 3-D gather: persistent tcgen05 kernel, weights on the fly
     bool pw12 = true;                   // FP32 dense 1-D / 2-D kernels: persistent, weights on the fly
+    bool spread_tc5 = false;            // FP32 dense 3-D spread: persistent tcgen05 kernel (A in tensor memory); measured slower
     std::vector<float> psi_host;        // host copy of psi_poly (kernel parameters of the persistent kernels)
     int bin_side[3] = {0, 0, 0};        // bin side of the dense 1-D / 2-D / 3-D windows (0: the default rule)
     std::vector<int> fft3_windows;      // 3-D windows on the batched box FFT
@@ -286,18 +323,24 @@ template <typename T>
 anova_status fft12_box_run(const Fft12Win* desc, int nw, size_t smem, cudaStream_t st, int uniform_n);
 anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, const float* poly,
                           cudaStream_t st);
-anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st);
+// plain FP64 CG from x = 0 on a plan holding FP64 data (matvec.cu)
+anova_status cg_fp64_solve(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
+                           int* iters, double* relres, cudaStream_t st);
 // persistent tcgen05 3-D kernels (tc3.cu): (R, m) pairs built, and the launches
 bool tc5_supported(int R, int m);
+// the persistent gather pays off once every SM has enough tiles to fill its pipeline
+inline bool tc5_gather_pays(int nsub, int sms) { return 2 * (int64_t)nsub >= 48 * (int64_t)sms; }
 anova_status gather3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const float* psi_host,
                          int sms, cudaStream_t st);
+anova_status spread3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const float* psi_host,
+                         int sms, const void* alpha, int alpha_double, cudaStream_t st);
 // persistent FP32 1-D / 2-D kernels with on-the-fly weights (dense12.cu)
 anova_status dense12_pw(int dA, bool spread, int R, int m, const int4* sub, int nsub, const DenseWin* descs,
                         const float* psi_host, int sms, const void* alpha, int alpha_double, cudaStream_t st);
 uint64_t wait_timeouts_on(cudaStream_t st);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
-                                     const float* psi_host = nullptr, int sms = 0);
+                                     const float* psi_host = nullptr, int sms = 0, bool tc5_3d = false);
 anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
                                      const float* psi_host = nullptr, int sms = 0);

@@ -11,8 +11,9 @@
 //   gather  the region is staged in shared memory once per bin; one thread per
 //           node forms wx, wy and s = sum_a wx[a] sum_b wy[b] h[a][b];
 //   spread  the block's warps split a sub-problem's nodes; each warp keeps the
-//           region in registers over every sub-problem of the bin, and the
-//           block adds its warps' regions to the grid once per bin.
+//           region in registers over up to kFlushSubs sub-problems of the bin,
+//           then the block adds its warps' regions to the grid (one set of
+//           atomics per kFlushSubs sub-problems instead of one per sub-problem).
 // The spread reads each node's coefficient through the node permutation from
 // the caller's vector (or a batch instance's sorted copy).
 #include <cuda_runtime.h>
@@ -24,6 +25,9 @@ namespace anova {
 
 constexpr int k12Threads = 256;          // one thread per node of a sub-problem (kSubChunk)
 constexpr int k12Warps = k12Threads / 32;
+// the spreads add their register regions to the grid at least every kFlushSubs
+// sub-problems, which bounds every FP32 running sum to kFlushSubs x 32 terms
+constexpr int kFlushSubs = 4;
 static_assert(kSubChunk == k12Threads, "one thread per node of a sub-problem");
 
 __device__ __forceinline__ float coef_of(const DenseWin& W, const void* alpha, int alpha_double, int64_t pos) {
@@ -171,13 +175,18 @@ k_spread2_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
         }
         __syncthreads();                                 // the staging rows are free again
     };
+    int nacc = 0;                                       // sub-problems in the accumulators
     for (int q = lo; q < hi; q++) {
         const int4 sp = sub[q];
         const DenseWin& W = descs[sp.w];
         if (W.live && !*W.live) continue;
-        if (cw >= 0 && (sp.w != cw || sp.x != cbin)) flush();
+        if (cw >= 0 && (sp.w != cw || sp.x != cbin || nacc == kFlushSubs)) {
+            flush();
+            nacc = 0;
+        }
         cw = sp.w;
         cbin = sp.x;
+        nacc++;
         const int nb = W.nb, by = sp.x % nb, bx = sp.x / nb;
         const int p = 32 * warp + lane;
         float wx[16], wy[16];
@@ -254,13 +263,18 @@ k_spread1_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
         }
         __syncthreads();
     };
+    int nacc = 0;                                       // sub-problems in the accumulators
     for (int q = lo; q < hi; q++) {
         const int4 sp = sub[q];
         const DenseWin& W = descs[sp.w];
         if (W.live && !*W.live) continue;
-        if (cw >= 0 && (sp.w != cw || sp.x != cbin)) flush();
+        if (cw >= 0 && (sp.w != cw || sp.x != cbin || nacc == kFlushSubs)) {
+            flush();
+            nacc = 0;
+        }
         cw = sp.w;
         cbin = sp.x;
+        nacc++;
         if (tid < sp.z) {
             const int64_t pos = (int64_t)sp.y + tid;
             const float al = coef_of(W, alpha, alpha_double, pos);

@@ -1024,7 +1024,9 @@ static bool table_kernels(const anova_plan* plan, int R) {
 static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  const void* alpha, int alpha_double, cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
-    if (plan->spread_tc && plan->spread_umma) return spread3_umma(R, sub, nsub, descs, plan->m, st);
+    if (plan->spread_tc5 && tc5_supported(R, plan->m))
+        return spread3_tc5(R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count, alpha, alpha_double,
+                           st);
     if (plan->spread_tc) {
         switch (R) {
 #define ANOVA_SPREAD_TC(R_) \
@@ -1050,7 +1052,7 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
 static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int nsub, const DenseWin* descs,
                                  cudaStream_t st) {
     if (nsub == 0) return ANOVA_OK;
-    if (plan->gather_tc5 && tc5_supported(R, plan->m))
+    if (plan->gather_tc5 && tc5_supported(R, plan->m) && tc5_gather_pays(nsub, plan->sm_count))
         return gather3_tc5(R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count, st);
     if (plan->gather_tc && plan->gather_umma) return gather3_umma(R, sub, nsub, descs, plan->m, plan->psi_poly, st);
     if (plan->gather_tc) {
@@ -1079,7 +1081,7 @@ static anova_status gather_table(anova_plan* plan, int R, const int4* sub, int n
 // sorted coefficients (plans and batches alike): one launch per (dims, R) group.
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
-                                     const float* psi_host, int sms) {
+                                     const float* psi_host, int sms, bool tc5_3d) {
     for (const auto& g : groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
         const int4* sub = sub_base + g[1];
@@ -1093,7 +1095,12 @@ anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin
 #define ANOVA_S(R_)                                                                           \
     case 100 + R_: k_spread1_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, m, nsub); break;              \
     case 200 + R_: k_spread2_f32<R_><<<(nsub + kGroupWarps - 1) / kGroupWarps, 32 * kGroupWarps, 0, st>>>(sub, descs, m, nsub); break;              \
-    case 300 + R_: k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, m); break;
+    case 300 + R_:                                                                            \
+        if (tc5_3d && psi_host && tc5_supported(R_, m)) {                                     \
+            ANOVA_TRY(spread3_tc5(R_, m, sub, nsub, descs, psi_host, sms, nullptr, 0, st));   \
+            continue;                                                                         \
+        }                                                                                     \
+        k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, m); break;
             ANOVA_S(4) ANOVA_S(6) ANOVA_S(8) ANOVA_S(10) ANOVA_S(12) ANOVA_S(14) ANOVA_S(16)
 #undef ANOVA_S
             default: set_error("dense FP32 spread: unsupported window dimension or region size"); return ANOVA_EINVAL;
@@ -1120,7 +1127,8 @@ anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_b
     case 100 + R_: k_gather1_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
     case 200 + R_: k_gather2_f32<R_><<<nsub, 128, 0, st>>>(sub, descs, m); break;             \
     case 300 + R_:                                                                            \
-        if (psi_host && tc5_supported(R_, m)) ANOVA_TRY(gather3_tc5(R_, m, sub, nsub, descs, psi_host, sms, st)); \
+        if (psi_host && tc5_supported(R_, m) && tc5_gather_pays(nsub, sms))                   \
+            ANOVA_TRY(gather3_tc5(R_, m, sub, nsub, descs, psi_host, sms, st));               \
         else ANOVA_TRY(gather3_umma(R_, sub, nsub, descs, m, poly, st));                      \
         break;
             ANOVA_G(4) ANOVA_G(6) ANOVA_G(8) ANOVA_G(10) ANOVA_G(12) ANOVA_G(14) ANOVA_G(16)
@@ -1142,8 +1150,9 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
     bool need_sort = false;
     for (const auto& g : plan->dense_groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
-        if (dA < 3 ? !(plan->pw12 && tc5_supported(R, plan->m)) : (!plan->spread_tc || plan->spread_umma))
-            need_sort = true;
+        const bool ok12 = plan->pw12 && tc5_supported(R, plan->m);
+        const bool ok3 = (plan->spread_tc5 && tc5_supported(R, plan->m)) || plan->spread_tc;
+        if (dA < 3 ? !ok12 : !ok3) need_sort = true;
     }
     if (sizeof(T) == 4 && plan->dense_asort && need_sort) {
         k_sort_alpha<<<grid_for(plan->N * nd, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
@@ -1234,14 +1243,25 @@ anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
     return ANOVA_OK;
 }
 
+// region size and sub-problem count of the plan's 3-D dense windows (0: none)
+static int region3(const anova_plan* plan, int* nsub = nullptr) {
+    for (const auto& g : plan->dense_groups)
+        if (g[0] / 100 == 3) {
+            if (nsub) *nsub = g[2];
+            return g[0] % 100;
+        }
+    return 0;
+}
+
 // kernel names of the FP32 3-D spread and gather the plan launches ("<R>" = region size)
 static const char* spread3_name(const anova_plan* plan) {
-    if (plan->spread_tc && plan->spread_umma) return "k_spread3_umma<R>";
+    if (plan->spread_tc5 && tc5_supported(region3(plan), plan->m)) return "k_spread3_tc5<R>";
     return plan->spread_tc ? "k_spread3_tc<R>" : "k_spread3_f32<R>";
 }
 static const char* gather3_name(const anova_plan* plan) {
-    if (plan->gather_tc5 && tc5_supported(plan->dense_groups.empty() ? 0 : plan->dense_groups[0][0] % 100, plan->m))
-        return "k_gather3_tc5<R>";
+    int n3 = 0;
+    const int R3 = region3(plan, &n3);
+    if (plan->gather_tc5 && tc5_supported(R3, plan->m) && tc5_gather_pays(n3, plan->sm_count)) return "k_gather3_tc5<R>";
     if (plan->gather_tc && plan->gather_umma) return "k_gather3_umma<R>";
     return plan->gather_tc ? "k_gather3_tc<R>" : "k_gather3_f32<R>";
 }

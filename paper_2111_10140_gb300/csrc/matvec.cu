@@ -261,13 +261,13 @@ struct CgBuffers {
 static anova_status cg_buffers(anova_plan* plan, int maxit, CgBuffers& B) {
     const int64_t N = plan->N;
     const int nblk = grid_for(N, kThreads, 2 * plan->sm_count);
-    if (!plan->cg_vec) ANOVA_CUDA_TRY(cudaMalloc(&plan->cg_vec, 4 * std::max<int64_t>(N, 1) * sizeof(double)));
-    if (!plan->cg_part) ANOVA_CUDA_TRY(cudaMalloc(&plan->cg_part, 2 * 2 * plan->sm_count * sizeof(double)));
+    if (!plan->cg_vec) ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->cg_vec, 4 * std::max<int64_t>(N, 1) * sizeof(double)));
+    if (!plan->cg_part) ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->cg_part, 2 * 2 * plan->sm_count * sizeof(double)));
     if (plan->cg_hist < maxit + 8) {
         cudaFree(plan->cg_scal);
         plan->cg_scal = nullptr;
         plan->cg_hist = maxit + 8;
-        ANOVA_CUDA_TRY(cudaMalloc(&plan->cg_scal, (plan->cg_hist + 4) * sizeof(double)));
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->cg_scal, (plan->cg_hist + 4) * sizeof(double)));
     }
     B.r = plan->cg_vec;
     B.p = plan->cg_vec + N;
@@ -418,6 +418,21 @@ static anova_status true_residual(anova_plan* plan, double lambda, const double*
     return ANOVA_OK;
 }
 
+// Plain FP64 CG on (K64 + lambda I) x = b from x = 0, whatever the plan's
+// precision (the plan must hold FP64 data): the fallback of the batched
+// refined solver for systems whose FP32 corrections stop helping.
+anova_status cg_fp64_solve(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
+                           int* iters, double* relres, cudaStream_t st) {
+    *iters = 0;
+    *relres = 0.0;
+    if (plan->N == 0 || maxit < 1) return ANOVA_OK;
+    CgBuffers B;
+    ANOVA_TRY(cg_buffers(plan, maxit, B));
+    double bb = 0.0;
+    ANOVA_TRY(cg_run<double>(plan, lambda, b, x, tol, maxit, B, iters, &bb, st));
+    return true_residual<double>(plan, lambda, b, x, bb, B, relres, st);
+}
+
 // Mixed precision: FP32-operator CG on the correction equation inside FP64
 // iterative refinement, x += CG32(r), r = b - (K64 + lambda I) x.
 static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, double* x, double tol, int maxit,
@@ -426,7 +441,8 @@ static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, d
     const double inner_tol = 1e-4;     // per refinement pass (tighter FP32 passes converge slowly near the floor)
     double* rhs = B.x2;            // current residual (right-hand side of the correction)
     double* dx = static_cast<double*>(nullptr);
-    ANOVA_CUDA_TRY(cudaMallocAsync(&dx, std::max<int64_t>(N, 1) * sizeof(double), st));
+    Scratch scratch(st);
+    ANOVA_CUDA_TRY(scratch.alloc(&dx, std::max<int64_t>(N, 1) * sizeof(double)));
     ANOVA_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double), st));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(rhs, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_cg_init<<<B.nblk, kThreads, 0, st>>>(b, N, B.q, B.r, B.p, 0, B.part);
@@ -459,7 +475,6 @@ static anova_status cg_mixed(anova_plan* plan, double lambda, const double* b, d
         }
         if (rel <= tol) break;
     }
-    cudaFreeAsync(dx, st);
     *iters = total;
     *relres = (bb > 0.0) ? rel : 0.0;
     if (s == ANOVA_OK && bb > 0.0 && rel > tol) s = ANOVA_ENOCONV;
@@ -534,8 +549,9 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
     const int P = plan->P;
     T* tmp = nullptr;
     double* zw = nullptr;
-    ANOVA_CUDA_TRY(cudaMallocAsync(&tmp, std::max<int64_t>(M, 1) * P * sizeof(T), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&zw, std::max<int64_t>(M, 1) * 3 * sizeof(double), st));
+    Scratch scratch(st);
+    ANOVA_CUDA_TRY(scratch.alloc(&tmp, std::max<int64_t>(M, 1) * P * sizeof(T)));
+    ANOVA_CUDA_TRY(scratch.alloc(&zw, std::max<int64_t>(M, 1) * 3 * sizeof(double)));
     anova_status s = ANOVA_OK;
     for (int l = 0; l < P && s == ANOVA_OK; l++) {
         s = extract_window(plan, Z, M, ldz, plan->win[l], zw, st);
@@ -551,8 +567,6 @@ static anova_status predict_t(anova_plan* plan, const double* alpha, const doubl
             s = ANOVA_ECUDA;
         }
     }
-    cudaFreeAsync(tmp, st);
-    cudaFreeAsync(zw, st);
     return s;
 }
 

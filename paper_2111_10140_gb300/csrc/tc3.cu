@@ -460,3 +460,373 @@ anova_status gather3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin
 }
 
 }  // namespace anova
+
+namespace anova {
+
+// ------------------------------------------------------------------ spread
+// Per run (consecutive sub-problems of one bin) the region
+//   C[(a,b)][c] = sum_p (wx_p[a] wy_p[b]) (alpha_p wz_p[c])
+// accumulates in tensor memory over chunks of 32 nodes: tcgen05.mma with
+// A = the products wx_p[a] wy_p[b] in tensor memory (row (a, b) at a*16 + b,
+// two M tiles of 128 rows; K = the chunk's nodes), B = alpha_p wz_p[c] in
+// shared memory (N = 16), D = 2 tiles x 16 columns; 3xTF32 as in the gather.
+// Warp roles (13 warps):
+//   warps 0-7   A builders: thread (tile w / 4, row 32 (w mod 4) + lane) owns
+//               row (a, b); per chunk it forms its row of A from the staged
+//               x and y weights and stores heads and tails with tcgen05.st;
+//               after a run it reads its row of the accumulator and adds it
+//               to the grid (one atomic per region cell and run).
+//   warps 8-11  weight warps: warp 8 + k mod 4 takes chunk k (lane = node)
+//               and owns weight buffer k mod 4: it forms the node's weights in
+//               registers, then (once its buffer is free) writes the x and y
+//               weights to shared memory (node-minor rows) and alpha wz
+//               (head, tail) as B.
+//   warp 12     lane 0 issues the MMAs and closes runs.
+// Four weight buffers (one producer each, so every mbarrier phase is waited
+// for in order), two A buffers in tensor memory (chunk k mod 2) and two
+// accumulators (runs alternate).
+constexpr int kS5KC = 32;                      // nodes per chunk (MMA K: 4 steps of 8)
+constexpr int kS5Threads = 13 * 32;
+constexpr int kS5WWarps = 4;                    // weight warps
+constexpr int kS5WPitch = 36;                  // floats per staged weight row (32 nodes + pad)
+constexpr uint32_t kS5Cols = 512;              // D: 2 x 32 columns at 0; A: 2 x 128 columns at 64
+
+struct S5Info {                                // one chunk, written by its weight warp
+    int w, bin, first, cnt;                    // window, bin, first node, nodes (w < 0: end marker)
+};
+
+constexpr size_t s5_smem() {
+    return (size_t)(kS5WWarps * 2 * 16 * kS5WPitch     // staged wx, wy rows: [buffer][x, y][16][pitch]
+                    + kS5WWarps * 2 * 16 * kS5KC       // B: [buffer][head, tail][16 x 32]
+                    ) * 4 +
+           kS5WWarps * sizeof(S5Info) + 4 * kT5SubCache * 4 + (2 * kS5WWarps + 4 * 2 + 1) * 8 + 64;
+}
+
+template <int R, int M>
+__global__ void __launch_bounds__(kS5Threads, 1)
+k_spread3_tc5(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict__ descs,
+              const __grid_constant__ PsiCoef<M> P, const void* __restrict__ alpha, int alpha_double,
+              unsigned long long* __restrict__ timeouts) {
+    static_assert(R <= 16 && R > 2 * M, "region up to 16");
+    constexpr int TB = R - 2 * M;
+    constexpr uint32_t idesc = umma_idesc_tf32(128, 16);
+    constexpr uint32_t kSbo = (kS5KC / 4) * 128;          // bytes between 8-row groups of B
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float* sW = reinterpret_cast<float*>(sm);             // [weight buffer][x, y][16][pitch]
+    float* sBm = sW + kS5WWarps * 2 * 16 * kS5WPitch;     // [weight buffer][head, tail][16 x 32]
+    S5Info* info = reinterpret_cast<S5Info*>(sBm + kS5WWarps * 2 * 16 * kS5KC);
+    int4* sCache = reinterpret_cast<int4*>(info + kS5WWarps);
+    uint64_t* wfull = reinterpret_cast<uint64_t*>(sCache + kT5SubCache);   // [4] weight buffer written
+    uint64_t* wfree = wfull + kS5WWarps;                  // [4] weights and B of the buffer read
+    uint64_t* afull = wfree + kS5WWarps;                  // [2] A of buffer b stored
+    uint64_t* afree = afull + 2;                          // [2] A of buffer b read by the MMAs
+    uint64_t* dready = afree + 2;                         // [2] accumulator d complete (run closed)
+    uint64_t* dfree = dready + 2;                         // [2] accumulator d added to the grid
+    uint64_t* drain = dfree + 2;                          // every issued MMA done (after an abort)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+
+    // chunk slots: sub-problem q is slots 8q .. 8q + 7 (nodes 32 s ..)
+    const int lo = (int)((int64_t)8 * nsub * blockIdx.x / gridDim.x);
+    const int hi = (int)((int64_t)8 * nsub * (blockIdx.x + 1) / gridDim.x);
+    if (lo >= hi) return;                                 // uniform over the block
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(su32(tslot), kS5Cols);
+    if (tid == 0) {
+        for (int b = 0; b < kS5WWarps; b++) {
+            mbar_init(su32(&wfull[b]), 1);
+            mbar_init(su32(&wfree[b]), 256 + 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(su32(&afull[b]), 256);
+            mbar_init(su32(&afree[b]), 1);
+            mbar_init(su32(&dready[b]), 1);
+            mbar_init(su32(&dfree[b]), 256);
+        }
+        mbar_init(su32(drain), 1);
+        *abort = 0;
+    }
+    // every thread walks the chunk sequence alike: sub-problems from a shared cache
+    // (filled by all threads before the roles split, reloaded by nobody: the cache
+    // holds the CTA's whole range when it fits, else the walk reads global memory)
+    const int q_lo = lo >> 3, q_hi = (hi + 7) >> 3;
+    const bool cached = q_hi - q_lo <= kT5SubCache;
+    if (cached)
+        for (int k = q_lo + tid; k < q_hi; k += kS5Threads) sCache[k - q_lo] = sub[k];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    auto give_up = [&]() {
+        if (atomicExch((int*)abort, 1) == 0 && timeouts) atomicAdd(timeouts, 1ull);
+    };
+    auto sub_at = [&](int q) -> int4 { return cached ? sCache[q - q_lo] : sub[q]; };
+    // the next non-empty chunk at or after slot *pt; false past the range
+    auto next_chunk = [&](int& pt, S5Info& c) -> bool {
+        while (pt < hi) {
+            const int4 q = sub_at(pt >> 3);
+            const int part = pt & 7;
+            pt++;
+            const int cnt = q.z - part * kS5KC;
+            if (cnt <= 0) continue;
+            const int* live = descs[q.w].live;
+            if (live && !*live) continue;
+            c = S5Info{q.w, q.x, q.y + part * kS5KC, min(cnt, kS5KC)};
+            return true;
+        }
+        return false;
+    };
+
+    if (warp >= 8 && warp < 8 + kS5WWarps) {
+        // ---------------------------------------------------------------- weight warps
+        const int me = warp - 8;                          // this warp's chunks: k = me, me + 4, ...
+        int pt = lo, k = 0;
+        for (;; k++) {
+            S5Info c;
+            const bool has = next_chunk(pt, c);
+            if ((k & (kS5WWarps - 1)) != me) {
+                if (!has) break;
+                continue;
+            }
+            const int b = me, use = k >> 2;               // this warp's weight buffer and its use count
+            float wx[16], wy[16], wz[16];
+            if (has && lane < c.cnt) {
+                const DenseWin& W = descs[c.w];
+                const int nb = W.nb, bz = c.bin % nb, by = (c.bin / nb) % nb, bx = c.bin / (nb * nb);
+                const int64_t pos = (int64_t)c.first + lane, Nn = W.N;
+                const float* __restrict__ fr = static_cast<const float*>(W.frac);
+                const float fx = fr[pos], fy = fr[Nn + pos], fz = fr[2 * Nn + pos];
+                const int cx = W.cell[pos] - TB * bx, cy = W.cell[Nn + pos] - TB * by, cz = W.cell[2 * Nn + pos] - TB * bz;
+                float al;
+                if (!alpha) al = W.asort[pos];
+                else {
+                    const int32_t i = W.perm[pos];
+                    al = alpha_double ? (float)static_cast<const double*>(alpha)[i] : static_cast<const float*>(alpha)[i];
+                }
+                float t[2 * M];
+                psi_taps<M>(P, fx, t);
+                place_taps<R, M>(t, cx, wx);
+                psi_taps<M>(P, fy, t);
+                place_taps<R, M>(t, cy, wy);
+                psi_taps<M>(P, fz, t);
+                place_taps<R, M>(t, cz, wz);
+#pragma unroll
+                for (int r = 0; r < 16; r++) wz[r] *= al;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; r++) wx[r] = wy[r] = wz[r] = 0.f;
+            }
+            // the buffer is free once this warp's previous chunk (k - 4) is consumed
+            const bool w = use == 0 || mbar_wait_abortable(su32(&wfree[b]), (use - 1) & 1, abort);
+            if (!__all_sync(0xffffffffu, w)) {
+                if (lane == 0) give_up();
+                break;
+            }
+            if (!has) {                                   // end marker
+                if (lane == 0) {
+                    info[b] = S5Info{-1, 0, 0, 0};
+                    mbar_arrive(su32(&wfull[b]), 1);
+                }
+                break;
+            }
+            float* sx = sW + (b * 2 + 0) * 16 * kS5WPitch;
+            float* sy = sW + (b * 2 + 1) * 16 * kS5WPitch;
+            float* bh = sBm + (b * 2 + 0) * 16 * kS5KC;
+            float* bl = sBm + (b * 2 + 1) * 16 * kS5KC;
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                sx[r * kS5WPitch + lane] = wx[r];
+                sy[r * kS5WPitch + lane] = wy[r];
+                // B: row c = r, column (K) = node lane, K-major core matrices of 8 rows x 4 nodes
+                const int o = ((r >> 3) * (kS5KC / 4) + (lane >> 2)) * 32 + (r & 7) * 4 + (lane & 3);
+                const float h = tf32_head(wz[r]);
+                bh[o] = h;
+                bl[o] = wz[r] - h;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                info[b] = c;
+                mbar_arrive(su32(&wfull[b]), 1);
+            }
+        }
+    } else if (warp < 8) {
+        // ---------------------------------------------------------------- A builders
+        const int t = warp >> 2, row = t * 128 + 32 * (warp & 3) + lane;
+        const int a = row >> 4, bb = row & 15;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        int rw = -1, rbin = -1, db = 1, runs = 0;          // the open run and its accumulator
+        auto flush = [&](int d, int w, int bin, int use) -> bool {
+            // add accumulator d (run `use` of it) to the grid
+            if (!__all_sync(0xffffffffu, mbar_wait_abortable(su32(&dready[d]), use & 1, abort))) return false;
+            tc_fence_after();
+            uint32_t v[16];
+            ANOVA_TMEM_LD16(tbase + lane_off + (uint32_t)(d * 32 + t * 16), v);
+            tmem_wait_ld();
+            tc_fence_before();
+            mbar_arrive(su32(&dfree[d]), 1);
+            if (a < R && bb < R) {
+                const DenseWin& W = descs[w];
+                const int nb = W.nb, nos = W.nos, bz = bin % nb, by = (bin / nb) % nb, bx = bin / (nb * nb);
+                float* __restrict__ grid = static_cast<float*>(W.grid);
+                const size_t rowbase =
+                    ((size_t)wrap_cell(TB * bx - M + a, nos) * nos + wrap_cell(TB * by - M + bb, nos)) * nos;
+#pragma unroll
+                for (int c = 0; c < R; c++) atomicAdd(&grid[rowbase + wrap_cell(TB * bz - M + c, nos)], __uint_as_float(v[c]));
+            }
+            return true;
+        };
+        bool ok = true;
+        for (int k = 0;; k++) {
+            const int b = k & 1, use = k >> 1;            // A buffer and its use count
+            const int wb = k & (kS5WWarps - 1);           // weight buffer
+            if (!__all_sync(0xffffffffu, mbar_wait_abortable(su32(&wfull[wb]), (k >> 2) & 1, abort))) {
+                ok = false;
+                break;
+            }
+            const S5Info c = info[wb];
+            if (c.w < 0) {                                // end marker: pass it on to the issuer
+                mbar_arrive(su32(&afull[b]), 1);
+                break;
+            }
+            // A of buffer b is free once the MMAs of chunk k - 2 have read it
+            if (use >= 1 && !__all_sync(0xffffffffu, mbar_wait_abortable(su32(&afree[b]), (use - 1) & 1, abort))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const float* sx = sW + (wb * 2 + 0) * 16 * kS5WPitch + a * kS5WPitch;
+            const float* sy = sW + (wb * 2 + 1) * 16 * kS5WPitch + bb * kS5WPitch;
+            const uint32_t acol = tbase + lane_off + (uint32_t)(64 + b * 128 + t * 64);
+#pragma unroll
+            for (int g = 0; g < kS5KC / 8; g++) {
+                uint32_t hv[8], tv[8];
+#pragma unroll
+                for (int h4 = 0; h4 < 2; h4++) {
+                    const float4 x4 = *reinterpret_cast<const float4*>(sx + 8 * g + 4 * h4);
+                    const float4 y4 = *reinterpret_cast<const float4*>(sy + 8 * g + 4 * h4);
+                    const float2 p0 = __fmul2_rn(make_float2(x4.x, x4.y), make_float2(y4.x, y4.y));
+                    const float2 p1 = __fmul2_rn(make_float2(x4.z, x4.w), make_float2(y4.z, y4.w));
+                    const float2 h0 = make_float2(tf32_head(p0.x), tf32_head(p0.y));
+                    const float2 h1 = make_float2(tf32_head(p1.x), tf32_head(p1.y));
+                    const float2 t0 = __fadd2_rn(p0, make_float2(-h0.x, -h0.y));
+                    const float2 t1 = __fadd2_rn(p1, make_float2(-h1.x, -h1.y));
+                    hv[4 * h4 + 0] = __float_as_uint(h0.x); hv[4 * h4 + 1] = __float_as_uint(h0.y);
+                    hv[4 * h4 + 2] = __float_as_uint(h1.x); hv[4 * h4 + 3] = __float_as_uint(h1.y);
+                    tv[4 * h4 + 0] = __float_as_uint(t0.x); tv[4 * h4 + 1] = __float_as_uint(t0.y);
+                    tv[4 * h4 + 2] = __float_as_uint(t1.x); tv[4 * h4 + 3] = __float_as_uint(t1.y);
+                }
+                ANOVA_TMEM_ST8(acol + (uint32_t)(8 * g), hv);
+                ANOVA_TMEM_ST8(acol + (uint32_t)(32 + 8 * g), tv);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(su32(&wfree[wb]), 1);             // the staged weights of the buffer are read
+            mbar_arrive(su32(&afull[b]), 1);
+            if (c.w != rw || c.bin != rbin) {
+                // chunk k opens a run: the run before it (accumulator db) is closed by the issuer
+                if (rw >= 0 && !flush(db, rw, rbin, (runs - 1) >> 1)) {
+                    ok = false;
+                    break;
+                }
+                rw = c.w;
+                rbin = c.bin;
+                db ^= 1;
+                runs++;
+            }
+        }
+        if (ok && rw >= 0) ok = flush(db, rw, rbin, (runs - 1) >> 1);
+        if (!ok && lane == 0) give_up();
+    } else if (warp == 8 + kS5WWarps && lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        int rw = -1, rbin = -1, db = 1, runs = 0;
+        bool first = true;
+        for (int k = 0;; k++) {
+            const int b = k & 1, use = k >> 1;
+            if (!mbar_wait_abortable(su32(&afull[b]), use & 1, abort)) {
+                give_up();
+                break;
+            }
+            const int wb = k & (kS5WWarps - 1);
+            const S5Info c = info[wb];
+            if (c.w < 0) break;
+            if (c.w != rw || c.bin != rbin) {
+                if (rw >= 0) umma_commit(su32(&dready[db]));   // close the open run
+                rw = c.w;
+                rbin = c.bin;
+                db ^= 1;
+                runs++;
+                // accumulator db was last used by run runs - 2: wait until it is in the grid
+                if (runs > 2 && !mbar_wait_abortable(su32(&dfree[db]), ((runs - 3) >> 1) & 1, abort)) {
+                    give_up();
+                    break;
+                }
+                first = true;
+            }
+            tc_fence_after();
+            const uint32_t b0 = su32(sBm + (wb * 2 + 0) * 16 * kS5KC), b1 = su32(sBm + (wb * 2 + 1) * 16 * kS5KC);
+#pragma unroll
+            for (int tt = 0; tt < 2; tt++) {
+                const uint32_t d = tbase + (uint32_t)(db * 32 + tt * 16);
+                const uint32_t ah = tbase + (uint32_t)(64 + b * 128 + tt * 64), al = ah + 32;
+#pragma unroll
+                for (int ks = 0; ks < kS5KC / 8; ks++) {
+                    const uint64_t dbh = umma_desc_sbo(b0 + ks * 256, kSbo), dbl = umma_desc_sbo(b1 + ks * 256, kSbo);
+                    umma_tf32_ts(d, ah + 8 * ks, dbh, idesc, (first && ks == 0) ? 0u : 1u);
+                    umma_tf32_ts(d, ah + 8 * ks, dbl, idesc, 1);
+                    umma_tf32_ts(d, al + 8 * ks, dbh, idesc, 1);
+                }
+            }
+            first = false;
+            umma_commit(su32(&afree[b]));
+            umma_commit(su32(&wfree[wb]));
+        }
+        if (!*abort) {
+            if (rw >= 0) umma_commit(su32(&dready[db]));   // close the last run
+        } else {
+            // after an abort the MMAs issued last may still run: let them finish (bounded)
+            umma_commit(su32(drain));
+            mbar_wait(su32(drain), 0);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tbase, kS5Cols);
+}
+
+template <int R, int M>
+static anova_status launch_spread_tc5(const int4* sub, int nsub, const DenseWin* descs, const float* psi_host, int sms,
+                                      const void* alpha, int alpha_double, cudaStream_t st) {
+    constexpr size_t sh = s5_smem();
+    static_assert(sh <= 227 * 1024, "shared memory per block");
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_spread3_tc5<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) ==
+               cudaSuccess;
+    }();
+    if (!attr) {
+        set_error("tcgen05 spread: shared-memory attribute refused");
+        return ANOVA_ECUDA;
+    }
+    const int grid = nsub < sms ? nsub : sms;
+    k_spread3_tc5<R, M><<<grid, kS5Threads, sh, st>>>(sub, nsub, descs, psi_coef<M>(psi_host), alpha, alpha_double,
+                                                      wait_counter());
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+anova_status spread3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const float* psi_host,
+                         int sms, const void* alpha, int alpha_double, cudaStream_t st) {
+    if (nsub == 0) return ANOVA_OK;
+#define ANOVA_S5(R_, M_) \
+    if (R == R_ && m == M_) return launch_spread_tc5<R_, M_>(sub, nsub, descs, psi_host, sms, alpha, alpha_double, st);
+    ANOVA_S5(10, 4) ANOVA_S5(12, 4) ANOVA_S5(14, 4) ANOVA_S5(16, 4)
+    ANOVA_S5(12, 5) ANOVA_S5(14, 5) ANOVA_S5(16, 5)
+    ANOVA_S5(14, 6) ANOVA_S5(16, 6)
+    ANOVA_S5(16, 7)
+#undef ANOVA_S5
+    set_error("tcgen05 spread: unsupported region size or cutoff");
+    return ANOVA_EINVAL;
+}
+
+}  // namespace anova

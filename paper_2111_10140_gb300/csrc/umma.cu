@@ -291,204 +291,6 @@ anova_status gather3_umma(int R, const int4* sub, int nsub, const DenseWin* desc
     return ANOVA_OK;
 }
 
-// ------------------------------------------------------------------ spread
-// Per sub-problem, the region C[(b,c)][a] = sum_p wy_p[b] wz_p[c] (alpha_p wx_p[a])
-// as tcgen05.mma over chunks of 32 nodes: A = the products wy_p[b] wz_p[c]
-// (rows (b,c) = pair index b R + c, M = 128 per tile, R^2 rows in one or two
-// tiles; built by the threads in shared memory), B = alpha_p wx_p[a] (N = 16
-// rows a, K = the chunk's nodes), both split into TF32 heads and tails,
-// 3xTF32 accumulation in tensor memory (16 columns per tile).  After the last
-// chunk every thread reads one accumulator row (16 values of a) and adds it
-// to the grid: one atomic per region cell per sub-problem.
-constexpr int kSpKC = 32;                   // nodes per chunk (MMA K, 4 steps of 8)
-constexpr int kSpPitch = 36;                // row pitch of the staged y / z weights (floats)
-constexpr uint32_t kSpCols = 32;            // tensor memory: two tiles x 16 columns
-
-template <int R>
-constexpr size_t spread_umma_need() {
-    constexpr int MT = (R * R + 127) / 128;
-    return (size_t)(MT * 128 * kSpKC * 2 + 16 * kSpKC * 2 + 2 * 16 * kSpPitch) * 4 + 16;
-}
-
-template <int R>
-__global__ void __launch_bounds__(kUmmaThreads, 3)
-k_spread3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m) {
-    static_assert(R >= 4 && R <= 16 && R % 2 == 0, "even region up to 16");
-    constexpr int MT = (R * R + 127) / 128;          // M tiles of 128 pair rows
-    constexpr int ROWS = MT * 128;
-    constexpr int TPR = kUmmaThreads / ROWS;         // threads per pair row (1 or 2)
-    constexpr int PG = kSpKC / 4 / TPR;              // node groups of 4 per thread
-    constexpr uint32_t kSbo = (kSpKC / 4) * 128;     // bytes between 8-row groups
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float* sAh = reinterpret_cast<float*>(sm);       // ROWS x 32: heads
-    float* sAl = sAh + ROWS * kSpKC;                 //           tails
-    float* sBh = sAl + ROWS * kSpKC;                 // 16 x 32: heads
-    float* sBl = sBh + 16 * kSpKC;                   //          tails
-    float* sy = sBl + 16 * kSpKC;                    // 16 x kSpPitch: wy_p[b] for the chunk's nodes
-    float* sz = sy + 16 * kSpPitch;                  // 16 x kSpPitch: wz_p[c]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sz + 16 * kSpPitch);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-
-    const int4 sp = sub[blockIdx.x];
-    const DenseWin W = descs[sp.w];
-    if (W.live && !*W.live) return;   // a batch system that has stopped
-    float* __restrict__ grid = static_cast<float*>(W.grid);
-    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
-    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                     "r"(kSpCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(mbar)), "r"(1));
-    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(16 >> 3) << 17) |
-                               ((uint32_t)(128 >> 4) << 24);
-    // this thread's pair row and share of the chunk's nodes
-    const int r = tid % ROWS, kp = tid / ROWS;
-    const int rb = r / R, rc = r - (r / R) * R;
-    const bool row_ok = r < R * R;
-    const int rt = r & 127;
-    float* aht = sAh + (r >> 7) * 128 * kSpKC;
-    float* alt = sAl + (r >> 7) * 128 * kSpKC;
-    uint32_t phase = 0, taddr = 0;
-    bool ok = true, first = true;
-    for (int c0 = 0; c0 < sp.z && ok; c0 += kSpKC) {
-        const int cnt = min(kSpKC, sp.z - c0);
-        // node weights of the chunk: alpha wx -> B (heads, tails), wy / wz -> staged rows
-        for (int i = tid; i < kSpKC * 12; i += kUmmaThreads) {
-            const int p = i / 12, k = i - (i / 12) * 12;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            float al = 0.f;
-            if (p < cnt) {
-                const int64_t pos = (int64_t)sp.y + c0 + p;
-                v = __ldg(reinterpret_cast<const float4*>(W.wtab + pos * 48) + k);
-                if (k < 4) al = W.asort[pos];
-            }
-            const float e4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int row = 4 * (k & 3) + e;
-                if (k < 4) {
-                    const float x = al * e4[e];
-                    const uint32_t hi = tf32_rna(x);
-                    const int o = ((row >> 3) * (kSpKC / 4) + (p >> 2)) * 32 + (row & 7) * 4 + (p & 3);
-                    sBh[o] = __uint_as_float(hi);
-                    sBl[o] = __uint_as_float(tf32_rna(x - __uint_as_float(hi)));
-                } else if (k < 8) {
-                    sy[row * kSpPitch + p] = e4[e];
-                } else {
-                    sz[row * kSpPitch + p] = e4[e];
-                }
-            }
-        }
-        __syncthreads();
-        // A rows: wy_p[b] wz_p[c] for this thread's row and node groups
-#pragma unroll
-        for (int g = 0; g < PG; g++) {
-            const int pg = kp * PG + g;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (row_ok) {
-                const float4 y4 = *reinterpret_cast<const float4*>(sy + rb * kSpPitch + 4 * pg);
-                const float4 z4 = *reinterpret_cast<const float4*>(sz + rc * kSpPitch + 4 * pg);
-                v[0] = y4.x * z4.x; v[1] = y4.y * z4.y; v[2] = y4.z * z4.z; v[3] = y4.w * z4.w;
-            }
-            float4 hv, lv;
-            split4(v, hv, lv);
-            const int o = ((rt >> 3) * (kSpKC / 4) + pg) * 32 + (rt & 7) * 4;
-            *reinterpret_cast<float4*>(aht + o) = hv;
-            *reinterpret_cast<float4*>(alt + o) = lv;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        taddr = *tslot;
-        if (tid == 0) {
-#pragma unroll
-            for (int t = 0; t < MT; t++) {
-#pragma unroll
-                for (int ks = 0; ks < kSpKC / 8; ks++) {
-                    const uint32_t ao = (uint32_t)(t * 128 * kSpKC * 4 + ks * 256);
-                    const uint64_t ah = umma_desc_sbo(su32(sAh) + ao, kSbo), al = umma_desc_sbo(su32(sAl) + ao, kSbo);
-                    const uint64_t bh = umma_desc_sbo(su32(sBh) + ks * 256, kSbo);
-                    const uint64_t bl = umma_desc_sbo(su32(sBl) + ks * 256, kSbo);
-                    const uint32_t d = taddr + 16 * t;
-                    umma_tf32(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
-                    umma_tf32(d, ah, bl, idesc, 1);
-                    umma_tf32(d, al, bh, idesc, 1);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(mbar)) : "memory");
-        }
-        first = false;
-        // the chunk's operands are read by the MMAs: wait before the next chunk overwrites them
-        ok = __syncthreads_and(mbar_wait(su32(mbar), phase)) != 0;
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok && tid == 0) atomicAdd(&g_wait_timeouts, 1ull);
-    }
-    if (ok && sp.z > 0) {
-        // row r2 of tile t: this warp's lanes; 16 columns a
-        const int t = warp >> 2;
-        const int r2 = t * 128 + 32 * (warp & 3) + lane;
-        if (t < MT) {
-            uint32_t v[16];
-            ANOVA_TMEM_LD16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * t), v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (r2 < R * R) {
-                const int b = r2 / R, c = r2 - (r2 / R) * R;
-                int gb = Tb * by - m + b, gc = Tb * bz - m + c;
-                gb += gb < 0 ? nos : (gb >= nos ? -nos : 0);
-                gc += gc < 0 ? nos : (gc >= nos ? -nos : 0);
-#pragma unroll
-                for (int a = 0; a < R; a++) {
-                    int ga = Tb * bx - m + a;
-                    ga += ga < 0 ? nos : (ga >= nos ? -nos : 0);
-                    atomicAdd(&grid[((size_t)ga * nos + gb) * nos + gc], __uint_as_float(v[a]));
-                }
-            }
-        }
-    }
-    if (!ok) mbar_wait(su32(mbar), phase ^ 1);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) {
-        taddr = *tslot;
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kSpCols));
-    }
-}
-
-template <int R>
-static void launch_spread_umma(const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
-    constexpr size_t sh = spread_umma_need<R>();
-    static_assert(sh <= 227 * 1024, "shared memory per block");
-    static bool attr = [] {
-        cudaFuncSetAttribute(k_spread3_umma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        return true;
-    }();
-    (void)attr;
-    k_spread3_umma<R><<<nsub, kUmmaThreads, sh, st>>>(sub, descs, m);
-}
-
-anova_status spread3_umma(int R, const int4* sub, int nsub, const DenseWin* descs, int m, cudaStream_t st) {
-    if (nsub == 0) return ANOVA_OK;
-    switch (R) {
-        case 4: launch_spread_umma<4>(sub, nsub, descs, m, st); break;
-        case 6: launch_spread_umma<6>(sub, nsub, descs, m, st); break;
-        case 8: launch_spread_umma<8>(sub, nsub, descs, m, st); break;
-        case 10: launch_spread_umma<10>(sub, nsub, descs, m, st); break;
-        case 12: launch_spread_umma<12>(sub, nsub, descs, m, st); break;
-        case 14: launch_spread_umma<14>(sub, nsub, descs, m, st); break;
-        case 16: launch_spread_umma<16>(sub, nsub, descs, m, st); break;
-        default: set_error("tcgen05 spread: unsupported region size"); return ANOVA_EINVAL;
-    }
-    ANOVA_CHECK_LAUNCH();
-    return ANOVA_OK;
-}
-
 // ------------------------------------------------------------- wait probe
 // One warp waits on an mbarrier that nothing arrives on, with the bounded poll
 // loop of the kernels above cut to `polls` polls, so the wait gives up; the
@@ -530,7 +332,7 @@ extern "C" anova_status anova_debug_wait_probe(int32_t polls, void* stream) {
     }
     cudaStream_t st = (cudaStream_t)stream;
     int* flag = nullptr;
-    ANOVA_CUDA_TRY(cudaMallocAsync(&flag, sizeof(int), st));
+    ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&flag, sizeof(int), st));
     ANOVA_CUDA_TRY(cudaMemsetAsync(flag, 0xff, sizeof(int), st));   // -1: the probe did not run
     anova::k_wait_probe<<<1, 32, 0, st>>>(polls, flag);
     ANOVA_CHECK_LAUNCH();

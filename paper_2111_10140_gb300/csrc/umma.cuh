@@ -97,9 +97,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar, uint32_t count = 1) {
 }
 
 // bounded wait that also gives up once *abort is set (by another role of the block);
-// the waiting thread sleeps in try_wait (suspend hint 20 us) instead of spinning
+// the waiting thread sleeps in try_wait (suspend hint 20 us) instead of spinning; at most
+// 2^14 polls (about 0.3 s)
 __device__ __forceinline__ bool mbar_wait_abortable(uint32_t mbar, uint32_t parity, const volatile int* abort,
-                                                    int polls = kUmmaSpin >> 6) {
+                                                    int polls = kUmmaSpin >> 8) {
     uint32_t done = 0;
     for (int it = 0; it < polls && !done; it++) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
