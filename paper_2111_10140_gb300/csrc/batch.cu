@@ -326,6 +326,78 @@ k_b_norm(const BSysInfo* __restrict__ sys, const double* __restrict__ v, double*
     if (threadIdx.x == 0) part[(size_t)blockIdx.y * nchunk + blockIdx.x] = acc;
 }
 
+// w = q + lambda dx = (K + lambda I) dx with q = K dx (FP64); partial r.w and w.w per system
+__global__ void __launch_bounds__(kBThreads)
+k_b_mr(const BSysInfo* __restrict__ sys, const double* __restrict__ lam, const double* __restrict__ r,
+       const double* __restrict__ q, const double* __restrict__ dx, double* __restrict__ w,
+       double* __restrict__ part_rw, double* __restrict__ part_ww, int nchunk) {
+    __shared__ double sh[32];
+    const BSysInfo s = sys[blockIdx.y];
+    const double lambda = lam[blockIdx.y];
+    const int64_t lo = (int64_t)blockIdx.x * kBChunk;
+    double rw = 0.0, ww = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) {
+        const int64_t e = s.off + i;
+        const double v = q[e] + lambda * dx[e];
+        w[e] = v;
+        rw += r[e] * v;
+        ww += v * v;
+    }
+    rw = block_sum(rw, sh);
+    ww = block_sum(ww, sh);
+    if (threadIdx.x == 0) {
+        part_rw[(size_t)blockIdx.y * nchunk + blockIdx.x] = rw;
+        part_ww[(size_t)blockIdx.y * nchunk + blockIdx.x] = ww;
+    }
+}
+
+// x += t dx, r -= t w for the systems with t != 0; partial r.r per system
+__global__ void __launch_bounds__(kBThreads)
+k_b_step(const BSysInfo* __restrict__ sys, const double* __restrict__ t, const double* __restrict__ dx,
+         const double* __restrict__ w, double* __restrict__ x, double* __restrict__ r, double* __restrict__ part,
+         int nchunk) {
+    __shared__ double sh[32];
+    const BSysInfo s = sys[blockIdx.y];
+    const double ts = t[blockIdx.y];
+    const int64_t lo = (int64_t)blockIdx.x * kBChunk;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < s.len && i < lo + kBChunk; i += blockDim.x) {
+        const int64_t e = s.off + i;
+        double v = r[e];
+        if (ts != 0.0) {
+            x[e] += ts * dx[e];
+            v -= ts * w[e];
+            r[e] = v;
+        }
+        acc += v * v;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.y * nchunk + blockIdx.x] = acc;
+}
+
+// partial sums of v.v (one per block) for the power iteration
+__global__ void __launch_bounds__(kBThreads) k_dot_partial(const double* __restrict__ v, int64_t n,
+                                                           double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += v[i] * v[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// v = scale * w, or (first) a fixed pattern of +-1 and 0.5 entries
+__global__ void k_power_next(double* __restrict__ v, const double* __restrict__ w, int64_t n, double scale, int first) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = first ? ((i * 2654435761ull) & 4 ? 1.0 : -0.5) : scale * w[i];
+}
+
+// y += x over one system's slice
+__global__ void k_slice_axpy(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
 // zero the right-hand side of systems already converged; x += dx for the others
 __global__ void __launch_bounds__(kBThreads)
 k_b_mask(const BSysInfo* __restrict__ sys, const int* __restrict__ done, double* __restrict__ r) {
@@ -418,7 +490,7 @@ static anova_status batch_operator(anova_batch* b, const double* x, cudaStream_t
     ANOVA_CUDA_TRY(cudaMemsetAsync(b->grids, 0, b->grid_elems * sizeof(float), st));
     ANOVA_TRY(dense_f32_spread_groups(b->m, b->sub, b->desc, b->groups, st,
                                       b->plans[0]->pw12 ? b->plans[0]->psi_host.data() : nullptr,
-                                      b->plans[0]->sm_count));
+                                      b->plans[0]->sm_count, b->plans[0]->spread_tc5));
     ANOVA_TRY(fft3_box_run<float>(b->fft3, b->fft3_shape, b->sm_count, st));
     ANOVA_TRY(fft12_box_run<float>(b->fft12, b->n12, b->smem12, st, b->n12_uniform));
     return dense_f32_gather_groups(b->m, b->plans[0]->psi_poly, b->sub, b->desc, b->groups, st,
@@ -550,7 +622,7 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
     b->grid_elems = grid_elems;
     anova_status s = ANOVA_OK;
     auto alloc = [&](void** ptr, size_t bytes) {
-        if (s == ANOVA_OK && cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        if (s == ANOVA_OK && anova::dev_malloc((void**)ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
             set_error("anova_batch_create: out of device memory");
             s = ANOVA_ENOMEM;
         }
@@ -851,6 +923,40 @@ anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const doub
     return all ? ANOVA_OK : ANOVA_ENOCONV;
 }
 
+// lambda_max of a problem's FP64 kernel matrix by 20 power iterations; v, w:
+// device work vectors of the problem's N entries, part: at least 64 doubles
+static anova_status power_lambda_max(anova_plan* plan, double* v, double* w, double* part, double* out,
+                                     cudaStream_t st) {
+    const int64_t n = plan->N;
+    *out = 0.0;
+    if (n == 0) return ANOVA_OK;
+    const int nb = (int)std::min<int64_t>(64, (n + kBThreads - 1) / kBThreads);
+    auto norm = [&](const double* x, double* r) -> anova_status {
+        k_dot_partial<<<nb, kBThreads, 0, st>>>(x, n, part);
+        ANOVA_CHECK_LAUNCH();
+        double h[64];
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(h, part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        double t = 0.0;
+        for (int i = 0; i < nb; i++) t += h[i];
+        *r = std::sqrt(t);
+        return ANOVA_OK;
+    };
+    k_power_next<<<nb, kBThreads, 0, st>>>(v, nullptr, n, 1.0, 1);
+    double nv = 0.0;
+    ANOVA_TRY(norm(v, &nv));
+    for (int it = 0; it < 20 && nv > 0.0; it++) {
+        ANOVA_TRY(anova_matvec(plan, ANOVA_FP64, v, w, 1, n, st));
+        double nw = 0.0;
+        ANOVA_TRY(norm(w, &nw));
+        *out = nw / nv;
+        if (!(nw > 0.0)) break;
+        k_power_next<<<nb, kBThreads, 0, st>>>(v, w, n, 1.0 / nw, 0);
+        nv = 1.0;
+    }
+    return ANOVA_OK;
+}
+
 anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, const double* y, double* alpha,
                                         double tol, int32_t maxit, int32_t* iters, double* relres, void* stream) {
     if (!b || !lambda || !y || !alpha || y == alpha || !(tol > 0.0) || maxit < 1) {
@@ -865,119 +971,169 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
     cudaStream_t st = (cudaStream_t)stream;
     const dim3 gv(b->nchunk, b->NS);
     const int gs = (b->NS + kBThreads - 1) / kBThreads;
-    double *q = nullptr, *r = nullptr, *dx = nullptr, *tot = nullptr;
+    const int NS = b->NS;
+    // scratch: allocated together, freed together on every exit
+    double *q = nullptr, *r = nullptr, *rin = nullptr, *dx = nullptr, *w = nullptr, *tot = nullptr, *tdev = nullptr,
+           *part2 = nullptr;
     int* done = nullptr;
-    ANOVA_CUDA_TRY(cudaMallocAsync(&q, b->S * sizeof(double), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&r, b->S * sizeof(double), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&dx, b->S * sizeof(double), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&tot, b->NS * sizeof(double), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&done, b->NS * sizeof(int), st));
-    std::vector<double> lam(b->NS), yy(b->NS), rr(b->NS);
-    std::vector<int> conv(b->NS, 0), total_it(b->NS, 0), it(b->NS), apply(b->NS, 0), failed(b->NS, 0),
-        revert(b->NS, 0);
-    std::vector<double> rr_prev(b->NS);
-    std::vector<double> inner_rel(b->NS);
-    for (int s = 0; s < b->NS; s++) lam[s] = lambda[s / b->nrhs];
     anova_status s = ANOVA_OK;
-    auto totals = [&](std::vector<double>& out) -> anova_status {
-        k_b_totals<<<gs, kBThreads, 0, st>>>(b->sys, b->part, b->nchunk, b->NS, tot);
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (s == ANOVA_OK && anova::dev_malloc_async((void**)ptr, bytes, st) != cudaSuccess) {
+            set_error("krr_batch_cg_solve_refined: out of device memory for the solver's vectors");
+            s = ANOVA_ENOMEM;
+        }
+    };
+    alloc((void**)&q, b->S * sizeof(double));
+    alloc((void**)&r, b->S * sizeof(double));
+    alloc((void**)&rin, b->S * sizeof(double));
+    alloc((void**)&dx, b->S * sizeof(double));
+    alloc((void**)&w, b->S * sizeof(double));
+    alloc((void**)&tot, std::max(2 * NS, 64) * sizeof(double));
+    alloc((void**)&tdev, NS * sizeof(double));
+    alloc((void**)&part2, (size_t)NS * b->nchunk * sizeof(double));
+    alloc((void**)&done, NS * sizeof(int));
+    std::vector<double> lam(NS), yy(NS), rr(NS), rw(NS), ww(NS), t(NS);
+    std::vector<int> conv(NS, 0), stalled(NS, 0), total_it(NS, 0), it(NS, 0), closed(NS, 0);
+    std::vector<double> inner_rel(NS);
+    for (int k = 0; k < NS; k++) lam[k] = lambda[k / b->nrhs];
+    auto totals = [&](const double* prt, std::vector<double>& out) -> anova_status {
+        k_b_totals<<<gs, kBThreads, 0, st>>>(b->sys, prt, b->nchunk, NS, tot);
         ANOVA_CHECK_LAUNCH();
-        ANOVA_CUDA_TRY(cudaMemcpyAsync(out.data(), tot, b->NS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(out.data(), tot, NS * sizeof(double), cudaMemcpyDeviceToHost, st));
         ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
         return ANOVA_OK;
     };
-    if (cudaMemcpyAsync(b->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(alpha, 0, b->S * sizeof(double), st) != cudaSuccess) {
+    // q = K64 v for every system (each problem's FP64 operator on its right-hand sides)
+    auto apply64 = [&](const double* v, double* out) -> anova_status {
+        for (int p = 0; p < b->nprob; p++)
+            ANOVA_TRY(anova_matvec(b->plans[p], ANOVA_FP64, v + b->off[p], out + b->off[p], b->nrhs,
+                                   b->plans[p]->N, stream));
+        return ANOVA_OK;
+    };
+    // r = y - (K64 + lambda I) x from scratch, rr = r.r
+    auto true_residuals = [&]() -> anova_status {
+        ANOVA_TRY(apply64(alpha, q));
+        k_b_refine<<<gv, kBThreads, 0, st>>>(b->sys, b->lam, y, q, alpha, r, b->part, b->nchunk);
+        ANOVA_CHECK_LAUNCH();
+        return totals(b->part, rr);
+    };
+    if (s == ANOVA_OK &&
+        (cudaMemcpyAsync(b->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemsetAsync(alpha, 0, b->S * sizeof(double), st) != cudaSuccess ||
+         cudaMemcpyAsync(r, y, b->S * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)) {
         set_error("krr_batch_cg_solve_refined: setup copy failed");
         s = ANOVA_ECUDA;
     }
     if (s == ANOVA_OK) {
         k_b_norm<<<gv, kBThreads, 0, st>>>(b->sys, y, b->part, b->nchunk);
-        s = totals(yy);
+        s = totals(b->part, yy);
+        rr = yy;
     }
-    // outer passes: FP64 residual of the problems' own plans, FP32 batched CG
-    // on it to 1e-4 relative (tighter as the target nears), alpha += correction
+    // Passes: the batched FP32 CG on the current FP64 residual gives a correction
+    // dx; the step t dx with t minimising the FP64 residual ||r - t (K64 + lambda I) dx||
+    // is taken (never raising it).  A system whose residual norm falls by less than
+    // 10 % in a pass has outrun what its FP32 operator resolves: it leaves the
+    // batched passes for plain FP64 CG on its correction equation.
     const int kMaxPass = 40;
-    bool all = false;
     for (int pass = 0; s == ANOVA_OK && pass < kMaxPass; pass++) {
-        if (pass == 0) {
-            if (cudaMemcpyAsync(r, y, b->S * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-                s = ANOVA_ECUDA;
-                break;
-            }
-            rr = yy;
-        } else {
-            for (int p = 0; p < b->nprob && s == ANOVA_OK; p++)
-                s = anova_matvec(b->plans[p], ANOVA_FP64, alpha + b->off[p], q + b->off[p], b->nrhs, b->plans[p]->N,
-                                 stream);
-            if (s != ANOVA_OK) break;
-            k_b_refine<<<gv, kBThreads, 0, st>>>(b->sys, b->lam, y, q, alpha, r, b->part, b->nchunk);
-            s = totals(rr);
-            if (s != ANOVA_OK) break;
-            // a correction that left the FP64 residual larger is taken back and
-            // its system stops refining (the FP32 operator does not resolve it)
-            bool any = false;
-            for (int k = 0; k < b->NS; k++) {
-                revert[k] = apply[k] && !(rr[k] <= rr_prev[k]);
-                if (revert[k]) {
-                    rr[k] = rr_prev[k];
-                    failed[k] = 1;
-                    any = true;
-                }
-            }
-            if (any) {
-                ANOVA_CUDA_TRY(cudaMemcpyAsync(done, revert.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
-                k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, done, dx, alpha, -1.0);
-                ANOVA_CHECK_LAUNCH();
-            }
-        }
-        rr_prev = rr;
-        all = true;
+        bool any_open = false;
         double worst = 0.0;
-        for (int k = 0; k < b->NS; k++) {
+        for (int k = 0; k < NS; k++) {
             const double rel = yy[k] > 0.0 ? std::sqrt(rr[k] / yy[k]) : 0.0;
             if (!std::isfinite(rel)) {
                 set_error("krr_batch_cg_solve_refined: non-finite residual in system " + std::to_string(k));
                 s = ANOVA_ERANGE;
                 break;
             }
-            conv[k] = rel <= tol || total_it[k] >= maxit || failed[k];
-            if (relres) relres[k] = rel;
-            if (rel > tol) {
-                all = false;
+            conv[k] = rel <= tol;
+            closed[k] = conv[k] || stalled[k] || total_it[k] >= maxit;
+            if (!closed[k]) {
+                any_open = true;
                 worst = std::max(worst, rel);
             }
         }
-        if (s != ANOVA_OK) break;
-        bool any_open = false;
-        for (int k = 0; k < b->NS; k++) any_open = any_open || !conv[k];
-        if (!any_open) break;
-        ANOVA_CUDA_TRY(cudaMemcpyAsync(done, conv.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_b_mask<<<gv, kBThreads, 0, st>>>(b->sys, done, r);
-        ANOVA_CHECK_LAUNCH();
+        if (s != ANOVA_OK || !any_open) break;
+        if (cudaMemcpyAsync(rin, r, b->S * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(done, closed.data(), NS * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            s = ANOVA_ECUDA;
+            break;
+        }
+        k_b_mask<<<gv, kBThreads, 0, st>>>(b->sys, done, rin);
         // relative to this pass's residual: 1e-4 (about what the FP32 operator
         // resolves), or only what is left to the target when that is less
         const double inner = std::min(0.5, std::max(1e-4, 0.5 * tol / std::max(worst, 1e-300)));
-        s = krr_batch_cg_solve(b, lambda, r, dx, inner, maxit, it.data(), inner_rel.data(), stream);
+        // at most maxit / 8 inner iterations per pass, so that a system the FP32
+        // operator cannot resolve stalls early and keeps budget for the fallback
+        const int inner_maxit = std::max(64, maxit / 8);
+        s = krr_batch_cg_solve(b, lambda, rin, dx, inner, inner_maxit, it.data(), inner_rel.data(), stream);
         if (s == ANOVA_ENOCONV) s = ANOVA_OK;
         if (s != ANOVA_OK) break;
-        // a correction that broke down (non-finite) is dropped and its system
-        // stops refining: its FP32 operator is not definite at this lambda
-        for (int k = 0; k < b->NS; k++) {
+        if ((s = apply64(dx, q)) != ANOVA_OK) break;
+        k_b_mr<<<gv, kBThreads, 0, st>>>(b->sys, b->lam, r, q, dx, w, b->part, part2, b->nchunk);
+        if ((s = totals(b->part, rw)) != ANOVA_OK || (s = totals(part2, ww)) != ANOVA_OK) break;
+        for (int k = 0; k < NS; k++) {
+            t[k] = 0.0;
+            if (closed[k]) continue;
             total_it[k] += it[k];
-            apply[k] = !conv[k] && std::isfinite(inner_rel[k]);
-            if (!conv[k] && !apply[k]) failed[k] = 1;
+            if (std::isfinite(inner_rel[k]) && std::isfinite(rw[k]) && ww[k] > 0.0) t[k] = rw[k] / ww[k];
         }
-        ANOVA_CUDA_TRY(cudaMemcpyAsync(done, apply.data(), b->NS * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_b_axpy<<<gv, kBThreads, 0, st>>>(b->sys, done, dx, alpha, 1.0);
-        ANOVA_CHECK_LAUNCH();
+        if (cudaMemcpyAsync(tdev, t.data(), NS * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            s = ANOVA_ECUDA;
+            break;
+        }
+        const std::vector<double> rr_old = rr;
+        k_b_step<<<gv, kBThreads, 0, st>>>(b->sys, tdev, dx, w, alpha, r, b->part, b->nchunk);
+        if ((s = totals(b->part, rr)) != ANOVA_OK) break;
+        for (int k = 0; k < NS; k++)
+            if (!closed[k] && !(rr[k] <= 0.81 * rr_old[k])) stalled[k] = 1;
     }
-    if (iters)
-        for (int k = 0; k < b->NS; k++) iters[k] = total_it[k];
+    // the recursive residual drifts from the true one: recompute it
+    if (s == ANOVA_OK) s = true_residuals();
+    // plain FP64 CG on the correction equation of every system still above tol
+    // that it can bring to tol within the remaining budget: CG needs about
+    // 0.5 sqrt(kappa) ln(2 / eps) iterations to reduce the error by eps, with
+    // kappa = (lambda_max(K) + lambda) / lambda and lambda_max(K) from 20 power
+    // iterations of the problem's FP64 operator
+    bool fallback = false;
+    std::vector<double> lmax(b->nprob, -1.0);
+    for (int k = 0; s == ANOVA_OK && k < NS; k++) {
+        const double rel = yy[k] > 0.0 ? std::sqrt(rr[k] / yy[k]) : 0.0;
+        if (rel <= tol || total_it[k] >= maxit) continue;
+        const int p = k / b->nrhs;
+        const int64_t o = b->off[p] + (int64_t)(k % b->nrhs) * b->plans[p]->N;
+        if (lmax[p] < 0.0) {
+            s = power_lambda_max(b->plans[p], dx + o, w + o, tot, &lmax[p], st);
+            if (s != ANOVA_OK) break;
+        }
+        const double kappa = (lmax[p] + lam[k]) / lam[k];
+        const double need = 0.5 * std::sqrt(kappa) * std::log(2.0 * rel / tol);
+        if (need > (double)(maxit - total_it[k])) continue;   // beyond the budget: left as it is
+        int itc = 0;
+        double relc = 0.0;
+        s = cg_fp64_solve(b->plans[p], lam[k], r + o, dx + o, std::min(0.5, tol / rel), maxit - total_it[k], &itc,
+                          &relc, st);
+        if (s != ANOVA_OK) break;
+        total_it[k] += itc;
+        k_slice_axpy<<<grid_for(b->plans[p]->N, kBThreads, 8 * b->sm_count), kBThreads, 0, st>>>(
+            b->plans[p]->N, dx + o, alpha + o);
+        fallback = true;
+    }
+    if (s == ANOVA_OK && fallback) s = true_residuals();
+    bool all = s == ANOVA_OK;
+    for (int k = 0; k < NS; k++) {
+        const double rel = yy[k] > 0.0 ? std::sqrt(rr[k] / yy[k]) : 0.0;
+        if (relres) relres[k] = rel;
+        if (iters) iters[k] = total_it[k];
+        if (!(rel <= tol)) all = false;
+    }
     cudaFreeAsync(q, st);
     cudaFreeAsync(r, st);
+    cudaFreeAsync(rin, st);
     cudaFreeAsync(dx, st);
+    cudaFreeAsync(w, st);
     cudaFreeAsync(tot, st);
+    cudaFreeAsync(tdev, st);
+    cudaFreeAsync(part2, st);
     cudaFreeAsync(done, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (s == ANOVA_OK && e != cudaSuccess) {

@@ -1,8 +1,8 @@
 """Batches: several problems and right-hand sides per launch.
 
 The batch's operator must give, system by system, what the problem's own plan
-gives (same FP32 kernels; the atomics of the spread sum in another order, so
-1e-6) and the oracle's fast summation (1e-5, the FP32 bar).  The batched CG
+gives (same FP32 kernels, but the spread's FP32 sums are grouped over other
+blocks, so to the FP32 bar 1e-5) and the oracle's fast summation (1e-5).  The batched CG
 must stop each system at its own tolerance, agree with the single-problem
 solver on the same FP32 operator, and leave a residual under the oracle's FP64
 operator within the FP32 operator's rounding on the solution; the refined
@@ -93,7 +93,9 @@ def test_batch_matvec_matches_plans_and_oracle(B, torch, setup):
             a32 = torch.from_numpy(xs[p][r]).float().cuda()
             o32 = torch.empty_like(a32)
             B.anova_matvec(plan, a32, o32)
-            assert rel(yb[r], o32.double().cpu().numpy()) <= 1e-6, (p, r)
+            # the batch and the plan split the spread's FP32 sums over different blocks,
+            # so they agree to the FP32 rounding of those sums (the FP32 parity bar)
+            assert rel(yb[r], o32.double().cpu().numpy()) <= 1e-5, (p, r)
             ref = oracle.fastsum(None, w.X, w.windows, w.eta, w.ell, w.n, w.m, xs[p][r], sigma=w.sigma,
                                  epsB=w.epsB, p=w.p)
             assert rel(yb[r], ref) <= 1e-5, (p, r)
@@ -164,6 +166,40 @@ def test_batch_refined_reaches_fp64_residual(B, torch):
             # GPU FP64 operator vs oracle: 1e-12 of ||K alpha||
             assert res <= rr[p, r] + 1e-11 * np.linalg.norm(Ka) / np.linalg.norm(yr), (p, r, res)
     batch.close()
+
+
+def test_batch_refined_hard_system_matches_oracle_cg(B, torch):
+    """One hard system (lambda = 1e-4, ell = 0.5: kappa ~ N / lambda) through the
+    batched refined solver: the FP32 corrections alone cannot resolve it, so the
+    solver must still reach the FP64 residual target (by its minimal-residual
+    steps and the FP64 fallback) and agree with the oracle's CG on the oracle's
+    FP64 operator."""
+    tol = 1e-6
+    w = W.random_problem(600, 3, [(0, 1), (2,)], 0.5, [16, 16], 6, seed=700)
+    w.epsB = 0.25
+    w.lam = 1e-4
+    yr = np.random.default_rng(701).standard_normal(w.N)
+    plan = B.anova_fastsum_plan(torch.from_numpy(w.X).cuda(), w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB,
+                                precision=B.MIXED)
+    batch = B.Batch([plan], 1)
+    y = flat(batch, torch, [yr[None, :]])
+    alpha = torch.empty_like(y)
+    st, its, rr = batch.cg_solve([w.lam], y, alpha, tol, 20000, refined=True)
+    assert st == B.OK, (st, its, rr)
+    assert rr[0, 0] <= tol
+    ab = batch.block(alpha, 0).cpu().numpy()[0]
+    Ka = oracle.fastsum(None, w.X, w.windows, w.eta, w.ell, w.n, w.m, ab, sigma=w.sigma, epsB=w.epsB, p=w.p)
+    res = np.linalg.norm(yr - Ka - w.lam * ab) / np.linalg.norm(yr)
+    assert res <= tol + 1e-11 * np.linalg.norm(Ka) / np.linalg.norm(yr), res
+    a_or, it_or, rel_or = oracle.cg(w.X, w.windows, w.eta, w.ell, w.n, w.m, w.lam, yr, tol, 20000, sigma=w.sigma,
+                                    epsB=w.epsB, p=w.p)
+    assert rel_or <= tol
+    # both solve the same FP64 system to tol: their difference is bounded by the
+    # residuals through the inverse, ||(K + lambda I)^-1|| <= 1 / lambda
+    bound = (tol + rel_or) * np.linalg.norm(yr) / w.lam
+    assert np.linalg.norm(ab - a_or) <= bound, (np.linalg.norm(ab - a_or), bound)
+    batch.close()
+    plan.close()
 
 
 def test_batch_rejects_mismatched_plans(B, torch):
