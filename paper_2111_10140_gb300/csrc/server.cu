@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -50,7 +51,7 @@ struct ServerRequest {
     double* out = nullptr;
     // bookkeeping
     int64_t bytes = 0;
-    std::chrono::steady_clock::time_point submitted;
+    std::chrono::steady_clock::time_point submitted, started;
     double latency_ms = 0.0;
     anova_status status = ANOVA_OK;
     int32_t iterations = 0;
@@ -87,6 +88,11 @@ struct anova_server {
     int running_fits = 0;
     int max_fits = 1;             // workers a fit may occupy; the rest stay free for predictions
     std::chrono::steady_clock::time_point t0;
+    // fit admission: nodes of the fits queued and running, and the measured fit rate
+    double fit_wait_bound_ms = 0.0;   // 0: no bound
+    int64_t fit_nodes_queued = 0, fit_nodes_running = 0;
+    double fit_nodes_per_ms = 0.0;    // per worker, over the completed fits (0: none yet)
+    int64_t fits_done = 0;
 };
 
 namespace anova {
@@ -121,7 +127,7 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
         if (s == ANOVA_OK) s = anova_plan_set_graphs(mdl.plan, 0);
         double* alpha = nullptr;
         if (s == ANOVA_OK) {
-            if (cudaMallocAsync(&alpha, std::max<int64_t>(r.N, 1) * sizeof(double), st) != cudaSuccess)
+            if (anova::dev_malloc_async((void**)&alpha, std::max<int64_t>(r.N, 1) * sizeof(double), st) != cudaSuccess)
                 s = ANOVA_ENOMEM;
         }
         if (s == ANOVA_OK)
@@ -220,7 +226,12 @@ static void worker_main(anova_server* sv) {
                     sv->queue.erase(pick);
                     sv->in_use += r->bytes;
                     sv->running++;
-                    if (r->kind == 0) sv->running_fits++;
+                    r->started = std::chrono::steady_clock::now();
+                    if (r->kind == 0) {
+                        sv->running_fits++;
+                        sv->fit_nodes_queued -= r->N;
+                        sv->fit_nodes_running += r->N;
+                    }
                     if (r->kind == 1) {
                         auto m = sv->models.find(r->model);
                         if (m != sv->models.end()) m->second.inflight++;
@@ -243,7 +254,16 @@ static void worker_main(anova_server* sv) {
             r->latency_ms = std::chrono::duration<double, std::milli>(t1 - r->submitted).count();
             r->done = true;
             sv->running--;
-            if (r->kind == 0) sv->running_fits--;
+            if (r->kind == 0) {
+                sv->running_fits--;
+                sv->fit_nodes_running -= r->N;
+                const double service = std::chrono::duration<double, std::milli>(t1 - r->started).count();
+                if ((r->status == ANOVA_OK || r->status == ANOVA_ENOCONV) && service > 0.0 && r->N > 0) {
+                    // running mean of the per-worker fit rate, nodes per millisecond
+                    sv->fits_done++;
+                    sv->fit_nodes_per_ms += ((double)r->N / service - sv->fit_nodes_per_ms) / (double)sv->fits_done;
+                }
+            }
             if (r->status == ANOVA_OK || r->status == ANOVA_ENOCONV) sv->latencies.push_back(r->latency_ms);
         }
         sv->cv_done.notify_all();
@@ -253,6 +273,19 @@ static void worker_main(anova_server* sv) {
 
 static anova_status enqueue(anova_server* sv, std::shared_ptr<ServerRequest> r, int64_t* ticket) {
     std::lock_guard<std::mutex> lock(sv->mu);
+    if (r->kind == 0) {
+        // expected wait of this fit: the fit nodes ahead of it at the measured rate
+        if (sv->fit_wait_bound_ms > 0.0 && sv->fit_nodes_per_ms > 0.0) {
+            const double wait_ms = (double)(sv->fit_nodes_queued + sv->fit_nodes_running) /
+                                   (sv->fit_nodes_per_ms * (double)sv->max_fits);
+            if (wait_ms > sv->fit_wait_bound_ms) {
+                set_error("anova_server_submit_fit: expected queue wait " + std::to_string((int64_t)wait_ms) +
+                          " ms exceeds the bound of " + std::to_string((int64_t)sv->fit_wait_bound_ms) + " ms");
+                return ANOVA_EBUSY;
+            }
+        }
+        sv->fit_nodes_queued += r->N;
+    }
     r->ticket = sv->next_ticket++;
     r->submitted = std::chrono::steady_clock::now();
     sv->requests[r->ticket] = r;
@@ -379,6 +412,54 @@ anova_status anova_server_release(anova_server* sv, int64_t model) {
     krr_model_destroy(mdl.model);
     anova_plan_destroy(mdl.plan);
     sv->cv_work.notify_all();
+    return ANOVA_OK;
+}
+
+anova_status anova_server_fit_alpha(anova_server* sv, int64_t fit, double* out, void* stream) {
+    if (!sv) return ANOVA_EINVAL;
+    krr_model* model = nullptr;
+    int64_t N = 0;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->models.find(fit);
+        if (it == sv->models.end() || !it->second.ready || it->second.releasing) {
+            set_error("anova_server_fit_alpha: unknown, failed or released fit");
+            return ANOVA_EINVAL;
+        }
+        model = it->second.model;
+        N = it->second.N;
+        it->second.inflight++;             // keeps the model while its coefficients are copied
+    }
+    anova_status s = (N > 0 && !out) ? ANOVA_EINVAL : krr_model_alpha(model, out, stream);
+    if (s == ANOVA_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) s = ANOVA_ECUDA;
+    bool free_now = false;
+    ServerModel mdl;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->models.find(fit);
+        it->second.inflight--;
+        if (it->second.releasing && it->second.inflight == 0) {
+            mdl = it->second;
+            sv->in_use -= mdl.bytes;
+            sv->models.erase(it);
+            free_now = true;
+        }
+    }
+    if (free_now) {
+        krr_model_destroy(mdl.model);
+        anova_plan_destroy(mdl.plan);
+    }
+    if (s == ANOVA_EINVAL) set_error("anova_server_fit_alpha: NULL output");
+    return s;
+}
+
+anova_status anova_server_set_fit_wait_bound(anova_server* sv, double max_wait_ms) {
+    if (!sv || !(max_wait_ms >= 0.0) || !std::isfinite(max_wait_ms)) {
+        set_error("anova_server_set_fit_wait_bound: NULL server or a negative or non-finite bound");
+        return ANOVA_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->fit_wait_bound_ms = max_wait_ms;
     return ANOVA_OK;
 }
 

@@ -1,5 +1,8 @@
 """The request server: fits and predictions served concurrently by worker
-threads give the results that the same calls give one at a time.
+threads give the results that the same calls give one at a time, and the
+oracle's: each served fit's coefficients agree with the oracle's CG on its
+FP64 operator, each served prediction with the oracle's fast summation at the
+oracle's coefficients (1e-5).
 
 Each model is fitted (mixed-precision CG of Sec. 2 to tol 1e-8) and evaluated
 at test points (Sec. 4.3) once through the plain entry points (krr_cg_solve,
@@ -12,6 +15,7 @@ problems), iteration counts within a refinement pass or so.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2111_10140_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -116,6 +120,23 @@ def test_server_matches_serial_calls(B, torch):
             # frame, the model in its wide frame: two approximations within
             # the fast summation's error of each other
             assert err_plain < 1e-5, report
+        # against the oracle: the served coefficients and predictions
+        for i, ((w, Z), f) in enumerate(zip(probs, fits)):
+            a_srv = torch.empty(w.N, dtype=torch.float64, device="cuda")
+            sv.fit_alpha(f, a_srv)
+            a_srv = a_srv.cpu().numpy()
+            a_or, it_or, rel_or = oracle.cg(w.X, w.windows, w.eta, w.ell, w.n, w.m, LAM, w.y, TOL, 5000,
+                                            sigma=w.sigma, epsB=w.epsB, p=w.p)
+            assert rel_or <= TOL
+            # both solve (K + lambda I) alpha = y to TOL (the GPU's FP64 operator within 1e-12 of
+            # the oracle's): ||alpha_srv - alpha_or|| <= (residuals) ||y|| / lambda
+            bound = (TOL + rel_or + 1e-11) * np.linalg.norm(w.y) / LAM
+            assert np.linalg.norm(a_srv - a_or) <= bound, (i, np.linalg.norm(a_srv - a_or), bound)
+            # predictions in the served batches against the oracle's summation at its coefficients
+            ref_pred = np.concatenate([oracle.fastsum(Z[500 * k:500 * (k + 1)], w.X, w.windows, w.eta, w.ell, w.n,
+                                                      w.m, a_or, sigma=w.sigma, epsB=w.epsB, p=w.p)
+                                       for k in range(6)])
+            assert np.linalg.norm(got[i] - ref_pred) / np.linalg.norm(ref_pred) <= 1e-5, i
         s = sv.stats()
         assert s["completed"] == len(fits) + len(tickets)
         assert 0 < s["p50_ms"] <= s["p99_ms"]
@@ -159,3 +180,41 @@ def test_server_budget_serialises_and_reports_errors(B, torch):
         assert sv.stats()["bytes_in_use"] == 0
     finally:
         sv.close()
+
+
+def test_server_fit_wait_bound_refuses_fits(B, torch):
+    """With a bound on the expected queue wait, a fit submitted behind enough
+    fit work is refused at once with EBUSY (nothing queued); without a bound,
+    or with an empty queue, fits are admitted; predictions are never refused."""
+    w, Z = problems()[1]
+    sv = B.Server(n_workers=2, hbm_budget_bytes=8 << 30)
+    try:
+        X = torch.from_numpy(w.X).cuda()
+        y = torch.from_numpy(w.y).cuda()
+        torch.cuda.synchronize()
+        # no bound and no measured rate yet: admitted
+        f0 = sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
+        assert sv.wait(f0)["status"] == B.OK
+        sv.set_fit_wait_bound(1e-6)
+        # the queue is empty: the expected wait is 0, admitted
+        f1 = sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
+        # behind f1 the expected wait is f1's nodes at the measured rate: refused
+        with pytest.raises(B.AnovaError) as e:
+            sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
+        assert e.value.status == B.EBUSY
+        Zt = torch.from_numpy(Z[:500]).cuda()
+        o = torch.empty(500, dtype=torch.float64, device="cuda")
+        tp = sv.submit_predict(f0, Zt, o)
+        assert sv.wait(f1)["status"] == B.OK
+        assert sv.wait(tp)["status"] == B.OK
+        with pytest.raises(B.AnovaError):
+            sv.set_fit_wait_bound(-1.0)
+        sv.set_fit_wait_bound(0.0)
+        f2 = sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
+        assert sv.wait(f2)["status"] == B.OK
+        for f in (f0, f1, f2):
+            sv.release(f)
+        assert sv.stats()["bytes_in_use"] == 0
+    finally:
+        sv.close()
+
