@@ -4,13 +4,13 @@
 // krr_predict needs per-call scratch for the test points (their window
 // coordinates, the binned and sorted copy, the sort's histograms and the
 // per-window results) and gets it from cudaMalloc.  Some callers cannot
-// allocate inside the call: a serving loop that records its request path
-// while a CUDA stream is being captured (allocation is not a capturable
-// operation), code that must keep a fixed device-memory footprint under an
-// admission budget, or a host process whose allocator is owned by another
-// framework.  This variant takes that scratch from one file-scope device
-// array instead.  The plan's own buffers (grid, FFT work arrays, the binned
-// training nodes), created once by anova_fastsum_plan, are used as before.
+// allocate inside the call: a server that keeps a fixed device-memory
+// footprint under an admission budget, or a host process whose allocator is
+// owned by another framework.  This variant takes that scratch from one
+// file-scope device array instead.  The plan's own buffers (grid, FFT work
+// arrays, the binned training nodes), created once by anova_fastsum_plan, are
+// used as before.  The call synchronises its stream: the ball check reads each
+// window's largest test-point radius back to the host.
 #include <cuda_runtime.h>
 
 #include <mutex>
