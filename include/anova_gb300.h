@@ -51,7 +51,8 @@ typedef enum {
     ANOVA_ECUDA = 3,     /* a CUDA call failed; see anova_last_error() */
     ANOVA_ENOCONV = 4,   /* CG reached maxit; outputs hold the last iterate */
     ANOVA_ERANGE = 5,    /* input outside the supported range */
-    ANOVA_ETIMEOUT = 6   /* a bounded device-side wait expired */
+    ANOVA_ETIMEOUT = 6,  /* a bounded device-side wait expired */
+    ANOVA_EBUSY = 7      /* a request refused: its expected queue wait exceeds the server's bound */
 } anova_status;
 
 /* precision bitmask for anova_fastsum_plan: which operators the plan holds */
@@ -188,10 +189,12 @@ anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z,
  * krr_predict_noalloc -- the same prediction as krr_predict, but the call
  * itself allocates no device memory: no cudaMalloc, cudaFree or allocating
  * library routine runs inside it.  The paper has no counterpart; this entry
- * point exists for callers that cannot allocate while serving a request, such
- * as a request path recorded while a CUDA stream is being captured (allocation
- * is not capturable), a server holding a fixed device-memory budget, or a
- * process whose device allocator belongs to another framework.
+ * point exists for callers that cannot allocate while serving a request: a
+ * server that admits requests against a fixed device-memory budget (an
+ * allocation inside a request could fail or push the process over its budget
+ * under load), or a process whose device allocator belongs to another
+ * framework (a cudaMalloc here would bypass that allocator's pool and
+ * accounting).
  *
  * Arguments and result are those of krr_predict, with these limits:
  *   - M <= 65536 test points per call; larger M returns ANOVA_EINVAL.
@@ -207,7 +210,9 @@ anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z,
  *     other streams) race and corrupt each other's results.  Serialise them.
  *   - A test point outside the plan's ball returns ANOVA_ERANGE (krr_predict
  *     would build a joint frame, which needs allocation).
- * Synchronises `stream`.
+ * Synchronises `stream`: the call reads each window's largest test-point
+ * radius back to the host for the ball check, and returns after the result
+ * is written.
  */
 anova_status krr_predict_noalloc(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
                                  int64_t ldz, double* out, void* stream);
@@ -308,6 +313,11 @@ anova_status krr_model_predict(krr_model* model, const double* Z, int64_t M, int
 /* Free the model's grids and coefficients.  NULL is ignored. */
 void krr_model_destroy(krr_model* model);
 
+/* Copy the model's coefficients alpha (N doubles, the model's own copy) to
+ * `out` (device, N entries), stream-ordered on `stream`.  Errors: EINVAL (NULL
+ * model, or NULL out with N > 0), ECUDA. */
+anova_status krr_model_alpha(const krr_model* model, double* out, void* stream);
+
 /* ----------------------------------------------------------------------------
  * Batches: many problems and right-hand sides per launch.  The paper fits one
  * problem at a time; a batch runs the fits of Sec. 2 for several problems
@@ -363,14 +373,23 @@ anova_status krr_batch_cg_solve(anova_batch* batch, const double* lambda, const 
                                 double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
 
 /*
- * As krr_batch_cg_solve, to an FP64 residual: every plan must hold FP64 too
- * (ANOVA_MIXED).  Passes: r = y - (K64 + lambda I) alpha with each problem's
- * FP64 operator (anova_matvec), systems with ||r|| <= tol ||y|| drop out, the
- * batched FP32 CG solves the rest to 1e-4 relative (less when less is left),
- * alpha += correction.  relres is the FP64 residual; iters sums the inner
- * iterations; maxit bounds them per system; a system whose correction breaks
- * down keeps its last iterate.  Synchronous on `stream`;
- * allocates its work vectors stream-ordered.  Errors as krr_batch_cg_solve.
+ * As krr_batch_cg_solve, to an FP64 residual (CG on (K + lambda I) alpha = y,
+ * Sec. 2): every plan must hold FP64 too (ANOVA_MIXED).  Passes: the batched
+ * FP32 CG solves the correction equation (K32 + lambda I) dx = r of every open
+ * system to 1e-4 relative (less when less is left; at most maxit / 8
+ * iterations per pass), and alpha += t dx with the step t that minimises the
+ * FP64 residual ||r - t (K64 + lambda I) dx|| (each problem's FP64 operator,
+ * anova_matvec), so no pass raises a system's residual.  A system whose
+ * residual norm falls by less than 10 % in a pass (its FP32 operator no longer
+ * resolves the correction) continues with plain FP64 CG on its correction
+ * equation, if CG can reach tol within the iterations left: about
+ * 0.5 sqrt(kappa) ln(2 relres / tol) with kappa = (lambda_max(K) + lambda) /
+ * lambda, lambda_max(K) from 20 power iterations of the problem's FP64
+ * operator.  relres is the recomputed FP64 residual; iters sums the FP32 and
+ * FP64 iterations of a system; maxit bounds that sum.  Returns ENOCONV when a
+ * system ends above tol (its last iterate kept).  Synchronous on `stream`;
+ * allocates its work vectors stream-ordered.  Errors as krr_batch_cg_solve,
+ * and ENOMEM when the work vectors cannot be allocated.
  */
 anova_status krr_batch_cg_solve_refined(anova_batch* batch, const double* lambda, const double* y, double* alpha,
                                         double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
@@ -407,7 +426,7 @@ anova_status anova_server_create(int32_t n_workers, int64_t hbm_budget_bytes, an
  * p 8); lambda, tol, maxit as in krr_cg_solve.  The ticket also names the model.
  * Returns at once; the fit's own errors arrive through anova_server_wait.
  * Errors: EINVAL (NULL server or ticket, P outside 1..256, N < 0, maxit out of
- * range).
+ * range); EBUSY (refused by the fit-wait bound, anova_server_set_fit_wait_bound).
  */
 anova_status anova_server_submit_fit(anova_server* server, const double* points, int64_t N, int32_t d,
                                      const int32_t* windows, int32_t P, double ell, const int32_t* n,
@@ -436,6 +455,28 @@ anova_status anova_server_wait(anova_server* server, int64_t ticket, anova_statu
  * ticket, a fit still queued or running, or a model already released);
  * predictions still running on it finish first, the last one frees it. */
 anova_status anova_server_release(anova_server* server, int64_t model);
+
+/* Copy the coefficients alpha of a served fit (the ticket of a fit whose
+ * anova_server_wait has returned OK or ENOCONV) to `out` (device, N doubles),
+ * synchronously on `stream`.  Errors: EINVAL (unknown, failed or released
+ * fit; NULL out), ECUDA. */
+anova_status anova_server_fit_alpha(anova_server* server, int64_t fit, double* out, void* stream);
+
+/*
+ * Bound on a fit's expected queue wait, in milliseconds (0, the default: no
+ * bound).  When a fit is submitted, the server estimates how long it would
+ * wait for a worker: the nodes of the fits queued and running ahead of it,
+ * divided by the fit throughput measured on the fits completed so far (nodes
+ * per millisecond of a worker's service time, times the workers fits may
+ * occupy).  A fit whose estimate exceeds the bound is refused at once:
+ * anova_server_submit_fit returns ANOVA_EBUSY and queues nothing.  Until a
+ * first fit completes there is no estimate and every fit is admitted.
+ * Predictions are never refused.  The paper has no counterpart: this keeps
+ * the fits the server accepts at a bounded latency when they are offered
+ * faster than the GPU can fit them.  Errors: EINVAL (NULL server, negative or
+ * non-finite bound).
+ */
+anova_status anova_server_set_fit_wait_bound(anova_server* server, double max_wait_ms);
 
 /* Latency percentiles of the completed requests, their number, and the budgeted
  * bytes currently held (resident models and running requests).  Output
@@ -554,6 +595,21 @@ anova_status anova_debug_diag(const anova_plan* plan, int32_t l, double* D_host)
  */
 anova_status anova_set_profiling(anova_plan* plan, int32_t enable);
 int32_t anova_stage_times(anova_plan* plan, double* ms, int64_t* launches, int32_t cap);
+
+/* Allocation-failure injection, for testing the error paths without a device
+ * fault: the k-th device allocation the library makes from now on (k >= 1,
+ * counted over all threads) fails as if the device were out of memory, once;
+ * k = 0 switches the injection off.  The failing call returns ENOMEM or ECUDA
+ * and frees what it had allocated.  Errors: EINVAL (k < 0).  The paper has no
+ * counterpart: a test aid. */
+anova_status anova_debug_fail_alloc(int64_t k);
+
+/* Device memory in use, for leak checks: free device bytes (cudaMemGetInfo),
+ * and the bytes in use and reserved in the current device's default
+ * stream-ordered pool (memory the library frees stream-ordered goes back to
+ * the pool, which may keep it reserved).  Output pointers may be NULL.
+ * Errors: ECUDA.  The paper has no counterpart: a test aid. */
+anova_status anova_debug_memory(int64_t* free_bytes, int64_t* pool_used_bytes, int64_t* pool_reserved_bytes);
 
 /* Names of the FP32 3-D spread and gather kernels the plan launches (static
  * strings such as "k_spread3_tc<R>", R standing for the region size), so that

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANGE, ETIMEOUT = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANGE, ETIMEOUT, EBUSY = range(8)
 FP64, FP32, MIXED = 1, 2, 3
 
 _lib = None
@@ -73,6 +73,11 @@ _SIGNATURES = {
     "anova_debug_diag": (_i32, [_vp, _i32, _pf64]),
     "anova_set_profiling": (_i32, [_vp, _i32]),
     "anova_stage_times": (_i32, [_vp, _pf64, _pi64, _i32]),
+    "krr_model_alpha": (_i32, [_vp, _vp, _vp]),
+    "anova_debug_fail_alloc": (_i32, [_i64]),
+    "anova_debug_memory": (_i32, [_pi64, _pi64, _pi64]),
+    "anova_server_fit_alpha": (_i32, [_vp, _i64, _vp, _vp]),
+    "anova_server_set_fit_wait_bound": (_i32, [_vp, _f64]),
     "anova_plan_dense3_kernels": (_i32, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_char_p)]),
 }
 
@@ -330,6 +335,18 @@ def anova_stage_times(plan: Plan):
     return list(ms[:k]), list(la[:k])
 
 
+def anova_debug_fail_alloc(k: int):
+    """Make the k-th device allocation of the library from now on fail (0: off)."""
+    _check(lib().anova_debug_fail_alloc(int(k)), "anova_debug_fail_alloc")
+
+
+def anova_debug_memory() -> dict:
+    """Free device bytes and the default stream-ordered pool's used / reserved bytes."""
+    f, u, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().anova_debug_memory(ctypes.byref(f), ctypes.byref(u), ctypes.byref(r)), "anova_debug_memory")
+    return {"free": f.value, "pool_used": u.value, "pool_reserved": r.value}
+
+
 def anova_dense3_kernels(plan: Plan) -> dict:
     """Kernel names of the plan's FP32 3-D spread and gather ("<R>": the region size)."""
     sp, ga = ctypes.c_char_p(), ctypes.c_char_p()
@@ -476,6 +493,13 @@ class Model:
                "krr_model_predict")
         return out
 
+    def alpha(self, out, stream=None):
+        """Copy the model's coefficients into `out` (device, float64, N)."""
+        import torch
+        _require_cuda(out, "out", torch.float64)
+        _check(lib().krr_model_alpha(self.handle, _ptr(out), _stream(stream)), "krr_model_alpha")
+        return out
+
     def close(self):
         if self.handle:
             lib().krr_model_destroy(self.handle)
@@ -534,6 +558,19 @@ class Server:
 
     def release(self, model):
         _check(lib().anova_server_release(self.handle, int(model)), "anova_server_release")
+
+    def fit_alpha(self, fit, out, stream=None):
+        """Copy a served fit's coefficients into `out` (device, float64, N)."""
+        import torch
+        _require_cuda(out, "out", torch.float64)
+        _check(lib().anova_server_fit_alpha(self.handle, int(fit), _ptr(out), _stream(stream)),
+               "anova_server_fit_alpha")
+        return out
+
+    def set_fit_wait_bound(self, max_wait_ms):
+        """Refuse fits (EBUSY at submission) whose expected queue wait exceeds max_wait_ms (0: never)."""
+        _check(lib().anova_server_set_fit_wait_bound(self.handle, float(max_wait_ms)),
+               "anova_server_set_fit_wait_bound")
 
     def stats(self):
         p50, p99 = ctypes.c_double(), ctypes.c_double()

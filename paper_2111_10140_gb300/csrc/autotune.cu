@@ -49,8 +49,9 @@ extern "C" anova_status anova_autotune_bins(const double* points, int64_t N, int
         if (dA >= 1) present[dA - 1] = true;
     }
     void *alpha = nullptr, *out = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&alpha, N * esz));
-    ANOVA_CUDA_TRY(cudaMalloc(&out, N * esz));
+    Scratch scratch(st, false);
+    ANOVA_CUDA_TRY(scratch.alloc(&alpha, N * esz));
+    ANOVA_CUDA_TRY(scratch.alloc(&out, N * esz));
     if (f32) k_tune_fill<float><<<grid_for(N, kThreads, 1024), kThreads, 0, st>>>((float*)alpha, N);
     else k_tune_fill<double><<<grid_for(N, kThreads, 1024), kThreads, 0, st>>>((double*)alpha, N);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -102,8 +103,6 @@ extern "C" anova_status anova_autotune_bins(const double* points, int64_t N, int
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(alpha);
-    cudaFree(out);
     if (s != ANOVA_OK) return s;
     for (int k = 0; k < 3; k++) bin_side[k] = best[k];
     if (ms) *ms = best_ms;

@@ -138,8 +138,9 @@ static anova_status model_predict(krr_model* md, const double* Z, int64_t M, int
     const int P = plan->P;
     T* tmp = nullptr;
     double* zw = nullptr;
-    ANOVA_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)M * P * sizeof(T), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&zw, (size_t)M * 3 * sizeof(double), st));
+    Scratch scratch(st);
+    ANOVA_CUDA_TRY(scratch.alloc(&tmp, (size_t)M * P * sizeof(T)));
+    ANOVA_CUDA_TRY(scratch.alloc(&zw, (size_t)M * 3 * sizeof(double)));
     anova_status s = ANOVA_OK;
     for (int l = 0; l < P && s == ANOVA_OK; l++) {
         s = extract_window(plan, Z, M, ldz, plan->win[l], zw, st);
@@ -155,8 +156,6 @@ static anova_status model_predict(krr_model* md, const double* Z, int64_t M, int
             s = ANOVA_ECUDA;
         }
     }
-    cudaFreeAsync(tmp, st);
-    cudaFreeAsync(zw, st);
     return s;
 }
 
@@ -194,8 +193,8 @@ anova_status krr_model_create(anova_plan* plan, const double* alpha, void* strea
         }
     }
     anova_status s = ANOVA_OK;
-    if (cudaMalloc(&md->alpha, std::max<int64_t>(plan->N, 1) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&md->grids, std::max<size_t>(md->elems, 1) * esz) != cudaSuccess) {
+    if (anova::dev_malloc((void**)&md->alpha, std::max<int64_t>(plan->N, 1) * sizeof(double)) != cudaSuccess ||
+        anova::dev_malloc((void**)&md->grids, std::max<size_t>(md->elems, 1) * esz) != cudaSuccess) {
         set_error("krr_model_create: out of device memory");
         s = ANOVA_ENOMEM;
     }
@@ -240,3 +239,15 @@ void krr_model_destroy(krr_model* md) {
 }
 
 }  // extern "C"
+
+extern "C" anova_status krr_model_alpha(const krr_model* model, double* out, void* stream) {
+    if (!model || (model->plan && model->plan->N > 0 && !out)) {
+        anova::set_error("krr_model_alpha: NULL model or output");
+        return ANOVA_EINVAL;
+    }
+    const int64_t N = model->plan ? model->plan->N : 0;
+    if (N == 0) return ANOVA_OK;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(out, model->alpha, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   (cudaStream_t)stream));
+    return ANOVA_OK;
+}

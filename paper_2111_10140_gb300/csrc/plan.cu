@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -286,53 +287,87 @@ __global__ void k_sub_list(const int32_t* __restrict__ bin_start, const int32_t*
     }
 }
 
-// stream-ordered release (no device-wide synchronisation)
+// Point sets are allocated from the stream-ordered pool (build_pointset), so
+// they go back to it with cudaFreeAsync (cudaFree would not return them).
+// Stream-ordered release, no device-wide synchronisation:
 void free_pointset_async(PointSet& ps, cudaStream_t st) {
-    cudaFreeAsync(ps.perm, st);
-    cudaFreeAsync(ps.cell, st);
-    cudaFreeAsync(ps.frac64, st);
-    cudaFreeAsync(ps.frac32, st);
-    cudaFreeAsync(ps.bin_start, st);
-    cudaFreeAsync(ps.sub, st);
+    void* p[6] = {ps.perm, ps.cell, ps.frac64, ps.frac32, ps.bin_start, ps.sub};
+    for (void* q : p)
+        if (q) cudaFreeAsync(q, st);
     ps = PointSet();
 }
 
+// release that has completed on return (owners that free synchronously)
 void free_pointset(PointSet& ps) {
-    cudaFree(ps.perm);
-    cudaFree(ps.cell);
-    cudaFree(ps.frac64);
-    cudaFree(ps.frac32);
-    cudaFree(ps.bin_start);
-    cudaFree(ps.sub);
-    ps = PointSet();
+    const bool any = ps.perm || ps.cell || ps.frac64 || ps.frac32 || ps.bin_start || ps.sub;
+    free_pointset_async(ps, nullptr);
+    if (any) cudaStreamSynchronize(nullptr);
+}
+
+// ------------------------------------------------------ device allocation
+static std::atomic<int64_t> g_fail_countdown{0};   // > 0: allocations left before the one that fails
+
+static bool injected_failure() {
+    int64_t v = g_fail_countdown.load();
+    while (v > 0)
+        if (g_fail_countdown.compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+    if (injected_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+cudaError_t dev_malloc_async(void** ptr, size_t bytes, cudaStream_t st) {
+    if (injected_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(ptr, bytes, st);
 }
 
 // Bin and sort the nodes of one window.  coords: device N x dA (user units).
+static anova_status build_pointset_impl(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
+                                        const double* centre, double scale, PointSet& ps, cudaStream_t st);
+
+// On failure the point set is left empty (nothing of it stays allocated).
 anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
                             int64_t /*ldc*/, const double* centre, double scale, PointSet& ps,
                             cudaStream_t st) {
     free_pointset(ps);
+    const anova_status s = build_pointset_impl(plan, w, coords, N, centre, scale, ps, st);
+    if (s != ANOVA_OK) free_pointset_async(ps, st);
+    return s;
+}
+
+static anova_status build_pointset_impl(anova_plan* plan, WindowPlan& w, const double* coords, int64_t N,
+                                        const double* centre, double scale, PointSet& ps, cudaStream_t st) {
     ps.N = N;
     const int dA = w.dA;
     const bool want64 = (plan->precision & ANOVA_FP64) != 0;
     const bool want32 = (plan->precision & ANOVA_FP32) != 0;
     if (N == 0) {
-        ANOVA_CUDA_TRY(cudaMallocAsync(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t), st));
+        ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.bin_start, (w.nbins + 1) * sizeof(int32_t), st));
         ANOVA_CUDA_TRY(cudaMemsetAsync(ps.bin_start, 0, (w.nbins + 1) * sizeof(int32_t), st));
         return ANOVA_OK;
     }
-    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.perm, N * sizeof(int32_t), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.cell, N * dA * sizeof(int32_t), st));
-    if (want64) ANOVA_CUDA_TRY(cudaMallocAsync(&ps.frac64, N * dA * sizeof(double), st));
-    if (want32) ANOVA_CUDA_TRY(cudaMallocAsync(&ps.frac32, N * dA * sizeof(float), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.bin_start, (w.nbins + 1) * sizeof(int32_t), st));
+    ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.perm, N * sizeof(int32_t), st));
+    ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.cell, N * dA * sizeof(int32_t), st));
+    if (want64) ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.frac64, N * dA * sizeof(double), st));
+    if (want32) ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.frac32, N * dA * sizeof(float), st));
+    ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.bin_start, (w.nbins + 1) * sizeof(int32_t), st));
 
     const int nchunk = (int)((N + kBinChunk - 1) / kBinChunk);
     const int64_t L = (int64_t)w.nbins * nchunk;
     int32_t *hist = nullptr, *nch = nullptr, *tot = nullptr;
-    ANOVA_CUDA_TRY(cudaMallocAsync(&hist, L * sizeof(int32_t), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&nch, (w.nbins + 1) * sizeof(int32_t), st));
-    ANOVA_CUDA_TRY(cudaMallocAsync(&tot, 2 * sizeof(int32_t), st));
+    Scratch scratch(st);
+    ANOVA_CUDA_TRY(scratch.alloc(&hist, L * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(scratch.alloc(&nch, (w.nbins + 1) * sizeof(int32_t)));
+    ANOVA_CUDA_TRY(scratch.alloc(&tot, 2 * sizeof(int32_t)));
     FrameArgs fr;
     for (int t = 0; t < 3; t++) fr.c[t] = centre[t];
     fr.s = scale;
@@ -359,13 +394,10 @@ anova_status build_pointset(anova_plan* plan, WindowPlan& w, const double* coord
         set_error("binning lost nodes");
         return ANOVA_ECUDA;
     }
-    ANOVA_CUDA_TRY(cudaMallocAsync(&ps.sub, std::max(ps.nsub, 1) * sizeof(int4), st));
+    ANOVA_CUDA_TRY(anova::dev_malloc_async((void**)&ps.sub, std::max(ps.nsub, 1) * sizeof(int4), st));
     k_sub_list<<<grid_for(w.nbins, kThreads, 1024), kThreads, 0, st>>>(ps.bin_start, nch, w.nbins, ps.sub);
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(nch, st);
-    cudaFreeAsync(tot, st);
     return ANOVA_OK;
 }
 
@@ -687,7 +719,8 @@ static anova_status window_box(anova_plan* plan, WindowPlan& w, cudaStream_t st)
     }
     if (w.X.N == 0) return ANOVA_OK;
     int* mm = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&mm, 6 * sizeof(int)));
+    Scratch scratch(st, false);
+    ANOVA_CUDA_TRY(scratch.alloc(&mm, 6 * sizeof(int)));
     int init[6] = {INT32_MAX, -1, INT32_MAX, -1, INT32_MAX, -1};
     ANOVA_CUDA_TRY(cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, st));
     k_cell_range<<<grid_for(w.X.N, kThreads, 2 * plan->sm_count), kThreads, 0, st>>>(w.X.cell, w.X.N, w.dA, mm);
@@ -695,7 +728,6 @@ static anova_status window_box(anova_plan* plan, WindowPlan& w, cudaStream_t st)
     int h[6];
     ANOVA_CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(mm);
     for (int t = 0; t < w.dA; t++) {
         const int blo = h[2 * t] / w.T, bhi = h[2 * t + 1] / w.T;
         const int ext = (bhi - blo + 1) * w.T + 2 * plan->m;
@@ -720,8 +752,8 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
     for (int t = 0; t < w.dA; t++) tk *= w.n;
     const bool want64 = (plan->precision & ANOVA_FP64) != 0;
     const bool want32 = (plan->precision & ANOVA_FP32) != 0;
-    if (!w.D64) ANOVA_CUDA_TRY(cudaMalloc(&w.D64, tk * sizeof(double)));
-    if (want32 && !w.D32) ANOVA_CUDA_TRY(cudaMalloc(&w.D32, tk * sizeof(float)));
+    if (!w.D64) ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.D64, tk * sizeof(double)));
+    if (want32 && !w.D32) ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.D32, tk * sizeof(float)));
     double* fa = scratch;
     double* fb = scratch + tk;
     const int g = grid_for(tk, kThreads, 4096);
@@ -741,7 +773,7 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
     if (w.dense && want32 && plan->N > 0) {
         cudaFree(w.wtab);
         w.wtab = nullptr;
-        ANOVA_CUDA_TRY(cudaMalloc(&w.wtab, plan->N * 16 * w.dA * sizeof(float)));
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.wtab, plan->N * 16 * w.dA * sizeof(float)));
         FrameArgs fr;
         for (int t = 0; t < 3; t++) fr.c[t] = w.centre[t];
         fr.s = w.scale;
@@ -779,10 +811,10 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
     plan->dense_nsub = total;
     const int nd = (int)plan->dense_windows.size();
     if (nd == 0) return ANOVA_OK;
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_sub, total * sizeof(int4)));
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_desc, 2 * nd * sizeof(DenseWin)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->dense_sub, total * sizeof(int4)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->dense_desc, 2 * nd * sizeof(DenseWin)));
     if (plan->precision & ANOVA_FP32)
-        ANOVA_CUDA_TRY(cudaMalloc(&plan->dense_asort, (size_t)nd * plan->N * sizeof(float)));
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->dense_asort, (size_t)nd * plan->N * sizeof(float)));
     std::vector<DenseWin> desc(2 * nd);
     int at = 0;
     for (int k = 0; k < nd; k++) {
@@ -851,7 +883,7 @@ static anova_status build_fft3_batch(anova_plan* plan, cudaStream_t st) {
             d.nos = w.nos;
         }
     }
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->fft3_desc, 2 * nw * sizeof(Fft3Win)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->fft3_desc, 2 * nw * sizeof(Fft3Win)));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->fft3_desc, desc.data(), 2 * nw * sizeof(Fft3Win),
                                    cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -892,7 +924,7 @@ static anova_status build_fft12_batch(anova_plan* plan, cudaStream_t st) {
             }
         }
     }
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->fft12_desc, 2 * nw * sizeof(Fft12Win)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->fft12_desc, 2 * nw * sizeof(Fft12Win)));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->fft12_desc, desc.data(), 2 * nw * sizeof(Fft12Win),
                                    cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -959,7 +991,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     plan->b = M_PI * (2.0 - 1.0 / sigma);
     plan->psi_norm = (double)m / std::sinh(plan->b * m);
     plan->win.resize(P);
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->psi_poly, 2 * m * kPsiStride * sizeof(float)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly, 2 * m * kPsiStride * sizeof(float)));
     k_psi_poly_fit<<<1, 64, 0, st>>>(m, plan->b, plan->psi_norm, plan->psi_poly);
     ANOVA_CHECK_LAUNCH();
     plan->psi_host.assign(2 * m * kPsiStride, 0.f);
@@ -990,25 +1022,25 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
         plan->grid_elems += (ge + 63) / 64 * 64;
         plan->work_elems += (we + 63) / 64 * 64;
         max_tk = std::max(max_tk, tk);
-        ANOVA_CUDA_TRY(cudaMalloc(&w.tw64, w.nos * sizeof(double2)));
-        ANOVA_CUDA_TRY(cudaMalloc(&w.tw32, w.nos * sizeof(float2)));
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.tw64, w.nos * sizeof(double2)));
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.tw32, w.nos * sizeof(float2)));
         k_twiddles<<<grid_for(w.nos, kThreads, 64), kThreads, 0, st>>>(w.nos, w.tw64, w.tw32);
         ANOVA_CHECK_LAUNCH();
         if (N > 0) {
-            ANOVA_CUDA_TRY(cudaMalloc(&w.xw, N * w.dA * sizeof(double)));
+            ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.xw, N * w.dA * sizeof(double)));
             k_extract<<<grid_for(N, kThreads, 4 * plan->sm_count), kThreads, 0, st>>>(
                 points, N, ld, w.dA, w.feat[0], w.feat[1], w.feat[2], w.xw);
             ANOVA_CHECK_LAUNCH();
         }
     }
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->grid, plan->grid_elems * sizeof(double)));
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->work1, plan->work_elems * sizeof(double2)));
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->work2, plan->work_elems * sizeof(double2)));
-    ANOVA_CUDA_TRY(cudaMalloc(&plan->tmp, std::max<int64_t>(N, 1) * P * sizeof(double)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->grid, plan->grid_elems * sizeof(double)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->work1, plan->work_elems * sizeof(double2)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->work2, plan->work_elems * sizeof(double2)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->tmp, std::max<int64_t>(N, 1) * P * sizeof(double)));
     {
         std::vector<double> eta(P);
         for (int l = 0; l < P; l++) eta[l] = plan->win[l].eta;
-        ANOVA_CUDA_TRY(cudaMalloc(&plan->eta_dev, P * sizeof(double)));
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->eta_dev, P * sizeof(double)));
         ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->eta_dev, eta.data(), P * sizeof(double),
                                        cudaMemcpyHostToDevice, st));
         ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1017,7 +1049,8 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     const int nblk = grid_for(std::max<int64_t>(N, 1), kThreads, 2 * plan->sm_count);
     size_t scratch_elems = std::max<size_t>(6 * nblk + 8, 2 * max_tk);
     double* scratch = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&scratch, scratch_elems * sizeof(double)));
+    Scratch guard(st, false);
+    ANOVA_CUDA_TRY(guard.alloc(&scratch, scratch_elems * sizeof(double)));
     anova_status s = ANOVA_OK;
     for (int l = 0; l < P && s == ANOVA_OK; l++) {
         WindowPlan& w = plan->win[l];
@@ -1035,7 +1068,6 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
             s = ANOVA_ECUDA;
         }
     }
-    cudaFree(scratch);
     return s;
 }
 
@@ -1065,12 +1097,12 @@ anova_status window_reframe(anova_plan* plan, int l, const double* zw, int64_t M
     for (int t = 0; t < src.dA; t++) tk *= src.n;
     const int nblk = grid_for(plan->N + M, kThreads, 2 * plan->sm_count);
     double* scratch = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&scratch, std::max<size_t>(6 * nblk + 8, 2 * tk) * sizeof(double)));
+    Scratch guard(st, false);
+    ANOVA_CUDA_TRY(guard.alloc(&scratch, std::max<size_t>(6 * nblk + 8, 2 * tk) * sizeof(double)));
     double frame[5];
     anova_status s = compute_frame(plan, src.xw, plan->N, zw, M, src.dA, scratch, frame, st);
     if (s == ANOVA_OK) s = window_setup(plan, dst, frame, scratch, st);
     cudaStreamSynchronize(st);
-    cudaFree(scratch);
     return s;
 }
 
@@ -1098,11 +1130,11 @@ anova_status window_widened(anova_plan* plan, int l, double rho, WindowPlan& dst
     int64_t tk = 1;
     for (int t = 0; t < src.dA; t++) tk *= src.n;
     double* scratch = nullptr;
-    ANOVA_CUDA_TRY(cudaMalloc(&scratch, std::max<size_t>(16, 2 * tk) * sizeof(double)));
+    Scratch guard(st, false);
+    ANOVA_CUDA_TRY(guard.alloc(&scratch, std::max<size_t>(16, 2 * tk) * sizeof(double)));
     const double frame[5] = {src.centre[0], src.centre[1], src.centre[2], src.scale / rho, 0.0};
     anova_status s = window_setup(plan, dst, frame, scratch, st);
     cudaStreamSynchronize(st);
-    cudaFree(scratch);
     return s;
 }
 
@@ -1121,7 +1153,8 @@ anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, c
     if (M == 0) return ANOVA_OK;
     const int nblk = grid_for(M, kThreads, 2 * plan->sm_count);
     double* scratch = nullptr;
-    ANOVA_CUDA_TRY(cudaMallocAsync(&scratch, (nblk + 8) * sizeof(double), st));
+    Scratch guard(st);
+    ANOVA_CUDA_TRY(guard.alloc(&scratch, (nblk + 8) * sizeof(double)));
     double* frame = scratch + nblk;
     double hf[5] = {centre[0], centre[1], centre[2], 1.0, 0.0};
     ANOVA_CUDA_TRY(cudaMemcpyAsync(frame, hf, 5 * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1130,7 +1163,6 @@ anova_status max_radius(anova_plan* plan, const double* zw, int64_t M, int dA, c
     ANOVA_CHECK_LAUNCH();
     ANOVA_CUDA_TRY(cudaMemcpyAsync(hf, frame, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFreeAsync(scratch, st);
     *rmax_host = hf[4];
     return ANOVA_OK;
 }
@@ -1305,6 +1337,32 @@ void anova_plan_destroy(anova_plan* plan) {
     delete plan;
 }
 
+anova_status anova_debug_fail_alloc(int64_t k) {
+    if (k < 0) {
+        anova::set_error("anova_debug_fail_alloc: k must be >= 0");
+        return ANOVA_EINVAL;
+    }
+    g_fail_countdown.store(k);
+    return ANOVA_OK;
+}
+
+anova_status anova_debug_memory(int64_t* free_bytes, int64_t* pool_used_bytes, int64_t* pool_reserved_bytes) {
+    size_t fr = 0, total = 0;
+    ANOVA_CUDA_TRY(cudaMemGetInfo(&fr, &total));
+    int dev = 0;
+    ANOVA_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    ANOVA_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t used = 0;
+    ANOVA_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    uint64_t reserved = 0;
+    ANOVA_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    if (free_bytes) *free_bytes = (int64_t)fr;
+    if (pool_used_bytes) *pool_used_bytes = (int64_t)used;
+    if (pool_reserved_bytes) *pool_reserved_bytes = (int64_t)reserved;
+    return ANOVA_OK;
+}
+
 const char* anova_status_string(anova_status s) {
     switch (s) {
         case ANOVA_OK: return "ANOVA_OK: success";
@@ -1314,6 +1372,7 @@ const char* anova_status_string(anova_status s) {
         case ANOVA_ENOCONV: return "ANOVA_ENOCONV: CG reached maxit";
         case ANOVA_ERANGE: return "ANOVA_ERANGE: input out of range";
         case ANOVA_ETIMEOUT: return "ANOVA_ETIMEOUT: device wait expired";
+        case ANOVA_EBUSY: return "ANOVA_EBUSY: refused, the expected queue wait exceeds the bound";
     }
     return "unknown anova_status";
 }
