@@ -536,9 +536,11 @@ def run_serve(args):
     resident model (N log-uniform in [1e4, 1e6]) and 30 % fits of new problems
     (N log-uniform in [1e3, 1e6]), d 9..28, 3..9 windows, served by the
     library's request server under a 150 GB budget (FP32 bulk, FP64
-    refinement to residual 1e-6).  Fitted stream models are released as soon
-    as their fit is done.  Prints one line with latency percentiles per kind
-    and the served throughput."""
+    refinement to residual 1e-6).  Fits whose expected queue wait exceeds
+    `--serve-fit-wait-ms` are refused at submission (counted).  Fitted stream
+    models are released as soon as their fit is done.  Prints one line with
+    latency percentiles per kind (fits also per half of the run) and the
+    served throughput."""
     import threading
     import time
 
@@ -569,6 +571,10 @@ def run_serve(args):
               for w, (X, y, _) in zip(res, res_dev)]
     init = [sv.wait(t) for t in models]
     t_init = time.perf_counter() - t0
+    # fits whose expected queue wait exceeds the bound are refused at submission
+    # (the rate estimate comes from the resident models' fits above)
+    sv.set_fit_wait_bound(args.serve_fit_wait_ms)
+    refused = 0
     # the stream
     n_req = int(args.serve_rate * args.serve_seconds)
     arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_req))
@@ -611,14 +617,20 @@ def run_serve(args):
         else:
             k = int(rng.integers(len(fit_pool)))
             w, (X, y) = fit_pool[k], fit_dev[k]
-            fit_tickets.append((sv.submit_fit(X, w.windows, w.ell, y, w.lam, n=w.n, m=w.m, eps_B=w.epsB,
-                                              tol=w.tol), w.N))
+            try:
+                fit_tickets.append((sv.submit_fit(X, w.windows, w.ell, y, w.lam, n=w.n, m=w.m, eps_B=w.epsB,
+                                                  tol=w.tol), w.N))
+            except B.AnovaError as e:
+                if e.status != B.EBUSY:
+                    raise
+                refused += 1
     t_sub = time.perf_counter() - t0
     plat = np.array([sv.wait(t)["latency_ms"] for t, _ in pred])
     stop.set()
     th.join()
     t_all = time.perf_counter() - t0
     flat = np.array([r["latency_ms"] for _, r in done_fits])
+    half = len(flat) // 2
     fitted = sum(N for N, r in done_fits)
     bad = sum(r["status"] not in (B.OK, B.ENOCONV) for _, r in done_fits)
     sv.close()
@@ -633,6 +645,8 @@ def run_serve(args):
         "requests": n_req, "predicts": len(pred), "fits": len(done_fits), "failed_fits": int(bad),
         "predict_p50_ms": pct(plat, 50), "predict_p99_ms": pct(plat, 99),
         "fit_p50_ms": pct(flat, 50), "fit_p99_ms": pct(flat, 99),
+        "fit_wait_bound_ms": args.serve_fit_wait_ms, "fits_refused": refused,
+        "fit_p50_ms_first_half": pct(flat[:half], 50), "fit_p50_ms_second_half": pct(flat[half:], 50),
         "submit_s": round(t_sub, 3), "drain_s": round(t_all, 3),
         "achieved_rps": n_req / t_all, "predicted_rows_per_s": rows / t_all, "fitted_points_per_s": fitted / t_all,
     }), flush=True)
@@ -687,6 +701,26 @@ def run_batch(args):
     (st32, its32, rr32), t32 = timed(lambda: batch.cg_solve(lams, y, alpha, tol, maxit))
     (st64, its64, rr64), t64 = timed(lambda: batch.cg_solve(lams, y, alpha, tol, maxit, refined=True))
     ns = len(probs) * args.batch_rhs
+    # systems the refined solve leaves above tol, each with an upper bound on its
+    # condition number: kappa(K + lambda I) <= (lambda_max(K) + lambda) / lambda,
+    # lambda_max(K) by 30 power iterations of the problem's FP64 operator
+    exceptions, lmax = [], {}
+    for p, r in zip(*np.nonzero(rr64 > tol)):
+        p, r = int(p), int(r)
+        if p not in lmax:
+            v = torch.from_numpy(np.random.default_rng(9).standard_normal(probs[p].N)).to(dev)
+            kv = torch.empty_like(v)
+            est = 0.0
+            for _ in range(30):
+                v /= torch.linalg.norm(v)
+                B.anova_matvec(plans[p], v, kv)
+                est = float(torch.linalg.norm(kv))
+                v, kv = kv, v
+            lmax[p] = est
+        w = probs[p]
+        exceptions.append({"problem": p, "rhs": r, "N": w.N, "windows": [len(x) for x in w.windows],
+                           "ell": round(w.ell, 4), "lambda": w.lam, "relres_fp64": float(rr64[p, r]),
+                           "iters": int(its64[p, r]), "kappa_upper": (lmax[p] + w.lam) / w.lam})
     work = np.array([w.N * len(w.windows) for w in probs], dtype=float)
     K = min(args.batch_sample, len(probs))
     share = work[:K].sum() / work.sum()
@@ -724,7 +758,11 @@ def run_batch(args):
         "fp64_refined": {"status": int(st64), "solve_s": round(t64, 4), "systems_per_s": ns / t64,
                          "iters_median": float(np.median(its64)), "relres_fp64_max": float(rr64.max()),
                          "converged": int((rr64 <= tol).sum()),
-                         "speedup_vs_single_fp64": single["fp64"]["est_all_systems_s"] / t64},
+                         "speedup_vs_single_fp64": single["fp64"]["est_all_systems_s"] / t64,
+                         # both at an FP64 residual <= tol: systems brought to tol per second
+                         "converged_per_s": float((rr64 <= tol).sum()) / t64,
+                         "single_fp64_converged_per_s": single["fp64"]["converged"] / single["fp64"]["sample_s"],
+                         "exceptions": exceptions},
         "single_sample_problems": K, "single_sample_work_share": round(float(share), 4),
         "single": single,
     }), flush=True)
@@ -917,6 +955,8 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-models", type=int, default=4)
     ap.add_argument("--serve-fit-pool", type=int, default=6)
+    ap.add_argument("--serve-fit-wait-ms", type=float, default=5000.0,
+                    help="refuse fits whose expected queue wait exceeds this (0: admit every fit)")
     ap.add_argument("--precision-form", action="store_true",
                     help="precision form (N = 1e6, nine windows): products, mixed KRR to 1e-8, error vs direct")
     ap.add_argument("--autotune", action="store_true", help="bin sides chosen by the autotuner (mid, precision form)")
