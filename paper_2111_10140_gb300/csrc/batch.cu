@@ -564,7 +564,8 @@ anova_status anova_batch_create(anova_plan* const* plans, int32_t nprob, int32_t
         }
         for (int l = 0; l < pl->P; l++) {
             const WindowPlan& w = pl->win[l];
-            if (!w.dense || !w.wtab || !(w.dA == 3 ? fft3_box_supported(w) : w.fft12)) {
+            const bool weights = w.wtab || (w.dA < 3 && pl->pw12 && tc5_supported(w.R, pl->m));
+            if (!w.dense || !weights || !(w.dA == 3 ? fft3_box_supported(w) : w.fft12)) {
                 set_error("anova_batch_create: problem " + std::to_string(p) + " window " + std::to_string(l) +
                           " is not on the dense kernels and box FFTs");
                 return ANOVA_EINVAL;

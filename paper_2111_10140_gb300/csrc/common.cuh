@@ -176,7 +176,8 @@ struct anova_plan {
     int d = 0, P = 0, m = 0, p = 0, precision = 0;
     double sigma = 2.0, epsB = 1.0 / 16, ell = 0.0, b = 0.0;
     double psi_norm = 1.0;              // m / sinh(b m): psi(t) = psi_norm * sinh(b s)/s
-    float* psi_poly = nullptr;          // 2m x kPsiStride: psi(q - m + f) ~ sum_k c_k (f - 1/2)^k
+    float* psi_poly = nullptr;          // 2m x kPsiStride: psi(q - m + f) ~ sum_k c_k (f - 1/2)^k; then psi(m)
+    double* psi_poly64 = nullptr;       // the same coefficients in FP64 (the FP32 weight tables)
     std::vector<anova::WindowPlan> win;
     // work buffers: every window has its own grid and FFT work arrays (offsets in WindowPlan)
     size_t grid_elems = 0, work_elems = 0;  // totals over the windows
@@ -244,11 +245,12 @@ __device__ __forceinline__ T kb_psi(T t, T m, T b, T norm) {
 }
 
 // FP32 window weight from the per-interval polynomials: t = j + f with integer
-// j and f in [0, 1); zero outside [-m, m) (the single point t = m, where psi is
-// about 1e-7 of its peak or less, is dropped in FP32).
+// j and f in [0, 1); zero outside [-m, m], psi(m) (kept after the 2m rows of
+// coefficients) at the closed end t = m.
 __device__ __forceinline__ float psi_poly_eval(const float* __restrict__ P, int j, float f, int m) {
     const int q = j + m;
-    if (q < 0 || q >= 2 * m) return 0.f;
+    if (q == 2 * m) return f == 0.f ? P[2 * m * kPsiStride] : 0.f;
+    if (q < 0 || q > 2 * m) return 0.f;
     const float* c = P + q * kPsiStride;
     const float u = f - 0.5f;
     float acc = c[kPsiDeg];

@@ -66,7 +66,7 @@ k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
     __shared__ __align__(16) T reg[R * R * kPitch];
     __shared__ float sP[2 * 8 * kPsiStride];
     if (kPoly)
-        for (int i = threadIdx.x; i < 2 * m * kPsiStride; i += blockDim.x) sP[i] = poly[i];
+        for (int i = threadIdx.x; i < 2 * m * kPsiStride + 1; i += blockDim.x) sP[i] = poly[i];
     const int4 sp = sub[blockIdx.x];
     const DenseWin W = descs ? descs[sp.w] : one;
     if (W.live && !*W.live) return;   // a batch system that has stopped
@@ -166,7 +166,7 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
         for (int k = 0; k < 8; k++) acc[i][k] = T(0);
 
     if (kPoly)
-        for (int i = tid; i < 2 * m * kPsiStride; i += NT) sP[i] = poly[i];
+        for (int i = tid; i < 2 * m * kPsiStride + 1; i += NT) sP[i] = poly[i];
     for (int first = 0; first < sp.z; first += kSpreadChunk) {
         const int cnt = min(kSpreadChunk, sp.z - first);
         __syncthreads();

@@ -222,6 +222,100 @@ __global__ void k_scan_exclusive(int32_t* __restrict__ v, int64_t L, int32_t* __
     if (threadIdx.x == nt - 1 && total) *total = sh[nt - 1];
 }
 
+// Multi-block exclusive scan for long histograms (bins x chunks of a large
+// point set): tile sums, a single-block scan of the tile sums, then every
+// tile scanned in shared memory from its offset.  Same result as
+// k_scan_exclusive (integer sums), in three launches that fill the GPU.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile_sums(const int32_t* __restrict__ v, int64_t L,
+                                                                  int32_t* __restrict__ tsum) {
+    __shared__ int32_t wsum[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int32_t s = 0;
+    for (int k = 0; k < kScanPer; k++) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < L) s += v[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = wsum[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) tsum[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int32_t* __restrict__ v, int64_t L,
+                                                              const int32_t* __restrict__ toff) {
+    __shared__ int32_t tile[kScanTile];
+    __shared__ int32_t wsum[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int k = 0; k < kScanPer; k++) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        tile[k * kScanThreads + threadIdx.x] = i < L ? v[i] : 0;
+    }
+    __syncthreads();
+    // thread t owns the kScanPer consecutive values from t * kScanPer
+    int32_t own[kScanPer];
+    int32_t s = 0;
+    for (int k = 0; k < kScanPer; k++) {
+        own[k] = tile[threadIdx.x * kScanPer + k];
+        s += own[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t inc = s;                                   // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t x = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        wsum[lane] = x;                                // inclusive over warps
+    }
+    __syncthreads();
+    int32_t run = toff[blockIdx.x] + (warp > 0 ? wsum[warp - 1] : 0) + inc - s;
+    for (int k = 0; k < kScanPer; k++) {
+        tile[threadIdx.x * kScanPer + k] = run;
+        run += own[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanPer; k++) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < L) v[i] = tile[k * kScanThreads + threadIdx.x];
+    }
+}
+
+// exclusive scan of v[0, L) in place, total -> *total (device)
+static anova_status scan_exclusive(int32_t* v, int64_t L, int32_t* total, Scratch& scratch, cudaStream_t st) {
+    if (L <= 4 * kScanTile) {
+        k_scan_exclusive<<<1, 1024, 0, st>>>(v, L, total);
+        ANOVA_CHECK_LAUNCH();
+        return ANOVA_OK;
+    }
+    const int64_t nt = (L + kScanTile - 1) / kScanTile;
+    if (nt > INT32_MAX) {
+        set_error("binning: histogram too long");
+        return ANOVA_EINVAL;
+    }
+    int32_t* tsum = nullptr;
+    ANOVA_CUDA_TRY(scratch.alloc(&tsum, nt * sizeof(int32_t)));
+    k_scan_tile_sums<<<(unsigned)nt, kScanThreads, 0, st>>>(v, L, tsum);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(tsum, nt, total);
+    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(v, L, tsum);
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
 // stable scatter: one warp per chunk, ranks of equal bins via match_any
 template <typename T>
 __global__ void k_bin_scatter(const double* __restrict__ xw, int64_t N, int dA, FrameArgs fr,
@@ -379,13 +473,14 @@ static anova_status build_pointset_impl(anova_plan* plan, WindowPlan& w, const d
     }();
     (void)attrs;
     k_bin_hist<<<nchunk, kThreads, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk, hist);
-    k_scan_exclusive<<<1, 1024, 0, st>>>(hist, L, tot);
+    ANOVA_CHECK_LAUNCH();
+    ANOVA_TRY(scan_exclusive(hist, L, tot, scratch, st));
     k_bin_scatter<double><<<nchunk, 32, shb, st>>>(coords, N, dA, fr, w.nos, w.T, w.nb, w.nbins, nchunk,
                                                   hist, ps.perm, ps.cell, ps.frac64, ps.frac32);
     k_bin_starts<<<grid_for(w.nbins + 1, kThreads, 1024), kThreads, 0, st>>>(hist, w.nbins, nchunk, N,
                                                                               ps.bin_start, nch);
-    k_scan_exclusive<<<1, 1024, 0, st>>>(nch, w.nbins, tot + 1);
     ANOVA_CHECK_LAUNCH();
+    ANOVA_TRY(scan_exclusive(nch, w.nbins, tot + 1, scratch, st));
     int32_t totals[2] = {0, 0};
     ANOVA_CUDA_TRY(cudaMemcpyAsync(totals, tot, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -519,8 +614,11 @@ __global__ void k_deconvolve(const double* __restrict__ f, int dA, int n, int no
 
 // Per-interval polynomials of the normalised window for the FP32 kernels:
 // on t in [q - m, q - m + 1), psi(t) is interpolated at kPsiDeg+1 Chebyshev
-// points in f = t - (q - m) and rewritten in powers of u = f - 1/2 (FP64).
-__global__ void k_psi_poly_fit(int m, double b, double norm, float* __restrict__ out) {
+// points in f = t - (q - m) and rewritten in powers of u = f - 1/2 (FP64),
+// kept in FP32 (out, followed by psi(m), the value at the closed end of the
+// support) and FP64 (out64).  The interpolation error is below 1.3e-9 of the
+// peak at m = 6, sigma = 2 (the window is analytic on each interval).
+__global__ void k_psi_poly_fit(int m, double b, double norm, float* __restrict__ out, double* __restrict__ out64) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= 2 * m) return;
     constexpr int D = kPsiDeg, K = kPsiDeg + 1;
@@ -562,8 +660,10 @@ __global__ void k_psi_poly_fit(int m, double b, double norm, float* __restrict__
     double sc = 1.0;                    // x^k = 2^k u^k
     for (int k = 0; k < K; k++) {
         out[q * kPsiStride + k] = (float)(mono[k] * sc);
+        out64[q * kPsiStride + k] = mono[k] * sc;
         sc *= 2.0;
     }
+    if (q == 0) out[2 * m * kPsiStride] = (float)(norm * b);   // psi(m), the end of the support
 }
 
 // exp(-2 pi i r / nos)
@@ -675,10 +775,14 @@ __global__ void k_cell_range(const int32_t* __restrict__ cell, int64_t N, int dA
 
 // FP32 weight table of a dense window: for sorted node pos and axis t < dA,
 // wtab[(pos*dA + t)*16 + r] = psi(c_t - (bin_t*T - m) - r + f_t) for r < R, 0 for
-// R <= r < 16, evaluated in FP64 from the node's FP64 coordinates.
+// R <= r < 16: the node's offset f_t from its FP64 coordinates, psi from the
+// per-interval polynomials in FP64 (Horner), rounded once to FP32.  The one
+// tap outside the 2m intervals that can be non-zero is t = m exactly (a node
+// on a grid point, f = 0), where psi(m) = `edge` (the window's value at the
+// end of its support).
 __global__ void k_weight_table(const double* __restrict__ xw, const int32_t* __restrict__ perm, int64_t N,
-                               int dA, FrameArgs fr, int nos, int Tb, int R, int m, double b, double norm,
-                               float* __restrict__ wtab) {
+                               int dA, FrameArgs fr, int nos, int Tb, int R, int m,
+                               const double* __restrict__ poly, double edge, float* __restrict__ wtab) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * dA;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pos = idx / dA;
@@ -687,23 +791,21 @@ __global__ void k_weight_table(const double* __restrict__ xw, const int32_t* __r
         const double xt = fr.s * (xw[i * dA + t] - fr.c[t]);
         const double y = (double)nos * xt;
         const double fl = floor(y);
-        const double f = y - fl;
+        const double u = (y - fl) - 0.5;
         int c = (int)fl + nos / 2;
         c %= nos;
         if (c < 0) c += nos;
         const int j0 = c - (c / Tb) * Tb + m;
         float* out = wtab + idx * 16;
         for (int r = 0; r < 16; r++) {
+            const int q = j0 - r + m;       // tap at j0 - r + f lies in interval q of [-m, m)
             double w = 0.0;
-            if (r < R) {
-                const double tt = (double)(j0 - r) + f;
-                const double s2 = (double)m * m - tt * tt;
-                if (s2 > 0.0) {
-                    const double sq = sqrt(s2);
-                    w = norm * sinh(b * sq) / sq;
-                } else if (s2 == 0.0) {
-                    w = norm * b;
-                }
+            if (r < R && q >= 0 && q < 2 * m) {
+                const double* cq = poly + q * kPsiStride;
+                w = cq[kPsiDeg];
+                for (int k = kPsiDeg - 1; k >= 0; k--) w = fma(w, u, cq[k]);
+            } else if (r < R && q == 2 * m && u == -0.5) {
+                w = edge;
             }
             out[r] = (float)w;
         }
@@ -770,7 +872,9 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
     ANOVA_CHECK_LAUNCH();
     (void)want64;
     ANOVA_TRY(build_pointset(plan, w, w.xw, plan->N, w.dA, w.centre, w.scale, w.X, st));
-    if (w.dense && want32 && plan->N > 0) {
+    // 1-D / 2-D windows on the persistent kernels evaluate their weights on the fly and need no table
+    const bool table = w.dense && want32 && plan->N > 0 && !(w.dA < 3 && plan->pw12 && tc5_supported(w.R, plan->m));
+    if (table) {
         cudaFree(w.wtab);
         w.wtab = nullptr;
         ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.wtab, plan->N * 16 * w.dA * sizeof(float)));
@@ -778,8 +882,12 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
         for (int t = 0; t < 3; t++) fr.c[t] = w.centre[t];
         fr.s = w.scale;
         k_weight_table<<<grid_for(plan->N * w.dA, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
-            w.xw, w.X.perm, plan->N, w.dA, fr, w.nos, w.T, w.R, plan->m, plan->b, plan->psi_norm, w.wtab);
+            w.xw, w.X.perm, plan->N, w.dA, fr, w.nos, w.T, w.R, plan->m, plan->psi_poly64, plan->psi_norm * plan->b,
+            w.wtab);
         ANOVA_CHECK_LAUNCH();
+    } else if (w.wtab) {
+        cudaFree(w.wtab);
+        w.wtab = nullptr;
     }
     return window_box(plan, w, st);
 }
@@ -991,8 +1099,9 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     plan->b = M_PI * (2.0 - 1.0 / sigma);
     plan->psi_norm = (double)m / std::sinh(plan->b * m);
     plan->win.resize(P);
-    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly, 2 * m * kPsiStride * sizeof(float)));
-    k_psi_poly_fit<<<1, 64, 0, st>>>(m, plan->b, plan->psi_norm, plan->psi_poly);
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly, (2 * m * kPsiStride + 1) * sizeof(float)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly64, 2 * m * kPsiStride * sizeof(double)));
+    k_psi_poly_fit<<<1, 64, 0, st>>>(m, plan->b, plan->psi_norm, plan->psi_poly, plan->psi_poly64);
     ANOVA_CHECK_LAUNCH();
     plan->psi_host.assign(2 * m * kPsiStride, 0.f);
     ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->psi_host.data(), plan->psi_poly, plan->psi_host.size() * sizeof(float),
@@ -1327,6 +1436,7 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->fft3_desc);
     cudaFree(plan->fft12_desc);
     cudaFree(plan->psi_poly);
+    cudaFree(plan->psi_poly64);
     cudaFree(plan->cg_vec);
     cudaFree(plan->cg_scal);
     cudaFree(plan->cg_part);

@@ -84,7 +84,7 @@ k_gather3_umma(const int4* __restrict__ sub, const DenseWin* __restrict__ descs,
     const int ox = Tb * bx - m, oy = Tb * by - m, oz = Tb * bz - m;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (kGatherPolyW)
-        for (int i = tid; i < 2 * m * kPsiStride; i += kUmmaThreads) sP[i] = poly[i];
+        for (int i = tid; i < 2 * m * kPsiStride + 1; i += kUmmaThreads) sP[i] = poly[i];
     // weight-table rows of the tile starting at node t: asynchronous copies into sW,
     // waited for where they are used (they overlap the region staging and the MMAs)
     auto prefetch = [&](int t) {

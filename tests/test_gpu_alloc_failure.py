@@ -92,7 +92,8 @@ def test_predict_and_model_free_on_failure(B, torch, problem):
         m.predict(Z, out)
         m.close()
 
-    assert sweep(B, torch, model_call) > 0
+    # a model builds grids in two frames per window and bins its test points per window: many allocations
+    assert sweep(B, torch, model_call, max_k=400) > 0
     plan.close()
 
 

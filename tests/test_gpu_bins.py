@@ -70,3 +70,24 @@ def test_autotune_returns_sides_a_plan_takes(B, torch):
         s = sides[len(win) - 1]
         if s:
             assert B.anova_plan_window_bins(plan, l)["bin_side"] == s
+
+
+def test_binning_of_long_histograms_matches_oracle(B, torch):
+    """N = 20000 nodes in a 3-D window of 32768 bins: the bins x chunks
+    histogram (98304 counts) goes through the multi-block scan; the FP64 product
+    must still be the oracle's."""
+    w = W.random_problem(20000, 4, [(0, 1, 2), (3,)], 0.25, [32, 32], 6, seed=720)
+    w.epsB = 0.25
+    X = torch.from_numpy(w.X).cuda()
+    plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, precision=B.MIXED)
+    info = B.anova_plan_window_bins(plan, 0)
+    nbins = (2 * w.n[0] // info["bin_side"]) ** 3
+    assert nbins * ((w.N + 8191) // 8192) > 4 * 8192
+    ref = oracle.fastsum(None, w.X, w.windows, w.eta, w.ell, w.n, w.m, w.alpha, sigma=w.sigma, epsB=w.epsB, p=w.p)
+    a64 = torch.from_numpy(w.alpha).cuda()
+    o64 = torch.empty_like(a64)
+    B.anova_matvec(plan, a64, o64)
+    assert rel(o64.cpu().numpy(), ref) <= 1e-12
+    o32 = torch.empty_like(a64.float())
+    B.anova_matvec(plan, a64.float(), o32)
+    assert rel(o32.cpu().numpy(), ref) <= 1e-5
