@@ -3,14 +3,20 @@
 // those below a threshold dropped, the rest grouped three at a time in rank
 // order; Sec. 6.1: z-score normalisation with training statistics).
 //
-// Column statistics read the row-major matrix in coalesced row blocks; each
-// block keeps per-column partials in shared memory and the column totals are
-// summed over the blocks in a fixed order.  The score is the plug-in mutual
-// information between the label and the feature's quantile bin, the quantile
-// bins coming from a fine equal-width histogram (bin of a value: floor((v -
-// lo) F / (hi - lo)), F = 4096, the last bin closed; quantile bin of fine bin
-// j: floor(B (2 C_j + c_j) / (2 N)) with C_j the count below j and c_j its
-// own count, in integers).
+// Column statistics read the row-major matrix in coalesced row blocks with
+// per-thread column accumulators; the blocks' partials are combined in a
+// fixed order (deterministic).  The z-score fit is one read of X: per block
+// and column the sums of x - K and (x - K)^2 with a shift K taken from the
+// block's first row, combined over blocks by the pairwise mean / M2 update.
+// The score is the plug-in mutual information between the label and the
+// feature's quantile bin, the quantile bins coming from a fine equal-width
+// histogram (bin of a value: floor((v - lo) F / (hi - lo)), F = 4096, the last
+// bin closed; quantile bin of fine bin j: floor(B (2 C_j + c_j) / (2 N)) with
+// C_j the count below j and c_j its own count, in integers).  The fine bin is
+// a non-decreasing function of v, so it is computed exactly from per-column
+// thresholds (found once per column in FP64 from the definition) by integer
+// comparisons of order keys: no FP64 division per element, the same bins as
+// the definition evaluated in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,76 +44,122 @@ __device__ __forceinline__ double of_ord(unsigned long long u) {
 
 // Element (r, c) of a block's rows goes to a fixed thread: with d <= 256 the
 // block reads G = 256 / d rows per step, thread t < G d owning column t mod d
-// and rows r0 + t / d, r0 + t / d + G, ... (a warp reads consecutive elements);
-// with d > 256 thread t owns columns t, t + 256, ... of every row.  Each thread
-// accumulates its columns in registers; the G threads of a column are summed in
-// a fixed order in shared memory.  Per block: column sums of x (mode 0, with
-// min and max) or of (x - mean)^2 (mode 1).
+// and rows r0 + t / d, r0 + t / d + G, ... (a warp reads consecutive elements;
+// four rows' loads in flight per step); with d > 256 thread t owns columns t,
+// t + 256, ... of every row.  Each thread accumulates its columns in
+// registers; the G threads of a column are combined in a fixed order in
+// shared memory.
 constexpr int kColsPerThread = (kFeatMaxD + kThreads - 1) / kThreads;
 
+// Per block and column, one read of X:
+//   kMoments  S = sum (x - K), Q = sum (x - K)^2 with the shift K = the
+//             column's value in the block's first row (same K for every thread
+//             of the block, so the thread sums add directly);
+//   kRange    min and max as order-preserving integer keys (no FP64 work).
+enum ColMode { kMoments = 0, kRange = 1 };
+
+template <int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_col_partials(const double* __restrict__ X, int64_t N, int d, int64_t ld, const double* __restrict__ mean, int mode,
-               int64_t rows_per_block, double* __restrict__ psum, unsigned long long* __restrict__ pmin,
-               unsigned long long* __restrict__ pmax) {
+k_col_partials(const double* __restrict__ X, int64_t N, int d, int64_t ld, int64_t rows_per_block,
+               double* __restrict__ pS, double* __restrict__ pQ, double* __restrict__ pK,
+               unsigned long long* __restrict__ pmin, unsigned long long* __restrict__ pmax) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int t = threadIdx.x;
     const int G = d <= kThreads ? kThreads / d : 1;          // rows per step
     const int active = d <= kThreads ? G * d : kThreads;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min(N, r0 + rows_per_block);
-    double sum[kColsPerThread];
+    double S[kColsPerThread], Q[kColsPerThread], K[kColsPerThread];
     unsigned long long mn[kColsPerThread], mx[kColsPerThread];
+    const int g = d <= kThreads ? t / d : 0;
+    const int c0 = d <= kThreads ? t % d : t;
 #pragma unroll
     for (int k = 0; k < kColsPerThread; k++) {
-        sum[k] = 0.0;
+        S[k] = 0.0;
+        Q[k] = 0.0;
+        K[k] = 0.0;
         mn[k] = ~0ull;
         mx[k] = 0ull;
     }
     if (t < active) {
-        const int g = d <= kThreads ? t / d : 0;
-        const int c0 = d <= kThreads ? t % d : t;
-        for (int64_t r = r0 + g; r < r1; r += G) {
-            const double* row = X + r * ld;
+        if (MODE == kMoments) {
 #pragma unroll
             for (int k = 0; k < kColsPerThread; k++) {
                 const int c = c0 + k * kThreads;
                 if (k > 0 && (d <= kThreads || c >= d)) break;
-                const double v = row[c];
-                if (mode == 0) {
-                    sum[k] += v;
-                    const unsigned long long o = ord_of(v);
-                    mn[k] = o < mn[k] ? o : mn[k];
-                    mx[k] = o > mx[k] ? o : mx[k];
-                } else {
-                    const double dv = v - mean[c];
-                    sum[k] = fma(dv, dv, sum[k]);
+                K[k] = X[r0 * ld + c];
+            }
+        }
+        auto take = [&](double v, int k) {
+            if (MODE == kMoments) {
+                const double dv = v - K[k];
+                S[k] += dv;
+                Q[k] = fma(dv, dv, Q[k]);
+            } else {
+                const unsigned long long o = ord_of(v);
+                mn[k] = o < mn[k] ? o : mn[k];
+                mx[k] = o > mx[k] ? o : mx[k];
+            }
+        };
+        if (d <= kThreads) {
+            const double* col = X + c0;
+            int64_t r = r0 + g;
+            for (; r + 3 * G < r1; r += 4 * G) {
+                const double v0 = col[r * ld], v1 = col[(r + G) * ld], v2 = col[(r + 2 * G) * ld],
+                             v3 = col[(r + 3 * G) * ld];
+                take(v0, 0);
+                take(v1, 0);
+                take(v2, 0);
+                take(v3, 0);
+            }
+            for (; r < r1; r += G) take(col[r * ld], 0);
+        } else {
+            for (int64_t r = r0; r < r1; r++) {
+                const double* row = X + r * ld;
+#pragma unroll
+                for (int k = 0; k < kColsPerThread; k++) {
+                    const int c = c0 + k * kThreads;
+                    if (c >= d) break;
+                    take(row[c], k);
                 }
             }
         }
     }
+    const size_t o = (size_t)blockIdx.x * d;
     if (d <= kThreads) {
-        // fixed-order sum over the G threads of each column
-        double* ssum = reinterpret_cast<double*>(sm);
-        unsigned long long* smin = reinterpret_cast<unsigned long long*>(ssum + active);
-        unsigned long long* smax = smin + active;
+        // fixed-order combination of the G threads of each column
+        double* s0 = reinterpret_cast<double*>(sm);
+        double* s1 = s0 + active;
+        unsigned long long* u0 = reinterpret_cast<unsigned long long*>(sm);
+        unsigned long long* u1 = u0 + active;
         if (t < active) {
-            ssum[t] = sum[0];
-            smin[t] = mn[0];
-            smax[t] = mx[0];
+            if (MODE == kMoments) {
+                s0[t] = S[0];
+                s1[t] = Q[0];
+            } else {
+                u0[t] = mn[0];
+                u1[t] = mx[0];
+            }
         }
         __syncthreads();
         for (int c = t; c < d; c += kThreads) {
-            double sc = 0.0;
-            unsigned long long a = ~0ull, z = 0ull;
-            for (int g = 0; g < G; g++) {
-                sc += ssum[g * d + c];
-                a = smin[g * d + c] < a ? smin[g * d + c] : a;
-                z = smax[g * d + c] > z ? smax[g * d + c] : z;
-            }
-            psum[(size_t)blockIdx.x * d + c] = sc;
-            if (mode == 0) {
-                pmin[(size_t)blockIdx.x * d + c] = a;
-                pmax[(size_t)blockIdx.x * d + c] = z;
+            if (MODE == kMoments) {
+                double a = 0.0, b = 0.0;
+                for (int h = 0; h < G; h++) {
+                    a += s0[h * d + c];
+                    b += s1[h * d + c];
+                }
+                pS[o + c] = a;
+                pQ[o + c] = b;
+                pK[o + c] = X[r0 * ld + c];
+            } else {
+                unsigned long long a = ~0ull, z = 0ull;
+                for (int h = 0; h < G; h++) {
+                    a = u0[h * d + c] < a ? u0[h * d + c] : a;
+                    z = u1[h * d + c] > z ? u1[h * d + c] : z;
+                }
+                pmin[o + c] = a;
+                pmax[o + c] = z;
             }
         }
     } else {
@@ -115,59 +167,87 @@ k_col_partials(const double* __restrict__ X, int64_t N, int d, int64_t ld, const
         for (int k = 0; k < kColsPerThread; k++) {
             const int c = t + k * kThreads;
             if (c >= d) break;
-            psum[(size_t)blockIdx.x * d + c] = sum[k];
-            if (mode == 0) {
-                pmin[(size_t)blockIdx.x * d + c] = mn[k];
-                pmax[(size_t)blockIdx.x * d + c] = mx[k];
+            if (MODE == kMoments) {
+                pS[o + c] = S[k];
+                pQ[o + c] = Q[k];
+                pK[o + c] = K[k];
+            } else {
+                pmin[o + c] = mn[k];
+                pmax[o + c] = mx[k];
             }
         }
     }
 }
 
-// column totals over the blocks, one block per column: thread t sums the
-// partials of blocks t, t + 256, ... in order, then a fixed tree over the
-// threads (deterministic); mode 0: mean, lo, hi; mode 1: std
+// (count, mean, sum of squared deviations) of two disjoint row sets combined
+// (the pairwise update of Chan, Golub and LeVeque)
+struct Moments {
+    double n, mean, m2;
+};
+__device__ __forceinline__ Moments merge(const Moments& a, const Moments& b) {
+    if (a.n == 0.0) return b;
+    if (b.n == 0.0) return a;
+    const double n = a.n + b.n;
+    const double delta = b.mean - a.mean;
+    return {n, a.mean + delta * (b.n / n), a.m2 + b.m2 + delta * delta * (a.n * (b.n / n))};
+}
+
+// column totals, one block per column: thread t combines the partials of
+// blocks t, t + 256, ... in order, then a fixed tree over the threads
+// (deterministic).  kMoments: mean and sd (divisor N, sd = 1 for a constant
+// column); kRange: lo and hi.
+template <int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_col_totals(const double* __restrict__ psum, const unsigned long long* __restrict__ pmin,
-             const unsigned long long* __restrict__ pmax, int nblk, int d, int64_t N, int mode,
-             double* __restrict__ out0, double* __restrict__ lo, double* __restrict__ hi) {
-    __shared__ double ss[kThreads];
+k_col_totals(const double* __restrict__ pS, const double* __restrict__ pQ, const double* __restrict__ pK,
+             const unsigned long long* __restrict__ pmin, const unsigned long long* __restrict__ pmax, int nblk,
+             int d, int64_t N, int64_t rows_per_block, double* __restrict__ out0, double* __restrict__ out1) {
+    __shared__ Moments sm_m[kThreads];
     __shared__ unsigned long long smn[kThreads], smx[kThreads];
     const int c = blockIdx.x, t = threadIdx.x;
-    double s = 0.0;
+    Moments acc = {0.0, 0.0, 0.0};
     unsigned long long mn = ~0ull, mx = 0ull;
     for (int b = t; b < nblk; b += kThreads) {
-        s += psum[(size_t)b * d + c];
-        if (mode == 0) {
-            const unsigned long long a = pmin[(size_t)b * d + c], z = pmax[(size_t)b * d + c];
-            mn = a < mn ? a : mn;
-            mx = z > mx ? z : mx;
+        const size_t i = (size_t)b * d + c;
+        if (MODE == kMoments) {
+            const int64_t r0 = (int64_t)b * rows_per_block;
+            const double nb = (double)(min(N, r0 + rows_per_block) - r0);
+            const double S = pS[i];
+            const double m2 = pQ[i] - S * (S / nb);
+            acc = merge(acc, Moments{nb, pK[i] + S / nb, m2 > 0.0 ? m2 : 0.0});
+        } else {
+            mn = pmin[i] < mn ? pmin[i] : mn;
+            mx = pmax[i] > mx ? pmax[i] : mx;
         }
     }
-    ss[t] = s;
+    sm_m[t] = acc;
     smn[t] = mn;
     smx[t] = mx;
     __syncthreads();
     for (int h = kThreads / 2; h > 0; h >>= 1) {
         if (t < h) {
-            ss[t] += ss[t + h];
-            smn[t] = smn[t + h] < smn[t] ? smn[t + h] : smn[t];
-            smx[t] = smx[t + h] > smx[t] ? smx[t + h] : smx[t];
+            if (MODE == kMoments) {
+                sm_m[t] = merge(sm_m[t], sm_m[t + h]);
+            } else {
+                smn[t] = smn[t + h] < smn[t] ? smn[t + h] : smn[t];
+                smx[t] = smx[t + h] > smx[t] ? smx[t + h] : smx[t];
+            }
         }
         __syncthreads();
     }
     if (t != 0) return;
-    if (mode == 0) {
-        out0[c] = ss[0] / (double)N;
-        if (lo) lo[c] = of_ord(smn[0]);
-        if (hi) hi[c] = of_ord(smx[0]);
+    if (MODE == kMoments) {
+        out0[c] = sm_m[0].mean;
+        const double sd = sqrt(sm_m[0].m2 / (double)N);
+        out1[c] = sd > 0.0 ? sd : 1.0;
     } else {
-        const double sd = sqrt(ss[0] / (double)N);
-        out0[c] = sd > 0.0 ? sd : 1.0;
+        out0[c] = of_ord(smn[0]);
+        out1[c] = of_ord(smx[0]);
     }
 }
 
-// x = (x - mean) / sd in place, elements owned as in k_col_partials
+// x = (x - mean) * (1 / sd) in place (two FP64 operations per element; within
+// 1.5 units in the last place of the quotient), elements owned as in
+// k_col_partials
 __global__ void __launch_bounds__(kThreads)
 k_zscore(double* __restrict__ X, int64_t N, int d, int64_t ld, const double* __restrict__ mean,
          const double* __restrict__ sd, int64_t rows_per_block) {
@@ -185,30 +265,171 @@ k_zscore(double* __restrict__ X, int64_t N, int d, int64_t ld, const double* __r
         const int c = c0 + k * kThreads;
         const bool ok = k == 0 || (d > kThreads && c < d);
         m[k] = ok ? mean[c] : 0.0;
-        s[k] = ok ? sd[c] : 1.0;
+        s[k] = ok ? 1.0 / sd[c] : 1.0;
     }
-    for (int64_t r = r0 + g; r < r1; r += G) {
+    if (d <= kThreads) {
+        double* col = X + c0;
+        int64_t r = r0 + g;
+        for (; r + 3 * G < r1; r += 4 * G) {
+            const double v0 = col[r * ld], v1 = col[(r + G) * ld], v2 = col[(r + 2 * G) * ld],
+                         v3 = col[(r + 3 * G) * ld];
+            col[r * ld] = (v0 - m[0]) * s[0];
+            col[(r + G) * ld] = (v1 - m[0]) * s[0];
+            col[(r + 2 * G) * ld] = (v2 - m[0]) * s[0];
+            col[(r + 3 * G) * ld] = (v3 - m[0]) * s[0];
+        }
+        for (; r < r1; r += G) col[r * ld] = (col[r * ld] - m[0]) * s[0];
+        return;
+    }
+    for (int64_t r = r0; r < r1; r++) {
         double* row = X + r * ld;
 #pragma unroll
         for (int k = 0; k < kColsPerThread; k++) {
             const int c = c0 + k * kThreads;
-            if (k > 0 && (d <= kThreads || c >= d)) break;
-            row[c] = (row[c] - m[k]) / s[k];
+            if (c >= d) break;
+            row[c] = (row[c] - m[k]) * s[k];
         }
     }
 }
 
-__device__ __forceinline__ int fine_of(double v, double lo, double hi) {
-    if (!(hi > lo)) return 0;
-    const double t = (v - lo) * (double)kFine / (hi - lo);
-    int j = (int)floor(t);
-    return j < 0 ? 0 : (j > kFine - 1 ? kFine - 1 : j);
+// The fine bin is a non-decreasing function of v, so it is fixed by the
+// thresholds thr_j = the smallest double v (as an order key) with bin >= j:
+// bin(v) = max{ j : thr_j <= key(v) }.  Row c of the table holds thr_0 = 0 (no
+// key below), thr_1 .. thr_{F-1}, and thr_F = ~0 (no key reaches it).  The bin
+// depends on v only through the rounded difference D = RN(v - lo), so each
+// threshold takes two monotone searches: the smallest difference D* in
+// [0, hi - lo] whose bin RN(D F / (hi - lo)) reaches j (the guess j (hi - lo) /
+// F is within a few units in the last place of it), then the smallest v in
+// [lo, hi] with RN(v - lo) >= D* (one subtraction per probe).  Both start from
+// a guess and gallop, then bisect, over the order keys.
+constexpr int kThrRow = kFine + 1;
+
+// smallest key in [klo, khi] where pred holds (pred monotone, pred(khi) true),
+// searched from the guess k0
+template <typename Pred>
+__device__ unsigned long long smallest_key(unsigned long long klo, unsigned long long khi, unsigned long long k0,
+                                           Pred pred) {
+    k0 = k0 < klo ? klo : (k0 > khi ? khi : k0);
+    unsigned long long a, b;   // !pred(a) (or a == klo untested), pred(b), a < b
+    if (pred(k0)) {
+        b = k0;
+        unsigned long long step = 1;
+        for (;;) {
+            if (b - klo < step) {
+                if (pred(klo)) return klo;
+                a = klo;
+                break;
+            }
+            const unsigned long long q = b - step;
+            if (pred(q)) {
+                b = q;
+                step <<= 1;
+            } else {
+                a = q;
+                break;
+            }
+        }
+    } else {
+        a = k0;
+        unsigned long long step = 1;
+        for (;;) {
+            if (khi - a <= step) {
+                b = khi;
+                break;
+            }
+            const unsigned long long q = a + step;
+            if (pred(q)) {
+                b = q;
+                break;
+            }
+            a = q;
+            step <<= 1;
+        }
+    }
+    while (b - a > 1) {
+        const unsigned long long q = a + (b - a) / 2;
+        if (pred(q)) b = q;
+        else a = q;
+    }
+    return b;
 }
 
-// MIS histograms: warp w of a block takes columns w, w + 8, ... of the block's
-// rows in groups of 32 (lane = row), so the values a warp holds belong to one
-// column and equal histogram cells are combined (__match_any_sync) before the
-// one atomic add per distinct cell.
+__device__ unsigned long long threshold_key(int j, double lo, double hi) {
+    const double h = hi - lo;
+    // bin of a rounded difference D, as the definition evaluates it
+    auto bin_of_d = [&](double D) {
+        int b = (int)floor(D * (double)kFine / h);
+        return b < 0 ? 0 : (b > kFine - 1 ? kFine - 1 : b);
+    };
+    const unsigned long long dstar = smallest_key(ord_of(0.0), ord_of(h), ord_of((double)j * (h / (double)kFine)),
+                                                  [&](unsigned long long k) { return bin_of_d(of_ord(k)) >= j; });
+    const double D = of_ord(dstar);
+    return smallest_key(ord_of(lo), ord_of(hi), ord_of(lo + D),
+                        [&](unsigned long long k) { return of_ord(k) - lo >= D; });
+}
+
+// thresholds of every column (one thread per (column, j)) and the column's
+// FP32 screen (lo, F / (hi - lo)) that gives a starting bin
+__global__ void __launch_bounds__(kThreads)
+k_fine_thresholds(const double* __restrict__ lo, const double* __restrict__ hi, int d,
+                  unsigned long long* __restrict__ thr, float2* __restrict__ screen) {
+    const int c = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d || j > kFine) return;
+    const double L = lo[c], H = hi[c];
+    unsigned long long key;
+    if (j == 0) key = 0ull;
+    else if (j == kFine || !(H > L)) key = ~0ull;
+    else key = threshold_key(j, L, H);
+    thr[(size_t)c * kThrRow + j] = key;
+    if (j == 0) screen[c] = H > L ? make_float2((float)L, (float)((double)kFine / (H - L))) : make_float2(0.f, 0.f);
+}
+
+// FP32 value of v from its high word (mantissa truncated to 20 bits), 0 where
+// the exponent is outside FP32's normal range: only a starting point
+__device__ __forceinline__ float approx_float(double v) {
+    const int h = __double2hiint(v);
+    const int e = (h >> 20) & 0x7ff;
+    if (e <= 896 || e >= 1151) return 0.0f;
+    return __int_as_float((h & (int)0x80000000) | (((h & 0x7fffffff) - (896 << 20)) << 3));
+}
+
+// fine bin of v from the thresholds of its column: an FP32 estimate, then
+// moved until thr_j <= key(v) < thr_{j+1} (exact; each loop ends within F steps)
+__device__ __forceinline__ int fine_bin(double v, const unsigned long long* __restrict__ thr, float2 scr) {
+    const unsigned long long key = ord_of(v);
+    const float t = (approx_float(v) - scr.x) * scr.y;
+    int j = (int)fminf(fmaxf(t, 0.0f), (float)(kFine - 1));
+    while (j > 0 && key < __ldg(thr + j)) j--;
+    while (j < kFine - 1 && key >= __ldg(thr + j + 1)) j++;
+    return j;
+}
+
+// fine bin of every element (anova_mis_fine_bins), elements owned as in
+// k_col_partials
+__global__ void __launch_bounds__(kThreads)
+k_fine_bins_out(const double* __restrict__ X, int64_t N, int d, int64_t ld,
+                const unsigned long long* __restrict__ thr, const float2* __restrict__ screen,
+                int64_t rows_per_block, int32_t* __restrict__ out) {
+    const int t = threadIdx.x;
+    const int G = d <= kThreads ? kThreads / d : 1;
+    const int active = d <= kThreads ? G * d : kThreads;
+    if (t >= active) return;
+    const int g = d <= kThreads ? t / d : 0;
+    const int c0 = d <= kThreads ? t % d : t;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(N, r0 + rows_per_block);
+    for (int64_t r = r0 + g; r < r1; r += G)
+        for (int c = c0; c < d; c += (d <= kThreads ? d : kThreads))
+            out[r * d + c] = fine_bin(X[r * ld + c], thr + (size_t)c * kThrRow, screen[c]);
+}
+
+// Three-pass MIS (any nclass): the fine histogram by global atomics, the
+// quantile map, then the joint counts in shared memory per block.  Warp w of a
+// block takes columns w, w + 8, ... of the block's rows in groups of 32 (lane
+// = row), so the values a warp holds belong to one column and equal histogram
+// cells are combined (__match_any_sync) before the one atomic add per
+// distinct cell.
 constexpr int kHistWarps = kThreads / 32;
 
 __device__ __forceinline__ void add_aggregated(unsigned int* base, int key, bool valid) {
@@ -219,8 +440,8 @@ __device__ __forceinline__ void add_aggregated(unsigned int* base, int key, bool
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_fine_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld, const double* __restrict__ lo,
-            const double* __restrict__ hi, int64_t rows_per_block, unsigned int* __restrict__ hist) {
+k_fine_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld, const unsigned long long* __restrict__ thr,
+            const float2* __restrict__ screen, int64_t rows_per_block, unsigned int* __restrict__ hist) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min(N, r0 + rows_per_block);
@@ -229,7 +450,8 @@ k_fine_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld, const do
         const bool in = r < r1;
         for (int c = warp; c < d; c += kHistWarps) {
             const double v = in ? X[r * ld + c] : 0.0;
-            add_aggregated(hist, c * kFine + fine_of(v, lo[c], hi[c]), in);
+            const int j = in ? fine_bin(v, thr + (size_t)c * kThrRow, screen[c]) : 0;
+            add_aggregated(hist, c * kFine + j, in);
         }
     }
 }
@@ -265,10 +487,10 @@ __global__ void __launch_bounds__(1024) k_quantile_map(const unsigned int* __res
 // joint counts (quantile bin, class) per column in shared memory per block;
 // labels outside [0, nclass) are counted in bad (once per row)
 __global__ void __launch_bounds__(kThreads)
-k_joint(const double* __restrict__ X, int64_t N, int d, int64_t ld, const double* __restrict__ lo,
-        const double* __restrict__ hi, const unsigned char* __restrict__ qmap, const int32_t* __restrict__ labels,
-        int B, int nclass, int64_t rows_per_block, unsigned long long* __restrict__ joint,
-        unsigned long long* __restrict__ bad) {
+k_joint(const double* __restrict__ X, int64_t N, int d, int64_t ld, const unsigned long long* __restrict__ thr,
+        const float2* __restrict__ screen, const unsigned char* __restrict__ qmap,
+        const int32_t* __restrict__ labels, int B, int nclass, int64_t rows_per_block,
+        unsigned long long* __restrict__ joint, unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) unsigned char sm[];
     unsigned int* sj = reinterpret_cast<unsigned int*>(sm);
     const int cells = d * B * nclass;
@@ -286,7 +508,7 @@ k_joint(const double* __restrict__ X, int64_t N, int d, int64_t ld, const double
         if (warp == 0 && in && !ok) nbad++;
         for (int c = warp; c < d; c += kHistWarps) {
             const double v = ok ? X[r * ld + c] : 0.0;
-            const int q = ok ? qmap[(size_t)c * kFine + fine_of(v, lo[c], hi[c])] : 0;
+            const int q = ok ? qmap[(size_t)c * kFine + fine_bin(v, thr + (size_t)c * kThrRow, screen[c])] : 0;
             add_aggregated(sj, (c * B + q) * nclass + y, ok);
         }
     }
@@ -294,6 +516,130 @@ k_joint(const double* __restrict__ X, int64_t N, int d, int64_t ld, const double
     __syncthreads();
     for (int i = threadIdx.x; i < cells; i += blockDim.x)
         if (sj[i]) atomicAdd(&joint[i], (unsigned long long)sj[i]);
+}
+
+// Two-pass MIS (nclass <= 4): one read of X gives the (fine bin, class)
+// counts of every column, from which the quantile map and the joint
+// (quantile bin, class) counts follow without reading X again.  Block (g, rr)
+// takes column group g (gcols consecutive columns) over row range rr and
+// counts in shared memory: per (column, fine bin) ceil(nclass / 2) 32-bit
+// words holding two 16-bit class counts each (a block takes at most 65535
+// rows, so a half never carries into the other).  Thread t handles column
+// t mod gc of rows t / gc, t / gc + NT / gc, ... (consecutive threads read
+// consecutive columns of a row).  The block writes its counts to its own slot
+// of a scratch array; k_class_hist_reduce adds the slots in a fixed order.
+constexpr int kCHThreads = 512;
+constexpr int kCHMaxRows = 65535;
+constexpr size_t kCHSmem = 100 * 1024;                 // shared counts per block: two blocks per SM
+constexpr size_t kCHPartMax = (size_t)512 << 20;       // largest scratch of block counts
+
+__global__ void __launch_bounds__(kCHThreads)
+k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
+                  const unsigned long long* __restrict__ thr, const float2* __restrict__ screen,
+                  const int32_t* __restrict__ labels, int nclass, int gcols, int ngroups, int64_t rows_per_block,
+                  unsigned int* __restrict__ part, unsigned long long* __restrict__ bad) {
+    extern __shared__ __align__(16) unsigned int sh[];
+    const int W = (nclass + 1) / 2;                       // words per (column, fine bin)
+    const int g = blockIdx.x % ngroups;
+    const int64_t rr = blockIdx.x / ngroups;
+    const int c_lo = g * gcols;
+    const int gc = min(gcols, d - c_lo);
+    const int words = gc * kFine * W;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const int64_t r0 = rr * rows_per_block;
+    const int64_t r1 = min(N, r0 + rows_per_block);
+    const int per = kCHThreads / gc;                      // rows per step
+    const int cl = threadIdx.x % gc;
+    const int c = c_lo + cl;
+    unsigned int nbad = 0;
+    if (threadIdx.x < per * gc) {
+        const unsigned long long* __restrict__ tc = thr + (size_t)c * kThrRow;
+        const float2 scr = screen[c];
+        for (int64_t r = r0 + threadIdx.x / gc; r < r1; r += per) {
+            const int y = labels[r];
+            if (y < 0 || y >= nclass) {
+                if (g == 0 && cl == 0) nbad++;
+                continue;
+            }
+            const int j = fine_bin(X[r * ld + c], tc, scr);
+            atomicAdd(&sh[(cl * kFine + j) * W + (y >> 1)], 1u << (16 * (y & 1)));
+        }
+    }
+    if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+    __syncthreads();
+    unsigned int* out = part + (size_t)blockIdx.x * gcols * kFine * W;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) out[i] = sh[i];
+}
+
+// hist[c][j][y] = sum over row ranges of the 16-bit counts (fixed order)
+__global__ void __launch_bounds__(kThreads)
+k_class_hist_reduce(const unsigned int* __restrict__ part, int d, int nclass, int gcols, int ngroups, int nranges,
+                    unsigned int* __restrict__ hist) {
+    const int W = (nclass + 1) / 2;
+    const int64_t total = (int64_t)d * kFine * W;
+    const size_t slot = (size_t)gcols * kFine * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(i % W);
+        const int64_t cj = i / W;                         // c * kFine + j
+        const int c = (int)(cj / kFine);
+        const int g = c / gcols;
+        const size_t inner = ((size_t)(c - g * gcols) * kFine + (size_t)(cj % kFine)) * W + w;
+        unsigned int lo = 0, hi = 0;
+        for (int rr = 0; rr < nranges; rr++) {
+            const unsigned int v = part[((size_t)rr * ngroups + g) * slot + inner];
+            lo += v & 0xffffu;
+            hi += v >> 16;
+        }
+        const int y0 = 2 * w;
+        hist[cj * nclass + y0] = lo;
+        if (y0 + 1 < nclass) hist[cj * nclass + y0 + 1] = hi;
+    }
+}
+
+// per column (one block): fine-bin counts c_j = sum_y hist[j][y], the quantile
+// bin q(j) = floor(B (2 C_j + c_j) / (2 N)), and the joint counts
+// n_qy = sum over j with q(j) = q of hist[j][y]
+__global__ void __launch_bounds__(1024)
+k_quantile_joint(const unsigned int* __restrict__ hist, int64_t N, int B, int nclass,
+                 unsigned long long* __restrict__ joint) {
+    __shared__ long long part[1024];
+    __shared__ unsigned long long sj[kMaxQBins * 4];
+    const int c = blockIdx.x;
+    const unsigned int* h = hist + (size_t)c * kFine * nclass;
+    for (int i = threadIdx.x; i < B * nclass; i += blockDim.x) sj[i] = 0ull;
+    constexpr int per = kFine / 1024;
+    long long cnt[per];
+    long long local = 0;
+    for (int k = 0; k < per; k++) {
+        const int j = threadIdx.x * per + k;
+        long long s = 0;
+        for (int y = 0; y < nclass; y++) s += h[(size_t)j * nclass + y];
+        cnt[k] = s;
+        local += s;
+    }
+    part[threadIdx.x] = local;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {      // inclusive scan of the thread totals
+        const long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long C = part[threadIdx.x] - local;        // count below this thread's first fine bin
+    for (int k = 0; k < per; k++) {
+        const int j = threadIdx.x * per + k;
+        long long q = ((long long)B * (2 * C + cnt[k])) / (2 * N);
+        if (q > B - 1) q = B - 1;
+        if (cnt[k] > 0)
+            for (int y = 0; y < nclass; y++) {
+                const unsigned int v = h[(size_t)j * nclass + y];
+                if (v) atomicAdd(&sj[q * nclass + y], (unsigned long long)v);
+            }
+        C += cnt[k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < B * nclass; i += blockDim.x) joint[(size_t)c * B * nclass + i] = sj[i];
 }
 
 // blocks and rows per block of the statistics and histogram kernels: every block
@@ -317,30 +663,58 @@ using namespace anova;
 
 namespace {
 
-// column statistics of one call: block partials (sums, min, max) and the grid
+// column statistics of one call: block partials and the grid
 struct ColStats {
-    double *psum = nullptr;
+    double *pS = nullptr, *pQ = nullptr, *pK = nullptr;
     unsigned long long *pmin = nullptr, *pmax = nullptr;
     int nblk = 0;
     int64_t rows = 0;
 };
 
-size_t partial_smem(int d) { return d <= kThreads ? (size_t)(kThreads / d) * d * 24 : 0; }
+size_t partial_smem(int d) { return d <= kThreads ? (size_t)(kThreads / d) * d * 16 : 0; }
 
-anova_status col_alloc(int64_t N, int d, ColStats& cs, Scratch& scratch) {
+anova_status col_alloc(int64_t N, int d, int mode, ColStats& cs, Scratch& scratch) {
     stat_grid(N, device_sms(), &cs.nblk, &cs.rows);
-    ANOVA_CUDA_TRY(scratch.alloc(&cs.psum, (size_t)cs.nblk * d * sizeof(double)));
-    ANOVA_CUDA_TRY(scratch.alloc(&cs.pmin, (size_t)cs.nblk * d * sizeof(unsigned long long)));
-    ANOVA_CUDA_TRY(scratch.alloc(&cs.pmax, (size_t)cs.nblk * d * sizeof(unsigned long long)));
+    const size_t n = (size_t)cs.nblk * d;
+    if (mode == kMoments) {
+        ANOVA_CUDA_TRY(scratch.alloc(&cs.pS, n * sizeof(double)));
+        ANOVA_CUDA_TRY(scratch.alloc(&cs.pQ, n * sizeof(double)));
+        ANOVA_CUDA_TRY(scratch.alloc(&cs.pK, n * sizeof(double)));
+    } else {
+        ANOVA_CUDA_TRY(scratch.alloc(&cs.pmin, n * sizeof(unsigned long long)));
+        ANOVA_CUDA_TRY(scratch.alloc(&cs.pmax, n * sizeof(unsigned long long)));
+    }
     return ANOVA_OK;
 }
 
-// mean (and lo, hi when given) of every column: one read of X
-anova_status col_mean(const double* X, int64_t N, int d, int64_t ld, const ColStats& cs, double* mean, double* lo,
-                      double* hi, cudaStream_t st) {
-    k_col_partials<<<cs.nblk, kThreads, partial_smem(d), st>>>(X, N, d, ld, nullptr, 0, cs.rows, cs.psum, cs.pmin,
-                                                               cs.pmax);
-    k_col_totals<<<d, kThreads, 0, st>>>(cs.psum, cs.pmin, cs.pmax, cs.nblk, d, N, 0, mean, lo, hi);
+// one read of X: mean and sd (kMoments) or lo and hi (kRange) of every column
+template <int MODE>
+anova_status col_stats(const double* X, int64_t N, int d, int64_t ld, const ColStats& cs, double* out0,
+                       double* out1, cudaStream_t st) {
+    k_col_partials<MODE><<<cs.nblk, kThreads, partial_smem(d), st>>>(X, N, d, ld, cs.rows, cs.pS, cs.pQ, cs.pK,
+                                                                     cs.pmin, cs.pmax);
+    k_col_totals<MODE><<<d, kThreads, 0, st>>>(cs.pS, cs.pQ, cs.pK, cs.pmin, cs.pmax, cs.nblk, d, N, cs.rows, out0,
+                                               out1);
+    ANOVA_CHECK_LAUNCH();
+    return ANOVA_OK;
+}
+
+// per-column thresholds of the fine bins (and their FP32 screens) from one read of X
+struct FineBins {
+    double *lo = nullptr, *hi = nullptr;
+    unsigned long long* thr = nullptr;
+    float2* screen = nullptr;
+};
+
+anova_status fine_bins_setup(const double* X, int64_t N, int d, int64_t ld, const ColStats& cs, FineBins& fb,
+                             Scratch& scratch, cudaStream_t st) {
+    ANOVA_CUDA_TRY(scratch.alloc(&fb.lo, d * sizeof(double)));
+    ANOVA_CUDA_TRY(scratch.alloc(&fb.hi, d * sizeof(double)));
+    ANOVA_CUDA_TRY(scratch.alloc(&fb.thr, (size_t)d * kThrRow * sizeof(unsigned long long)));
+    ANOVA_CUDA_TRY(scratch.alloc(&fb.screen, d * sizeof(float2)));
+    ANOVA_TRY(col_stats<kRange>(X, N, d, ld, cs, fb.lo, fb.hi, st));
+    k_fine_thresholds<<<dim3((kThrRow + kThreads - 1) / kThreads, d), kThreads, 0, st>>>(fb.lo, fb.hi, d, fb.thr,
+                                                                                         fb.screen);
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
 }
@@ -362,13 +736,9 @@ anova_status anova_zscore_fit(const double* X, int64_t N, int32_t d, int64_t ld,
     cudaStream_t st = (cudaStream_t)stream;
     Scratch scratch(st);
     ColStats cs;
-    ANOVA_TRY(col_alloc(N, d, cs, scratch));
-    ANOVA_TRY(col_mean(X, N, d, ld, cs, mean, nullptr, nullptr, st));
-    // second pass: sums of squared deviations from the mean (the two-pass form)
-    k_col_partials<<<cs.nblk, kThreads, partial_smem(d), st>>>(X, N, d, ld, mean, 1, cs.rows, cs.psum, nullptr,
-                                                               nullptr);
-    k_col_totals<<<d, kThreads, 0, st>>>(cs.psum, nullptr, nullptr, cs.nblk, d, N, 1, sd, nullptr, nullptr);
-    ANOVA_CHECK_LAUNCH();
+    ANOVA_TRY(col_alloc(N, d, kMoments, cs, scratch));
+    // one pass: shifted block sums, combined over blocks by the pairwise update
+    ANOVA_TRY(col_stats<kMoments>(X, N, d, ld, cs, mean, sd, st));
     return ANOVA_OK;
 }
 
@@ -398,33 +768,59 @@ anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const 
     cudaStream_t st = (cudaStream_t)stream;
     Scratch scratch(st);
     ColStats cs;
-    double *mean = nullptr, *lo = nullptr, *hi = nullptr;
-    unsigned int* hist = nullptr;
-    unsigned char* qmap = nullptr;
+    FineBins fb;
     unsigned long long *joint = nullptr, *bad = nullptr;
     const size_t cells = (size_t)d * bins * nclass;
-    ANOVA_TRY(col_alloc(N, d, cs, scratch));
-    ANOVA_CUDA_TRY(scratch.alloc(&mean, d * sizeof(double)));
-    ANOVA_CUDA_TRY(scratch.alloc(&lo, d * sizeof(double)));
-    ANOVA_CUDA_TRY(scratch.alloc(&hi, d * sizeof(double)));
-    ANOVA_CUDA_TRY(scratch.alloc(&hist, (size_t)d * kFine * sizeof(unsigned int)));
-    ANOVA_CUDA_TRY(scratch.alloc(&qmap, (size_t)d * kFine));
+    ANOVA_TRY(col_alloc(N, d, kRange, cs, scratch));
     ANOVA_CUDA_TRY(scratch.alloc(&joint, (cells + 1) * sizeof(unsigned long long)));
     bad = joint + cells;
-    ANOVA_TRY(col_mean(X, N, d, ld, cs, mean, lo, hi, st));
-    std::vector<unsigned long long> hj(cells + 1);
-    ANOVA_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)d * kFine * sizeof(unsigned int), st));
+    ANOVA_TRY(fine_bins_setup(X, N, d, ld, cs, fb, scratch, st));
     ANOVA_CUDA_TRY(cudaMemsetAsync(joint, 0, (cells + 1) * sizeof(unsigned long long), st));
-    k_fine_hist<<<cs.nblk, kThreads, 0, st>>>(X, N, d, ld, lo, hi, cs.rows, hist);
-    k_quantile_map<<<d, 1024, 0, st>>>(hist, N, bins, qmap);
-    static bool attr = [] {
-        cudaFuncSetAttribute(k_joint, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        return true;
-    }();
-    (void)attr;
-    k_joint<<<cs.nblk, kThreads, cells * sizeof(unsigned int), st>>>(X, N, d, ld, lo, hi, qmap, labels, bins, nclass,
-                                                                    cs.rows, joint, bad);
+    // two passes over X (privatised (fine bin, class) counts) where they fit, else three
+    const int W = (nclass + 1) / 2;
+    const int sms = device_sms();
+    const int gmax = std::max(1, (int)(kCHSmem / ((size_t)kFine * W * sizeof(unsigned int))));
+    const int ngroups = (d + gmax - 1) / gmax;
+    const int gcols = (d + ngroups - 1) / ngroups;
+    int64_t nranges = std::max<int64_t>((N + kCHMaxRows - 1) / kCHMaxRows,
+                                        std::min<int64_t>((2 * sms + ngroups - 1) / ngroups, (N + 4095) / 4096));
+    nranges = std::max<int64_t>(nranges, 1);
+    const int64_t rows_pb = (N + nranges - 1) / nranges;
+    nranges = (N + rows_pb - 1) / rows_pb;
+    const size_t slot = (size_t)gcols * kFine * W;
+    const size_t part_bytes = (size_t)nranges * ngroups * slot * sizeof(unsigned int);
+    if (nclass <= 4 && part_bytes <= kCHPartMax && nranges * ngroups <= INT32_MAX) {
+        unsigned int *part = nullptr, *chist = nullptr;
+        ANOVA_CUDA_TRY(scratch.alloc(&part, part_bytes));
+        ANOVA_CUDA_TRY(scratch.alloc(&chist, (size_t)d * kFine * nclass * sizeof(unsigned int)));
+        static bool attr2 = [] {
+            cudaFuncSetAttribute(k_fine_class_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCHSmem);
+            return true;
+        }();
+        (void)attr2;
+        k_fine_class_hist<<<(unsigned)(nranges * ngroups), kCHThreads, slot * sizeof(unsigned int), st>>>(
+            X, N, d, ld, fb.thr, fb.screen, labels, nclass, gcols, ngroups, rows_pb, part, bad);
+        k_class_hist_reduce<<<grid_for((int64_t)d * kFine * W, kThreads, 8 * sms), kThreads, 0, st>>>(
+            part, d, nclass, gcols, ngroups, (int)nranges, chist);
+        k_quantile_joint<<<d, 1024, 0, st>>>(chist, N, bins, nclass, joint);
+    } else {
+        unsigned int* hist = nullptr;
+        unsigned char* qmap = nullptr;
+        ANOVA_CUDA_TRY(scratch.alloc(&hist, (size_t)d * kFine * sizeof(unsigned int)));
+        ANOVA_CUDA_TRY(scratch.alloc(&qmap, (size_t)d * kFine));
+        ANOVA_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)d * kFine * sizeof(unsigned int), st));
+        k_fine_hist<<<cs.nblk, kThreads, 0, st>>>(X, N, d, ld, fb.thr, fb.screen, cs.rows, hist);
+        k_quantile_map<<<d, 1024, 0, st>>>(hist, N, bins, qmap);
+        static bool attr = [] {
+            cudaFuncSetAttribute(k_joint, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            return true;
+        }();
+        (void)attr;
+        k_joint<<<cs.nblk, kThreads, cells * sizeof(unsigned int), st>>>(X, N, d, ld, fb.thr, fb.screen, qmap, labels,
+                                                                        bins, nclass, cs.rows, joint, bad);
+    }
     ANOVA_CHECK_LAUNCH();
+    std::vector<unsigned long long> hj(cells + 1);
     ANOVA_CUDA_TRY(cudaMemcpyAsync(hj.data(), joint, (cells + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                    st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -449,6 +845,22 @@ anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const 
             }
         mis[c] = v;
     }
+    return ANOVA_OK;
+}
+
+anova_status anova_mis_fine_bins(const double* X, int64_t N, int32_t d, int64_t ld, int32_t* bins, void* stream) {
+    if (!shapes_ok(X, N, d, ld) || !bins) {
+        set_error("anova_mis_fine_bins: need N >= 1, 1 <= d <= 2048, ld >= d and device pointers");
+        return ANOVA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch scratch(st);
+    ColStats cs;
+    FineBins fb;
+    ANOVA_TRY(col_alloc(N, d, kRange, cs, scratch));
+    ANOVA_TRY(fine_bins_setup(X, N, d, ld, cs, fb, scratch, st));
+    k_fine_bins_out<<<cs.nblk, kThreads, 0, st>>>(X, N, d, ld, fb.thr, fb.screen, cs.rows, bins);
+    ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
 }
 
