@@ -316,12 +316,20 @@ def dominant_roofline(B, plan, w, stage_ms, stage_la, steps):
             "stage_ms_per_step": {k: v / steps for k, v in stage_ms.items()}}
 
 
+_DIRECT = {}
+
+
 def accuracy_vs_direct(B, torch, np, X, w, out, rows_n, seed, dev):
-    """Relative 2-norm error of the FP32 product against the FP64 direct sum on sampled rows."""
+    """Relative 2-norm error of the FP32 product against the FP64 direct sum on sampled rows
+    (the direct sums are computed once per workload, rows and seed)."""
     rows = torch.from_numpy(np.sort(np.random.default_rng(seed).choice(w.N, rows_n, replace=False))).to(dev)
-    dref = torch.empty(rows_n, dtype=torch.float64, device=dev)
-    B.anova_direct_matvec(X[rows].contiguous(), X, w.windows, w.ell, torch.from_numpy(w.alpha).to(dev), dref,
-                          dtype=B.FP64)
+    key = (w.name, rows_n, seed)
+    if key not in _DIRECT:
+        dref = torch.empty(rows_n, dtype=torch.float64, device=dev)
+        B.anova_direct_matvec(X[rows].contiguous(), X, w.windows, w.ell, torch.from_numpy(w.alpha).to(dev), dref,
+                              dtype=B.FP64)
+        _DIRECT[key] = dref
+    dref = _DIRECT[key]
     torch.cuda.synchronize()
     err = (torch.linalg.norm(out.double()[rows] - dref) / torch.linalg.norm(dref)).item()
     return {"rel_err_vs_direct": err, "sample_rows": rows_n, "direct": "anova_direct_matvec FP64",
@@ -362,7 +370,7 @@ def run_ours(args):
     # the CPU baseline runs before any kernel work (rank 0, N = 1 only)
     cpu = cpu_baseline(args.cpu_sample) if (rank == 0 and ws == 1 and not args.skip_cpu) else None
 
-    w = W.precision_form(seed=2 + rank)
+    w = W.precision_form(N=args.points, seed=2 + rank)
     N = w.N
     X = torch.from_numpy(w.X).to(dev)
     # bin sides per window dimension from the library's autotuner (outside any timed region)
@@ -373,8 +381,12 @@ def run_ours(args):
                                          precision=B.FP32, reps=5)
     else:
         sides = [0, 0, 0]
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter()
     plan = B.anova_fastsum_plan_bins(X, w.windows, w.ell, sides, n=w.n, m=w.m, sigma=w.sigma, eps_B=w.epsB, p=w.p,
                                      precision=B.MIXED)
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t_plan) * 1e3
     alpha = torch.from_numpy(w.alpha).to(dev).float()
     out = torch.empty_like(alpha)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -399,6 +411,21 @@ def run_ours(args):
 
     B.anova_matvec(plan, alpha, out)
     accuracy = accuracy_vs_direct(B, torch, np, X, w, out, args.check_rows, 7, dev)
+
+    # the same product with the 3-D spread and gather on FP32 FMA kernels (no tensor cores), for comparison
+    fsteps = max(5, args.steps // 2)
+    B.anova_plan_set_tensor_cores(plan, False)
+    fma_ms = time_matvec(B, plan, alpha, out, flush, fsteps, args.warmup, stream)
+    fma_stage, _ = stage_profile(B, plan, alpha, out, flush, fsteps)
+    fma_names = B.anova_dense3_kernels(plan)
+    B.anova_matvec(plan, alpha, out)
+    fma_acc = accuracy_vs_direct(B, torch, np, X, w, out, args.check_rows, 7, dev)
+    B.anova_plan_set_tensor_cores(plan, True)
+    no_tensor = {"ms_per_matvec": statistics.median(fma_ms), "gpts": N / statistics.median(fma_ms) / 1e6,
+                 "spread_3d_kernel_ms": fma_stage["spread_3d_kernel"],
+                 "gather_3d_kernel_ms": fma_stage["gather_3d_kernel"],
+                 "kernels": fma_names, "rel_err_vs_direct": fma_acc["rel_err_vs_direct"],
+                 "what": "3-D spread and gather on FP32 FMA kernels (anova_plan_set_tensor_cores off), same plan"}
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     a_host = torch.from_numpy(w.alpha.astype(np.float32)).pin_memory()
@@ -478,11 +505,15 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg,
                 "plan": {"bin_side_1d_2d_3d": sides,
-                         "bin_sides": "given" if args.bin_side else ("autotuned" if not args.no_autotune else "rule")},
+                         "bin_sides": "given" if args.bin_side else ("autotuned" if not args.no_autotune else "rule"),
+                         "create_ms": plan_ms,
+                         "create_note": "anova_fastsum_plan_bins (frames, binning, D_k, FP32 weight tables, "
+                                        "FP64 data), wall clock, outside the timed steps"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": 4 * N,
                         "d2h_bytes_per_step": 4 * N},
-                "gpu_launches": launches, "latency_ms": lat, "accuracy": accuracy, "krr": krr,
+                "gpu_launches": launches, "latency_ms": lat, "accuracy": accuracy, "no_tensor_cores": no_tensor,
+                "krr": krr,
                 "plain_mid": mid,
                 "clocks": dict(clk.summary(), window="0.6 s busy lead-in, timed steps, profiled steps, e2e steps "
                                                      "and the KRR solve of the headline workload")}
@@ -944,6 +975,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--check-rows", type=int, default=10_000)
     ap.add_argument("--skip-mid", action="store_true", help="no secondary mid-workload figures")
+    ap.add_argument("--points", type=int, default=1_000_000,
+                    help="points of the headline workload (1e6 = the precision form; smaller only for profiler "
+                         "captures of the same kernels)")
     ap.add_argument("--no-autotune", action="store_true", help="bin sides from the default rule")
     ap.add_argument("--bin-side", default="", help="bin sides for 1-D,2-D,3-D windows (e.g. 0,0,4), no autotuning")
     ap.add_argument("--crossover", action="store_true",

@@ -138,7 +138,10 @@ anova_status anova_autotune_bins(const double* points, int64_t N, int32_t d, int
  * (cudaDeviceSynchronize, torch.cuda.synchronize): CUDA refuses that while any
  * stream captures.  Multi-threaded callers switch capture off with
  * anova_plan_set_graphs.  Calls on one plan must not overlap on the GPU: they
- * share the plan's work buffers.
+ * share the plan's work buffers.  The call does not wait for its kernels, so a
+ * bounded wait that gave up inside one (the result is then invalid) shows only
+ * in anova_wait_timeouts; the synchronous calls below compare that counter
+ * and return ETIMEOUT.
  * Errors: EINVAL.
  */
 anova_status anova_matvec(anova_plan* plan, int32_t dtype, const void* alpha, void* out,
@@ -180,7 +183,8 @@ anova_status krr_cg_solve(anova_plan* plan, double lambda, const double* y, doub
  * together (the kernel is shift- and scale-invariant in user units), so the
  * call still returns ANOVA_OK.  Synchronises `stream`; allocates its scratch
  * stream-ordered.  Errors: EINVAL (M < 0 or M >= 2^31, ldz < d, missing
- * pointers), ECUDA (a failed allocation included).
+ * pointers), ECUDA (a failed allocation included), ETIMEOUT (a bounded wait
+ * inside a kernel gave up during the call; out is not to be trusted).
  */
 anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z, int64_t M,
                          int64_t ldz, double* out, void* stream);
@@ -271,6 +275,13 @@ anova_status anova_zscore_apply(double* X, int64_t N, int32_t d, int64_t ld, con
 anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const int32_t* labels, int32_t nclass,
                        int32_t bins, double* mis, void* stream);
 
+/* anova_mis_fine_bins -- the fine bin floor((v - lo) 4096 / (hi - lo)) (last
+ * bin closed, lo / hi the column's minimum and maximum) of every element of X,
+ * the integer intermediate of anova_mis, into bins (device, N x d int32,
+ * row-major, row stride d).  Asynchronous on `stream`.  Errors: EINVAL (shapes
+ * as anova_zscore_fit, missing pointers), ENOMEM, ECUDA. */
+anova_status anova_mis_fine_bins(const double* X, int64_t N, int32_t d, int64_t ld, int32_t* bins, void* stream);
+
 /*
  * anova_windows_from_mis -- Sec. 5's grouping: features ranked by score
  * (descending, equal scores by index), scores below `threshold` dropped, the
@@ -305,7 +316,7 @@ anova_status krr_model_create(anova_plan* plan, const double* alpha, void* strea
  * and allocate their own scratch (stream-ordered).  A call whose test points
  * leave the plan's ball in some window runs krr_predict (re-framed) on the
  * plan's grids instead, one such call per model at a time.
- * Errors: EINVAL, ECUDA.
+ * Errors: EINVAL, ECUDA, ETIMEOUT (as krr_predict).
  */
 anova_status krr_model_predict(krr_model* model, const double* Z, int64_t M, int64_t ldz, double* out,
                                void* stream);
@@ -365,7 +376,8 @@ anova_status anova_batch_matvec(anova_batch* batch, const double* x, double* y, 
  * rounding).  Systems that stop iterate no more (their kernels exit at once).
  * Returns ENOCONV if a system stopped short of tol, EINVAL for a NULL batch,
  * lambda, y or alpha, y aliasing alpha, tol <= 0 or maxit < 1, ECUDA if a CUDA
- * call fails.  Synchronous on `stream`; the iteration is
+ * call fails, ETIMEOUT if a bounded wait inside a kernel gave up during the
+ * call (alpha is then not to be trusted).  Synchronous on `stream`; the iteration is
  * captured as a CUDA graph on the second block of iterations (same caveat as
  * anova_matvec on device-wide synchronisation from other threads).
  */
@@ -622,6 +634,15 @@ anova_status anova_plan_dense3_kernels(const anova_plan* plan, const char** spre
  * no counterpart: this is a launch-overhead setting.  Errors: EINVAL (NULL
  * plan). */
 anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable);
+
+/* anova_plan_set_tensor_cores -- run the plan's FP32 3-D spread and gather on
+ * tensor cores (enable != 0, the default: the contraction of a bin's nodes
+ * into its region, and the region against the nodes' weights, as 3xTF32
+ * mma.sync / tcgen05 products with FP32 accuracy) or on FP32 FMA kernels
+ * (enable = 0), e.g. to compare the two.  The 1-D / 2-D kernels and batches
+ * are not affected.  Drops the plan's captured graphs.  Must not overlap with
+ * other calls on the plan.  Errors: EINVAL (NULL plan). */
+anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@ _SIGNATURES = {
     "anova_direct_matvec": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _pi32, _i32, _pf64, _f64, _i32, _vp,
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
+    "anova_plan_set_tensor_cores": (_i32, [_vp, _i32]),
     "anova_fastsum_plan_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
                                        _i32, _i32, _pi32, _vp, ctypes.POINTER(_vp)]),
     "anova_autotune_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
@@ -47,6 +48,7 @@ _SIGNATURES = {
     "anova_zscore_fit": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_zscore_apply": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp, _vp]),
     "anova_mis": (_i32, [_vp, _i64, _i32, _i64, _vp, _i32, _i32, _pf64, _vp]),
+    "anova_mis_fine_bins": (_i32, [_vp, _i64, _i32, _i64, _vp, _vp]),
     "anova_windows_from_mis": (_i32, [_pf64, _i32, _f64, _pi32, _pi32]),
     "anova_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "anova_batch_layout": (_i32, [_vp, _pi64]),
@@ -328,6 +330,10 @@ def anova_plan_set_graphs(plan: Plan, enable: bool):
     _check(lib().anova_plan_set_graphs(plan.handle, 1 if enable else 0), "anova_plan_set_graphs")
 
 
+def anova_plan_set_tensor_cores(plan: Plan, enable: bool):
+    _check(lib().anova_plan_set_tensor_cores(plan.handle, 1 if enable else 0), "anova_plan_set_tensor_cores")
+
+
 def anova_stage_times(plan: Plan):
     ms = (ctypes.c_double * 8)()
     la = (ctypes.c_int64 * 8)()
@@ -381,6 +387,16 @@ def anova_mis(X, labels, nclass, bins=16, stream=None):
     out = np.zeros(X.shape[1], dtype=np.float64)
     _check(lib().anova_mis(_ptr(X), X.shape[0], X.shape[1], X.stride(0), _ptr(labels), int(nclass), int(bins),
                            out.ctypes.data_as(_pf64), _stream(stream)), "anova_mis")
+    return out
+
+
+def anova_mis_fine_bins(X, stream=None):
+    """Fine bin (0..4095) of every element of X, the integer intermediate of anova_mis."""
+    import torch
+    _require_cuda(X, "X", torch.float64)
+    out = torch.empty(X.shape, dtype=torch.int32, device=X.device)
+    _check(lib().anova_mis_fine_bins(_ptr(X), X.shape[0], X.shape[1], X.stride(0), _ptr(out), _stream(stream)),
+           "anova_mis_fine_bins")
     return out
 
 

@@ -821,8 +821,8 @@ anova_status anova_batch_matvec(anova_batch* b, const double* x, double* y, void
     return ANOVA_OK;
 }
 
-anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const double* y, double* alpha, double tol,
-                                int32_t maxit, int32_t* iters, double* relres, void* stream) {
+static anova_status batch_cg_solve(anova_batch* b, const double* lambda, const double* y, double* alpha, double tol,
+                                   int32_t maxit, int32_t* iters, double* relres, void* stream) {
     if (!b || !lambda || !y || !alpha || y == alpha || !(tol > 0.0) || maxit < 1) {
         set_error("krr_batch_cg_solve: bad batch, lambda, vectors, tol or maxit");
         return ANOVA_EINVAL;
@@ -958,8 +958,8 @@ static anova_status power_lambda_max(anova_plan* plan, double* v, double* w, dou
     return ANOVA_OK;
 }
 
-anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, const double* y, double* alpha,
-                                        double tol, int32_t maxit, int32_t* iters, double* relres, void* stream) {
+static anova_status batch_cg_solve_refined(anova_batch* b, const double* lambda, const double* y, double* alpha,
+                                           double tol, int32_t maxit, int32_t* iters, double* relres, void* stream) {
     if (!b || !lambda || !y || !alpha || y == alpha || !(tol > 0.0) || maxit < 1) {
         set_error("krr_batch_cg_solve_refined: bad batch, lambda, vectors, tol or maxit");
         return ANOVA_EINVAL;
@@ -1143,6 +1143,22 @@ anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, co
     }
     if (s != ANOVA_OK) return s;
     return all ? ANOVA_OK : ANOVA_ENOCONV;
+}
+
+// The synchronous solves report ETIMEOUT when a bounded wait inside one of
+// their kernels gave up (the device counter moved during the call).
+anova_status krr_batch_cg_solve(anova_batch* b, const double* lambda, const double* y, double* alpha, double tol,
+                                int32_t maxit, int32_t* iters, double* relres, void* stream) {
+    const uint64_t w0 = wait_timeouts_on((cudaStream_t)stream);
+    const anova_status s = batch_cg_solve(b, lambda, y, alpha, tol, maxit, iters, relres, stream);
+    return waits_moved(w0, (cudaStream_t)stream, "krr_batch_cg_solve", s);
+}
+
+anova_status krr_batch_cg_solve_refined(anova_batch* b, const double* lambda, const double* y, double* alpha,
+                                        double tol, int32_t maxit, int32_t* iters, double* relres, void* stream) {
+    const uint64_t w0 = wait_timeouts_on((cudaStream_t)stream);
+    const anova_status s = batch_cg_solve_refined(b, lambda, y, alpha, tol, maxit, iters, relres, stream);
+    return waits_moved(w0, (cudaStream_t)stream, "krr_batch_cg_solve_refined", s);
 }
 
 }  // extern "C"

@@ -340,6 +340,9 @@ anova_status spread3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin
 anova_status dense12_pw(int dA, bool spread, int R, int m, const int4* sub, int nsub, const DenseWin* descs,
                         const float* psi_host, int sms, const void* alpha, int alpha_double, cudaStream_t st);
 uint64_t wait_timeouts_on(cudaStream_t st);
+// s, or ETIMEOUT when the wait counter moved since `before` (the call's result
+// is then invalid); synchronises st
+anova_status waits_moved(uint64_t before, cudaStream_t st, const char* who, anova_status s);
 anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin* descs,
                                      const std::vector<std::array<int, 3>>& groups, cudaStream_t st,
                                      const float* psi_host = nullptr, int sms = 0, bool tc5_3d = false);

@@ -664,8 +664,10 @@ anova_status krr_predict(anova_plan* plan, const double* alpha, const double* Z,
     }
     if (M == 0) return ANOVA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    if (plan->precision & ANOVA_FP64) return predict_t<double>(plan, alpha, Z, M, ldz, out, st);
-    return predict_t<float>(plan, alpha, Z, M, ldz, out, st);
+    const uint64_t w0 = wait_timeouts_on(st);
+    const anova_status s = (plan->precision & ANOVA_FP64) ? predict_t<double>(plan, alpha, Z, M, ldz, out, st)
+                                                          : predict_t<float>(plan, alpha, Z, M, ldz, out, st);
+    return waits_moved(w0, st, "krr_predict", s);
 }
 
 anova_status anova_debug_spread(anova_plan* plan, int32_t l, int32_t dtype, const void* alpha, void* grid,
@@ -694,6 +696,20 @@ anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
         plan->graphs.clear();
     }
+    return ANOVA_OK;
+}
+
+anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable) {
+    if (!plan) return ANOVA_EINVAL;
+    const bool on = enable != 0;
+    plan->spread_tc = on;
+    plan->gather_tc = on;
+    plan->gather_umma = on;
+    plan->gather_tc5 = on;
+    plan->spread_tc5 = false;
+    for (auto& g : plan->graphs)      // the captured launch sequences name the old kernels
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    plan->graphs.clear();
     return ANOVA_OK;
 }
 

@@ -228,7 +228,10 @@ anova_status krr_model_predict(krr_model* md, const double* Z, int64_t M, int64_
     }
     if (M == 0) return ANOVA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    return md->fp64 ? model_predict<double>(md, Z, M, ldz, out, st) : model_predict<float>(md, Z, M, ldz, out, st);
+    const uint64_t w0 = wait_timeouts_on(st);
+    const anova_status s =
+        md->fp64 ? model_predict<double>(md, Z, M, ldz, out, st) : model_predict<float>(md, Z, M, ldz, out, st);
+    return waits_moved(w0, st, "krr_model_predict", s);
 }
 
 void krr_model_destroy(krr_model* md) {

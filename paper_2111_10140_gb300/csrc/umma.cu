@@ -323,6 +323,15 @@ uint64_t wait_timeouts_on(cudaStream_t st) {
     return v;
 }
 
+anova_status waits_moved(uint64_t before, cudaStream_t st, const char* who, anova_status s) {
+    if (s != ANOVA_OK && s != ANOVA_ENOCONV) return s;
+    if (wait_timeouts_on(st) != before) {
+        set_error(std::string(who) + ": a bounded wait inside a kernel gave up; the result is invalid");
+        return ANOVA_ETIMEOUT;
+    }
+    return s;
+}
+
 }  // namespace anova
 
 extern "C" anova_status anova_debug_wait_probe(int32_t polls, void* stream) {

@@ -115,7 +115,7 @@ def precision_form(N=1_000_000, seed=2):
     y = y + 0.05 * rng.standard_normal(N)
     P = len(windows)
     n = [32 if len(w) == 3 else 64 for w in windows]
-    return Workload("precision_N1000000_d28_mixed", X, windows, np.full(P, 1.0 / P), 0.25,
+    return Workload(f"precision_N{N}_d28_mixed", X, windows, np.full(P, 1.0 / P), 0.25,
                     n, 6, 2.0, alpha, y, 1e-2, 1e-8, epsB=0.25,
                     meta={"heavy_tailed": heavy})
 
