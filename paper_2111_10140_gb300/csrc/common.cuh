@@ -192,6 +192,7 @@ struct anova_plan {
     anova::DenseWin* dense_desc = nullptr;  // device, 2 x dense_windows.size(): FP64 then FP32
     float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
+    bool spread_pipe = true;            // ... with the next chunk's rows copied (cp.async) during the current MMAs
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
     bool gather_tc5 = true;             // FP32 dense 3-D gather: persistent tcgen05 kernel, weights on the fly

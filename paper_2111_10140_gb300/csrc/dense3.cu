@@ -595,6 +595,160 @@ k_spread3_tc(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, i
     }
 }
 
+// The same spread with the staging pipelined: while the MMAs of chunk k run,
+// cp.async copies chunk k + 1's weight-table rows and coefficients into the
+// other of two shared buffers (raw rows: x weights 0..15, y 16..31, z 32..47).
+// Per chunk: wait for its copies, one barrier, start the next chunk's copies,
+// form (alpha wz) as TF32 head and tail, a second barrier, the MMAs.  The
+// node permutation is read one chunk ahead into a register, so the coefficient
+// copy (through the permutation) does not wait for it.
+constexpr int kTpPitch = 56;   // floats per staged row: 224 bytes, conflict-free fragment reads
+
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * (R / 2), (R <= 14 ? 5 : 4))
+k_spread3_tcp(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, int m,
+              const void* __restrict__ alpha = nullptr, int alpha_double = 0) {
+    static_assert(R <= kPitch && R % 2 == 0, "even region up to 16");
+    constexpr int NW = R / 2;
+    constexpr int NT = 32 * NW;
+    __shared__ __align__(16) float raw[2][kSpreadChunk][kTpPitch];
+    __shared__ __align__(16) double sal[2][kSpreadChunk];             // coefficients as copied (FP32 or FP64)
+    __shared__ __align__(16) uint32_t szh[kSpreadChunk][kTcPitch];   // alpha wz, TF32 head
+    __shared__ __align__(16) uint32_t szl[kSpreadChunk][kTcPitch];   // and tail
+    const int4 sp = sub[blockIdx.x];
+    const DenseWin W = descs[sp.w];
+    if (W.live && !*W.live) return;   // a batch system that has stopped
+    float* __restrict__ grid = static_cast<float*>(W.grid);
+    const int nos = W.nos, Tb = W.Tb, nb = W.nb;
+    const int bz = sp.x % nb, by = (sp.x / nb) % nb, bx = sp.x / (nb * nb);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const bool dbl = alpha && alpha_double;
+    // copies of chunk [first, first + cnt) into buffer b; `pm` is the permutation entry of node
+    // first + tid (tid < cnt) when the coefficients come through the permutation
+    auto stage = [&](int b, int first, int32_t pm) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        for (int i = tid; i < cnt * 12; i += NT) {
+            const int p = i / 12, k = i % 12;
+            cp_async_16(&raw[b][p][4 * k], W.wtab + ((int64_t)sp.y + first + p) * 48 + 4 * k);
+        }
+        if (tid < cnt) {
+            const int64_t pos = (int64_t)sp.y + first + tid;
+            if (!alpha) cp_async_4(&sal[b][tid], W.asort + pos);
+            else if (dbl) cp_async_8(&sal[b][tid], static_cast<const double*>(alpha) + pm);
+            else cp_async_4(&sal[b][tid], static_cast<const float*>(alpha) + pm);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto perm_of = [&](int first) -> int32_t {
+        return (alpha && first + tid < sp.z && tid < kSpreadChunk) ? W.perm[(int64_t)sp.y + first + tid] : 0;
+    };
+    float acc[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
+    stage(0, 0, perm_of(0));
+    int32_t pnext = perm_of(kSpreadChunk);
+    int b = 0;
+    for (int first = 0; first < sp.z; first += kSpreadChunk, b ^= 1) {
+        const int cnt = min(kSpreadChunk, sp.z - first);
+        const int cnt8 = (cnt + 7) & ~7;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();          // chunk `first` is in buffer b; the MMAs of the previous chunk are done
+        if (first + kSpreadChunk < sp.z) {
+            stage(b ^ 1, first + kSpreadChunk, pnext);
+            pnext = perm_of(first + 2 * kSpreadChunk);
+        }
+        for (int i = tid; i < cnt8 * 16; i += NT) {
+            const int p = i >> 4, e = i & 15;
+            uint32_t hi = 0u, lo = 0u;
+            if (p < cnt) {
+                const float al = dbl ? (float)sal[b][p] : reinterpret_cast<const float*>(&sal[b][p])[0];
+                tf32_split_fast(al * raw[b][p][32 + e], hi, lo);
+            } else {
+                raw[b][p][e] = 0.f;
+                raw[b][p][16 + e] = 0.f;
+            }
+            szh[p][e] = hi;
+            szl[p][e] = lo;
+        }
+        __syncthreads();
+        for (int p0 = 0; p0 < cnt8; p0 += 8) {
+            const int pa = p0 + t, pb = p0 + t + 4;
+            const float y0 = raw[b][pa][16 + g], y1 = raw[b][pa][24 + g], y2 = raw[b][pb][16 + g],
+                        y3 = raw[b][pb][24 + g];
+            uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                bh[nt][0] = szh[pa][8 * nt + g];
+                bl[nt][0] = szl[pa][8 * nt + g];
+                bh[nt][1] = szh[pb][8 * nt + g];
+                bl[nt][1] = szl[pb][8 * nt + g];
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int a = 2 * warp + i;
+                const float x0 = raw[b][pa][a], x1 = raw[b][pb][a];
+                uint32_t ah[4], alo[4];
+                tf32_split_fast(x0 * y0, ah[0], alo[0]);
+                tf32_split_fast(x0 * y1, ah[1], alo[1]);
+                tf32_split_fast(x1 * y2, ah[2], alo[2]);
+                tf32_split_fast(x1 * y3, ah[3], alo[3]);
+#pragma unroll
+                for (int nt = 0; nt < 2; nt++) {
+                    mma_tf32(acc[i][nt], ah, bh[nt][0], bh[nt][1]);
+                    mma_tf32(acc[i][nt], ah, bl[nt][0], bl[nt][1]);
+                    mma_tf32(acc[i][nt], alo, bh[nt][0], bh[nt][1]);
+                }
+            }
+        }
+    }
+    // flush as in k_spread3_tc
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(grid) & 7) == 0;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int a = 2 * warp + i;
+        const int ga = wrap_idx(Tb * bx - m + a, nos);
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int bb = g + 8 * h;
+                const int c = 8 * nt + 2 * t;
+                if (bb < R && c < R) {
+                    const int row = (ga * nos + wrap_idx(Tb * by - m + bb, nos)) * nos;
+                    const int gc = wrap_idx(Tb * bz - m + c, nos);
+                    const float v0 = acc[i][nt][2 * h], v1 = acc[i][nt][2 * h + 1];
+                    if (vec_ok && (gc & 1) == 0 && gc + 1 < nos) {
+                        atomicAdd(reinterpret_cast<float2*>(&grid[row + gc]), make_float2(v0, v1));
+                    } else {
+                        atomicAdd(&grid[row + gc], v0);
+                        atomicAdd(&grid[row + wrap_idx(Tb * bz - m + c + 1, nos)], v1);
+                    }
+                }
+            }
+    }
+}
+
 // ------------------------------------------------- tensor-core gather (TF32)
 // Per warp, 16 nodes j of the bin: U[j][(a,b)] = sum_c wz_j[c] h[a][b][c] on
 // mma.sync m16n8k8 TF32 (A = the nodes' z weights, B = rows of the staged
@@ -1027,6 +1181,16 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
     if (plan->spread_tc5 && tc5_supported(R, plan->m))
         return spread3_tc5(R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count, alpha, alpha_double,
                            st);
+    if (plan->spread_tc && plan->spread_pipe) {
+        switch (R) {
+#define ANOVA_SPREAD_TCP(R_) \
+    case R_: k_spread3_tcp<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, plan->m, alpha, alpha_double); ANOVA_CHECK_LAUNCH(); return ANOVA_OK;
+            ANOVA_SPREAD_TCP(4) ANOVA_SPREAD_TCP(6) ANOVA_SPREAD_TCP(8) ANOVA_SPREAD_TCP(10) ANOVA_SPREAD_TCP(12)
+            ANOVA_SPREAD_TCP(14) ANOVA_SPREAD_TCP(16)
+#undef ANOVA_SPREAD_TCP
+            default: break;
+        }
+    }
     if (plan->spread_tc) {
         switch (R) {
 #define ANOVA_SPREAD_TC(R_) \
@@ -1100,7 +1264,7 @@ anova_status dense_f32_spread_groups(int m, const int4* sub_base, const DenseWin
             ANOVA_TRY(spread3_tc5(R_, m, sub, nsub, descs, psi_host, sms, nullptr, 0, st));   \
             continue;                                                                         \
         }                                                                                     \
-        k_spread3_tc<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, m); break;
+        k_spread3_tcp<R_><<<nsub, 32 * (R_ / 2), 0, st>>>(sub, descs, m); break;
             ANOVA_S(4) ANOVA_S(6) ANOVA_S(8) ANOVA_S(10) ANOVA_S(12) ANOVA_S(14) ANOVA_S(16)
 #undef ANOVA_S
             default: set_error("dense FP32 spread: unsupported window dimension or region size"); return ANOVA_EINVAL;
@@ -1256,6 +1420,7 @@ static int region3(const anova_plan* plan, int* nsub = nullptr) {
 // kernel names of the FP32 3-D spread and gather the plan launches ("<R>" = region size)
 static const char* spread3_name(const anova_plan* plan) {
     if (plan->spread_tc5 && tc5_supported(region3(plan), plan->m)) return "k_spread3_tc5<R>";
+    if (plan->spread_tc && plan->spread_pipe) return "k_spread3_tcp<R>";
     return plan->spread_tc ? "k_spread3_tc<R>" : "k_spread3_f32<R>";
 }
 static const char* gather3_name(const anova_plan* plan) {

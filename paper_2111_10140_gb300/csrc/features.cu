@@ -396,13 +396,17 @@ __device__ __forceinline__ float approx_float(double v) {
 
 // fine bin of v from the thresholds of its column: an FP32 estimate, then
 // moved until thr_j <= key(v) < thr_{j+1} (exact; each loop ends within F steps)
-__device__ __forceinline__ int fine_bin(double v, const unsigned long long* __restrict__ thr, float2 scr) {
-    const unsigned long long key = ord_of(v);
+__device__ __forceinline__ int screen_bin(double v, float2 scr) {
     const float t = (approx_float(v) - scr.x) * scr.y;
-    int j = (int)fminf(fmaxf(t, 0.0f), (float)(kFine - 1));
+    return (int)fminf(fmaxf(t, 0.0f), (float)(kFine - 1));
+}
+__device__ __forceinline__ int fix_bin(unsigned long long key, int j, const unsigned long long* __restrict__ thr) {
     while (j > 0 && key < __ldg(thr + j)) j--;
     while (j < kFine - 1 && key >= __ldg(thr + j + 1)) j++;
     return j;
+}
+__device__ __forceinline__ int fine_bin(double v, const unsigned long long* __restrict__ thr, float2 scr) {
+    return fix_bin(ord_of(v), screen_bin(v, scr), thr);
 }
 
 // fine bin of every element (anova_mis_fine_bins), elements owned as in
@@ -556,14 +560,33 @@ k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
     if (threadIdx.x < per * gc) {
         const unsigned long long* __restrict__ tc = thr + (size_t)c * kThrRow;
         const float2 scr = screen[c];
-        for (int64_t r = r0 + threadIdx.x / gc; r < r1; r += per) {
-            const int y = labels[r];
-            if (y < 0 || y >= nclass) {
-                if (g == 0 && cl == 0) nbad++;
-                continue;
+        // four rows per step: their loads, then their two threshold loads each, are in flight together
+        constexpr int U = 4;
+        for (int64_t r = r0 + threadIdx.x / gc; r < r1; r += U * per) {
+            double v[U];
+            int y[U], j[U];
+            unsigned long long key[U], tl[U], th[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t ru = r + (int64_t)u * per;
+                const bool in = ru < r1;
+                y[u] = in ? labels[ru] : -1;
+                v[u] = in ? X[ru * ld + c] : 0.0;
+                if (in && (y[u] < 0 || y[u] >= nclass) && g == 0 && cl == 0) nbad++;
             }
-            const int j = fine_bin(X[r * ld + c], tc, scr);
-            atomicAdd(&sh[(cl * kFine + j) * W + (y >> 1)], 1u << (16 * (y & 1)));
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                key[u] = ord_of(v[u]);
+                j[u] = screen_bin(v[u], scr);
+                tl[u] = __ldg(tc + j[u]);
+                th[u] = __ldg(tc + j[u] + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (y[u] < 0 || y[u] >= nclass) continue;
+                if (key[u] < tl[u] || key[u] >= th[u]) j[u] = fix_bin(key[u], j[u], tc);
+                atomicAdd(&sh[(cl * kFine + j[u]) * W + (y[u] >> 1)], 1u << (16 * (y[u] & 1)));
+            }
         }
     }
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
@@ -627,17 +650,29 @@ k_quantile_joint(const unsigned int* __restrict__ hist, int64_t N, int B, int nc
         __syncthreads();
     }
     long long C = part[threadIdx.x] - local;        // count below this thread's first fine bin
+    // the thread's bins in order: q(j) is non-decreasing, so counts are summed over a run
+    // of equal q and added once per run
+    long long qrun = -1;
+    unsigned long long run[4] = {0ull, 0ull, 0ull, 0ull};
     for (int k = 0; k < per; k++) {
         const int j = threadIdx.x * per + k;
         long long q = ((long long)B * (2 * C + cnt[k])) / (2 * N);
         if (q > B - 1) q = B - 1;
-        if (cnt[k] > 0)
-            for (int y = 0; y < nclass; y++) {
-                const unsigned int v = h[(size_t)j * nclass + y];
-                if (v) atomicAdd(&sj[q * nclass + y], (unsigned long long)v);
+        if (cnt[k] > 0) {
+            if (q != qrun) {
+                if (qrun >= 0)
+                    for (int y = 0; y < nclass; y++)
+                        if (run[y]) atomicAdd(&sj[qrun * nclass + y], run[y]);
+                qrun = q;
+                for (int y = 0; y < 4; y++) run[y] = 0ull;
             }
+            for (int y = 0; y < nclass; y++) run[y] += h[(size_t)j * nclass + y];
+        }
         C += cnt[k];
     }
+    if (qrun >= 0)
+        for (int y = 0; y < nclass; y++)
+            if (run[y]) atomicAdd(&sj[qrun * nclass + y], run[y]);
     __syncthreads();
     for (int i = threadIdx.x; i < B * nclass; i += blockDim.x) joint[(size_t)c * B * nclass + i] = sj[i];
 }
