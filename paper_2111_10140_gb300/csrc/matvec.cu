@@ -80,6 +80,41 @@ k_window_sum(const Tin* __restrict__ tmp, const double* __restrict__ eta, int P,
     }
 }
 
+// FP32 operator: out_i = sum_l eta_l tmp_l[i] in FP32 (the weights rounded to
+// FP32 once per thread), four elements per step when `vec` (N a multiple of 4,
+// tmp and out 16-byte aligned).
+// The FP64 form above converts every term to FP64, which on this GPU's FP64
+// rate costs more than the memory traffic.
+__global__ void __launch_bounds__(kThreads)
+k_window_sum_f32(const float* __restrict__ tmp, const double* __restrict__ eta, int P, int64_t N,
+                 float* __restrict__ out, int vec) {
+    __shared__ float e[64];
+    for (int l = threadIdx.x; l < 64; l += blockDim.x) e[l] = l < P ? (float)eta[l] : 0.f;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (vec && P <= 64) {
+        const int64_t N4 = N >> 2;
+        for (int64_t i = t0; i < N4; i += stride) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int l = 0; l < P; l++) {
+                const float4 v = reinterpret_cast<const float4*>(tmp + (int64_t)l * N)[i];
+                acc.x = fmaf(e[l], v.x, acc.x);
+                acc.y = fmaf(e[l], v.y, acc.y);
+                acc.z = fmaf(e[l], v.z, acc.z);
+                acc.w = fmaf(e[l], v.w, acc.w);
+            }
+            reinterpret_cast<float4*>(out)[i] = acc;
+        }
+        return;
+    }
+    for (int64_t i = t0; i < N; i += stride) {
+        float acc = 0.f;
+        for (int l = 0; l < P; l++) acc = fmaf(l < 64 ? e[l] : (float)eta[l], tmp[(int64_t)l * N + i], acc);
+        out[i] = acc;
+    }
+}
+
 // -------------------------------------------------------------- matvec core
 // tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum).
 // `tmp` must be plan->tmp: the batched dense kernels write their slices of it.
@@ -147,8 +182,14 @@ static anova_status matvec_one(anova_plan* plan, const T* alpha, T* out, cudaStr
     T* tmp = static_cast<T*>(plan->tmp);
     ANOVA_TRY(windows_apply<T>(plan, alpha, sizeof(T) == 8, tmp, st));
     clock_begin(plan, 3, st);
-    k_window_sum<T, T><<<grid_for(N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
-        tmp, plan->eta_dev, plan->P, N, out);
+    if constexpr (sizeof(T) == 4)
+        k_window_sum_f32<<<grid_for((N + 3) / 4, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            tmp, plan->eta_dev, plan->P, N, out,
+            (N % 4 == 0 && reinterpret_cast<uintptr_t>(tmp) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0)
+                ? 1 : 0);
+    else
+        k_window_sum<T, T><<<grid_for(N, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            tmp, plan->eta_dev, plan->P, N, out);
     ANOVA_CHECK_LAUNCH();
     clock_end(plan, 3, 1, st);
     return ANOVA_OK;
@@ -186,11 +227,22 @@ __global__ void __launch_bounds__(kThreads)
 k_cg_q(const T* __restrict__ tmp, const double* __restrict__ eta, int P, int64_t N, double lambda,
        const double* __restrict__ p, double* __restrict__ q, double* __restrict__ part) {
     __shared__ double sh[32];
+    __shared__ float ef[64];          // FP32 operator: the window sum in FP32 (one FP64 conversion per element)
+    if (sizeof(T) == 4) {
+        for (int l = threadIdx.x; l < 64; l += blockDim.x) ef[l] = l < P ? (float)eta[l] : 0.f;
+        __syncthreads();
+    }
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         double v = lambda * p[i];
-        for (int l = 0; l < P; l++) v += eta[l] * (double)tmp[l * N + i];
+        if (sizeof(T) == 4 && P <= 64) {
+            float s = 0.f;
+            for (int l = 0; l < P; l++) s = fmaf(ef[l], (float)tmp[l * N + i], s);
+            v += (double)s;
+        } else {
+            for (int l = 0; l < P; l++) v += eta[l] * (double)tmp[l * N + i];
+        }
         q[i] = v;
         acc += p[i] * v;
     }
