@@ -469,6 +469,13 @@ __device__ __forceinline__ void tf32_split_fast(float x, uint32_t& hi, uint32_t&
     hi = tf32_of(x);
     lo = __float_as_uint(x - __uint_as_float(hi));
 }
+// head by truncation to TF32's 10 mantissa bits (one logic operation), tail
+// the exact FP32 residual x - head (at most 2^-10 |x|; the tensor core reads
+// its TF32 bits, so the pair keeps x to 2^-20 relative)
+__device__ __forceinline__ void tf32_split_trunc(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
 __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
     asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
                  : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -683,7 +690,7 @@ k_spread3_tcp(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
             uint32_t hi = 0u, lo = 0u;
             if (p < cnt) {
                 const float al = dbl ? (float)sal[b][p] : reinterpret_cast<const float*>(&sal[b][p])[0];
-                tf32_split_fast(al * raw[b][p][32 + e], hi, lo);
+                tf32_split_trunc(al * raw[b][p][32 + e], hi, lo);
             } else {
                 raw[b][p][e] = 0.f;
                 raw[b][p][16 + e] = 0.f;
@@ -709,10 +716,10 @@ k_spread3_tcp(const int4* __restrict__ sub, const DenseWin* __restrict__ descs, 
                 const int a = 2 * warp + i;
                 const float x0 = raw[b][pa][a], x1 = raw[b][pb][a];
                 uint32_t ah[4], alo[4];
-                tf32_split_fast(x0 * y0, ah[0], alo[0]);
-                tf32_split_fast(x0 * y1, ah[1], alo[1]);
-                tf32_split_fast(x1 * y2, ah[2], alo[2]);
-                tf32_split_fast(x1 * y3, ah[3], alo[3]);
+                tf32_split_trunc(x0 * y0, ah[0], alo[0]);
+                tf32_split_trunc(x0 * y1, ah[1], alo[1]);
+                tf32_split_trunc(x1 * y2, ah[2], alo[2]);
+                tf32_split_trunc(x1 * y3, ah[3], alo[3]);
 #pragma unroll
                 for (int nt = 0; nt < 2; nt++) {
                     mma_tf32(acc[i][nt], ah, bh[nt][0], bh[nt][1]);
