@@ -447,6 +447,21 @@ def run_ours(args):
     # KRR solves/s (mixed precision: FP32 inner CG, FP64 refinement) to the workload's tolerance
     krr = None if args.skip_krr else krr_solve(B, torch, plan, w, dev, 20000,
                                                "mixed (FP32 inner CG, FP64 refinement)")
+    if krr is not None and not args.skip_fp64:
+        # the FP64 product the refinement's residuals use (same plan, FP64 coefficients)
+        a64 = torch.from_numpy(w.alpha).to(dev)
+        o64 = torch.empty_like(a64)
+        B.anova_matvec(plan, a64, o64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            B.anova_matvec(plan, a64, o64)
+        e1.record(stream)
+        e1.synchronize()
+        krr["fp64_matvec_ms"] = e0.elapsed_time(e1) / 3
+        krr["fp32_matvec_ms"] = ms_per_step
+        del a64, o64
     clk.__exit__(None, None, None)
     plan.close()
     del X

@@ -11,6 +11,7 @@ across a call.  This file is collected last so that a failure here cannot
 hide the other GPU tests.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -92,6 +93,7 @@ def test_noalloc_predict_leaves_device_memory_unchanged(env):
     Z = torch.from_numpy(w.X[:3000] * 0.9).cuda()
     out = torch.empty(3000, dtype=torch.float64, device="cuda")
     B.krr_predict_noalloc(plan, alpha, Z, out)           # warm-up: module load, scratch address lookup
+    gc.collect()                                          # tensors left by earlier tests are freed now, not below
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     used0 = torch.cuda.memory_allocated()
