@@ -227,6 +227,126 @@ k_spread2_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
     if (cw >= 0) flush();
 }
 
+// ------------------------------------------- 2-D spread on tensor cores
+// As k_spread2_pw, with each warp's 32-node contribution to its region
+// C[a][b] += sum_p (alpha_p wx_p[a]) wy_p[b] run as mma.sync m16n8k8 TF32
+// (M = a, N = b in two tiles of 8, K = 8 nodes per step; operands split into
+// a TF32 head rounded to nearest and the FP32 residual, head*head + head*tail
+// + tail*head in FP32: FP32 accuracy, the dropped tail*tail at most 2^-22 and
+// of either sign).  Thread (g = lane / 4, t = lane mod 4)
+// holds C[g][8 nt + 2t .. +1] and C[g + 8][8 nt + 2t .. +1] of n-tile nt.
+__device__ __forceinline__ void tf32_split2(float x, uint32_t& hi, uint32_t& lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32_16x8x8(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int R, int M>
+__global__ void __launch_bounds__(k12Threads)
+k_spread2_tc(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict__ descs,
+             const __grid_constant__ PsiCoef<M> P, const void* __restrict__ alpha, int alpha_double) {
+    constexpr int TB = R - 2 * M;
+    constexpr int kP = 24;                              // staging row pitch: conflict-free fragment reads
+    __shared__ __align__(16) float stage[2][k12Warps][32][kP];
+    float (*sx)[32][kP] = stage[0];                     // alpha wx rows of each warp's nodes
+    float (*sy)[32][kP] = stage[1];                     // wy rows
+    float (*red)[16][16] = reinterpret_cast<float (*)[16][16]>(&stage[0][0][0][0]);
+    const int lo = (int)((int64_t)nsub * blockIdx.x / gridDim.x);
+    const int hi = (int)((int64_t)nsub * (blockIdx.x + 1) / gridDim.x);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    float acc[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc[nt][k] = 0.f;
+    int cw = -1, cbin = -1;
+    auto flush = [&]() {
+        __syncthreads();
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+            red[warp][g][8 * nt + 2 * t] = acc[nt][0];
+            red[warp][g][8 * nt + 2 * t + 1] = acc[nt][1];
+            red[warp][g + 8][8 * nt + 2 * t] = acc[nt][2];
+            red[warp][g + 8][8 * nt + 2 * t + 1] = acc[nt][3];
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[nt][k] = 0.f;
+        }
+        __syncthreads();
+        const DenseWin& W = descs[cw];
+        const int a = tid >> 4, b = tid & 15;
+        if (a < R && b < R) {
+            float v = 0.f;
+#pragma unroll
+            for (int w2 = 0; w2 < k12Warps; w2++) v += red[w2][a][b];
+            const int nb = W.nb, by = cbin % nb, bx = cbin / nb, nos = W.nos;
+            atomicAdd(&static_cast<float*>(W.grid)[wrap_cell(TB * bx - M + a, nos) * nos + wrap_cell(TB * by - M + b, nos)],
+                      v);
+        }
+        __syncthreads();                                 // the staging rows are free again
+    };
+    int nacc = 0;
+    for (int q = lo; q < hi; q++) {
+        const int4 sp = sub[q];
+        const DenseWin& W = descs[sp.w];
+        if (W.live && !*W.live) continue;
+        if (cw >= 0 && (sp.w != cw || sp.x != cbin || nacc == kFlushSubs)) {
+            flush();
+            nacc = 0;
+        }
+        cw = sp.w;
+        cbin = sp.x;
+        nacc++;
+        const int nb = W.nb, by = sp.x % nb, bx = sp.x / nb;
+        const int p = 32 * warp + lane;
+        float wx[16], wy[16];
+        if (p < sp.z) {
+            const int64_t pos = (int64_t)sp.y + p, Nn = W.N;
+            const float* __restrict__ fr = static_cast<const float*>(W.frac);
+            const float al = coef_of(W, alpha, alpha_double, pos);
+            float tp[2 * M];
+            psi_taps<M>(P, fr[pos], tp);
+            place_taps<R, M>(tp, W.cell[pos] - TB * bx, wx);
+            psi_taps<M>(P, fr[Nn + pos], tp);
+            place_taps<R, M>(tp, W.cell[Nn + pos] - TB * by, wy);
+#pragma unroll
+            for (int r = 0; r < 16; r++) wx[r] *= al;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; r++) wx[r] = wy[r] = 0.f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            reinterpret_cast<float4*>(sx[warp][lane])[k] = make_float4(wx[4 * k], wx[4 * k + 1], wx[4 * k + 2], wx[4 * k + 3]);
+            reinterpret_cast<float4*>(sy[warp][lane])[k] = make_float4(wy[4 * k], wy[4 * k + 1], wy[4 * k + 2], wy[4 * k + 3]);
+        }
+        __syncwarp();
+        const int cnt = min(32, sp.z - 32 * warp);
+        for (int s0 = 0; s0 < cnt; s0 += 8) {
+            const int p0 = s0 + t, p1 = s0 + t + 4;
+            uint32_t ah[4], al[4];
+            tf32_split2(sx[warp][p0][g], ah[0], al[0]);
+            tf32_split2(sx[warp][p0][g + 8], ah[1], al[1]);
+            tf32_split2(sx[warp][p1][g], ah[2], al[2]);
+            tf32_split2(sx[warp][p1][g + 8], ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                uint32_t bh0, bl0, bh1, bl1;
+                tf32_split2(sy[warp][p0][8 * nt + g], bh0, bl0);
+                tf32_split2(sy[warp][p1][8 * nt + g], bh1, bl1);
+                mma_tf32_16x8x8(acc[nt], ah, bh0, bh1);
+                mma_tf32_16x8x8(acc[nt], ah, bl0, bl1);
+                mma_tf32_16x8x8(acc[nt], al, bh0, bh1);
+            }
+        }
+    }
+    if (cw >= 0) flush();
+}
+
 // --------------------------------------------------------------- 1-D spread
 // Every thread keeps the region of the nodes it has seen in registers
 // (acc[r] += alpha_p wx_p[r]); per bin the block sums them (warp shuffles, then
@@ -295,7 +415,7 @@ static anova_status launch12(int dA, bool spread, const int4* sub, int nsub, con
     const PsiCoef<M> P = psi_coef<M>(psi_host);
     const int grid = nsub < 8 * sms ? nsub : 8 * sms;
     if (dA == 2) {
-        if (spread) k_spread2_pw<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
+        if (spread) k_spread2_tc<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
         else k_gather2_pw<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P);
     } else {
         if (spread) k_spread1_pw<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
