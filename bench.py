@@ -624,7 +624,7 @@ def run_serve(args):
     # the stream
     n_req = int(args.serve_rate * args.serve_seconds)
     arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_req))
-    kinds = rng.uniform(size=n_req) < 0.7
+    kinds = rng.uniform(size=n_req) < 1.0 - args.serve_fit_share
     fit_tickets, pred = [], []
     done_fits = []
 
@@ -683,13 +683,16 @@ def run_serve(args):
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     print(json.dumps({
         "serve": True,
-        "workload": "Poisson stream, 70% predict (M log-uniform 1e2..1e5) on resident models, "
-                    "30% fit (N log-uniform 1e3..1e6); d 9..28, 3..9 windows of 1-3 features",
+        "workload": "Poisson stream of predictions (M log-uniform 1e2..1e5) on resident models and "
+                    "fits (N log-uniform 1e3..1e6; share fit_share); d 9..28, 3..9 windows of 1-3 features",
         "offered_rate_rps": args.serve_rate, "seconds_offered": args.serve_seconds, "workers": args.serve_workers,
         "resident_models_N": res_N, "initial_fits_s": round(t_init, 3),
         "initial_fit_iters": [r["iterations"] for r in init],
         "requests": n_req, "predicts": len(pred), "fits": len(done_fits), "failed_fits": int(bad),
+        "fit_share": args.serve_fit_share,
         "predict_p50_ms": pct(plat, 50), "predict_p99_ms": pct(plat, 99),
+        "predict_p50_ms_first_half": pct(plat[:len(plat) // 2], 50),
+        "predict_p50_ms_second_half": pct(plat[len(plat) // 2:], 50),
         "fit_p50_ms": pct(flat, 50), "fit_p99_ms": pct(flat, 99),
         "fit_wait_bound_ms": args.serve_fit_wait_ms, "fits_refused": refused,
         "fit_p50_ms_first_half": pct(flat[:half], 50), "fit_p50_ms_second_half": pct(flat[half:], 50),
@@ -1004,6 +1007,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-models", type=int, default=4)
     ap.add_argument("--serve-fit-pool", type=int, default=6)
+    ap.add_argument("--serve-fit-share", type=float, default=0.3, help="share of the requests that are fits")
     ap.add_argument("--serve-fit-wait-ms", type=float, default=5000.0,
                     help="refuse fits whose expected queue wait exceeds this (0: admit every fit)")
     ap.add_argument("--precision-form", action="store_true",

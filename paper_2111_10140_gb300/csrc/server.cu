@@ -88,11 +88,13 @@ struct anova_server {
     int running_fits = 0;
     int max_fits = 1;             // workers a fit may occupy; the rest stay free for predictions
     std::chrono::steady_clock::time_point t0;
-    // fit admission: nodes of the fits queued and running, and the measured fit rate
+    // fit admission: nodes of the fits queued and running, and the rate at which
+    // the server has been finishing fit nodes (the last completions, all workers together)
     double fit_wait_bound_ms = 0.0;   // 0: no bound
     int64_t fit_nodes_queued = 0, fit_nodes_running = 0;
     double fit_nodes_per_ms = 0.0;    // per worker, over the completed fits (0: none yet)
     int64_t fits_done = 0;
+    std::deque<std::pair<std::chrono::steady_clock::time_point, int64_t>> fit_log;   // (completion, N)
 };
 
 namespace anova {
@@ -262,6 +264,8 @@ static void worker_main(anova_server* sv) {
                     // running mean of the per-worker fit rate, nodes per millisecond
                     sv->fits_done++;
                     sv->fit_nodes_per_ms += ((double)r->N / service - sv->fit_nodes_per_ms) / (double)sv->fits_done;
+                    sv->fit_log.emplace_back(t1, r->N);
+                    if (sv->fit_log.size() > 16) sv->fit_log.pop_front();
                 }
             }
             if (r->status == ANOVA_OK || r->status == ANOVA_ENOCONV) sv->latencies.push_back(r->latency_ms);
@@ -274,13 +278,33 @@ static void worker_main(anova_server* sv) {
 static anova_status enqueue(anova_server* sv, std::shared_ptr<ServerRequest> r, int64_t* ticket) {
     std::lock_guard<std::mutex> lock(sv->mu);
     if (r->kind == 0) {
-        // expected wait of this fit: the fit nodes ahead of it at the measured rate
-        if (sv->fit_wait_bound_ms > 0.0 && sv->fit_nodes_per_ms > 0.0) {
-            const double wait_ms = (double)(sv->fit_nodes_queued + sv->fit_nodes_running) /
-                                   (sv->fit_nodes_per_ms * (double)sv->max_fits);
+        // Expected wait of this fit before a worker takes it: the fit nodes queued
+        // ahead of it, plus half of those running, at the rate the server has been
+        // finishing fit nodes over its last completions (all workers together, so
+        // the rate already carries the load of concurrent fits and predictions).
+        // Before two fits have finished the rate is unknown and a fit is taken
+        // only if it would not queue behind another.
+        if (sv->fit_wait_bound_ms > 0.0) {
+            double wait_ms = 0.0;
+            const auto now = std::chrono::steady_clock::now();
+            if (sv->fit_log.size() >= 2) {
+                int64_t nodes = 0;
+                for (size_t i = 1; i < sv->fit_log.size(); i++) nodes += sv->fit_log[i].second;
+                // the span ends now if no fit has finished for longer than the log covers
+                const auto end = std::max(sv->fit_log.back().first, now - (sv->fit_log.back().first -
+                                                                            sv->fit_log.front().first));
+                const double span = std::chrono::duration<double, std::milli>(end - sv->fit_log.front().first).count();
+                const double rate = span > 0.0 ? (double)nodes / span : 0.0;
+                const double ahead = (double)sv->fit_nodes_queued + 0.5 * (double)sv->fit_nodes_running;
+                wait_ms = rate > 0.0 ? ahead / rate : (ahead > 0.0 ? 1e300 : 0.0);
+            } else if (sv->running_fits >= sv->max_fits || sv->fit_nodes_queued > 0) {
+                wait_ms = 1e300;
+            }
             if (wait_ms > sv->fit_wait_bound_ms) {
-                set_error("anova_server_submit_fit: expected queue wait " + std::to_string((int64_t)wait_ms) +
-                          " ms exceeds the bound of " + std::to_string((int64_t)sv->fit_wait_bound_ms) + " ms");
+                set_error("anova_server_submit_fit: expected queue wait " +
+                          (wait_ms > 1e18 ? std::string("(unknown: no fit rate measured yet, the fit would queue)")
+                                          : std::to_string((int64_t)wait_ms) + " ms") +
+                          " exceeds the bound of " + std::to_string((int64_t)sv->fit_wait_bound_ms) + " ms");
                 return ANOVA_EBUSY;
             }
         }

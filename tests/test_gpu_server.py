@@ -198,7 +198,7 @@ def test_server_fit_wait_bound_refuses_fits(B, torch):
         sv.set_fit_wait_bound(1e-6)
         # the queue is empty: the expected wait is 0, admitted
         f1 = sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
-        # behind f1 the expected wait is f1's nodes at the measured rate: refused
+        # behind f1 the fit would queue, and with one finished fit there is no rate yet: refused
         with pytest.raises(B.AnovaError) as e:
             sv.submit_fit(X, w.windows, w.ell, y, LAM, n=w.n, m=w.m, eps_B=w.epsB, tol=TOL)
         assert e.value.status == B.EBUSY
