@@ -477,14 +477,15 @@ anova_status anova_server_fit_alpha(anova_server* server, int64_t fit, double* o
 /*
  * Bound on a fit's expected queue wait, in milliseconds (0, the default: no
  * bound).  When a fit is submitted, the server estimates how long it would
- * wait for a worker: the nodes of the fits queued ahead of it plus half of
- * those running, divided by the rate at which the server has been finishing
- * fit nodes over its last (up to 16) completed fits, all workers together, so
- * that the rate includes the load of concurrent fits and predictions.  A fit
- * whose estimate exceeds the bound is refused at once:
- * anova_server_submit_fit returns ANOVA_EBUSY and queues nothing.  Until two
- * fits have completed there is no rate, and a fit is refused only if it would
- * have to queue behind another.
+ * wait for a worker: the fits queued ahead of it, plus itself, divided by the
+ * rate at which fits that had to wait for a worker have been starting (their
+ * last up to 16 starts), so the rate follows the mix of fits and the load of
+ * the predictions beside them.  A fit whose estimate exceeds the bound is
+ * refused at once: anova_server_submit_fit returns ANOVA_EBUSY and queues
+ * nothing.  Until two such starts are recorded there is no rate, and a fit is
+ * refused only if it would have to queue.  Fits run on low-priority streams
+ * and predictions on high-priority ones (cudaStreamCreateWithPriority), so a
+ * prediction's kernels are scheduled ahead of the fits' waiting blocks.
  * Predictions are never refused.  The paper has no counterpart: this keeps
  * the fits the server accepts at a bounded latency when they are offered
  * faster than the GPU can fit them.  Errors: EINVAL (NULL server, negative or

@@ -114,6 +114,7 @@ struct WindowPlan {
     size_t grid_off = 0;       // element offset of this window's grid in plan->grid
     size_t work_off = 0;       // element offset of this window's FFT work arrays
     float* wtab = nullptr;     // dense 3-D windows, FP32 plans: N x 3 x 16 zero-padded window weights (sorted order)
+    double* wtap64 = nullptr;  // FP64 plans: N x dA x (2m+1) window taps psi(m - k + f) of the nodes (sorted order)
     int box_lo[kMaxDim] = {0, 0, 0};   // grid cells touched by the training nodes: start (may be < 0)
     int box_ext[kMaxDim] = {0, 0, 0};  // and extent per axis (<= nos)
     bool fft12 = false;        // 1-D / 2-D window on the batched box FFT (fft12.cu)
@@ -149,6 +150,7 @@ struct DenseWin {
     const int32_t* cell;
     const void* frac;          // FP32 or FP64, as the launch
     const float* wtab;         // FP32 weight table (N x 48) or null
+    const double* wtap = nullptr;   // FP64 tap table of the plan's nodes (N x 3 x (2m+1)) or null
     float* asort;              // FP32 coefficients in this window's sorted order (filled per matvec)
     void* grid;                // this window's grid
     void* out;                 // gather output (this window's slice of plan->tmp)

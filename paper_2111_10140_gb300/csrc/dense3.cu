@@ -97,18 +97,27 @@ k_gather3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
         const T fx = frac[pos], fy = frac[N + pos], fz = frac[2 * N + pos];
         const int jx = cell[pos] - Tb * bx + m, jy = cell[N + pos] - Tb * by + m, jz = cell[2 * N + pos] - Tb * bz + m;
         const T tx = (T)jx + fx, ty = (T)jy + fy, tz = (T)jz + fz;
+        // FP64 with the plan's tap table: the tap of region row r is k = r - (j - m), if in [0, 2m]
+        const double* __restrict__ tp = (!kPoly && W.wtap) ? W.wtap + pos * 3 * (2 * m + 1) : nullptr;
+        auto tap = [&](int t, int j, int r) -> T {
+            const int k = r - j + m;
+            return (k >= 0 && k <= 2 * m) ? (T)tp[t * (2 * m + 1) + k] : T(0);
+        };
         T wy[R], wz[kPitch];
 #pragma unroll
         for (int r = 0; r < R; r++)
-            wy[r] = kPoly ? (T)psi_poly_eval(sP, jy - r, (float)fy, m) : kb_psi<T>(ty - (T)r, mm, b, norm);
+            wy[r] = kPoly ? (T)psi_poly_eval(sP, jy - r, (float)fy, m)
+                          : (tp ? tap(1, jy, r) : kb_psi<T>(ty - (T)r, mm, b, norm));
 #pragma unroll
         for (int r = 0; r < kPitch; r++)
-            wz[r] = (r < R) ? (kPoly ? (T)psi_poly_eval(sP, jz - r, (float)fz, m) : kb_psi<T>(tz - (T)r, mm, b, norm))
+            wz[r] = (r < R) ? (kPoly ? (T)psi_poly_eval(sP, jz - r, (float)fz, m)
+                                     : (tp ? tap(2, jz, r) : kb_psi<T>(tz - (T)r, mm, b, norm)))
                             : T(0);
         T acc = T(0);
 #pragma unroll 1
         for (int a = 0; a < R; a++) {
-            const T wa = kPoly ? (T)psi_poly_eval(sP, jx - a, (float)fx, m) : kb_psi<T>(tx - (T)a, mm, b, norm);
+            const T wa = kPoly ? (T)psi_poly_eval(sP, jx - a, (float)fx, m)
+                               : (tp ? tap(0, jx, a) : kb_psi<T>(tx - (T)a, mm, b, norm));
             const T* rows = reg + a * R * kPitch;
             T sa = T(0);
 #pragma unroll
@@ -176,9 +185,17 @@ k_spread3_dense(const int4* __restrict__ sub, const DenseWin* __restrict__ descs
             const int64_t pos = (int64_t)sp.y + first + p;
             const int bcoord = (ax == 0) ? bx : (ax == 1) ? by : bz;
             const int j = cell[ax * N + pos] - Tb * bcoord + m - r;
-            const T f = frac[ax * N + pos];
             T w = T(0);
-            if (r < R) w = kPoly ? (T)psi_poly_eval(sP, j, (float)f, m) : kb_psi<T>((T)j + f, mm, b, norm);
+            if (r < R) {
+                if (!kPoly && W.wtap) {
+                    // FP64 with the plan's tap table: j = m - k for tap k
+                    const int k = m - j;
+                    w = (k >= 0 && k <= 2 * m) ? (T)W.wtap[(pos * 3 + ax) * (2 * m + 1) + k] : T(0);
+                } else {
+                    const T f = frac[ax * N + pos];
+                    w = kPoly ? (T)psi_poly_eval(sP, j, (float)f, m) : kb_psi<T>((T)j + f, mm, b, norm);
+                }
+            }
             if (ax == 0) {
                 if (r < R) {
                     const int32_t src = perm[pos];
@@ -1150,6 +1167,7 @@ static DenseWin single_desc(const WindowPlan& w, const PointSet& ps, const void*
     d.cell = ps.cell;
     d.frac = frac;
     d.wtab = nullptr;
+    d.wtap = (&ps == &w.X) ? w.wtap64 : nullptr;   // the tap table describes the plan's own nodes only
     d.asort = nullptr;
     d.grid = grid;
     d.out = out;

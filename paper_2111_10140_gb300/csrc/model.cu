@@ -83,6 +83,7 @@ static anova_status model_grids(krr_model* md, cudaStream_t st) {
         WindowPlan keep = wide;       // frame and binning parameters only
         keep.X = PointSet();
         keep.wtab = nullptr;
+        keep.wtap64 = nullptr;
         keep.D64 = nullptr;
         keep.D32 = nullptr;
         keep.tw64 = nullptr;

@@ -812,6 +812,23 @@ __global__ void k_weight_table(const double* __restrict__ xw, const int32_t* __r
     }
 }
 
+// FP64 taps of every node of a window, for the FP64 kernels of the plan's
+// own nodes: tap[(pos * dA + t) * (2m + 1) + k] = psi(m - k + f_t), the window
+// at the node's offset from cell c_t + k - m, in FP64 exactly as the kernels
+// evaluate it (kb_psi); computed once per frame instead of in every product.
+__global__ void k_tap_table64(const double* __restrict__ frac64, int64_t N, int dA, int m, double b, double norm,
+                              double* __restrict__ tap) {
+    const int ntap = 2 * m + 1;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * dA;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pos = idx / dA;
+        const int t = (int)(idx % dA);
+        const double f = frac64[t * N + pos];
+        double* out = tap + idx * ntap;
+        for (int k = 0; k < ntap; k++) out[k] = kb_psi<double>((double)(m - k) + f, (double)m, b, norm);
+    }
+}
+
 // Box of grid cells that spreading writes and gathering reads: the union of
 // the regions [bin*T - m, bin*T + T + m) of the occupied bins, per axis.
 static anova_status window_box(anova_plan* plan, WindowPlan& w, cudaStream_t st) {
@@ -889,6 +906,14 @@ static anova_status window_setup(anova_plan* plan, WindowPlan& w, const double* 
         cudaFree(w.wtab);
         w.wtab = nullptr;
     }
+    cudaFree(w.wtap64);
+    w.wtap64 = nullptr;
+    if (want64 && plan->N > 0 && w.X.frac64) {
+        ANOVA_CUDA_TRY(anova::dev_malloc((void**)&w.wtap64, (size_t)plan->N * w.dA * (2 * plan->m + 1) * sizeof(double)));
+        k_tap_table64<<<grid_for(plan->N * w.dA, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
+            w.X.frac64, plan->N, w.dA, plan->m, plan->b, plan->psi_norm, w.wtap64);
+        ANOVA_CHECK_LAUNCH();
+    }
     return window_box(plan, w, st);
 }
 
@@ -936,6 +961,7 @@ static anova_status build_dense_batch(anova_plan* plan, cudaStream_t st) {
             d.cell = w.X.cell;
             d.frac = prec == 0 ? (const void*)w.X.frac64 : (const void*)w.X.frac32;
             d.wtab = prec == 0 ? nullptr : w.wtab;
+            d.wtap = prec == 0 ? w.wtap64 : nullptr;
             d.asort = (prec == 0 || !plan->dense_asort) ? nullptr : plan->dense_asort + (size_t)k * plan->N;
             d.grid = prec == 0 ? (void*)(static_cast<double*>(plan->grid) + w.grid_off)
                                : (void*)(static_cast<float*>(plan->grid) + w.grid_off);
@@ -1249,6 +1275,7 @@ anova_status window_widened(anova_plan* plan, int l, double rho, WindowPlan& dst
 
 void window_release_reframed(WindowPlan& w) {
     cudaFree(w.wtab);
+    cudaFree(w.wtap64);
     cudaFree(w.D64);
     cudaFree(w.D32);
     free_pointset(w.X);
@@ -1418,6 +1445,7 @@ void anova_plan_destroy(anova_plan* plan) {
     if (!plan) return;
     for (auto& w : plan->win) {
         cudaFree(w.wtab);
+        cudaFree(w.wtap64);
         cudaFree(w.D64);
         cudaFree(w.D32);
         cudaFree(w.tw64);

@@ -95,21 +95,24 @@ struct anova_server {
     double fit_nodes_per_ms = 0.0;    // per worker, over the completed fits (0: none yet)
     int64_t fits_done = 0;
     std::deque<std::pair<std::chrono::steady_clock::time_point, int64_t>> fit_log;   // (completion, N)
+    std::deque<std::chrono::steady_clock::time_point> fit_starts;                    // last fit start times
+    int fits_queued = 0;
 };
 
 namespace anova {
 
-// device bytes of a fitted model: the plan's node arrays, weight tables,
-// grids and work buffers, the CG vectors, the coefficients and the model's
-// convolved grids
-static int64_t fit_bytes(int64_t N, const std::vector<int32_t>& windows, int32_t P, const std::vector<int32_t>& n) {
+// device bytes of a fitted model: the plan's node arrays, weight tables (FP32
+// and the FP64 taps of the mixed plan), grids and work buffers, the CG vectors,
+// the coefficients and the model's convolved grids
+static int64_t fit_bytes(int64_t N, const std::vector<int32_t>& windows, int32_t P, const std::vector<int32_t>& n,
+                         int32_t m) {
     int64_t b = 0;
     for (int l = 0; l < P; l++) {
         int dA = 0;
         while (dA < 3 && windows[3 * l + dA] >= 0) dA++;
         int64_t nos = 2 * (n.empty() ? 32 : n[l]), grid = 1;
         for (int t = 0; t < dA; t++) grid *= nos;
-        b += N * (8 * dA + 4 + 4 * dA + 8 * dA + 4 * dA + 64 * dA + 8 + 4) + grid * 8 * 4;
+        b += N * (8 * dA + 4 + 4 * dA + 8 * dA + 4 * dA + 64 * dA + 8 + 4 + 8 * dA * (2 * m + 1)) + grid * 8 * 4;
     }
     return b + N * (8 * 5) + (64 << 20);
 }
@@ -188,8 +191,15 @@ static void run_request(anova_server* sv, ServerRequest& r, cudaStream_t st) {
 
 static void worker_main(anova_server* sv) {
     cudaSetDevice(sv->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // predictions on a high-priority stream, fits on a low-priority one: when both
+    // have blocks waiting, the GPU schedules the prediction's first, so a
+    // prediction's latency does not wait on the fits running beside it
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    cudaStream_t st_pred = nullptr, st_fit = nullptr;
+    cudaStreamCreateWithPriority(&st_pred, cudaStreamNonBlocking, prio_high);
+    cudaStreamCreateWithPriority(&st_fit, cudaStreamNonBlocking, prio_low);
+    cudaStream_t st = st_pred;
     for (;;) {
         std::shared_ptr<ServerRequest> r;
         {
@@ -197,7 +207,8 @@ static void worker_main(anova_server* sv) {
             for (;;) {
                 if (sv->stop) {
                     lock.unlock();
-                    cudaStreamDestroy(st);
+                    cudaStreamDestroy(st_pred);
+                    cudaStreamDestroy(st_fit);
                     return;
                 }
                 // admit the oldest request whose memory fits; a prediction waits
@@ -231,8 +242,14 @@ static void worker_main(anova_server* sv) {
                     r->started = std::chrono::steady_clock::now();
                     if (r->kind == 0) {
                         sv->running_fits++;
+                        sv->fits_queued--;
                         sv->fit_nodes_queued -= r->N;
                         sv->fit_nodes_running += r->N;
+                        // a start that had to wait for a worker measures how fast fits drain
+                        if (std::chrono::duration<double, std::milli>(r->started - r->submitted).count() > 2.0) {
+                            sv->fit_starts.push_back(r->started);
+                            if (sv->fit_starts.size() > 16) sv->fit_starts.pop_front();
+                        }
                     }
                     if (r->kind == 1) {
                         auto m = sv->models.find(r->model);
@@ -243,6 +260,7 @@ static void worker_main(anova_server* sv) {
                 sv->cv_work.wait(lock);
             }
         }
+        st = r->kind == 0 ? st_fit : st_pred;
         run_request(sv, *r, st);
         // completion means the result is in device memory
         const cudaError_t se = cudaStreamSynchronize(st);
@@ -278,27 +296,28 @@ static void worker_main(anova_server* sv) {
 static anova_status enqueue(anova_server* sv, std::shared_ptr<ServerRequest> r, int64_t* ticket) {
     std::lock_guard<std::mutex> lock(sv->mu);
     if (r->kind == 0) {
-        // Expected wait of this fit before a worker takes it: the fit nodes queued
-        // ahead of it, plus half of those running, at the rate the server has been
-        // finishing fit nodes over its last completions (all workers together, so
-        // the rate already carries the load of concurrent fits and predictions).
-        // Before two fits have finished the rate is unknown and a fit is taken
-        // only if it would not queue behind another.
+        // Expected wait of this fit before a worker takes it: the fits queued ahead
+        // of it (and itself) divided by the rate at which fits that had to wait
+        // for a worker have been starting (their last up to 16 starts; the
+        // interval up to now counts when none has started for longer than those
+        // starts span).  Counting fits rather than nodes makes the estimate follow
+        // the mix of fits actually served under the current load.  Until two such
+        // starts are recorded the rate is unknown and a fit is taken only if it
+        // would not queue.
         if (sv->fit_wait_bound_ms > 0.0) {
             double wait_ms = 0.0;
             const auto now = std::chrono::steady_clock::now();
-            if (sv->fit_log.size() >= 2) {
-                int64_t nodes = 0;
-                for (size_t i = 1; i < sv->fit_log.size(); i++) nodes += sv->fit_log[i].second;
-                // the span ends now if no fit has finished for longer than the log covers
-                const auto end = std::max(sv->fit_log.back().first, now - (sv->fit_log.back().first -
-                                                                            sv->fit_log.front().first));
-                const double span = std::chrono::duration<double, std::milli>(end - sv->fit_log.front().first).count();
-                const double rate = span > 0.0 ? (double)nodes / span : 0.0;
-                const double ahead = (double)sv->fit_nodes_queued + 0.5 * (double)sv->fit_nodes_running;
-                wait_ms = rate > 0.0 ? ahead / rate : (ahead > 0.0 ? 1e300 : 0.0);
-            } else if (sv->running_fits >= sv->max_fits || sv->fit_nodes_queued > 0) {
-                wait_ms = 1e300;
+            const bool would_queue = sv->fits_queued > 0 || sv->running_fits >= sv->max_fits;
+            if (would_queue) {
+                if (sv->fit_starts.size() >= 2) {
+                    const auto first = sv->fit_starts.front(), last = sv->fit_starts.back();
+                    const auto end = std::max(last, now - (last - first));
+                    const double span = std::chrono::duration<double, std::milli>(end - first).count();
+                    const double rate = span > 0.0 ? (double)(sv->fit_starts.size() - 1) / span : 0.0;
+                    wait_ms = rate > 0.0 ? (double)(sv->fits_queued + 1) / rate : 1e300;
+                } else {
+                    wait_ms = 1e300;
+                }
             }
             if (wait_ms > sv->fit_wait_bound_ms) {
                 set_error("anova_server_submit_fit: expected queue wait " +
@@ -309,6 +328,7 @@ static anova_status enqueue(anova_server* sv, std::shared_ptr<ServerRequest> r, 
             }
         }
         sv->fit_nodes_queued += r->N;
+        sv->fits_queued++;
     }
     r->ticket = sv->next_ticket++;
     r->submitted = std::chrono::steady_clock::now();
@@ -365,7 +385,7 @@ anova_status anova_server_submit_fit(anova_server* sv, const double* points, int
     r->y = y;
     r->tol = tol;
     r->maxit = maxit;
-    r->bytes = fit_bytes(N, r->windows, P, r->n);
+    r->bytes = fit_bytes(N, r->windows, P, r->n, m);
     return enqueue(sv, r, ticket);
 }
 

@@ -46,15 +46,23 @@ __device__ __forceinline__ int region_to_grid(int i, int R, const int* bc, int T
     return g;
 }
 
+// taps w[t][k] = psi(m - k + f_t) of a node; from the plan's FP64 tap table when
+// given (the plan's own nodes in an FP64 plan), else evaluated
 template <typename T, int DA>
 __device__ __forceinline__ void node_weights(const int32_t* __restrict__ cell, const T* __restrict__ frac,
                                              int64_t N, int64_t pos, const int* bc, int Tb, int m,
-                                             T b, T norm, T (*w)[2 * kMaxM + 1], int* off) {
+                                             T b, T norm, const double* __restrict__ tap, T (*w)[2 * kMaxM + 1],
+                                             int* off) {
     const T mm = (T)m;
     for (int t = 0; t < DA; t++) {
         off[t] = cell[t * N + pos] - bc[t] * Tb;
-        const T f = frac[t * N + pos];
-        for (int k = 0; k <= 2 * m; k++) w[t][k] = kb_psi<T>(f + mm - (T)k, mm, b, norm);
+        if (tap) {
+            const double* tp = tap + (pos * DA + t) * (2 * m + 1);
+            for (int k = 0; k <= 2 * m; k++) w[t][k] = (T)tp[k];
+        } else {
+            const T f = frac[t * N + pos];
+            for (int k = 0; k <= 2 * m; k++) w[t][k] = kb_psi<T>(f + mm - (T)k, mm, b, norm);
+        }
     }
 }
 
@@ -62,7 +70,7 @@ template <typename T, int DA>
 __global__ void __launch_bounds__(kThreads)
 k_spread(const int4* __restrict__ sub, const int32_t* __restrict__ perm, const int32_t* __restrict__ cell,
          const T* __restrict__ frac, int64_t N, const void* __restrict__ alpha, int alpha_double,
-         T* __restrict__ grid, int nos, int Tb, int nb, int R, int m, T b, T norm) {
+         T* __restrict__ grid, int nos, int Tb, int nb, int R, int m, T b, T norm, const double* __restrict__ tap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
     const int4 sp = sub[blockIdx.x];
@@ -81,7 +89,7 @@ k_spread(const int4* __restrict__ sub, const int32_t* __restrict__ perm, const i
                                  : (T)(static_cast<const float*>(alpha)[src]);
         T w[DA][2 * kMaxM + 1];
         int off[DA];
-        node_weights<T, DA>(cell, frac, N, pos, bc, Tb, m, b, norm, w, off);
+        node_weights<T, DA>(cell, frac, N, pos, bc, Tb, m, b, norm, tap, w, off);
         if (DA == 1) {
             for (int k0 = 0; k0 < ntap; k0++) atomicAdd(&acc[off[0] + k0], a * w[0][k0]);
         } else if (DA == 2) {
@@ -112,7 +120,7 @@ template <typename T, int DA>
 __global__ void __launch_bounds__(kThreads)
 k_gather(const int4* __restrict__ sub, const int32_t* __restrict__ perm, const int32_t* __restrict__ cell,
          const T* __restrict__ frac, int64_t N, const T* __restrict__ h, int nos, int Tb, int nb, int R,
-         int m, T b, T norm, T* __restrict__ out) {
+         int m, T b, T norm, T* __restrict__ out, const double* __restrict__ tap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* reg = reinterpret_cast<T*>(smem_raw);
     const int4 sp = sub[blockIdx.x];
@@ -128,7 +136,7 @@ k_gather(const int4* __restrict__ sub, const int32_t* __restrict__ perm, const i
         const int64_t pos = (int64_t)sp.y + q;
         T w[DA][2 * kMaxM + 1];
         int off[DA];
-        node_weights<T, DA>(cell, frac, N, pos, bc, Tb, m, b, norm, w, off);
+        node_weights<T, DA>(cell, frac, N, pos, bc, Tb, m, b, norm, tap, w, off);
         T acc = T(0);
         if (DA == 1) {
             for (int k0 = 0; k0 < ntap; k0++) acc += reg[off[0] + k0] * w[0][k0];
@@ -181,13 +189,15 @@ anova_status spread_window(anova_plan* plan, const WindowPlan& w, const PointSet
     const size_t sh = (size_t)region_elems(w) * sizeof(T);
     const T b = (T)plan->b, norm = (T)plan->psi_norm;
     const T* frac = frac_of<T>(ps);
+    // the FP64 tap table describes the plan's own nodes
+    const double* tap = (sizeof(T) == 8 && &ps == &w.X) ? w.wtap64 : nullptr;
 #define ANOVA_SPREAD(DA_)                                                                    \
     {                                                                                        \
         auto k = k_spread<T, DA_>;                                                           \
         static bool once = (allow_big_smem(k), true);                                        \
         (void)once;                                                                          \
         k<<<ps.nsub, kThreads, sh, st>>>(ps.sub, ps.perm, ps.cell, frac, ps.N, alpha,          \
-                                         alpha_is_double, grid, w.nos, w.T, w.nb, w.R, plan->m, b, norm); \
+                                         alpha_is_double, grid, w.nos, w.T, w.nb, w.R, plan->m, b, norm, tap); \
     }
     if (w.dA == 1) ANOVA_SPREAD(1) else if (w.dA == 2) ANOVA_SPREAD(2) else ANOVA_SPREAD(3)
 #undef ANOVA_SPREAD
@@ -203,13 +213,14 @@ anova_status gather_window(anova_plan* plan, const WindowPlan& w, const PointSet
     const size_t sh = (size_t)region_elems(w) * sizeof(T);
     const T b = (T)plan->b, norm = (T)plan->psi_norm;
     const T* frac = frac_of<T>(ps);
+    const double* tap = (sizeof(T) == 8 && &ps == &w.X) ? w.wtap64 : nullptr;
 #define ANOVA_GATHER(DA_)                                                                    \
     {                                                                                        \
         auto k = k_gather<T, DA_>;                                                           \
         static bool once = (allow_big_smem(k), true);                                        \
         (void)once;                                                                          \
         k<<<ps.nsub, kThreads, sh, st>>>(ps.sub, ps.perm, ps.cell, frac, ps.N, h, w.nos, w.T,  \
-                                         w.nb, w.R, plan->m, b, norm, out);                  \
+                                         w.nb, w.R, plan->m, b, norm, out, tap);             \
     }
     if (w.dA == 1) ANOVA_GATHER(1) else if (w.dA == 2) ANOVA_GATHER(2) else ANOVA_GATHER(3)
 #undef ANOVA_GATHER
