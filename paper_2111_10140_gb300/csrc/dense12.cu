@@ -409,17 +409,31 @@ k_spread1_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
 }
 
 // ------------------------------------------------------------------ launches
+// blocks of `kernel` resident per SM (looked up once per kernel): the persistent
+// kernels launch exactly that many per SM, so their contiguous sub-problem
+// ranges run in one wave
+template <typename K>
+static int resident_blocks(K kernel) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, k12Threads, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
 template <int R, int M>
 static anova_status launch12(int dA, bool spread, const int4* sub, int nsub, const DenseWin* descs,
                              const float* psi_host, int sms, const void* alpha, int alpha_double, cudaStream_t st) {
     const PsiCoef<M> P = psi_coef<M>(psi_host);
-    const int grid = nsub < 8 * sms ? nsub : 8 * sms;
+    static const int res_s2 = resident_blocks(k_spread2_tc<R, M>), res_g2 = resident_blocks(k_gather2_pw<R, M>);
+    static const int res_s1 = resident_blocks(k_spread1_pw<R, M>), res_g1 = resident_blocks(k_gather1_pw<R, M>);
+    auto grid_of = [&](int res) { return nsub < res * sms ? nsub : res * sms; };
     if (dA == 2) {
-        if (spread) k_spread2_tc<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
-        else k_gather2_pw<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P);
+        if (spread)
+            k_spread2_tc<R, M><<<grid_of(res_s2), k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
+        else k_gather2_pw<R, M><<<grid_of(res_g2), k12Threads, 0, st>>>(sub, nsub, descs, P);
     } else {
-        if (spread) k_spread1_pw<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
-        else k_gather1_pw<R, M><<<grid, k12Threads, 0, st>>>(sub, nsub, descs, P);
+        if (spread)
+            k_spread1_pw<R, M><<<grid_of(res_s1), k12Threads, 0, st>>>(sub, nsub, descs, P, alpha, alpha_double);
+        else k_gather1_pw<R, M><<<grid_of(res_g1), k12Threads, 0, st>>>(sub, nsub, descs, P);
     }
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;
