@@ -195,6 +195,9 @@ struct anova_plan {
     float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool spread_pipe = true;            // ... with the next chunk's rows copied (cp.async) during the current MMAs
+    bool overlap12 = true;              // FP32 product: the 1-D / 2-D windows on a second stream beside the 3-D ones
+    cudaStream_t side = nullptr;        // that stream (created with the plan)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync
     bool gather_tc5 = true;             // FP32 dense 3-D gather: persistent tcgen05 kernel, weights on the fly
@@ -364,11 +367,13 @@ template <typename T>
 anova_status fft3_box_run(const Fft3Win* wins, const Fft3Shape& sh, int sm_count, cudaStream_t st);
 size_t fft12_window_smem(const WindowPlan& w, size_t real_bytes);
 bool fft3_slab_supported(const WindowPlan& w);
+// which dense groups a dense3_*_all call launches (and whether the spread sorts the coefficients first)
+constexpr int kDense12 = 1, kDense3 = 2, kDenseSort = 4, kDenseAll = 7;
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st,
-                              int* launches = nullptr);
+                              int* launches = nullptr, int dims = kDenseAll);
 template <typename T>
-anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st);
+anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st, int dims = kDenseAll);
 
 template <typename T>
 inline T* grid_of(anova_plan* plan, const WindowPlan& w) {

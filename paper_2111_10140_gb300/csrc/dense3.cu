@@ -1331,7 +1331,7 @@ anova_status dense_f32_gather_groups(int m, const float* poly, const int4* sub_b
 
 template <typename T>
 anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_double, cudaStream_t st,
-                              int* launches) {
+                              int* launches, int dims) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
     // the sorted coefficient copies serve the 1-D / 2-D kernels and the packed
@@ -1343,17 +1343,18 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
         const bool ok3 = (plan->spread_tc5 && tc5_supported(R, plan->m)) || plan->spread_tc;
         if (dA < 3 ? !ok12 : !ok3) need_sort = true;
     }
-    if (sizeof(T) == 4 && plan->dense_asort && need_sort) {
+    if ((dims & kDenseSort) && sizeof(T) == 4 && plan->dense_asort && need_sort) {
         k_sort_alpha<<<grid_for(plan->N * nd, kThreads, 8 * plan->sm_count), kThreads, 0, st>>>(
             descs, nd, plan->N, alpha, alpha_double);
         ANOVA_CHECK_LAUNCH();
         if (launches) ++*launches;
     }
-    if (launches) *launches += (int)plan->dense_groups.size();
     for (const auto& g : plan->dense_groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
         const int4* sub = plan->dense_sub + g[1];
         const int nsub = g[2];
+        if (!(dims & (dA < 3 ? kDense12 : kDense3))) continue;
+        if (launches) ++*launches;
         if (dA < 3) {
             if (sizeof(T) != 4 || !plan->dense_asort) continue;   // FP64: generic kernels per window
             if (plan->pw12 && tc5_supported(R, plan->m)) {
@@ -1390,13 +1391,14 @@ anova_status dense3_spread_all(anova_plan* plan, const void* alpha, int alpha_do
 }
 
 template <typename T>
-anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st) {
+anova_status dense3_gather_all(anova_plan* plan, cudaStream_t st, int dims) {
     const int nd = (int)plan->dense_windows.size();
     const DenseWin* descs = plan->dense_desc + (sizeof(T) == 8 ? 0 : nd);
     for (const auto& g : plan->dense_groups) {
         const int dA = g[0] / 100, R = g[0] % 100;
         const int4* sub = plan->dense_sub + g[1];
         const int nsub = g[2];
+        if (!(dims & (dA < 3 ? kDense12 : kDense3))) continue;
         if (dA < 3) {
             if (sizeof(T) != 4 || !plan->dense_asort) continue;
             if (plan->pw12 && tc5_supported(R, plan->m)) {
@@ -1456,10 +1458,10 @@ static const char* gather3_name(const anova_plan* plan) {
     return plan->gather_tc ? "k_gather3_tc<R>" : "k_gather3_f32<R>";
 }
 
-template anova_status dense3_spread_all<float>(anova_plan*, const void*, int, cudaStream_t, int*);
-template anova_status dense3_spread_all<double>(anova_plan*, const void*, int, cudaStream_t, int*);
-template anova_status dense3_gather_all<float>(anova_plan*, cudaStream_t);
-template anova_status dense3_gather_all<double>(anova_plan*, cudaStream_t);
+template anova_status dense3_spread_all<float>(anova_plan*, const void*, int, cudaStream_t, int*, int);
+template anova_status dense3_spread_all<double>(anova_plan*, const void*, int, cudaStream_t, int*, int);
+template anova_status dense3_gather_all<float>(anova_plan*, cudaStream_t, int);
+template anova_status dense3_gather_all<double>(anova_plan*, cudaStream_t, int);
 template anova_status spread3_dense<float>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,
                                            float*, cudaStream_t);
 template anova_status spread3_dense<double>(anova_plan*, const WindowPlan&, const PointSet&, const void*, int,

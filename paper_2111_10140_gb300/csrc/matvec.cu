@@ -116,11 +116,70 @@ k_window_sum_f32(const float* __restrict__ tmp, const double* __restrict__ eta, 
 }
 
 // -------------------------------------------------------------- matvec core
+// The FP32 product with the 1-D / 2-D windows' chain (spread, box FFT, gather)
+// on the plan's second stream beside the 3-D windows' chain: the two touch
+// disjoint grids and result slices, and the 1-D / 2-D box FFT (one block per
+// window) or the 3-D FFT then run while the other chain keeps the SMs busy.
+// A fork / join by events, so a graph captured on `st` holds both branches.
+static bool overlap_ok(const anova_plan* plan) {
+    if (!plan->overlap12 || plan->clock.enabled || !plan->side || plan->dense_windows.empty()) return false;
+    bool has12 = false, has3 = false;
+    for (const auto& g : plan->dense_groups) (g[0] / 100 < 3 ? has12 : has3) = true;
+    if (!has12 || !has3) return false;
+    for (int l = 0; l < plan->P; l++) {
+        const WindowPlan& w = plan->win[l];
+        if (w.dense && w.dA < 3 && !w.fft12) return false;   // its FFT would run on the other stream
+    }
+    return true;
+}
+
+template <typename T>
+static anova_status windows_apply_overlapped(anova_plan* plan, const void* alpha, int alpha_is_double, T* tmp,
+                                             cudaStream_t st) {
+    const int64_t N = plan->N;
+    cudaStream_t side = plan->side;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(T), st));
+    ANOVA_TRY(dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDenseSort));
+    ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_fork, st));
+    ANOVA_CUDA_TRY(cudaStreamWaitEvent(side, plan->ev_fork, 0));
+    anova_status s12 = dense3_spread_all<T>(plan, alpha, alpha_is_double, side, nullptr, kDense12);
+    if (s12 == ANOVA_OK) s12 = fft12_box_all<T>(plan, side);
+    if (s12 == ANOVA_OK) s12 = dense3_gather_all<T>(plan, side, kDense12);
+    // the join is recorded whatever happened, so a capture on `st` stays well formed
+    const cudaError_t ej = cudaEventRecord(plan->ev_join, side);
+    anova_status s3 = dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDense3);
+    for (int l = 0; l < plan->P && s3 == ANOVA_OK; l++) {
+        const WindowPlan& w = plan->win[l];
+        if (!w.dense) s3 = spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid_of<T>(plan, w), st);
+    }
+    if (s3 == ANOVA_OK && !plan->fft3_windows.empty()) s3 = fft3_box_all<T>(plan, st);
+    for (int l = 0; l < plan->P && s3 == ANOVA_OK; l++) {
+        const WindowPlan& w = plan->win[l];
+        if (fft3_box_supported(w) || w.fft12) continue;
+        s3 = fft_convolve_window<T>(plan, w, grid_of<T>(plan, w), st);
+    }
+    if (s3 == ANOVA_OK) s3 = dense3_gather_all<T>(plan, st, kDense3);
+    for (int l = 0; l < plan->P && s3 == ANOVA_OK; l++) {
+        const WindowPlan& w = plan->win[l];
+        if (!w.dense) s3 = gather_window<T>(plan, w, w.X, grid_of<T>(plan, w), tmp + (int64_t)l * N, st);
+    }
+    const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(st, plan->ev_join, 0) : ej;
+    if (s12 != ANOVA_OK) return s12;
+    if (s3 != ANOVA_OK) return s3;
+    if (ew != cudaSuccess) {
+        set_error(std::string("anova product: joining the 1-D / 2-D stream: ") + cudaGetErrorString(ew));
+        return ANOVA_ECUDA;
+    }
+    return ANOVA_OK;
+}
+
 // tmp_l = K_l alpha for every window (fast summation of Sec. 4.2 Eq. fastsum).
 // `tmp` must be plan->tmp: the batched dense kernels write their slices of it.
 template <typename T>
 static anova_status windows_apply(anova_plan* plan, const void* alpha, int alpha_is_double, T* tmp,
                                   cudaStream_t st) {
+    if constexpr (sizeof(T) == 4)
+        if (overlap_ok(plan)) return windows_apply_overlapped<T>(plan, alpha, alpha_is_double, tmp, st);
     const int64_t N = plan->N;
     ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(T), st));
     int nl = 0;

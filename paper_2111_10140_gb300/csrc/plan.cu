@@ -1124,6 +1124,9 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     plan->ell = ell;
     plan->b = M_PI * (2.0 - 1.0 / sigma);
     plan->psi_norm = (double)m / std::sinh(plan->b * m);
+    ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking));
+    ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming));
+    ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming));
     plan->win.resize(P);
     ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly, (2 * m * kPsiStride + 1) * sizeof(float)));
     ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly64, 2 * m * kPsiStride * sizeof(double)));
@@ -1465,6 +1468,9 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->fft12_desc);
     cudaFree(plan->psi_poly);
     cudaFree(plan->psi_poly64);
+    if (plan->side) cudaStreamDestroy(plan->side);
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     cudaFree(plan->cg_vec);
     cudaFree(plan->cg_scal);
     cudaFree(plan->cg_part);
