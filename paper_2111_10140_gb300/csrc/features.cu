@@ -369,10 +369,18 @@ __device__ unsigned long long threshold_key(int j, double lo, double hi) {
 }
 
 // thresholds of every column (one thread per (column, j)) and the column's
-// FP32 screen (lo, F / (hi - lo)) that gives a starting bin
+// FP32 screen: x = lo, y = F / (hi - lo) (the estimate t = (v - lo) y in FP32),
+// z = delta, a bound on |t - t_def| where t_def is the definition's FP64
+// quotient.  With M = max(|lo|, |hi|): the 20-bit truncation of v and the
+// rounding of lo to FP32 move t by at most (F / h) M (2^-20 + 2^-24); the FP32
+// subtraction, the rounding of F / h and the product by at most 3.1 2^-24 F
+// (< 8e-4); denormal v (read as 0) by (F / h) 2^-126; the definition's own
+// FP64 roundings by < 1e-12.  delta = 1.25 (first and third) + 1e-3.  Where
+// the FP32 form cannot hold the column (|values| or F / h beyond 1e37) or
+// delta >= 1/4, z = 1: every element goes to the thresholds.
 __global__ void __launch_bounds__(kThreads)
 k_fine_thresholds(const double* __restrict__ lo, const double* __restrict__ hi, int d,
-                  unsigned long long* __restrict__ thr, float2* __restrict__ screen) {
+                  unsigned long long* __restrict__ thr, float4* __restrict__ screen) {
     const int c = blockIdx.y;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d || j > kFine) return;
@@ -382,7 +390,16 @@ k_fine_thresholds(const double* __restrict__ lo, const double* __restrict__ hi, 
     else if (j == kFine || !(H > L)) key = ~0ull;
     else key = threshold_key(j, L, H);
     thr[(size_t)c * kThrRow + j] = key;
-    if (j == 0) screen[c] = H > L ? make_float2((float)L, (float)((double)kFine / (H - L))) : make_float2(0.f, 0.f);
+    if (j == 0) {
+        if (H > L) {
+            const double M = fmax(fabs(L), fabs(H)), sfd = (double)kFine / (H - L);
+            double delta = 1.25 * (sfd * M * (0x1p-20 + 0x1p-24) + sfd * 0x1p-126) + 1e-3;
+            if (!(M < 1e37) || !(sfd < 1e37) || !(delta < 0.25)) delta = 1.0;
+            screen[c] = make_float4((float)L, (float)sfd, __double2float_ru(delta), 0.f);
+        } else {
+            screen[c] = make_float4(0.f, 0.f, 0.f, 0.f);   // constant column: t = 0, bin 0 for every value
+        }
+    }
 }
 
 // FP32 value of v from its high word (mantissa truncated to 20 bits), 0 where
@@ -396,24 +413,36 @@ __device__ __forceinline__ float approx_float(double v) {
 
 // fine bin of v from the thresholds of its column: an FP32 estimate, then
 // moved until thr_j <= key(v) < thr_{j+1} (exact; each loop ends within F steps)
-__device__ __forceinline__ int screen_bin(double v, float2 scr) {
+__device__ __forceinline__ int screen_bin(double v, float4 scr) {
     const float t = (approx_float(v) - scr.x) * scr.y;
     return (int)fminf(fmaxf(t, 0.0f), (float)(kFine - 1));
+}
+// the bin from the FP32 estimate alone where it is at least delta from every
+// bin boundary (then the definition's bin is the same), else -1
+__device__ __forceinline__ int fast_bin(double v, float4 scr) {
+    const float t = (approx_float(v) - scr.x) * scr.y;
+    const float dl = scr.z;
+    if (!(dl < 0.5f) || !(t == t)) return -1;
+    if (t < __fsub_rd(1.0f, dl)) return 0;                        // t_def < 1: bin 0 (clamped below)
+    if (t >= __fadd_ru((float)(kFine - 1), dl)) return kFine - 1;  // t_def >= F - 1: the last bin
+    const float fl = floorf(t);
+    return (t - fl < dl || fl + 1.0f - t < dl) ? -1 : (int)fl;
 }
 __device__ __forceinline__ int fix_bin(unsigned long long key, int j, const unsigned long long* __restrict__ thr) {
     while (j > 0 && key < __ldg(thr + j)) j--;
     while (j < kFine - 1 && key >= __ldg(thr + j + 1)) j++;
     return j;
 }
-__device__ __forceinline__ int fine_bin(double v, const unsigned long long* __restrict__ thr, float2 scr) {
-    return fix_bin(ord_of(v), screen_bin(v, scr), thr);
+__device__ __forceinline__ int fine_bin(double v, const unsigned long long* __restrict__ thr, float4 scr) {
+    const int j = fast_bin(v, scr);
+    return j >= 0 ? j : fix_bin(ord_of(v), screen_bin(v, scr), thr);
 }
 
 // fine bin of every element (anova_mis_fine_bins), elements owned as in
 // k_col_partials
 __global__ void __launch_bounds__(kThreads)
 k_fine_bins_out(const double* __restrict__ X, int64_t N, int d, int64_t ld,
-                const unsigned long long* __restrict__ thr, const float2* __restrict__ screen,
+                const unsigned long long* __restrict__ thr, const float4* __restrict__ screen,
                 int64_t rows_per_block, int32_t* __restrict__ out) {
     const int t = threadIdx.x;
     const int G = d <= kThreads ? kThreads / d : 1;
@@ -445,7 +474,7 @@ __device__ __forceinline__ void add_aggregated(unsigned int* base, int key, bool
 
 __global__ void __launch_bounds__(kThreads)
 k_fine_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld, const unsigned long long* __restrict__ thr,
-            const float2* __restrict__ screen, int64_t rows_per_block, unsigned int* __restrict__ hist) {
+            const float4* __restrict__ screen, int64_t rows_per_block, unsigned int* __restrict__ hist) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min(N, r0 + rows_per_block);
@@ -492,7 +521,7 @@ __global__ void __launch_bounds__(1024) k_quantile_map(const unsigned int* __res
 // labels outside [0, nclass) are counted in bad (once per row)
 __global__ void __launch_bounds__(kThreads)
 k_joint(const double* __restrict__ X, int64_t N, int d, int64_t ld, const unsigned long long* __restrict__ thr,
-        const float2* __restrict__ screen, const unsigned char* __restrict__ qmap,
+        const float4* __restrict__ screen, const unsigned char* __restrict__ qmap,
         const int32_t* __restrict__ labels, int B, int nclass, int64_t rows_per_block,
         unsigned long long* __restrict__ joint, unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -539,12 +568,12 @@ constexpr size_t kCHPartMax = (size_t)512 << 20;       // largest scratch of blo
 
 __global__ void __launch_bounds__(kCHThreads)
 k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
-                  const unsigned long long* __restrict__ thr, const float2* __restrict__ screen,
+                  const unsigned long long* __restrict__ thr, const float4* __restrict__ screen,
                   const int32_t* __restrict__ labels, int nclass, int gcols, int ngroups, int64_t rows_per_block,
                   unsigned int* __restrict__ part, unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) unsigned int sh[];
     const int W = (nclass + 1) / 2;                       // words per (column, fine bin)
-    const int g = blockIdx.x % ngroups;
+        const int g = blockIdx.x % ngroups;
     const int64_t rr = blockIdx.x / ngroups;
     const int c_lo = g * gcols;
     const int gc = min(gcols, d - c_lo);
@@ -559,13 +588,13 @@ k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
     unsigned int nbad = 0;
     if (threadIdx.x < per * gc) {
         const unsigned long long* __restrict__ tc = thr + (size_t)c * kThrRow;
-        const float2 scr = screen[c];
-        // four rows per step: their loads, then their two threshold loads each, are in flight together
+        const float4 scr = screen[c];
+        // four rows per step, their loads in flight together; an element near a bin
+        // boundary (rare) takes its bin from the thresholds
         constexpr int U = 4;
         for (int64_t r = r0 + threadIdx.x / gc; r < r1; r += U * per) {
             double v[U];
-            int y[U], j[U];
-            unsigned long long key[U], tl[U], th[U];
+            int y[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int64_t ru = r + (int64_t)u * per;
@@ -576,16 +605,10 @@ k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                key[u] = ord_of(v[u]);
-                j[u] = screen_bin(v[u], scr);
-                tl[u] = __ldg(tc + j[u]);
-                th[u] = __ldg(tc + j[u] + 1);
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
                 if (y[u] < 0 || y[u] >= nclass) continue;
-                if (key[u] < tl[u] || key[u] >= th[u]) j[u] = fix_bin(key[u], j[u], tc);
-                atomicAdd(&sh[(cl * kFine + j[u]) * W + (y[u] >> 1)], 1u << (16 * (y[u] & 1)));
+                int j = fast_bin(v[u], scr);
+                if (j < 0) j = fix_bin(ord_of(v[u]), screen_bin(v[u], scr), tc);
+                atomicAdd(&sh[(cl * kFine + j) * W + (y[u] >> 1)], 1u << (16 * (y[u] & 1)));
             }
         }
     }
@@ -738,7 +761,7 @@ anova_status col_stats(const double* X, int64_t N, int d, int64_t ld, const ColS
 struct FineBins {
     double *lo = nullptr, *hi = nullptr;
     unsigned long long* thr = nullptr;
-    float2* screen = nullptr;
+    float4* screen = nullptr;
 };
 
 anova_status fine_bins_setup(const double* X, int64_t N, int d, int64_t ld, const ColStats& cs, FineBins& fb,
@@ -746,7 +769,7 @@ anova_status fine_bins_setup(const double* X, int64_t N, int d, int64_t ld, cons
     ANOVA_CUDA_TRY(scratch.alloc(&fb.lo, d * sizeof(double)));
     ANOVA_CUDA_TRY(scratch.alloc(&fb.hi, d * sizeof(double)));
     ANOVA_CUDA_TRY(scratch.alloc(&fb.thr, (size_t)d * kThrRow * sizeof(unsigned long long)));
-    ANOVA_CUDA_TRY(scratch.alloc(&fb.screen, d * sizeof(float2)));
+    ANOVA_CUDA_TRY(scratch.alloc(&fb.screen, d * sizeof(float4)));
     ANOVA_TRY(col_stats<kRange>(X, N, d, ld, cs, fb.lo, fb.hi, st));
     k_fine_thresholds<<<dim3((kThrRow + kThreads - 1) / kThreads, d), kThreads, 0, st>>>(fb.lo, fb.hi, d, fb.thr,
                                                                                          fb.screen);
