@@ -30,6 +30,11 @@
  *     by every call on it, so calls on one plan from several threads (or on
  *     several streams at once) must be serialised by the caller.  Fitted
  *     models and the server state their own rules below.
+ *   - Scratch the calls need comes stream-ordered from the device's default
+ *     memory pool.  On its first such allocation on a device the library
+ *     raises that pool's release threshold to 1 GiB (unless it is higher
+ *     already), so freed scratch stays reserved across synchronisations
+ *     instead of being unmapped and mapped again by the next call.
  *   - Arrays of points are row-major: point i, feature f at [i*ld + f].
  *   - Multiple right-hand sides are column-major: column r at [r*ld + i].
  */
@@ -642,10 +647,24 @@ anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable);
  * tensor cores (enable != 0, the default: the contraction of a bin's nodes
  * into its region, and the region against the nodes' weights, as 3xTF32
  * mma.sync / tcgen05 products with FP32 accuracy) or on FP32 FMA kernels
- * (enable = 0), e.g. to compare the two.  The 1-D / 2-D kernels and batches
- * are not affected.  Drops the plan's captured graphs.  Must not overlap with
+ * (enable = 0), e.g. to compare the two; enable = 2 also moves the 3-D spread
+ * from mma.sync to the persistent tcgen05 kernel (off by default: measured
+ * slower).  The 1-D / 2-D kernels and batches are not affected.  Drops the plan's captured graphs.  Must not overlap with
  * other calls on the plan.  Errors: EINVAL (NULL plan). */
 anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable);
+
+/* anova_plan_set_overlap -- how the FP32 product schedules the 1-D / 2-D
+ * windows' chain (spread, box FFT, gather) against the 3-D windows' chain.
+ * The two touch disjoint grids and result slices; the plan runs the first on
+ * a second stream, forked from and joined back to the call's stream by
+ * events.  mode & 3: 0 one stream (no overlap); 1 forked before the 3-D
+ * spread is queued; 2 (the default) forked before, queued after the 3-D
+ * spread; 3 forked after the 3-D spread has run.  mode & 4: the second stream at the
+ * device's highest stream priority instead of its lowest.  A scheduling
+ * choice only: the results are the same.  Drops the plan's captured graphs.
+ * Must not overlap with other calls on the plan.  Errors: EINVAL (NULL plan,
+ * mode outside 0..3 and 5..7). */
+anova_status anova_plan_set_overlap(anova_plan* plan, int32_t mode);
 
 #ifdef __cplusplus
 }

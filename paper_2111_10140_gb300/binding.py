@@ -37,6 +37,7 @@ _SIGNATURES = {
                                    _vp, _vp]),
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
     "anova_plan_set_tensor_cores": (_i32, [_vp, _i32]),
+    "anova_plan_set_overlap": (_i32, [_vp, _i32]),
     "anova_fastsum_plan_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
                                        _i32, _i32, _pi32, _vp, ctypes.POINTER(_vp)]),
     "anova_autotune_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
@@ -330,8 +331,14 @@ def anova_plan_set_graphs(plan: Plan, enable: bool):
     _check(lib().anova_plan_set_graphs(plan.handle, 1 if enable else 0), "anova_plan_set_graphs")
 
 
-def anova_plan_set_tensor_cores(plan: Plan, enable: bool):
-    _check(lib().anova_plan_set_tensor_cores(plan.handle, 1 if enable else 0), "anova_plan_set_tensor_cores")
+def anova_plan_set_tensor_cores(plan: Plan, enable):
+    """enable: False (FMA kernels), True (the default kernels) or 2 (also the tcgen05 3-D spread)."""
+    mode = 2 if enable == 2 else (1 if enable else 0)
+    _check(lib().anova_plan_set_tensor_cores(plan.handle, mode), "anova_plan_set_tensor_cores")
+
+
+def anova_plan_set_overlap(plan: Plan, mode: int):
+    _check(lib().anova_plan_set_overlap(plan.handle, int(mode)), "anova_plan_set_overlap")
 
 
 def anova_stage_times(plan: Plan):

@@ -195,8 +195,11 @@ struct anova_plan {
     float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool spread_pipe = true;            // ... with the next chunk's rows copied (cp.async) during the current MMAs
-    bool overlap12 = true;              // FP32 product: the 1-D / 2-D windows on a second stream beside the 3-D ones
-    cudaStream_t side = nullptr;        // that stream (created with the plan)
+    int overlap12 = 1;                  // FP32 product: the 1-D / 2-D windows on a second stream beside the 3-D
+                                        // ones (anova_plan_set_overlap: 0 off, 1 forked before the 3-D spread,
+                                        // 2 after the 3-D spread is queued, 3 after it has run; +4 high priority)
+    cudaStream_t side = nullptr;        // that stream (created with the plan, lowest priority)
+    cudaStream_t side_hi = nullptr;     // the same at the highest priority
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool gather_tc = true;              // FP32 dense gather on tensor cores (3xTF32) instead of FFMA2
     bool gather_umma = true;            // ... on tcgen05 (tensor memory accumulators) instead of mma.sync

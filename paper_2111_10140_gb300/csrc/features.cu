@@ -557,7 +557,9 @@ k_joint(const double* __restrict__ X, int64_t N, int d, int64_t ld, const unsign
 // takes column group g (gcols consecutive columns) over row range rr and
 // counts in shared memory: per (column, fine bin) ceil(nclass / 2) 32-bit
 // words holding two 16-bit class counts each (a block takes at most 65535
-// rows, so a half never carries into the other).  Thread t handles column
+// rows, so a half never carries into the other), and one spare word after
+// each column's counts, so that equal bins of neighbouring columns sit in
+// different banks.  Thread t handles column
 // t mod gc of rows t / gc, t / gc + NT / gc, ... (consecutive threads read
 // consecutive columns of a row).  The block writes its counts to its own slot
 // of a scratch array; k_class_hist_reduce adds the slots in a fixed order.
@@ -573,11 +575,12 @@ k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
                   unsigned int* __restrict__ part, unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) unsigned int sh[];
     const int W = (nclass + 1) / 2;                       // words per (column, fine bin)
-        const int g = blockIdx.x % ngroups;
+    const int CS = kFine * W + 1;                          // words per column: odd, so columns fall on other banks
+    const int g = blockIdx.x % ngroups;
     const int64_t rr = blockIdx.x / ngroups;
     const int c_lo = g * gcols;
     const int gc = min(gcols, d - c_lo);
-    const int words = gc * kFine * W;
+    const int words = gc * CS;
     for (int i = threadIdx.x; i < words; i += blockDim.x) sh[i] = 0u;
     __syncthreads();
     const int64_t r0 = rr * rows_per_block;
@@ -608,13 +611,13 @@ k_fine_class_hist(const double* __restrict__ X, int64_t N, int d, int64_t ld,
                 if (y[u] < 0 || y[u] >= nclass) continue;
                 int j = fast_bin(v[u], scr);
                 if (j < 0) j = fix_bin(ord_of(v[u]), screen_bin(v[u], scr), tc);
-                atomicAdd(&sh[(cl * kFine + j) * W + (y[u] >> 1)], 1u << (16 * (y[u] & 1)));
+                atomicAdd(&sh[cl * CS + j * W + (y[u] >> 1)], 1u << (16 * (y[u] & 1)));
             }
         }
     }
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
     __syncthreads();
-    unsigned int* out = part + (size_t)blockIdx.x * gcols * kFine * W;
+    unsigned int* out = part + (size_t)blockIdx.x * gcols * CS;
     for (int i = threadIdx.x; i < words; i += blockDim.x) out[i] = sh[i];
 }
 
@@ -623,14 +626,15 @@ __global__ void __launch_bounds__(kThreads)
 k_class_hist_reduce(const unsigned int* __restrict__ part, int d, int nclass, int gcols, int ngroups, int nranges,
                     unsigned int* __restrict__ hist) {
     const int W = (nclass + 1) / 2;
+    const int CS = kFine * W + 1;                          // words per column in a block's slot
     const int64_t total = (int64_t)d * kFine * W;
-    const size_t slot = (size_t)gcols * kFine * W;
+    const size_t slot = (size_t)gcols * CS;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int w = (int)(i % W);
         const int64_t cj = i / W;                         // c * kFine + j
         const int c = (int)(cj / kFine);
         const int g = c / gcols;
-        const size_t inner = ((size_t)(c - g * gcols) * kFine + (size_t)(cj % kFine)) * W + w;
+        const size_t inner = (size_t)(c - g * gcols) * CS + (size_t)(cj % kFine) * W + w;
         unsigned int lo = 0, hi = 0;
         for (int rr = 0; rr < nranges; rr++) {
             const unsigned int v = part[((size_t)rr * ngroups + g) * slot + inner];
@@ -731,18 +735,39 @@ struct ColStats {
 
 size_t partial_smem(int d) { return d <= kThreads ? (size_t)(kThreads / d) * d * 16 : 0; }
 
-anova_status col_alloc(int64_t N, int d, int mode, ColStats& cs, Scratch& scratch) {
-    stat_grid(N, device_sms(), &cs.nblk, &cs.rows);
+// Hands out 256-byte aligned pieces of one scratch allocation.  A call lays its
+// buffers out twice: once with base == nullptr to learn the total, then over
+// the allocation, so each call makes one allocation and one free.
+struct Carve {
+    unsigned char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    void take(T** p, size_t bytes) {
+        *p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+    }
+};
+
+template <typename Layout>
+anova_status carve_all(Scratch& scratch, Layout&& layout) {
+    Carve size;
+    layout(size);
+    Carve c;
+    ANOVA_CUDA_TRY(scratch.alloc(&c.base, size.off));
+    layout(c);
+    return ANOVA_OK;
+}
+
+void col_layout(int d, int mode, ColStats& cs, Carve& c) {
     const size_t n = (size_t)cs.nblk * d;
     if (mode == kMoments) {
-        ANOVA_CUDA_TRY(scratch.alloc(&cs.pS, n * sizeof(double)));
-        ANOVA_CUDA_TRY(scratch.alloc(&cs.pQ, n * sizeof(double)));
-        ANOVA_CUDA_TRY(scratch.alloc(&cs.pK, n * sizeof(double)));
+        c.take(&cs.pS, n * sizeof(double));
+        c.take(&cs.pQ, n * sizeof(double));
+        c.take(&cs.pK, n * sizeof(double));
     } else {
-        ANOVA_CUDA_TRY(scratch.alloc(&cs.pmin, n * sizeof(unsigned long long)));
-        ANOVA_CUDA_TRY(scratch.alloc(&cs.pmax, n * sizeof(unsigned long long)));
+        c.take(&cs.pmin, n * sizeof(unsigned long long));
+        c.take(&cs.pmax, n * sizeof(unsigned long long));
     }
-    return ANOVA_OK;
 }
 
 // one read of X: mean and sd (kMoments) or lo and hi (kRange) of every column
@@ -764,12 +789,15 @@ struct FineBins {
     float4* screen = nullptr;
 };
 
+void fine_layout(int d, FineBins& fb, Carve& c) {
+    c.take(&fb.lo, d * sizeof(double));
+    c.take(&fb.hi, d * sizeof(double));
+    c.take(&fb.thr, (size_t)d * kThrRow * sizeof(unsigned long long));
+    c.take(&fb.screen, d * sizeof(float4));
+}
+
 anova_status fine_bins_setup(const double* X, int64_t N, int d, int64_t ld, const ColStats& cs, FineBins& fb,
-                             Scratch& scratch, cudaStream_t st) {
-    ANOVA_CUDA_TRY(scratch.alloc(&fb.lo, d * sizeof(double)));
-    ANOVA_CUDA_TRY(scratch.alloc(&fb.hi, d * sizeof(double)));
-    ANOVA_CUDA_TRY(scratch.alloc(&fb.thr, (size_t)d * kThrRow * sizeof(unsigned long long)));
-    ANOVA_CUDA_TRY(scratch.alloc(&fb.screen, d * sizeof(float4)));
+                             cudaStream_t st) {
     ANOVA_TRY(col_stats<kRange>(X, N, d, ld, cs, fb.lo, fb.hi, st));
     k_fine_thresholds<<<dim3((kThrRow + kThreads - 1) / kThreads, d), kThreads, 0, st>>>(fb.lo, fb.hi, d, fb.thr,
                                                                                          fb.screen);
@@ -794,7 +822,8 @@ anova_status anova_zscore_fit(const double* X, int64_t N, int32_t d, int64_t ld,
     cudaStream_t st = (cudaStream_t)stream;
     Scratch scratch(st);
     ColStats cs;
-    ANOVA_TRY(col_alloc(N, d, kMoments, cs, scratch));
+    stat_grid(N, device_sms(), &cs.nblk, &cs.rows);
+    ANOVA_TRY(carve_all(scratch, [&](Carve& c) { col_layout(d, kMoments, cs, c); }));
     // one pass: shifted block sums, combined over blocks by the pairwise update
     ANOVA_TRY(col_stats<kMoments>(X, N, d, ld, cs, mean, sd, st));
     return ANOVA_OK;
@@ -827,17 +856,13 @@ anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const 
     Scratch scratch(st);
     ColStats cs;
     FineBins fb;
-    unsigned long long *joint = nullptr, *bad = nullptr;
+    unsigned long long* joint = nullptr;
     const size_t cells = (size_t)d * bins * nclass;
-    ANOVA_TRY(col_alloc(N, d, kRange, cs, scratch));
-    ANOVA_CUDA_TRY(scratch.alloc(&joint, (cells + 1) * sizeof(unsigned long long)));
-    bad = joint + cells;
-    ANOVA_TRY(fine_bins_setup(X, N, d, ld, cs, fb, scratch, st));
-    ANOVA_CUDA_TRY(cudaMemsetAsync(joint, 0, (cells + 1) * sizeof(unsigned long long), st));
+    stat_grid(N, device_sms(), &cs.nblk, &cs.rows);
     // two passes over X (privatised (fine bin, class) counts) where they fit, else three
     const int W = (nclass + 1) / 2;
     const int sms = device_sms();
-    const int gmax = std::max(1, (int)(kCHSmem / ((size_t)kFine * W * sizeof(unsigned int))));
+    const int gmax = std::max(1, (int)(kCHSmem / (((size_t)kFine * W + 1) * sizeof(unsigned int))));
     const int ngroups = (d + gmax - 1) / gmax;
     const int gcols = (d + ngroups - 1) / ngroups;
     int64_t nranges = std::max<int64_t>((N + kCHMaxRows - 1) / kCHMaxRows,
@@ -845,12 +870,27 @@ anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const 
     nranges = std::max<int64_t>(nranges, 1);
     const int64_t rows_pb = (N + nranges - 1) / nranges;
     nranges = (N + rows_pb - 1) / rows_pb;
-    const size_t slot = (size_t)gcols * kFine * W;
+    const size_t slot = (size_t)gcols * (kFine * W + 1);
     const size_t part_bytes = (size_t)nranges * ngroups * slot * sizeof(unsigned int);
-    if (nclass <= 4 && part_bytes <= kCHPartMax && nranges * ngroups <= INT32_MAX) {
-        unsigned int *part = nullptr, *chist = nullptr;
-        ANOVA_CUDA_TRY(scratch.alloc(&part, part_bytes));
-        ANOVA_CUDA_TRY(scratch.alloc(&chist, (size_t)d * kFine * nclass * sizeof(unsigned int)));
+    const bool two_pass = nclass <= 4 && part_bytes <= kCHPartMax && nranges * ngroups <= INT32_MAX;
+    unsigned int *part = nullptr, *chist = nullptr, *hist = nullptr;
+    unsigned char* qmap = nullptr;
+    ANOVA_TRY(carve_all(scratch, [&](Carve& c) {
+        col_layout(d, kRange, cs, c);
+        fine_layout(d, fb, c);
+        c.take(&joint, (cells + 1) * sizeof(unsigned long long));
+        if (two_pass) {
+            c.take(&part, part_bytes);
+            c.take(&chist, (size_t)d * kFine * nclass * sizeof(unsigned int));
+        } else {
+            c.take(&hist, (size_t)d * kFine * sizeof(unsigned int));
+            c.take(&qmap, (size_t)d * kFine);
+        }
+    }));
+    unsigned long long* bad = joint + cells;
+    ANOVA_TRY(fine_bins_setup(X, N, d, ld, cs, fb, st));
+    ANOVA_CUDA_TRY(cudaMemsetAsync(joint, 0, (cells + 1) * sizeof(unsigned long long), st));
+    if (two_pass) {
         static bool attr2 = [] {
             cudaFuncSetAttribute(k_fine_class_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCHSmem);
             return true;
@@ -862,10 +902,6 @@ anova_status anova_mis(const double* X, int64_t N, int32_t d, int64_t ld, const 
             part, d, nclass, gcols, ngroups, (int)nranges, chist);
         k_quantile_joint<<<d, 1024, 0, st>>>(chist, N, bins, nclass, joint);
     } else {
-        unsigned int* hist = nullptr;
-        unsigned char* qmap = nullptr;
-        ANOVA_CUDA_TRY(scratch.alloc(&hist, (size_t)d * kFine * sizeof(unsigned int)));
-        ANOVA_CUDA_TRY(scratch.alloc(&qmap, (size_t)d * kFine));
         ANOVA_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)d * kFine * sizeof(unsigned int), st));
         k_fine_hist<<<cs.nblk, kThreads, 0, st>>>(X, N, d, ld, fb.thr, fb.screen, cs.rows, hist);
         k_quantile_map<<<d, 1024, 0, st>>>(hist, N, bins, qmap);
@@ -915,8 +951,12 @@ anova_status anova_mis_fine_bins(const double* X, int64_t N, int32_t d, int64_t 
     Scratch scratch(st);
     ColStats cs;
     FineBins fb;
-    ANOVA_TRY(col_alloc(N, d, kRange, cs, scratch));
-    ANOVA_TRY(fine_bins_setup(X, N, d, ld, cs, fb, scratch, st));
+    stat_grid(N, device_sms(), &cs.nblk, &cs.rows);
+    ANOVA_TRY(carve_all(scratch, [&](Carve& c) {
+        col_layout(d, kRange, cs, c);
+        fine_layout(d, fb, c);
+    }));
+    ANOVA_TRY(fine_bins_setup(X, N, d, ld, cs, fb, st));
     k_fine_bins_out<<<cs.nblk, kThreads, 0, st>>>(X, N, d, ld, fb.thr, fb.screen, cs.rows, bins);
     ANOVA_CHECK_LAUNCH();
     return ANOVA_OK;

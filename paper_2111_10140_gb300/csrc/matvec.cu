@@ -122,7 +122,9 @@ k_window_sum_f32(const float* __restrict__ tmp, const double* __restrict__ eta, 
 // window) or the 3-D FFT then run while the other chain keeps the SMs busy.
 // A fork / join by events, so a graph captured on `st` holds both branches.
 static bool overlap_ok(const anova_plan* plan) {
-    if (!plan->overlap12 || plan->clock.enabled || !plan->side || plan->dense_windows.empty()) return false;
+    if ((plan->overlap12 & 3) == 0 || plan->clock.enabled || !plan->side || !plan->side_hi ||
+        plan->dense_windows.empty())
+        return false;
     bool has12 = false, has3 = false;
     for (const auto& g : plan->dense_groups) (g[0] / 100 < 3 ? has12 : has3) = true;
     if (!has12 || !has3) return false;
@@ -137,17 +139,22 @@ template <typename T>
 static anova_status windows_apply_overlapped(anova_plan* plan, const void* alpha, int alpha_is_double, T* tmp,
                                              cudaStream_t st) {
     const int64_t N = plan->N;
-    cudaStream_t side = plan->side;
+    const int when = plan->overlap12 & 3;
+    cudaStream_t side = (plan->overlap12 & 4) ? plan->side_hi : plan->side;
     ANOVA_CUDA_TRY(cudaMemsetAsync(plan->grid, 0, plan->grid_elems * sizeof(T), st));
     ANOVA_TRY(dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDenseSort));
+    anova_status s3 = ANOVA_OK;
+    if (when == 3) s3 = dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDense3);
     ANOVA_CUDA_TRY(cudaEventRecord(plan->ev_fork, st));
-    ANOVA_CUDA_TRY(cudaStreamWaitEvent(side, plan->ev_fork, 0));
-    anova_status s12 = dense3_spread_all<T>(plan, alpha, alpha_is_double, side, nullptr, kDense12);
+    if (when == 2 && s3 == ANOVA_OK) s3 = dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDense3);
+    // the fork is waited on and the join recorded whatever happened, so a capture on `st` stays well formed
+    const cudaError_t ef = cudaStreamWaitEvent(side, plan->ev_fork, 0);
+    anova_status s12 = ef == cudaSuccess ? ANOVA_OK : ANOVA_ECUDA;
+    if (s12 == ANOVA_OK) s12 = dense3_spread_all<T>(plan, alpha, alpha_is_double, side, nullptr, kDense12);
     if (s12 == ANOVA_OK) s12 = fft12_box_all<T>(plan, side);
     if (s12 == ANOVA_OK) s12 = dense3_gather_all<T>(plan, side, kDense12);
-    // the join is recorded whatever happened, so a capture on `st` stays well formed
     const cudaError_t ej = cudaEventRecord(plan->ev_join, side);
-    anova_status s3 = dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDense3);
+    if (when == 1 && s3 == ANOVA_OK) s3 = dense3_spread_all<T>(plan, alpha, alpha_is_double, st, nullptr, kDense3);
     for (int l = 0; l < plan->P && s3 == ANOVA_OK; l++) {
         const WindowPlan& w = plan->win[l];
         if (!w.dense) s3 = spread_window<T>(plan, w, w.X, alpha, alpha_is_double, grid_of<T>(plan, w), st);
@@ -164,6 +171,10 @@ static anova_status windows_apply_overlapped(anova_plan* plan, const void* alpha
         if (!w.dense) s3 = gather_window<T>(plan, w, w.X, grid_of<T>(plan, w), tmp + (int64_t)l * N, st);
     }
     const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(st, plan->ev_join, 0) : ej;
+    if (ef != cudaSuccess) {
+        set_error(std::string("anova product: forking the 1-D / 2-D stream: ") + cudaGetErrorString(ef));
+        return ANOVA_ECUDA;
+    }
     if (s12 != ANOVA_OK) return s12;
     if (s3 != ANOVA_OK) return s3;
     if (ew != cudaSuccess) {
@@ -817,8 +828,20 @@ anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable) {
     plan->gather_tc = on;
     plan->gather_umma = on;
     plan->gather_tc5 = on;
-    plan->spread_tc5 = false;
+    plan->spread_tc5 = enable == 2;
     for (auto& g : plan->graphs)      // the captured launch sequences name the old kernels
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    plan->graphs.clear();
+    return ANOVA_OK;
+}
+
+anova_status anova_plan_set_overlap(anova_plan* plan, int32_t mode) {
+    if (!plan || mode < 0 || mode > 7 || ((mode & 3) == 0 && mode != 0)) {
+        set_error("anova_plan_set_overlap: mode must be 0, 1..3 or 5..7");
+        return ANOVA_EINVAL;
+    }
+    plan->overlap12 = mode;
+    for (auto& g : plan->graphs)      // the captured launch sequences hold the old schedule
         if (g.exec) cudaGraphExecDestroy(g.exec);
     plan->graphs.clear();
     return ANOVA_OK;
