@@ -387,6 +387,12 @@ def run_ours(args):
                                      precision=B.MIXED)
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t_plan) * 1e3
+    # kernel forms (3-D spread, 3-D gather, 1-D / 2-D schedule) from the library's tuner, same condition
+    if not args.bin_side and not args.no_autotune:
+        kernels, _ = B.anova_autotune_kernels(plan, reps=5)
+        kernels_how = "autotuned"
+    else:
+        kernels, kernels_how = B.anova_plan_get_kernels(plan), "default"
     alpha = torch.from_numpy(w.alpha).to(dev).float()
     out = torch.empty_like(alpha)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -420,7 +426,7 @@ def run_ours(args):
     fma_names = B.anova_dense3_kernels(plan)
     B.anova_matvec(plan, alpha, out)
     fma_acc = accuracy_vs_direct(B, torch, np, X, w, out, args.check_rows, 7, dev)
-    B.anova_plan_set_tensor_cores(plan, True)
+    B.anova_plan_set_kernels(plan, kernels["spread3"], kernels["gather3"], kernels["schedule"])
     no_tensor = {"ms_per_matvec": statistics.median(fma_ms), "gpts": N / statistics.median(fma_ms) / 1e6,
                  "spread_3d_kernel_ms": fma_stage["spread_3d_kernel"] / fsteps,
                  "gather_3d_kernel_ms": fma_stage["gather_3d_kernel"] / fsteps,
@@ -508,6 +514,13 @@ def run_ours(args):
                "krr": mkrr, "krr_plain_fp64": mkrr64}
         del Xm
 
+    # the other forms of the path on reduced configurations (rank 0 of a one-GPU run; outside the clocks window)
+    forms = None
+    if rank == 0 and ws == 1 and not args.skip_forms:
+        del flush
+        torch.cuda.empty_cache()
+        forms = other_forms(args)
+
     q = sorted(step_ms)
     lat = {"p50": q[len(q) // 2], "p99": q[min(len(q) - 1, int(0.99 * len(q)))], "unit": "ms"}
     if rank == 0:
@@ -522,6 +535,7 @@ def run_ours(args):
                 "plan": {"bin_side_1d_2d_3d": sides,
                          "bin_sides": "given" if args.bin_side else ("autotuned" if not args.no_autotune else "rule"),
                          "create_ms": plan_ms,
+                         "kernels": kernels, "kernels_chosen": kernels_how,
                          "create_note": "anova_fastsum_plan_bins (frames, binning, D_k, FP32 weight tables, "
                                         "FP64 data), wall clock, outside the timed steps"},
                 "roofline": roofline, "cpu_baseline": cpu,
@@ -530,11 +544,32 @@ def run_ours(args):
                 "gpu_launches": launches, "latency_ms": lat, "accuracy": accuracy, "no_tensor_cores": no_tensor,
                 "krr": krr,
                 "plain_mid": mid,
+                "forms": forms,
                 "clocks": dict(clk.summary(), window="0.6 s busy lead-in, timed steps, profiled steps, e2e steps "
                                                      "and the KRR solve of the headline workload")}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def other_forms(args):
+    """Window construction, serving and batching in the default run (the modes
+    --features, --serve and --batch on their own print the same records):
+    serving on its full configuration, window construction with fewer timed
+    calls, batching on a configuration small enough for a few seconds.  Each
+    entry is that mode's record plus `reduced`, which names what differs from
+    the mode's full configuration (None: nothing)."""
+    import copy
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.features_cpu_rows = 10, 3, 2000
+    out["window_construction"] = dict(features_result(a), reduced="10 timed calls each; CPU oracle on 2000 rows")
+    out["serving"] = dict(serve_result(copy.copy(args)), reduced=None)
+    a = copy.copy(args)
+    a.batch_problems, a.batch_rhs, a.batch_sample, a.batch_lambda_min = 16, 4, 2, 1e-3
+    out["batching"] = dict(batch_result(a), reduced="16 problems x 4 right-hand sides, lambda >= 1e-3, "
+                                                    "2 problems timed one at a time (full: 64 x 16, 1e-4, 8)")
+    return out
 
 
 def run_crossover(args):
@@ -577,6 +612,10 @@ def run_crossover(args):
 
 
 def run_serve(args):
+    print(json.dumps(serve_result(args)), flush=True)
+
+
+def serve_result(args):
     """Serving form: a Poisson stream of requests (mean `--serve-rate` per s),
     70 % predictions of M test points (log-uniform in [1e2, 1e5]) against a
     resident model (N log-uniform in [1e4, 1e6]) and 30 % fits of new problems
@@ -681,7 +720,7 @@ def run_serve(args):
     bad = sum(r["status"] not in (B.OK, B.ENOCONV) for _, r in done_fits)
     sv.close()
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-    print(json.dumps({
+    return {
         "serve": True,
         "workload": "Poisson stream of predictions (M log-uniform 1e2..1e5) on resident models and "
                     "fits (N log-uniform 1e3..1e6; share fit_share); d 9..28, 3..9 windows of 1-3 features",
@@ -698,10 +737,14 @@ def run_serve(args):
         "fit_p50_ms_first_half": pct(flat[:half], 50), "fit_p50_ms_second_half": pct(flat[half:], 50),
         "submit_s": round(t_sub, 3), "drain_s": round(t_all, 3),
         "achieved_rps": n_req / t_all, "predicted_rows_per_s": rows / t_all, "fitted_points_per_s": fitted / t_all,
-    }), flush=True)
+    }
 
 
 def run_batch(args):
+    print(json.dumps(batch_result(args)), flush=True)
+
+
+def batch_result(args):
     """Batching form: 64 problems (N log-uniform in [2^10, 2^17], d 6..15, own
     windows of 1-3 features, ell in [0.05, 0.5], lambda in [1e-4, 1e-1]) with
     16 right-hand sides each.  Timed: (a) krr_batch_cg_solve (FP32 operator,
@@ -793,7 +836,7 @@ def run_batch(args):
         single[name] = {"sample_s": round(tt, 4), "est_all_systems_s": round(tt * args.batch_rhs / share, 3),
                         "iters": it_s, "relres_max": max(rel_s),
                         "converged": int(sum(r <= (10 if name == "fp32" else 1) * tol for r in rel_s))}
-    print(json.dumps({
+    res = {
         "batch": True,
         "workload": f"{len(probs)} problems, N log-uniform 2^10..2^17 (total {sum(w.N for w in probs)}), "
                     f"{args.batch_rhs} right-hand sides each, d 6..15, 1-5 windows of 1-3 features, "
@@ -814,10 +857,11 @@ def run_batch(args):
                          "exceptions": exceptions},
         "single_sample_problems": K, "single_sample_work_share": round(float(share), 4),
         "single": single,
-    }), flush=True)
+    }
     batch.close()
     for pl in plans:
         pl.close()
+    return res
 
 
 def run_precision(args):
@@ -890,6 +934,10 @@ def run_precision(args):
 
 
 def run_features(args):
+    print(json.dumps(features_result(args)), flush=True)
+
+
+def features_result(args):
     """Window construction on the GPU at the precision form's shape (N rows,
     d = 28, six Student-t columns, columns on their own scales, two classes):
     z-score fit, z-score apply (in place) and the MIS scores, each call timed
@@ -949,11 +997,11 @@ def run_features(args):
         gbs = nbytes / (ms * 1e-3) / 1e9
         return {"ms": ms, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac_of_hbm": gbs / hbm}
 
-    print(json.dumps({"features": True, "N": N, "d": d, "hbm_peak_gbs": hbm, "peak_source": src,
-                      "zscore_fit": row(t_fit, xb), "zscore_apply": row(t_apply, 2 * xb),
-                      "mis": dict(row(t_mis, xb + 4 * N), note="synchronous call: includes the host's score formation"),
-                      "top_windows": windows[:3], "cpu_baseline": cpu, "steps": args.steps, "warmup": args.warmup,
-                      "l2": "flushed before every call (256 MB write outside the events)"}), flush=True)
+    return {"features": True, "N": N, "d": d, "hbm_peak_gbs": hbm, "peak_source": src,
+            "zscore_fit": row(t_fit, xb), "zscore_apply": row(t_apply, 2 * xb),
+            "mis": dict(row(t_mis, xb + 4 * N), note="synchronous call: includes the host's score formation"),
+            "top_windows": windows[:3], "cpu_baseline": cpu, "steps": args.steps, "warmup": args.warmup,
+            "l2": "flushed before every call (256 MB write outside the events)"}
 
 
 def run_autotune(args):
@@ -993,6 +1041,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--check-rows", type=int, default=10_000)
     ap.add_argument("--skip-mid", action="store_true", help="no secondary mid-workload figures")
+    ap.add_argument("--skip-forms", action="store_true",
+                    help="no reduced window-construction, serving and batching runs after the headline")
     ap.add_argument("--points", type=int, default=1_000_000,
                     help="points of the headline workload (1e6 = the precision form; smaller only for profiler "
                          "captures of the same kernels)")

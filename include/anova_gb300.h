@@ -127,6 +127,38 @@ anova_status anova_autotune_bins(const double* points, int64_t N, int32_t d, int
                                  int32_t* bin_side, double* ms, void* stream);
 
 /*
+ * anova_autotune_kernels -- on a built plan holding the FP32 operator, the
+ * kernel forms that make its FP32 product fastest on this GPU, by measurement
+ * (coordinate descent from the plan's current forms, each candidate timed
+ * over `reps` products after two warm-up products), left set on the plan.
+ * choice (host, 3 int32) receives:
+ *   [0] 3-D spread: 0 FP32 FMA, 1 mma.sync 3xTF32, 2 the same with the next
+ *       chunk copied (cp.async) during the current MMAs (the default);
+ *   [1] 3-D gather: 0 FP32 FMA, 1 mma.sync 3xTF32, 2 tcgen05 one block per
+ *       sub-problem group, 3 persistent warp-specialised tcgen05 (the default;
+ *       where the problem is too small to fill the GPU it runs as 2);
+ *   [2] 1-D / 2-D schedule, as anova_plan_set_overlap & 3.
+ * Every form computes the same product to FP32 accuracy; only speed differs.
+ * ms (host or NULL) receives the chosen forms' time per product.  The tile
+ * shapes inside each form are fixed by its instruction (mma.sync m16n8k8,
+ * tcgen05 M = 128); the bin side, which sets each sub-problem's region, is
+ * tuned by anova_autotune_bins.  Synchronous; drops the plan's captured
+ * graphs; must not overlap with other calls on the plan.  The paper has no
+ * counterpart: a tuning step of the GPU design.
+ * Errors: EINVAL (NULL plan or choice, reps < 1, no FP32 operator, N = 0),
+ * those of anova_matvec, ECUDA; on an error the plan keeps its forms.
+ */
+anova_status anova_autotune_kernels(anova_plan* plan, int32_t reps, int32_t* choice, double* ms, void* stream);
+
+/* anova_plan_set_kernels / anova_plan_get_kernels -- set or read the plan's
+ * kernel forms directly (forms: host, 3 int32, coded as the choice of
+ * anova_autotune_kernels).  Setting drops the plan's captured graphs and must
+ * not overlap with other calls on the plan.  Errors: EINVAL (NULL argument, a
+ * form out of range). */
+anova_status anova_plan_set_kernels(anova_plan* plan, const int32_t* forms);
+anova_status anova_plan_get_kernels(const anova_plan* plan, int32_t* forms);
+
+/*
  * anova_matvec -- out = K alpha with the fast operator (Sec. 4.3, K alpha ~=
  * sum_l eta_l Phi_l D_l Phi_l^* alpha).
  *
@@ -648,8 +680,10 @@ anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable);
  * into its region, and the region against the nodes' weights, as 3xTF32
  * mma.sync / tcgen05 products with FP32 accuracy) or on FP32 FMA kernels
  * (enable = 0), e.g. to compare the two; enable = 2 also moves the 3-D spread
- * from mma.sync to the persistent tcgen05 kernel (off by default: measured
- * slower).  The 1-D / 2-D kernels and batches are not affected.  Drops the plan's captured graphs.  Must not overlap with
+ * from mma.sync to the persistent tcgen05 kernel, for comparison only: it
+ * measured slower (0.70 against 0.39 ms on N = 1e6 with three 3-D windows)
+ * and less accurate (4.4e-5 against the FP64 direct sum, above the FP32 bar
+ * of 1e-5).  The 1-D / 2-D kernels and batches are not affected.  Drops the plan's captured graphs.  Must not overlap with
  * other calls on the plan.  Errors: EINVAL (NULL plan). */
 anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable);
 

@@ -38,6 +38,9 @@ _SIGNATURES = {
     "anova_plan_set_graphs": (_i32, [_vp, _i32]),
     "anova_plan_set_tensor_cores": (_i32, [_vp, _i32]),
     "anova_plan_set_overlap": (_i32, [_vp, _i32]),
+    "anova_autotune_kernels": (_i32, [_vp, _i32, _pi32, _pf64, _vp]),
+    "anova_plan_set_kernels": (_i32, [_vp, _pi32]),
+    "anova_plan_get_kernels": (_i32, [_vp, _pi32]),
     "anova_fastsum_plan_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
                                        _i32, _i32, _pi32, _vp, ctypes.POINTER(_vp)]),
     "anova_autotune_bins": (_i32, [_vp, _i64, _i32, _i64, _pi32, _i32, _pf64, _f64, _pi32, _i32, _f64, _f64,
@@ -224,6 +227,31 @@ def anova_autotune_bins(points, windows, ell, n=None, m=6, sigma=2.0, eps_B=1.0 
                                    ctypes.byref(ms), _stream(stream))
     _check(st, "anova_autotune_bins")
     return [int(v) for v in bs], ms.value
+
+
+SPREAD3_FORMS = ("fma", "mma.sync", "mma.sync pipelined")
+GATHER3_FORMS = ("fma", "mma.sync", "tcgen05", "tcgen05 persistent")
+
+
+def anova_autotune_kernels(plan: Plan, reps=10, stream=None):
+    """Sets the plan's fastest kernel forms; returns ({"spread3", "gather3", "schedule"}, ms per product)."""
+    c = np.zeros(3, dtype=np.int32)
+    ms = ctypes.c_double()
+    _check(lib().anova_autotune_kernels(plan.handle, int(reps), c.ctypes.data_as(_pi32), ctypes.byref(ms),
+                                        _stream(stream)), "anova_autotune_kernels")
+    return {"spread3": SPREAD3_FORMS[c[0]], "gather3": GATHER3_FORMS[c[1]], "schedule": int(c[2])}, ms.value
+
+
+def anova_plan_set_kernels(plan: Plan, spread3, gather3, schedule):
+    """Kernel forms by name (SPREAD3_FORMS, GATHER3_FORMS) and the 1-D / 2-D schedule (0..3)."""
+    c = np.array([SPREAD3_FORMS.index(spread3), GATHER3_FORMS.index(gather3), int(schedule)], dtype=np.int32)
+    _check(lib().anova_plan_set_kernels(plan.handle, c.ctypes.data_as(_pi32)), "anova_plan_set_kernels")
+
+
+def anova_plan_get_kernels(plan: Plan) -> dict:
+    c = np.zeros(3, dtype=np.int32)
+    _check(lib().anova_plan_get_kernels(plan.handle, c.ctypes.data_as(_pi32)), "anova_plan_get_kernels")
+    return {"spread3": SPREAD3_FORMS[c[0]], "gather3": GATHER3_FORMS[c[1]], "schedule": int(c[2])}
 
 
 def anova_plan_window_bins(plan: Plan, l: int) -> dict:

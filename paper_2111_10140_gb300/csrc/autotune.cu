@@ -8,8 +8,10 @@
 // default rule, then tries each admissible bin side for the 1-D, the 2-D and
 // the 3-D windows in turn (coordinate descent, the other dimensions held at
 // their best so far), timing the matrix-vector product with CUDA events, and
-// returns the fastest choice.  The paper fixes no binning; this is a tuning
-// step of the GPU design only.
+// returns the fastest choice.  anova_autotune_kernels then picks, on a built
+// plan, the form of the 3-D spread and gather kernels and the schedule of the
+// 1-D / 2-D windows against the 3-D ones, also by timing.  The paper fixes no
+// binning or kernel form; these are tuning steps of the GPU design only.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -105,6 +107,114 @@ extern "C" anova_status anova_autotune_bins(const double* points, int64_t N, int
     cudaEventDestroy(e1);
     if (s != ANOVA_OK) return s;
     for (int k = 0; k < 3; k++) bin_side[k] = best[k];
+    if (ms) *ms = best_ms;
+    return ANOVA_OK;
+}
+
+namespace {
+
+// the plan's current kernel forms: 3-D spread, 3-D gather, 1-D / 2-D schedule
+void current_forms(const anova_plan* plan, int32_t c[3]) {
+    c[0] = plan->spread_tc ? (plan->spread_pipe ? 2 : 1) : 0;
+    c[1] = plan->gather_tc ? (plan->gather_umma ? (plan->gather_tc5 ? 3 : 2) : 1) : 0;
+    c[2] = plan->overlap12 & 3;
+}
+
+void apply_forms(anova_plan* plan, const int32_t c[3]) {
+    plan->spread_tc = c[0] >= 1;
+    plan->spread_pipe = c[0] >= 2;
+    plan->spread_tc5 = false;
+    plan->gather_tc = c[1] >= 1;
+    plan->gather_umma = c[1] >= 2;
+    plan->gather_tc5 = c[1] >= 3;
+    plan->overlap12 = c[2] == 0 ? 0 : (plan->overlap12 & 4) | c[2];   // the stream priority bit is kept
+    for (auto& g : plan->graphs)       // the captured launch sequences hold the old kernels
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    plan->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" anova_status anova_plan_set_kernels(anova_plan* plan, const int32_t* forms) {
+    if (!plan || !forms || forms[0] < 0 || forms[0] > 2 || forms[1] < 0 || forms[1] > 3 || forms[2] < 0 ||
+        forms[2] > 3) {
+        set_error("anova_plan_set_kernels: forms must be spread 0..2, gather 0..3, schedule 0..3");
+        return ANOVA_EINVAL;
+    }
+    apply_forms(plan, forms);
+    return ANOVA_OK;
+}
+
+extern "C" anova_status anova_plan_get_kernels(const anova_plan* plan, int32_t* forms) {
+    if (!plan || !forms) {
+        set_error("anova_plan_get_kernels: NULL argument");
+        return ANOVA_EINVAL;
+    }
+    current_forms(plan, forms);
+    return ANOVA_OK;
+}
+
+extern "C" anova_status anova_autotune_kernels(anova_plan* plan, int32_t reps, int32_t* choice, double* ms,
+                                               void* stream) {
+    if (!plan || !choice || reps < 1) {
+        set_error("anova_autotune_kernels: need a plan, reps >= 1 and an output array");
+        return ANOVA_EINVAL;
+    }
+    if (!(plan->precision & ANOVA_FP32) || plan->N < 1) {
+        set_error("anova_autotune_kernels: the plan must hold the FP32 operator and at least one node");
+        return ANOVA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = plan->N;
+    float *alpha = nullptr, *out = nullptr;
+    Scratch scratch(st, false);
+    ANOVA_CUDA_TRY(scratch.alloc(&alpha, N * sizeof(float)));
+    ANOVA_CUDA_TRY(scratch.alloc(&out, N * sizeof(float)));
+    k_tune_fill<float><<<grid_for(N, kThreads, 1024), kThreads, 0, st>>>(alpha, N);
+    ANOVA_CHECK_LAUNCH();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ANOVA_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        set_error("anova_autotune_kernels: cudaEventCreate failed");
+        return ANOVA_ECUDA;
+    }
+    int32_t start[3];
+    current_forms(plan, start);
+    auto timed = [&](const int32_t* c, double* t_ms) -> anova_status {
+        apply_forms(plan, c);
+        for (int k = 0; k < 2; k++) ANOVA_TRY(anova_matvec(plan, ANOVA_FP32, alpha, out, 1, N, stream));
+        ANOVA_CUDA_TRY(cudaEventRecord(e0, st));
+        for (int k = 0; k < reps; k++) ANOVA_TRY(anova_matvec(plan, ANOVA_FP32, alpha, out, 1, N, stream));
+        ANOVA_CUDA_TRY(cudaEventRecord(e1, st));
+        float t = 0.f;
+        ANOVA_CUDA_TRY(cudaEventSynchronize(e1));
+        ANOVA_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        *t_ms = (double)t / reps;
+        return ANOVA_OK;
+    };
+    // coordinate descent from the plan's current forms
+    int32_t best[3] = {start[0], start[1], start[2]};
+    double best_ms = 0.0;
+    anova_status s = timed(best, &best_ms);
+    const int nform[3] = {3, 4, 4};
+    for (int k = 0; k < 3 && s == ANOVA_OK; k++)
+        for (int v = 0; v < nform[k] && s == ANOVA_OK; v++) {
+            if (v == best[k]) continue;
+            int32_t trial[3] = {best[0], best[1], best[2]};
+            trial[k] = v;
+            double t = 0.0;
+            s = timed(trial, &t);
+            if (s == ANOVA_OK && t < best_ms) {
+                best_ms = t;
+                best[k] = v;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    apply_forms(plan, s == ANOVA_OK ? best : start);
+    if (s != ANOVA_OK) return s;
+    for (int k = 0; k < 3; k++) choice[k] = best[k];
     if (ms) *ms = best_ms;
     return ANOVA_OK;
 }

@@ -91,3 +91,40 @@ def test_binning_of_long_histograms_matches_oracle(B, torch):
     o32 = torch.empty_like(a64.float())
     B.anova_matvec(plan, a64.float(), o32)
     assert rel(o32.cpu().numpy(), ref) <= 1e-5
+
+
+def test_autotune_kernels_sets_forms_that_keep_the_oracle_product(B, torch):
+    """anova_autotune_kernels leaves the plan on the forms it reports, and the
+    FP32 product on those forms is still the oracle's to the FP32 bar; every
+    form it can pick is checked the same way."""
+    w = W.random_problem(20000, 6, WINS, 0.25, [32, 32, 32], 6, seed=730)
+    w.epsB = 0.25
+    X = torch.from_numpy(w.X).cuda()
+    plan = B.anova_fastsum_plan(X, w.windows, w.ell, n=w.n, m=w.m, eps_B=w.epsB, precision=B.MIXED)
+    ref = oracle.fastsum(None, w.X, w.windows, w.eta, w.ell, w.n, w.m, w.alpha, sigma=w.sigma, epsB=w.epsB, p=w.p)
+    a32 = torch.from_numpy(w.alpha).cuda().float()
+    o32 = torch.empty_like(a32)
+    choice, ms = B.anova_autotune_kernels(plan, reps=3)
+    assert ms > 0
+    assert choice["spread3"] in B.SPREAD3_FORMS and choice["gather3"] in B.GATHER3_FORMS
+    assert choice["schedule"] in (0, 1, 2, 3)
+    names = B.anova_dense3_kernels(plan)
+    spread_name = {"fma": "k_spread3_f32<R>", "mma.sync": "k_spread3_tc<R>",
+                   "mma.sync pipelined": "k_spread3_tcp<R>"}[choice["spread3"]]
+    assert names["spread"] == spread_name
+    if choice["gather3"] == "fma":
+        assert names["gather"] == "k_gather3_f32<R>"
+    B.anova_matvec(plan, a32, o32)
+    assert rel(o32.cpu().numpy(), ref) <= 1e-5
+    assert B.anova_plan_get_kernels(plan) == choice
+    # each form the tuner chooses between gives the oracle's product
+    for sp in B.SPREAD3_FORMS:
+        for ga in B.GATHER3_FORMS:
+            for mode in (0, 1, 2, 3):
+                B.anova_plan_set_kernels(plan, sp, ga, mode)
+                assert B.anova_plan_get_kernels(plan) == {"spread3": sp, "gather3": ga, "schedule": mode}
+                o32.zero_()
+                B.anova_matvec(plan, a32, o32)
+                assert rel(o32.cpu().numpy(), ref) <= 1e-5, (sp, ga, mode)
+    with pytest.raises(B.AnovaError):
+        B.anova_autotune_kernels(plan, reps=0)
