@@ -5,7 +5,8 @@
 // from a per-node table.
 //
 // Persistent blocks: block k takes a contiguous range of the merged
-// sub-problem list (bin, first node, count <= 256, window).  Consecutive
+// sub-problem list (bin, first node, count <= 256, window), with each node's
+// data loaded one sub-problem ahead of its use (NodeAhead).  Consecutive
 // sub-problems of one bin share the bin's region (R = Tb + 2m cells per axis
 // starting at bin*Tb - m):
 //   gather  the region is staged in shared memory once per bin; one thread per
@@ -36,9 +37,48 @@ __device__ __forceinline__ float coef_of(const DenseWin& W, const void* alpha, i
     return alpha_double ? (float)static_cast<const double*>(alpha)[i] : static_cast<const float*>(alpha)[i];
 }
 
+// A node's data, loaded one sub-problem ahead of its use: while a block computes
+// sub-problem q, the loads of q + 1 are in flight (and the sub-problem entry of
+// q + 2, which those loads need next time).  idx is the node's original index
+// (its entry of the window's permutation); al the coefficient where it is read
+// from a sorted copy (no permutation).
+template <int DA>
+struct NodeAhead {
+    float f[DA];
+    int c[DA];
+    int32_t idx;
+    float al;
+};
+
+template <int DA>
+__device__ __forceinline__ void node_ahead(const DenseWin* __restrict__ descs, const int4& sp, int t, bool sorted_coef,
+                                           NodeAhead<DA>& nd) {
+    const DenseWin& W = descs[sp.w];
+    if (t < sp.z) {
+        const int64_t pos = (int64_t)sp.y + t, Nn = W.N;
+        const float* __restrict__ fr = static_cast<const float*>(W.frac);
+#pragma unroll
+        for (int d = 0; d < DA; d++) {
+            nd.f[d] = fr[d * Nn + pos];
+            nd.c[d] = W.cell[d * Nn + pos];
+        }
+        if (sorted_coef) nd.al = W.asort[pos];
+        else nd.idx = W.perm[pos];
+    }
+}
+
+__device__ __forceinline__ float coef_ahead(const void* alpha, int alpha_double, int32_t idx, float sorted) {
+    if (!alpha) return sorted;
+    return alpha_double ? (float)static_cast<const double*>(alpha)[idx] : static_cast<const float*>(alpha)[idx];
+}
+
+__device__ __forceinline__ int4 sub_at(const int4* __restrict__ sub, int q, int hi) {
+    return q < hi ? sub[q] : make_int4(0, 0, 0, 0);
+}
+
 // --------------------------------------------------------------- 2-D gather
 template <int R, int M>
-__global__ void __launch_bounds__(k12Threads)
+__global__ void __launch_bounds__(k12Threads, 5)
 k_gather2_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict__ descs,
              const __grid_constant__ PsiCoef<M> P) {
     constexpr int TB = R - 2 * M;
@@ -47,8 +87,13 @@ k_gather2_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
     const int hi = (int)((int64_t)nsub * (blockIdx.x + 1) / gridDim.x);
     const int tid = threadIdx.x;
     int cw = -1, cbin = -1;
-    for (int q = lo; q < hi; q++) {
-        const int4 sp = sub[q];
+    int4 spA = sub_at(sub, lo, hi), spB = sub_at(sub, lo + 1, hi), spC;
+    NodeAhead<2> ndA = {}, ndB = {};
+    if (lo < hi) node_ahead<2>(descs, spA, tid, false, ndA);
+    for (int q = lo; q < hi; q++, spA = spB, spB = spC, ndA = ndB) {
+        spC = sub_at(sub, q + 2, hi);
+        if (q + 1 < hi) node_ahead<2>(descs, spB, tid, false, ndB);
+        const int4 sp = spA;
         const DenseWin& W = descs[sp.w];
         if (W.live && !*W.live) continue;              // a batch system that has stopped
         const int nb = W.nb, by = sp.x % nb, bx = sp.x / nb;
@@ -63,13 +108,11 @@ k_gather2_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
             cbin = sp.x;
         }
         if (tid < sp.z) {
-            const int64_t pos = (int64_t)sp.y + tid, Nn = W.N;
-            const float* __restrict__ fr = static_cast<const float*>(W.frac);
             float t[2 * M], wx[16], wy[16];
-            psi_taps<M>(P, fr[pos], t);
-            place_taps<R, M>(t, W.cell[pos] - TB * bx, wx);
-            psi_taps<M>(P, fr[Nn + pos], t);
-            place_taps<R, M>(t, W.cell[Nn + pos] - TB * by, wy);
+            psi_taps<M>(P, ndA.f[0], t);
+            place_taps<R, M>(t, ndA.c[0] - TB * bx, wx);
+            psi_taps<M>(P, ndA.f[1], t);
+            place_taps<R, M>(t, ndA.c[1] - TB * by, wy);
             float s = 0.f;
 #pragma unroll
             for (int a = 0; a < R; a++) {
@@ -87,7 +130,7 @@ k_gather2_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
                 }
                 s = fmaf(wx[a], e0 + e1, s);
             }
-            static_cast<float*>(W.out)[W.perm[pos]] = s;
+            static_cast<float*>(W.out)[ndA.idx] = s;
         }
     }
 }
@@ -103,8 +146,13 @@ k_gather1_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
     const int hi = (int)((int64_t)nsub * (blockIdx.x + 1) / gridDim.x);
     const int tid = threadIdx.x;
     int cw = -1, cbin = -1;
-    for (int q = lo; q < hi; q++) {
-        const int4 sp = sub[q];
+    int4 spA = sub_at(sub, lo, hi), spB = sub_at(sub, lo + 1, hi), spC;
+    NodeAhead<1> ndA = {}, ndB = {};
+    if (lo < hi) node_ahead<1>(descs, spA, tid, false, ndA);
+    for (int q = lo; q < hi; q++, spA = spB, spB = spC, ndA = ndB) {
+        spC = sub_at(sub, q + 2, hi);
+        if (q + 1 < hi) node_ahead<1>(descs, spB, tid, false, ndB);
+        const int4 sp = spA;
         const DenseWin& W = descs[sp.w];
         if (W.live && !*W.live) continue;
         const int bx = sp.x;
@@ -117,17 +165,16 @@ k_gather1_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
             cbin = sp.x;
         }
         if (tid < sp.z) {
-            const int64_t pos = (int64_t)sp.y + tid;
             float t[2 * M], wx[16];
-            psi_taps<M>(P, static_cast<const float*>(W.frac)[pos], t);
-            place_taps<R, M>(t, W.cell[pos] - TB * bx, wx);
+            psi_taps<M>(P, ndA.f[0], t);
+            place_taps<R, M>(t, ndA.c[0] - TB * bx, wx);
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll
             for (int a = 0; a < R; a += 2) {
                 s0 = fmaf(wx[a], reg[a], s0);
                 if (a + 1 < R) s1 = fmaf(wx[a + 1], reg[a + 1], s1);
             }
-            static_cast<float*>(W.out)[W.perm[pos]] = s0 + s1;
+            static_cast<float*>(W.out)[ndA.idx] = s0 + s1;
         }
     }
 }
@@ -246,7 +293,7 @@ __device__ __forceinline__ void mma_tf32_16x8x8(float* c, const uint32_t* a, uin
 }
 
 template <int R, int M>
-__global__ void __launch_bounds__(k12Threads)
+__global__ void __launch_bounds__(k12Threads, 4)
 k_spread2_tc(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict__ descs,
              const __grid_constant__ PsiCoef<M> P, const void* __restrict__ alpha, int alpha_double) {
     constexpr int TB = R - 2 * M;
@@ -289,8 +336,13 @@ k_spread2_tc(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
         __syncthreads();                                 // the staging rows are free again
     };
     int nacc = 0;
-    for (int q = lo; q < hi; q++) {
-        const int4 sp = sub[q];
+    int4 spA = sub_at(sub, lo, hi), spB = sub_at(sub, lo + 1, hi), spC;
+    NodeAhead<2> ndA = {}, ndB = {};
+    if (lo < hi) node_ahead<2>(descs, spA, tid, !alpha, ndA);
+    for (int q = lo; q < hi; q++, spA = spB, spB = spC, ndA = ndB) {
+        spC = sub_at(sub, q + 2, hi);
+        if (q + 1 < hi) node_ahead<2>(descs, spB, tid, !alpha, ndB);
+        const int4 sp = spA;
         const DenseWin& W = descs[sp.w];
         if (W.live && !*W.live) continue;
         if (cw >= 0 && (sp.w != cw || sp.x != cbin || nacc == kFlushSubs)) {
@@ -304,14 +356,12 @@ k_spread2_tc(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
         const int p = 32 * warp + lane;
         float wx[16], wy[16];
         if (p < sp.z) {
-            const int64_t pos = (int64_t)sp.y + p, Nn = W.N;
-            const float* __restrict__ fr = static_cast<const float*>(W.frac);
-            const float al = coef_of(W, alpha, alpha_double, pos);
+            const float al = coef_ahead(alpha, alpha_double, ndA.idx, ndA.al);
             float tp[2 * M];
-            psi_taps<M>(P, fr[pos], tp);
-            place_taps<R, M>(tp, W.cell[pos] - TB * bx, wx);
-            psi_taps<M>(P, fr[Nn + pos], tp);
-            place_taps<R, M>(tp, W.cell[Nn + pos] - TB * by, wy);
+            psi_taps<M>(P, ndA.f[0], tp);
+            place_taps<R, M>(tp, ndA.c[0] - TB * bx, wx);
+            psi_taps<M>(P, ndA.f[1], tp);
+            place_taps<R, M>(tp, ndA.c[1] - TB * by, wy);
 #pragma unroll
             for (int r = 0; r < 16; r++) wx[r] *= al;
         } else {
@@ -384,8 +434,13 @@ k_spread1_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
         __syncthreads();
     };
     int nacc = 0;                                       // sub-problems in the accumulators
-    for (int q = lo; q < hi; q++) {
-        const int4 sp = sub[q];
+    int4 spA = sub_at(sub, lo, hi), spB = sub_at(sub, lo + 1, hi), spC;
+    NodeAhead<1> ndA = {}, ndB = {};
+    if (lo < hi) node_ahead<1>(descs, spA, tid, !alpha, ndA);
+    for (int q = lo; q < hi; q++, spA = spB, spB = spC, ndA = ndB) {
+        spC = sub_at(sub, q + 2, hi);
+        if (q + 1 < hi) node_ahead<1>(descs, spB, tid, !alpha, ndB);
+        const int4 sp = spA;
         const DenseWin& W = descs[sp.w];
         if (W.live && !*W.live) continue;
         if (cw >= 0 && (sp.w != cw || sp.x != cbin || nacc == kFlushSubs)) {
@@ -396,11 +451,10 @@ k_spread1_pw(const int4* __restrict__ sub, int nsub, const DenseWin* __restrict_
         cbin = sp.x;
         nacc++;
         if (tid < sp.z) {
-            const int64_t pos = (int64_t)sp.y + tid;
-            const float al = coef_of(W, alpha, alpha_double, pos);
+            const float al = coef_ahead(alpha, alpha_double, ndA.idx, ndA.al);
             float t[2 * M], w[16];
-            psi_taps<M>(P, static_cast<const float*>(W.frac)[pos], t);
-            place_taps<R, M>(t, W.cell[pos] - TB * sp.x, w);
+            psi_taps<M>(P, ndA.f[0], t);
+            place_taps<R, M>(t, ndA.c[0] - TB * sp.x, w);
 #pragma unroll
             for (int r = 0; r < 16; r++) acc[r] = fmaf(al, w[r], acc[r]);
         }
