@@ -300,18 +300,21 @@ def dominant_roofline(B, plan, w, stage_ms, stage_la, steps):
     flops = 2.0 * taps * units
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    tc_flops = 3.0 * flops                                    # 3xTF32: three TF32 products per FP32 multiply-add
-    tf32 = tf32_peak_tflops()
+    tc_flops = 3.0 * flops                                    # three tensor-core products per FP32 multiply-add
+    f16 = "tch" in kernel                                     # FP16-split form: against the FP16 (= bf16) peak
+    tc_peak = float(measured_peaks()[0]["bf16_tflops"]) if f16 else tf32_peak_tflops()
     _, src = measured_peaks()
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic_per_launch(kernel, w.name),
             "units_per_launch": units, "flop_per_unit": 2 * taps,
             "peak_source": f"derived FP32 FMA peak ({FP32_PEAK_NOTE}); algorithmic FP32 multiply-adds "
                            f"(executed on tcgen05 / mma.sync tensor cores as 3xTF32)",
-            "tensor_view": {"achieved": tc_flops / (per_launch_ms * 1e-3) / 1e12, "peak": tf32,
-                            "frac": tc_flops / (per_launch_ms * 1e-3) / 1e12 / tf32,
-                            "what": "the FP32-accurate contraction as 3 TF32 products per multiply-add, unpadded",
-                            "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25"},
+            "tensor_view": {"achieved": tc_flops / (per_launch_ms * 1e-3) / 1e12, "peak": tc_peak,
+                            "frac": tc_flops / (per_launch_ms * 1e-3) / 1e12 / tc_peak,
+                            "what": "the FP32-accurate contraction as 3 " + ("FP16" if f16 else "TF32") +
+                                    " products per multiply-add, unpadded",
+                            "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)" +
+                                           ("" if f16 else " x nominal tf32/bf16 ratio 1.1/2.25")},
             "per_launch_ms": per_launch_ms,
             "stage_ms_per_step": {k: v / steps for k, v in stage_ms.items()}}
 
@@ -387,8 +390,13 @@ def run_ours(args):
                                      precision=B.MIXED)
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t_plan) * 1e3
-    # kernel forms (3-D spread, 3-D gather, 1-D / 2-D schedule) from the library's tuner, same condition
-    if not args.bin_side and not args.no_autotune:
+    # kernel forms (3-D spread, 3-D gather, 1-D / 2-D schedule): given, or from the library's tuner
+    # when the bin sides are tuned too
+    if args.forms:
+        f = [int(v) for v in args.forms.split(",")]
+        B.anova_plan_set_kernels(plan, B.SPREAD3_FORMS[f[0]], B.GATHER3_FORMS[f[1]], f[2])
+        kernels, kernels_how = B.anova_plan_get_kernels(plan), "given"
+    elif not args.bin_side and not args.no_autotune:
         kernels, _ = B.anova_autotune_kernels(plan, reps=5)
         kernels_how = "autotuned"
     else:
@@ -1048,6 +1056,9 @@ def main():
                          "captures of the same kernels)")
     ap.add_argument("--no-autotune", action="store_true", help="bin sides from the default rule")
     ap.add_argument("--bin-side", default="", help="bin sides for 1-D,2-D,3-D windows (e.g. 0,0,4), no autotuning")
+    ap.add_argument("--forms", default="",
+                    help="kernel forms 'spread3,gather3,schedule' as anova_autotune_kernels codes (e.g. 3,3,2), "
+                         "no kernel tuning")
     ap.add_argument("--crossover", action="store_true",
                     help="direct vs fast matvec time over N (the paper's Fig. 1 on synthetic data); prints one line per N")
     ap.add_argument("--serve", action="store_true",

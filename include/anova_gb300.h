@@ -133,12 +133,16 @@ anova_status anova_autotune_bins(const double* points, int64_t N, int32_t d, int
  * over `reps` products after two warm-up products), left set on the plan.
  * choice (host, 3 int32) receives:
  *   [0] 3-D spread: 0 FP32 FMA, 1 mma.sync 3xTF32, 2 the same with the next
- *       chunk copied (cp.async) during the current MMAs (the default);
+ *       chunk copied (cp.async) during the current MMAs (the default), 3 as 2
+ *       with FP16 operands split in three terms (m16n8k16: twice the nodes
+ *       per tensor-core instruction; coefficients scaled by max |alpha|, one
+ *       extra reduction per product);
  *   [1] 3-D gather: 0 FP32 FMA, 1 mma.sync 3xTF32, 2 tcgen05 one block per
  *       sub-problem group, 3 persistent warp-specialised tcgen05 (the default;
  *       where the problem is too small to fill the GPU it runs as 2);
  *   [2] 1-D / 2-D schedule, as anova_plan_set_overlap & 3.
- * Every form computes the same product to FP32 accuracy; only speed differs.
+ * Every form computes the same product to the FP32 bar (1e-5 relative);
+ * only speed and rounding differ.
  * ms (host or NULL) receives the chosen forms' time per product.  The tile
  * shapes inside each form are fixed by its instruction (mma.sync m16n8k8,
  * tcgen05 M = 128); the bin side, which sets each sub-problem's region, is

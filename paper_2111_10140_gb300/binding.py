@@ -229,7 +229,7 @@ def anova_autotune_bins(points, windows, ell, n=None, m=6, sigma=2.0, eps_B=1.0 
     return [int(v) for v in bs], ms.value
 
 
-SPREAD3_FORMS = ("fma", "mma.sync", "mma.sync pipelined")
+SPREAD3_FORMS = ("fma", "mma.sync", "mma.sync pipelined", "mma.sync fp16 split")
 GATHER3_FORMS = ("fma", "mma.sync", "tcgen05", "tcgen05 persistent")
 
 

@@ -115,7 +115,7 @@ namespace {
 
 // the plan's current kernel forms: 3-D spread, 3-D gather, 1-D / 2-D schedule
 void current_forms(const anova_plan* plan, int32_t c[3]) {
-    c[0] = plan->spread_tc ? (plan->spread_pipe ? 2 : 1) : 0;
+    c[0] = plan->spread_tc ? (plan->spread_f16 ? 3 : (plan->spread_pipe ? 2 : 1)) : 0;
     c[1] = plan->gather_tc ? (plan->gather_umma ? (plan->gather_tc5 ? 3 : 2) : 1) : 0;
     c[2] = plan->overlap12 & 3;
 }
@@ -123,6 +123,7 @@ void current_forms(const anova_plan* plan, int32_t c[3]) {
 void apply_forms(anova_plan* plan, const int32_t c[3]) {
     plan->spread_tc = c[0] >= 1;
     plan->spread_pipe = c[0] >= 2;
+    plan->spread_f16 = c[0] == 3;
     plan->spread_tc5 = false;
     plan->gather_tc = c[1] >= 1;
     plan->gather_umma = c[1] >= 2;
@@ -136,9 +137,9 @@ void apply_forms(anova_plan* plan, const int32_t c[3]) {
 }  // namespace
 
 extern "C" anova_status anova_plan_set_kernels(anova_plan* plan, const int32_t* forms) {
-    if (!plan || !forms || forms[0] < 0 || forms[0] > 2 || forms[1] < 0 || forms[1] > 3 || forms[2] < 0 ||
+    if (!plan || !forms || forms[0] < 0 || forms[0] > 3 || forms[1] < 0 || forms[1] > 3 || forms[2] < 0 ||
         forms[2] > 3) {
-        set_error("anova_plan_set_kernels: forms must be spread 0..2, gather 0..3, schedule 0..3");
+        set_error("anova_plan_set_kernels: forms must be spread 0..3, gather 0..3, schedule 0..3");
         return ANOVA_EINVAL;
     }
     apply_forms(plan, forms);
@@ -197,7 +198,7 @@ extern "C" anova_status anova_autotune_kernels(anova_plan* plan, int32_t reps, i
     int32_t best[3] = {start[0], start[1], start[2]};
     double best_ms = 0.0;
     anova_status s = timed(best, &best_ms);
-    const int nform[3] = {3, 4, 4};
+    const int nform[3] = {4, 4, 4};
     for (int k = 0; k < 3 && s == ANOVA_OK; k++)
         for (int v = 0; v < nform[k] && s == ANOVA_OK; v++) {
             if (v == best[k]) continue;

@@ -195,6 +195,8 @@ struct anova_plan {
     float* dense_asort = nullptr;       // dense_windows.size() x N sorted FP32 coefficients
     bool spread_tc = true;              // FP32 dense spread on tensor cores (3xTF32) instead of FFMA2
     bool spread_pipe = true;            // ... with the next chunk's rows copied (cp.async) during the current MMAs
+    bool spread_f16 = false;            // ... as FP16-split m16n8k16 MMAs (coefficients scaled by max |alpha|)
+    unsigned* f16_scale = nullptr;      // device word: bits of max |alpha| for that form
     int overlap12 = 1;                  // FP32 product: the 1-D / 2-D windows on a second stream beside the 3-D
                                         // ones (anova_plan_set_overlap: 0 off, 1 forked before the 3-D spread,
                                         // 2 after the 3-D spread is queued, 3 after it has run; +4 high priority)
@@ -345,6 +347,8 @@ anova_status gather3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin
                          int sms, cudaStream_t st);
 anova_status spread3_tc5(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const float* psi_host,
                          int sms, const void* alpha, int alpha_double, cudaStream_t st);
+anova_status spread3_f16(int R, int m, const int4* sub, int nsub, const DenseWin* descs, const void* alpha,
+                         int alpha_double, int64_t N, unsigned* scale, int sms, cudaStream_t st);
 // persistent FP32 1-D / 2-D kernels with on-the-fly weights (dense12.cu)
 anova_status dense12_pw(int dA, bool spread, int R, int m, const int4* sub, int nsub, const DenseWin* descs,
                         const float* psi_host, int sms, const void* alpha, int alpha_double, cudaStream_t st);

@@ -1206,6 +1206,9 @@ static anova_status spread_table(anova_plan* plan, int R, const int4* sub, int n
     if (plan->spread_tc5 && tc5_supported(R, plan->m))
         return spread3_tc5(R, plan->m, sub, nsub, descs, plan->psi_host.data(), plan->sm_count, alpha, alpha_double,
                            st);
+    if (plan->spread_tc && plan->spread_f16 && alpha)
+        return spread3_f16(R, plan->m, sub, nsub, descs, alpha, alpha_double, plan->N, plan->f16_scale,
+                           plan->sm_count, st);
     if (plan->spread_tc && plan->spread_pipe) {
         switch (R) {
 #define ANOVA_SPREAD_TCP(R_) \
@@ -1447,6 +1450,7 @@ static int region3(const anova_plan* plan, int* nsub = nullptr) {
 // kernel names of the FP32 3-D spread and gather the plan launches ("<R>" = region size)
 static const char* spread3_name(const anova_plan* plan) {
     if (plan->spread_tc5 && tc5_supported(region3(plan), plan->m)) return "k_spread3_tc5<R>";
+    if (plan->spread_tc && plan->spread_f16) return "k_spread3_tch<R>";
     if (plan->spread_tc && plan->spread_pipe) return "k_spread3_tcp<R>";
     return plan->spread_tc ? "k_spread3_tc<R>" : "k_spread3_f32<R>";
 }

@@ -829,6 +829,7 @@ anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable) {
     plan->gather_umma = on;
     plan->gather_tc5 = on;
     plan->spread_tc5 = enable == 2;
+    plan->spread_f16 = false;
     for (auto& g : plan->graphs)      // the captured launch sequences name the old kernels
         if (g.exec) cudaGraphExecDestroy(g.exec);
     plan->graphs.clear();

@@ -1164,6 +1164,7 @@ static anova_status plan_build(const double* points, int64_t N, int32_t d, int64
     plan->win.resize(P);
     ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly, (2 * m * kPsiStride + 1) * sizeof(float)));
     ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->psi_poly64, 2 * m * kPsiStride * sizeof(double)));
+    ANOVA_CUDA_TRY(anova::dev_malloc((void**)&plan->f16_scale, sizeof(unsigned)));
     k_psi_poly_fit<<<1, 64, 0, st>>>(m, plan->b, plan->psi_norm, plan->psi_poly, plan->psi_poly64);
     ANOVA_CHECK_LAUNCH();
     plan->psi_host.assign(2 * m * kPsiStride, 0.f);
@@ -1502,6 +1503,7 @@ void anova_plan_destroy(anova_plan* plan) {
     cudaFree(plan->fft12_desc);
     cudaFree(plan->psi_poly);
     cudaFree(plan->psi_poly64);
+    cudaFree(plan->f16_scale);
     if (plan->side) cudaStreamDestroy(plan->side);
     if (plan->side_hi) cudaStreamDestroy(plan->side_hi);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);

@@ -110,7 +110,8 @@ def test_autotune_kernels_sets_forms_that_keep_the_oracle_product(B, torch):
     assert choice["schedule"] in (0, 1, 2, 3)
     names = B.anova_dense3_kernels(plan)
     spread_name = {"fma": "k_spread3_f32<R>", "mma.sync": "k_spread3_tc<R>",
-                   "mma.sync pipelined": "k_spread3_tcp<R>"}[choice["spread3"]]
+                   "mma.sync pipelined": "k_spread3_tcp<R>",
+                   "mma.sync fp16 split": "k_spread3_tch<R>"}[choice["spread3"]]
     assert names["spread"] == spread_name
     if choice["gather3"] == "fma":
         assert names["gather"] == "k_gather3_f32<R>"

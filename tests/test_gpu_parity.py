@@ -202,6 +202,31 @@ def test_cg_reduced_precision_reaches_tolerance(B, torch, precision):
     assert rel(q, w.y) <= (2e-8 if precision == "MIXED" else 3 * tol)
 
 
+@pytest.mark.parametrize("form", ["fma", "mma.sync", "mma.sync pipelined", "mma.sync fp16 split"])
+@pytest.mark.parametrize("precision", ["FP32", "MIXED"])
+def test_cg_every_spread_form_reaches_tolerance(B, torch, form, precision):
+    """CG feeds the FP32 operator FP64 vectors: every 3-D spread form (the FP16
+    split one scales them by their largest entry first) must still solve the
+    system.  Mixed refinement must meet tol on the FP64 residual, as the FP64
+    oracle operator sees it.  Plain FP32 CG solves the FP32 operator's system:
+    its recursive residual drifts from the true one (hence 10 tol on relres),
+    and the FP64 operator sees the FP32 operator's error (about 1e-6 relative;
+    the truncated TF32 heads of the TF32 forms round one way) amplified by the
+    system's conditioning, so the oracle residual is held to 1e-2 there."""
+    w = W.random_problem(3000, 6, [(0, 1, 2), (3, 4, 5)], 0.25, 32, 6, seed=61)
+    w.epsB = 0.25
+    plan = make_plan(B, torch, w, getattr(B, precision))
+    B.anova_plan_set_kernels(plan, form, "tcgen05 persistent", 2)
+    assert B.anova_plan_get_kernels(plan)["spread3"] == form
+    y = torch.from_numpy(w.y).cuda()
+    alpha = torch.zeros_like(y)
+    tol = 1e-8 if precision == "MIXED" else 1e-4
+    st, its, relres = B.krr_cg_solve(plan, w.lam, y, alpha, tol, 3000)
+    assert st == B.OK and relres[0] <= (tol if precision == "MIXED" else 10 * tol)
+    q = oracle_fast(w, alpha=alpha.cpu().numpy()) + w.lam * alpha.cpu().numpy()
+    assert rel(q, w.y) <= (2e-8 if precision == "MIXED" else 1e-2)
+
+
 @pytest.mark.parametrize("scale_z", [0.5, 1.7])
 def test_predict_matches_oracle(B, torch, scale_z):
     w = W.random_problem(1500, 5, [(0, 1, 2), (3, 4)], 0.2, 32, 6, seed=51)
