@@ -489,6 +489,7 @@ def run_ours(args):
                                       p=wm.p, precision=B.FP32, reps=5)
         pm = B.anova_fastsum_plan_bins(Xm, wm.windows, wm.ell, sm, n=wm.n, m=wm.m, sigma=wm.sigma, eps_B=wm.epsB,
                                        p=wm.p, precision=B.MIXED)
+        mkern, _ = B.anova_autotune_kernels(pm, reps=5)
         am = torch.from_numpy(wm.alpha).to(dev).float()
         om = torch.empty_like(am)
         mid_ms = time_matvec(B, pm, am, om, flush, args.steps, args.warmup, stream)
@@ -516,7 +517,7 @@ def run_ours(args):
             e1.synchronize()
             mkrr64["fp64_matvec_ms"] = e0.elapsed_time(e1) / 5
             p64.close()
-        mid = {"config": workload_config(wm), "bin_side_1d_2d_3d": sm,
+        mid = {"config": workload_config(wm), "bin_side_1d_2d_3d": sm, "kernels": mkern,
                "value": wm.N * len(mid_ms) / (sum(mid_ms) * 1e-3) / 1e9, "unit": "Gpts/s",
                "ms_per_step": sum(mid_ms) / len(mid_ms), "roofline": mroof, "accuracy": macc,
                "krr": mkrr, "krr_plain_fp64": mkrr64}
