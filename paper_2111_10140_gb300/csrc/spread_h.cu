@@ -11,13 +11,12 @@
 // reduction over the vector before the launch; the region is multiplied by s
 // when it is added to the grid).  Each operand x is split into its FP16
 // rounding h and the FP16 rounding of x - h; h*h + h*l + l*h accumulate in
-// FP32.  For |x| >= 2^-2 (normal FP16 tails) the pair keeps x to 2^-22
-// relative and the dropped l*l is below 2^-22 of the product; below that the
-// tail's FP16 spacing (2^-24 at the subnormals) bounds the error of a term by
-// 2^-25 of the largest possible term, i.e. errors are at most 2^-22 of the
-// region's scale rather than of each term.  The result meets the FP32 bar of
-// the product (1e-5 relative); terms that are tiny against the bin's largest
-// lose relative, not absolute, accuracy.
+// FP32.  A product a*b of operands of at least 2^-2 (normal FP16 tails) is
+// kept to 3 * 2^-22 of itself (the dropped l*l and the tails' roundings);
+// below that FP16's subnormal spacing adds at most 2^-24 (|a| + |b|), an
+// absolute error against operands of at most 1.  The result meets the FP32
+// bar of the product (1e-5 relative); terms that are tiny against the bin's
+// largest lose relative, not absolute, accuracy.
 //
 // Layout and pipeline as the TF32 form (k_spread3_tcp): one block per
 // sub-problem, warp w owns the M-tiles a = 2w, 2w+1 and both N-tiles; chunks
