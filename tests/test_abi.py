@@ -90,6 +90,22 @@ def test_wait_probe_rejects_bad_poll_counts_without_touching_the_gpu(lib):
     assert "polls" in L.anova_last_error().decode()
 
 
+def test_plan_settings_reject_bad_arguments_without_touching_the_gpu(lib):
+    """The kernel-form, schedule and tuning entry points check their arguments
+    before any CUDA call (NULL plan, forms or schedule out of range)."""
+    import ctypes
+    from paper_2111_10140_gb300 import binding as B
+    L = B.lib()
+    forms = (ctypes.c_int32 * 3)(2, 3, 2)
+    assert L.anova_plan_set_kernels(None, forms) == B.EINVAL
+    assert L.anova_plan_get_kernels(None, forms) == B.EINVAL
+    assert L.anova_plan_set_overlap(None, 1) == B.EINVAL
+    assert L.anova_plan_set_tensor_cores(None, 1) == B.EINVAL
+    choice = (ctypes.c_int32 * 3)()
+    ms = ctypes.c_double()
+    assert L.anova_autotune_kernels(None, 5, choice, ctypes.byref(ms), None) == B.EINVAL
+
+
 def test_bin_rule_is_host_logic(lib):
     """The plan's binning rule for one window, computed without a GPU."""
     from paper_2111_10140_gb300 import binding as B
