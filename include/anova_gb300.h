@@ -687,8 +687,11 @@ anova_status anova_plan_set_graphs(anova_plan* plan, int32_t enable);
  * from mma.sync to the persistent tcgen05 kernel, for comparison only: it
  * measured slower (0.70 against 0.39 ms on N = 1e6 with three 3-D windows)
  * and less accurate (4.4e-5 against the FP64 direct sum, above the FP32 bar
- * of 1e-5).  The 1-D / 2-D kernels and batches are not affected.  Drops the plan's captured graphs.  Must not overlap with
- * other calls on the plan.  Errors: EINVAL (NULL plan). */
+ * of 1e-5).  enable = 1 restores the default forms (3xTF32 spread with the
+ * copy pipeline, persistent tcgen05 gather; anova_plan_set_kernels codes 2
+ * and 3), replacing a form chosen by anova_autotune_kernels.  The 1-D / 2-D
+ * kernels and batches are not affected.  Drops the plan's captured graphs.
+ * Must not overlap with other calls on the plan.  Errors: EINVAL (NULL plan). */
 anova_status anova_plan_set_tensor_cores(anova_plan* plan, int32_t enable);
 
 /* anova_plan_set_overlap -- how the FP32 product schedules the 1-D / 2-D
