@@ -54,3 +54,37 @@ def test_traffic_figure_only_for_the_kernel_source_it_was_taken_on(tmp_path):
     assert bench.traffic_per_launch("k_x<14>", "other", path=str(f)) is None
     assert bench.traffic_per_launch("k_y<14>", "wl", path=str(f)) is None     # stale: sources changed
     assert bench.traffic_per_launch("k_z<14>", "wl", path=str(f)) is None
+
+
+def test_other_forms_report_a_failing_form_and_keep_the_rest(monkeypatch):
+    """The default run's window-construction, serving and batching entries: a
+    form that raises is reported in its own entry (the headline line is still
+    printed), the others keep their records and say how they were reduced."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+
+    seen = {}
+
+    def ok(name):
+        def fn(a):
+            seen[name] = a
+            return {"ran": name}
+        return fn
+
+    def broken(a):
+        raise RuntimeError("no device")
+
+    monkeypatch.setattr(bench, "features_result", ok("features"))
+    monkeypatch.setattr(bench, "serve_result", broken)
+    monkeypatch.setattr(bench, "batch_result", ok("batch"))
+    args = argparse.Namespace(steps=50, warmup=5, features_cpu_rows=20000, serve_seconds=10.0, batch_problems=64,
+                              batch_rhs=16, batch_sample=8, batch_lambda_min=1e-4)
+    out = bench.other_forms(args)
+    assert set(out) == {"window_construction", "serving", "batching"}
+    assert out["serving"]["error"] == "RuntimeError: no device" and out["serving"]["reduced"] is None
+    assert out["window_construction"]["ran"] == "features" and "10 timed calls" in out["window_construction"]["reduced"]
+    assert out["batching"]["ran"] == "batch" and "16 problems" in out["batching"]["reduced"]
+    # the reduced copies do not touch the caller's arguments
+    assert seen["features"].steps == 10 and args.steps == 50
+    assert seen["batch"].batch_problems == 16 and args.batch_problems == 64
